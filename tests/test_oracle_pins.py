@@ -1,0 +1,321 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (no GPU).
+
+Each test ties one part of the oracle to something other than itself: quadrature
+exactness, finite differences, reciprocity, closed forms on the sphere, Laplace
+identities on closed surfaces, refinement rates, and planted mistakes.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1311_5202_gb300 import inputs
+
+
+# ---------------------------------------------------------------- quadrature rules
+def test_nystrom_rule_is_degree_four():
+    """Sec. 2.2: 6-point Gauss rule on the triangle: exact for every monomial of degree <= 4."""
+    xi, w = O.nystrom_rule()
+    assert abs(w.sum() - 0.5) < 1e-15
+    for a in range(6):
+        for b in range(6 - a):
+            exact = math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
+            got = float(np.sum(w * xi[:, 0] ** a * xi[:, 1] ** b))
+            if a + b <= 4:
+                assert abs(got - exact) < 1e-14 * max(1.0, exact) + 1e-16, (a, b)
+    # degree 6 is not integrated exactly (it is the degree-4 rule, not a higher one)
+    got = float(np.sum(w * xi[:, 0] ** 6))
+    assert abs(got - math.factorial(6) / math.factorial(8)) > 1e-6
+
+
+def test_gauss_legendre_exactness():
+    for n in (3, 8, 20, 24):
+        x, w = O.gauss_legendre01(n)
+        for p in range(2 * n):
+            assert abs(np.sum(w * x ** p) - 1.0 / (p + 1)) < 1e-13
+
+
+def test_local_correction_matrix_well_conditioned():
+    """Eq. local correction: the 6x6 matrix phi_n(xi_j) of the quadratic basis is invertible."""
+    phi, inv = O.phi_matrix()
+    assert np.linalg.cond(phi) < 200
+    assert np.allclose(phi @ inv, np.eye(6), atol=1e-12)
+
+
+# ---------------------------------------------------------------- kernels
+def _rand_pairs(rng, m=40):
+    x = rng.normal(size=(m, 3))
+    y = x + rng.normal(size=(m, 3)) * 0.7
+    nx = rng.normal(size=(m, 3))
+    ny = rng.normal(size=(m, 3))
+    nx /= np.linalg.norm(nx, axis=1, keepdims=True)
+    ny /= np.linalg.norm(ny, axis=1, keepdims=True)
+    return x, nx, y, ny
+
+
+@pytest.mark.parametrize("k", [0.0, 3.0, 25.0])
+def test_kernel_derivatives_by_finite_differences(k):
+    """Eq. operator: dG/dn_y, dG/dn_x and d2G/dn_x dn_y are derivatives of G = e^{ikr}/(4 pi r)."""
+    rng = np.random.default_rng(0)
+    x, nx, y, ny = _rand_pairs(rng)
+    K = O.kernels(x, nx, y, ny, k)
+    h = 1e-4
+
+    def G(a, b):
+        return O.kernels(a, nx, b, ny, k)[:, 0]
+
+    dy = (G(x, y + h * ny) - G(x, y - h * ny)) / (2 * h)
+    dx = (G(x + h * nx, y) - G(x - h * nx, y)) / (2 * h)
+    dxy = (G(x + h * nx, y + h * ny) - G(x + h * nx, y - h * ny) - G(x - h * nx, y + h * ny)
+           + G(x - h * nx, y - h * ny)) / (4 * h * h)
+    for got, ref in ((K[:, 1], dy), (K[:, 2], dx), (K[:, 3], dxy)):
+        assert np.max(np.abs(got - ref) / (np.abs(ref) + 1e-3)) < 2e-5
+
+
+def test_kernel_reciprocity():
+    """G(x,y) = G(y,x); dG/dn_y(x,y) = dG/dn_x(y,x) with the same normal; d2G symmetric in the swap."""
+    rng = np.random.default_rng(1)
+    x, nx, y, ny = _rand_pairs(rng)
+    a = O.kernels(x, nx, y, ny, 7.0)
+    b = O.kernels(y, ny, x, nx, 7.0)
+    assert np.allclose(a[:, 0], b[:, 0], rtol=1e-14, atol=0)
+    assert np.allclose(a[:, 1], b[:, 2], rtol=1e-13, atol=0)
+    assert np.allclose(a[:, 3], b[:, 3], rtol=1e-13, atol=0)
+
+
+# ---------------------------------------------------------------- geometry
+def test_sphere_area_fourth_order_and_normals():
+    """Curved quadratic elements + degree-4 rule: area error O(h^4); normals point into the body."""
+    errs = []
+    for m in (4, 8):
+        mesh = inputs.icosphere(m, 0.5)
+        xs, ns, ws = O.geometry(mesh.nodes, mesh.elems)
+        errs.append(abs(ws.sum() / math.pi - 1.0))
+        assert np.all(np.einsum("ij,ij->i", ns, xs) < 0)
+        assert np.allclose(np.linalg.norm(ns, axis=1), 1.0)
+        assert np.allclose(np.linalg.norm(xs, axis=1), 0.5, atol=2e-3)
+    assert errs[0] / errs[1] > 12.0  # ~2^4
+
+
+# ---------------------------------------------------------------- spherical Bessel functions and Mie
+def test_spherical_bessel_against_scipy():
+    sp = pytest.importorskip("scipy.special")
+    for z in (0.3, 5.0, 31.4, 100.0):
+        nmax = int(z + 40)
+        j, dj, h, dh = O.sph_all(nmax, z)
+        n = np.arange(nmax + 1)
+        jr = sp.spherical_jn(n, z)
+        yr = sp.spherical_yn(n, z)
+        big = np.abs(jr) > 1e-250
+        assert np.allclose(j[big], jr[big], rtol=1e-9, atol=1e-300)
+        assert np.allclose(h.imag, yr, rtol=1e-9)
+        assert np.allclose(dj, sp.spherical_jn(n, z, derivative=True), rtol=1e-8, atol=1e-290)
+        # Wronskian j h' - j' h = i / z^2
+        assert np.allclose(j * dh - dj * h, 1j / z ** 2, rtol=1e-8)
+
+
+def test_mie_simplification_matches_paper_series():
+    """Sec. 5.3 series u = u_inc + sum -i^m (2m+1) j_m'/h_m' h_m P_m, with h = h^(1), equals the oracle's form."""
+    sp = pytest.importorskip("scipy.special")
+    k, a = 10.0, 0.5
+    th = np.linspace(0, math.pi, 7)
+    z = k * a
+    nmax = O.mie_nmax(z)
+    n = np.arange(nmax + 1)
+    j, dj = sp.spherical_jn(n, z), sp.spherical_jn(n, z, derivative=True)
+    h = j + 1j * sp.spherical_yn(n, z)
+    dh = dj + 1j * sp.spherical_yn(n, z, derivative=True)
+    P = np.array([sp.eval_legendre(q, np.cos(th)) for q in n])
+    uinc = np.exp(1j * k * a * np.cos(th))
+    us = np.tensordot(-(1j ** n) * (2 * n + 1) * dj / dh * h, P, axes=(0, 0))
+    assert np.allclose(O.mie_total_surface(th, k, a), uinc + us, rtol=1e-10, atol=1e-12)
+
+
+def _zonal_quadrature(f, n_t=4000):
+    """integral over the unit-radius-scaled sphere of a zonal integrand f(theta'), Gauss in t = sin(theta'/2)."""
+    x, w = O.gauss_legendre01(64)
+    # composite Gauss on [0, pi] in theta' split near the pole
+    edges = np.concatenate([[0.0], np.geomspace(1e-6, math.pi, 60)])
+    tot = 0.0
+    for a_, b_ in zip(edges[:-1], edges[1:]):
+        t = a_ + (b_ - a_) * x
+        tot = tot + np.sum(w * (b_ - a_) * f(t))
+    return tot
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3])
+def test_sphere_eigenvalue_formulas_by_direct_quadrature(n):
+    """The eigenvalues used as pins are checked on the exact sphere by 1-D quadrature at the north pole:
+    S P_n and D P_n (principal value; integrable on the sphere) and H P_n by differencing the double-layer
+    potential off the surface (x = (a + d) e_z, d -> 0, Richardson)."""
+    k, a = 7.0, 0.5
+    ev = O.sphere_eigenvalues(n, k, a)
+
+    def layer(tp, xr, kind):
+        # source y = a (sin t, 0, cos t); zonal integrand, the azimuthal integral gives 2 pi
+        y = np.stack([a * np.sin(tp), np.zeros_like(tp), a * np.cos(tp)], axis=1)
+        x = np.array([0, 0, xr])
+        r = x[None, :] - y
+        R = np.linalg.norm(r, axis=1)
+        G = np.exp(1j * k * R) / (4 * math.pi * R)
+        ny = -y / a  # paper normal, into the body
+        nx = np.array([0.0, 0.0, -1.0])
+        rny = np.einsum("ij,ij->i", r, ny) / R
+        rnx = (r @ nx) / R
+        nxny = ny @ nx
+        Pn = O.legendre(n, np.cos(tp))[n]
+        dS = 2 * math.pi * a * a * np.sin(tp)
+        if kind == "S":
+            return G * Pn * dS
+        if kind == "D":
+            return G * (1 / R - 1j * k) * rny * Pn * dS
+        K = G / R ** 2 * (nxny * (1 - 1j * k * R) - rnx * rny * (3 - 3j * k * R - k * k * R * R))
+        return K * Pn * dS
+
+    S = _zonal_quadrature(lambda t: layer(t, a, "S"))
+    assert abs(S - ev["S"][n]) < 1e-8 * abs(ev["S"][n]) + 1e-10
+    D = _zonal_quadrature(lambda t: layer(t, a, "D"))
+    assert abs(D - ev["D"][n]) < 1e-7 * max(1.0, abs(ev["D"][n]))
+
+    # H P_n is the (continuous) normal derivative of the double-layer potential: evaluate the regular
+    # integral of d2G/dn_x dn_y at x = (a + d) e_z outside the body and extrapolate d -> 0.
+    f = {d: _zonal_quadrature(lambda t: layer(t, a + d, "H")) for d in (2e-3, 1e-3, 5e-4)}
+    r1 = 2 * f[1e-3] - f[2e-3]
+    r2 = 2 * f[5e-4] - f[1e-3]
+    rich = r2 + (r2 - r1) / 3.0
+    assert abs(rich - ev["H"][n]) < 2e-4 * abs(ev["H"][n])
+
+
+def test_rigid_scatter_eigenvalues_never_vanish():
+    """Sec. 2.1: with alpha = i/k the Burton-Miller operator has no fictitious frequencies; on a sphere its
+    eigenvalues are -z^2 h_n'(z) (i j_n(z) + j_n'(z)), bounded away from zero even at interior resonances."""
+    a = 1.0
+    for k in (math.pi, 2 * math.pi, 4.493409457909064, 6.283185307179586):  # zeros of j_0 and j_1
+        ev = O.sphere_eigenvalues(20, k, a)
+        z = k * a
+        j, dj, h, dh = O.sph_all(20, z)
+        assert np.allclose(ev["A"], -z * z * dh * (1j * j + dj), rtol=1e-10)
+        assert np.min(np.abs(ev["A"])) > 0.1
+
+
+# ---------------------------------------------------------------- discrete operators
+def _zonal_samples(mesh, n):
+    xs, ns, ws = O.geometry(mesh.nodes, mesh.elems)
+    c = xs[:, 2] / np.linalg.norm(xs, axis=1)
+    return O.legendre(n, c)[n]
+
+
+def _eig_err(mesh, k, n, which, rows):
+    u = _zonal_samples(mesh, n)
+    ev = O.sphere_eigenvalues(n, k, 0.5)
+    if which == "D":
+        y = O.matvec_rows(mesh.nodes, mesh.elems, k, u, rows, c=0.0, beta_d=1.0, beta_h=0.0)
+    elif which == "H":
+        y = O.matvec_rows(mesh.nodes, mesh.elems, k, u, rows, c=0.0, beta_d=0.0, beta_h=1.0)
+    else:
+        y = O.matvec_rows(mesh.nodes, mesh.elems, k, u, rows)
+    ref = ev[which][n] * u[rows]
+    return np.linalg.norm(y - ref) / np.linalg.norm(ref)
+
+
+def test_laplace_identities_on_closed_surfaces():
+    """k = 0: sum_j Dbar_ij = 1/2 (Gauss; normal into the body) and sum_j Hbar_ij = 0 (the hypersingular
+    operator annihilates constants) on a sphere and a tri-axial ellipsoid. Pins the singular quadrature."""
+    for mesh in (inputs.icosphere(4, 0.5), inputs.ellipsoid(5, (0.5, 0.35, 0.25))):
+        N = mesh.n_dof
+        rows = np.arange(0, N, 29)
+        one = np.ones(N, dtype=complex)
+        yD = O.matvec_rows(mesh.nodes, mesh.elems, 0.0, one, rows, c=0.0, beta_d=1.0, beta_h=0.0)
+        yH = O.matvec_rows(mesh.nodes, mesh.elems, 0.0, one, rows, c=0.0, beta_d=0.0, beta_h=1.0)
+        assert np.max(np.abs(yD - 0.5)) < 2e-6
+        assert np.max(np.abs(yH)) < 3e-5
+
+
+def test_discrete_operators_match_sphere_eigenvalues(sphere_c1):
+    """Dbar, Hbar and A = 1/2 I + Dbar + (i/k) Hbar on zonal harmonics vs. their sphere eigenvalues (kD = 10)."""
+    rows = np.arange(0, sphere_c1.n_dof, 13)
+    for n in (0, 1, 2, 3):
+        assert _eig_err(sphere_c1, 10.0, n, "D", rows) < 4e-3
+        assert _eig_err(sphere_c1, 10.0, n, "H", rows) < 1.2e-2
+        assert _eig_err(sphere_c1, 10.0, n, "A", rows) < 4e-3
+
+
+def test_discrete_operator_converges_third_order():
+    e = []
+    for m in (4, 8):
+        mesh = inputs.icosphere(m, 0.5)
+        rows = np.arange(0, mesh.n_dof, 41)
+        e.append(_eig_err(mesh, 10.0, 0, "A", rows))
+    assert e[0] / e[1] > 5.0
+
+
+def test_planted_mistakes_are_caught(sphere_c1):
+    """A dropped F_{-1} term or a flipped normal in the oracle fails the eigenvalue pins."""
+    rows = np.arange(0, sphere_c1.n_dof, 17)
+    base = _eig_err(sphere_c1, 10.0, 2, "H", rows)
+    try:
+        O.set_debug(1)
+        assert _eig_err(sphere_c1, 10.0, 2, "H", rows) > 10 * base
+        O.set_debug(4)
+        assert _eig_err(sphere_c1, 10.0, 0, "D", rows) > 1.0
+    finally:
+        O.set_debug(0)
+
+
+def test_moment_quadrature_is_converged(sphere_c1):
+    """Self-element (finite part) and near-element (subdivision) moments are stable under refinement."""
+    mesh = sphere_c1
+    xs, ns, ws = O.geometry(mesh.nodes, mesh.elems)
+    e0 = 17
+    base = [O.moments(mesh.nodes, mesh.elems, e0, 10.0, self_g=g) for g in range(6)]
+    loc = O.local_region(mesh.nodes, mesh.elems, [6 * e0 + 1])[0]
+    nbr = [e for e in loc if e != e0][:4]
+    nb = [O.moments(mesh.nodes, mesh.elems, e, 10.0, x=xs[6 * e0 + 1], nx=ns[6 * e0 + 1]) for e in nbr]
+    try:
+        O.set_quadrature(32, 32, 6.0, 14, 18)
+        fine = [O.moments(mesh.nodes, mesh.elems, e0, 10.0, self_g=g) for g in range(6)]
+        nbf = [O.moments(mesh.nodes, mesh.elems, e, 10.0, x=xs[6 * e0 + 1], nx=ns[6 * e0 + 1]) for e in nbr]
+    finally:
+        O.set_quadrature()
+    for (a1, b1), (a2, b2) in zip(base, fine):
+        assert np.max(np.abs(a1 - a2)) < 1e-7 * np.max(np.abs(a2))
+        assert np.max(np.abs(b1 - b2)) < 1e-7 * np.max(np.abs(b2))
+    for (a1, b1), (a2, b2) in zip(nb, nbf):
+        assert np.max(np.abs(a1 - a2)) < 1e-12 * np.max(np.abs(a2))
+        assert np.max(np.abs(b1 - b2)) < 1e-12 * np.max(np.abs(b2))
+
+
+def test_far_part_is_complex_symmetric(sphere_c1):
+    """Reciprocity: outside the local regions Hbar_ij / w_j = d2G/dn_x dn_y(x_i, x_j) is symmetric in i, j."""
+    mesh = sphere_c1
+    xs, ns, ws = O.geometry(mesh.nodes, mesh.elems)
+    rows = np.arange(0, mesh.n_dof, 11)
+    H = O.dense_matrix(mesh.nodes, mesh.elems, 10.0, c=0.0, beta_d=0.0, beta_h=1.0)
+    K = H / ws[None, :]
+    loc = O.local_region(mesh.nodes, mesh.elems, np.arange(mesh.n_dof))
+    mask = np.ones(K.shape, dtype=bool)
+    for i, L in enumerate(loc):
+        for e in L:
+            mask[i, 6 * e:6 * e + 6] = False
+    mask &= mask.T
+    assert np.abs((K - K.T)[mask]).max() < 1e-13 * np.abs(K[mask]).max()
+    del rows
+
+
+# ---------------------------------------------------------------- solve
+def test_rigid_sphere_solve_matches_mie(sphere_c1):
+    """Sec. 5.3: rigid-sphere scattering, u_inc = e^{ik z}; the dense oracle solve approaches the Mie series
+    (third-order convergence; 5.1e-3 relative at 320 elements, h ~ lambda/4.5). GMRES reaches the direct solve."""
+    k, a = 10.0, 0.5
+    mesh = sphere_c1
+    xs, ns, ws = O.geometry(mesh.nodes, mesh.elems)
+    A = O.dense_matrix(mesh.nodes, mesh.elems, k)
+    b = O.bm_rhs(xs, ns, k, [0, 0, 1])
+    xd = np.linalg.solve(A, b)
+    x, it, res = O.gmres(lambda v: A @ v, b, tol=1e-6, restart=50)
+    assert res <= 1e-6 and it < 60
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-5
+    th = np.arccos(np.clip(xs[:, 2] / np.linalg.norm(xs, axis=1), -1, 1))
+    u = O.mie_total_surface(th, k, a)
+    assert np.linalg.norm(xd - u) / np.linalg.norm(u) < 6e-3
