@@ -1,0 +1,234 @@
+/*
+ * fdbem.h — C ABI of the GB300 fast directional Burton-Miller BEM library.
+ *
+ * The library solves the rigid-scatter Burton-Miller equation of Cao, Wen, Xiao & Liu,
+ * "A fast directional BEM for large-scale acoustic problems based on the Burton-Miller
+ * formulation" (Eng. Anal. Bound. Elem.):
+ *     (1/2) u + (D + alpha H) u = u_inc + alpha du_inc/dn          (Eq. bm with q = 0)
+ * discretised by the locally corrected Nystrom method on curved 6-node triangles (Sec. 2.2),
+ * A x = b (Eq. Axb), solved by GMRES whose matrix-vector product is the kernel-independent
+ * wideband fast directional algorithm (Sec. 3) with compressed and low-rank translation
+ * matrices (Sec. 4).
+ *
+ * Conventions shared by every entry point:
+ *  - Mesh: nodes (n_nodes x 3 doubles, row-major), elems (n_elems x 6 int32, node order
+ *    v0, v1, v2, m01, m12, m20, counter-clockwise seen from outside the body).
+ *  - Unknowns: N = 6 * n_elems Nystrom points; DOF index = 6 * element + j where j runs over
+ *    the 6-point Gauss rule in the order (xi1, xi2) = (a1,a1),(b1,a1),(a1,b1),(a2,a2),(b2,a2),(a2,b2),
+ *    a1 = 0.44594849091596488632, b1 = 1 - 2 a1, a2 = 0.09157621350977074346, b2 = 1 - 2 a2.
+ *  - Normals: the paper's n points out of the fluid, i.e. into the scatterer.
+ *  - Vectors: caller-owned DEVICE memory, interleaved complex (re, im), column-major N x nrhs,
+ *    in the user's DOF order. dtype FDA_CPLX128 (double) or FDA_CPLX64 (float).
+ *  - Streams: `stream` is a cudaStream_t (or NULL for the legacy default stream). Work is
+ *    enqueued on it; the call returns once the work is enqueued unless stated otherwise.
+ *  - Handles are library-owned and freed by the matching *_destroy. A handle must not be used
+ *    from two host threads at once.
+ *  - Every function returns FDA_OK (0) or a negative FDA_E_* code; fda_last_error() then
+ *    describes the failure (thread-local string, valid until the next call on that thread).
+ *    No C++ exception crosses this boundary.
+ */
+#ifndef FDBEM_H
+#define FDBEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  FDA_OK = 0,
+  FDA_E_INVALID_ARG = -1,   /* bad size, null pointer, unsupported option */
+  FDA_E_OOM = -2,           /* device or host allocation failed */
+  FDA_E_CUDA = -3,          /* a CUDA runtime call or kernel launch failed */
+  FDA_E_NOT_CONVERGED = -4, /* GMRES hit max_iter before tol */
+  FDA_E_BREAKDOWN = -5,     /* GMRES stagnated (residual did not decrease over a full restart cycle) */
+  FDA_E_NAN = -6,           /* NaN or Inf detected in a vector */
+  FDA_E_TIMEOUT = -7,       /* a bounded device-side wait gave up */
+  FDA_E_STATE = -8          /* call not valid for this handle's state */
+};
+
+enum { FDA_CPLX128 = 0, FDA_CPLX64 = 1 };
+
+/* Arithmetic of the matrix-vector product (near field and translations). */
+enum {
+  FDA_PREC_FP64 = 0, /* plain FP64 everywhere */
+  FDA_PREC_FP32 = 1  /* near field and translations in FP32 with FP32 accumulation */
+};
+
+typedef struct bm_problem_s bm_problem_t;
+typedef struct fda_tree_s fda_tree_t;
+typedef struct fda_plan_s fda_plan_t;
+
+/* ------------------------------------------------------------------------------------------ */
+/* Problem: mesh, wavenumber, Burton-Miller coupling (Sec. 2.1-2.2).                          */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Create a problem from a host mesh. Computes on the GPU the Nystrom points, the paper's
+ * normals (into the body) and the quadrature weights w_j = Gauss weight * area Jacobian
+ * (6-point rule, Sec. 2.2). alpha is the Burton-Miller coupling constant (the paper uses
+ * alpha = i/k, Eq. bm). Inputs are host pointers, copied; the caller keeps ownership.
+ * Errors: FDA_E_INVALID_ARG for n_elems < 1, k <= 0, a node index out of range. */
+int bm_problem_create(const double* nodes, int64_t n_nodes, const int32_t* elems6, int64_t n_elems, double k,
+                      double alpha_re, double alpha_im, bm_problem_t** out);
+
+/* Copy the Nystrom points (N x 3), normals (N x 3) and weights (N) to caller DEVICE buffers
+ * (any of them may be NULL). Synchronous. */
+int bm_problem_geometry(const bm_problem_t* prob, double* x_dev, double* n_dev, double* w_dev);
+
+/* Right-hand side of the rigid-scatter problem for plane waves u_inc = exp(i k d.x):
+ * b = u_inc + alpha du_inc/dn_x (Eq. bm with q = 0; Sec. 5.3). dirs: host, nrhs x 3 (normalised
+ * inside). b_dev: DEVICE, N x nrhs complex128, column-major. */
+int bm_rhs_plane_wave(const bm_problem_t* prob, const double* dirs, int nrhs, void* b_dev, void* stream);
+
+void bm_problem_destroy(bm_problem_t* prob);
+
+/* ------------------------------------------------------------------------------------------ */
+/* Octree and interaction lists (Sec. 3.1.1), built by GPU kernels under integer rules:        */
+/*  - root cube: bounding-box centre, side = largest extent * (1 + 2^-20); points quantised to */
+/*    21-bit integer coordinates, 63-bit Morton keys, stable sort (ties by DOF index);          */
+/*  - a box splits while it holds more than leaf_max points (N_p of Eq. npleaf);               */
+/*  - level l (width w) is high-frequency iff k w >= 2 pi; near field: LF adjacent boxes, HF    */
+/*    max-norm box offset m with m - 1 <= floor(k w / pi) (dist <= c_d k w^2, c_d = 1/pi);      */
+/*  - interaction lists I^C = N^P \ N^C by a dual recursion over near pairs from (root, root);  */
+/*    a near pair with a leaf on either side becomes a direct (near-field) block;              */
+/*  - directional wedges: n x n cells on each face of [-1,1]^3, n = 2^(L_hf - l) where L_hf is */
+/*    the finest HF level; a direction picks the face of its largest |component| (lowest axis  */
+/*    on ties) and, along each remaining axis j, cell min(n-1, floor(n (d_j + m) / (2 m))).    */
+/* ------------------------------------------------------------------------------------------ */
+int fda_build_tree(bm_problem_t* prob, int leaf_max, fda_tree_t** out);
+
+/* Host view of a tree, for tests and diagnostics. Arrays are owned by the tree handle and stay
+ * valid until fda_tree_destroy. Boxes are ordered level by level, Morton order within a level;
+ * children of a box are contiguous. Lists are sorted by (target box, source box). */
+typedef struct {
+  int64_t n_points, n_boxes, n_levels, n_direct, n_m2l;
+  double corner[3], side;
+  const int64_t* perm;        /* tree position -> DOF index (n_points) */
+  const uint64_t* keys;       /* sorted Morton keys (n_points) */
+  const int32_t* box_level;   /* n_boxes each */
+  const int32_t* box_ix;
+  const int32_t* box_iy;
+  const int32_t* box_iz;
+  const int32_t* box_nchild;
+  const int32_t* box_leaf;
+  const int64_t* box_parent;  /* -1 for the root */
+  const int64_t* box_child_begin; /* -1 for leaves */
+  const int64_t* box_pbeg;    /* point range [pbeg, pend) in tree order */
+  const int64_t* box_pend;
+  const int32_t* level_hf;    /* n_levels each */
+  const int32_t* level_T;
+  const int32_t* level_n;
+  const int64_t* direct;      /* n_direct x 2: (target box, source box) */
+  const int64_t* m2l_box;     /* n_m2l x 2: (target box, source box) */
+  const int32_t* m2l_info;    /* n_m2l x 6: level, dx, dy, dz (source - target, box units),
+                                 outgoing wedge of the source, incoming wedge of the target */
+} fda_tree_view_t;
+
+int fda_tree_export(const fda_tree_t* tree, fda_tree_view_t* view);
+void fda_tree_destroy(fda_tree_t* tree);
+
+/* ------------------------------------------------------------------------------------------ */
+/* Plan: translation operators (Sec. 3.1.2, 3.2, 4) and near-field corrections (Sec. 2.2).    */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct {
+  double eps;        /* FDA accuracy: equivalent/check point selection and SVD truncation at
+                        sigma_i >= eps sigma_1 (Eq. invr), low-rank M2L truncation (Eq. lrdk) */
+  int precision;     /* FDA_PREC_FP64 or FDA_PREC_FP32: arithmetic of fda_matvec */
+  int lowrank;       /* 1: factor compressed M2L matrices K~ = U^ V^ when rank < s/2 (Sec. 4.2) */
+  int nrhs_max;      /* largest nrhs fda_matvec / bm_gmres_solve will be called with (>= 1) */
+  int reserved[5];
+} fda_config_t;
+
+/* Build every translation operator and the near-field matrices on the GPU (FP64 masters):
+ *  - per level: equivalent points b and check points a selected by pivoted QR from candidate
+ *    sets (LF: cube surfaces; HF: spheres around the box and a cone of far check points for
+ *    the canonical wedge direction (1,0,0), rotated to every other wedge), R = G(a, b) and its
+ *    truncated SVD (Eq. svdr, invr);
+ *  - compressed S~ (with dG/dn_y check potentials, Eq. evas2mh), M~, K~, L~ = M~^T and T~
+ *    (with E_dn = G + alpha dG/dn_x, Eq. eval2t) of Eq. cmps..cmpt;
+ *  - optional low-rank factors of each K~;
+ *  - the local regions D_i, the locally corrected weights (Eq. local correction; singular and
+ *    hypersingular self-element moments in FP64), the direct near-field blocks and the
+ *    correction matrix of Eq. kcorrection.
+ * Synchronous (returns when the plan is complete). The tree and problem must outlive the plan. */
+int fda_precompute_translations(fda_tree_t* tree, const fda_config_t* cfg, fda_plan_t** out);
+
+/* y = A x with A = (1/2) I + Dbar + alpha Hbar (Eq. bm, q = 0; Eq. kcorrection), evaluated
+ * as near field + FDA far field. x, y: DEVICE, N x nrhs complex (dtype), column-major, user
+ * DOF order; x and y must not overlap. 1 <= nrhs <= cfg.nrhs_max. Asynchronous on `stream`. */
+int fda_matvec(fda_plan_t* plan, const void* x, void* y, int nrhs, int dtype, void* stream);
+
+/* Plan statistics for measurement (sizes, algorithmic bytes and flops per matvec). */
+typedef struct {
+  int32_t n_levels, lmin, precision, lowrank;
+  int32_t s[32];            /* compressed dimension per level (0 where unused) */
+  int32_t n_equiv[32];      /* selected equivalent points per level */
+  int32_t n_check[32];      /* selected check points per level */
+  int32_t n_wedges[32];     /* wedges per level (1 in LF) */
+  int64_t m2l_pairs[32];    /* M2L pairs per level */
+  int64_t m2l_offsets[32];  /* distinct K~ per level */
+  int64_t m2l_lowrank[32];  /* of which stored as U^ V^ */
+  int64_t n_leaves, n_direct_blocks;
+  int64_t near_entries;     /* stored complex entries of the direct near-field blocks */
+  int64_t corr_entries;     /* stored complex entries of the correction matrix */
+  double bytes_near;        /* algorithmic bytes of the near-field apply per RHS */
+  double bytes_s2m_l2t;     /* algorithmic bytes of S2M + L2T per RHS */
+  double flops_m2l;         /* algorithmic flops of M2L per RHS */
+  double flops_m2m_l2l;     /* algorithmic flops of M2M + L2L per RHS */
+  double flops_near;        /* 8 flops per stored complex entry per RHS */
+  double device_bytes;      /* device memory held by the plan */
+  double setup_ms[8];       /* lists/points, SVD, S~T~, M~, K~, low-rank, corrections, near blocks */
+} fda_plan_info_t;
+
+int fda_plan_info(const fda_plan_t* plan, fda_plan_info_t* info);
+
+/* Export the correction matrix of Eq. kcorrection for tests: for rows[r] (DOF indices, host),
+ * fills cnt[r] (host) and, up to cap entries per row, cols[r*cap + q] (DOF index, host) and
+ * vals[2*(r*cap + q)] (complex, host) with C_ij = wbar_ij - [j != i] K_H(x_i, y_j) w_j.
+ * Synchronous. */
+int fda_corrections_export(const fda_plan_t* plan, const int64_t* rows, int64_t nrows, int64_t cap, int64_t* cnt,
+                           int64_t* cols, double* vals);
+
+void fda_plan_destroy(fda_plan_t* plan);
+
+/* ------------------------------------------------------------------------------------------ */
+/* GMRES on A x = b (Eq. Axb; Sec. 2.2, 5.2).                                                  */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct {
+  double tol;          /* relative residual ||b - A x|| / ||b|| target */
+  int restart;         /* Krylov dimension m of GMRES(m) (1..512) */
+  int max_iter;        /* total matvec budget */
+  int x0_given;        /* 1: x holds the initial guess on entry; 0: x0 = 0 */
+  int refine;          /* 1: FP64 iterative refinement around an inner solve in the plan's
+                          precision (outer residual with the FP64 operator); 0: plain GMRES */
+  int inner_restart;   /* inner Krylov dimension when refine = 1 */
+  double inner_tol;    /* inner relative tolerance when refine = 1 */
+  int reserved[6];
+} bm_gmres_opts_t;
+
+typedef struct {
+  int iterations;      /* matvecs in the Krylov loops (inner + outer) */
+  int outer_iterations;/* refinement steps (refine = 1) */
+  double rel_residual; /* final true relative residual with the FP64 operator */
+  double ms_total;
+  double ms_matvec;
+  int status;          /* same as the return code */
+  int reserved[5];
+} bm_gmres_stats_t;
+
+/* Solve A x = b for nrhs right-hand sides (one Krylov space per column). b, x: DEVICE,
+ * N x nrhs complex128, user DOF order. Synchronous (it reads back the Givens residual estimate
+ * once per iteration). Returns FDA_E_NOT_CONVERGED / FDA_E_BREAKDOWN / FDA_E_NAN with x holding
+ * the best iterate. The refine = 1 form needs a plan built with FDA_PREC_FP32 and uses the
+ * plan's FP64 operator for the outer residual. */
+int bm_gmres_solve(fda_plan_t* plan, const void* b, void* x, int nrhs, const bm_gmres_opts_t* opts,
+                   bm_gmres_stats_t* stats, void* stream);
+
+/* Last error message of the calling thread. */
+const char* fda_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

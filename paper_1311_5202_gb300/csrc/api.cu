@@ -1,0 +1,291 @@
+// C ABI of the library (declared in include/fdbem.h): handle lifetime, argument checks, error strings.
+#include <stdarg.h>
+
+#include <new>
+
+#include "plan.cuh"
+
+namespace fda {
+static thread_local char g_err[1024] = "";
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+const char* last_error() { return g_err; }
+
+int nystrom_points(bm_problem_s* P);
+int gmres_solve(fda_plan_s* P, const double2* b, double2* x, int nrhs, const bm_gmres_opts_t* o,
+                bm_gmres_stats_t* st, cudaStream_t s);
+}  // namespace fda
+
+int fda_tree_build_impl(bm_problem_s* P, int leaf_max, fda_tree_s* T);
+
+using namespace fda;
+
+#define ARG_CHECK(cond, msg)          \
+  do {                                \
+    if (!(cond)) {                    \
+      set_error("%s", msg);           \
+      return FDA_E_INVALID_ARG;       \
+    }                                 \
+  } while (0)
+
+static __global__ void k_check_elems(const int32_t* e, int64_t n, int64_t nn, int* bad) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && (e[i] < 0 || e[i] >= nn)) atomicExch(bad, 1);
+}
+
+extern "C" {
+
+const char* fda_last_error(void) { return last_error(); }
+
+int bm_problem_create(const double* nodes, int64_t n_nodes, const int32_t* elems6, int64_t n_elems, double k,
+                      double alpha_re, double alpha_im, bm_problem_t** out) {
+  ARG_CHECK(out, "out is NULL");
+  *out = nullptr;
+  ARG_CHECK(nodes && elems6, "nodes/elems is NULL");
+  ARG_CHECK(n_nodes >= 3 && n_elems >= 1, "empty mesh");
+  ARG_CHECK(n_elems <= ((int64_t)1 << 31) / 6, "too many elements");
+  ARG_CHECK(k > 0 && std::isfinite(k), "k must be positive and finite");
+  bm_problem_s* P = new (std::nothrow) bm_problem_s();
+  if (!P) {
+    set_error("host allocation failed");
+    return FDA_E_OOM;
+  }
+  P->ne = n_elems;
+  P->N = 6 * n_elems;
+  P->nn = n_nodes;
+  P->k = k;
+  P->alpha = make_double2(alpha_re, alpha_im);
+  int rc = P->nodes.upload(nodes, 3 * n_nodes);
+  if (rc == FDA_OK) rc = P->elems.upload(elems6, 6 * n_elems);
+  if (rc == FDA_OK) {
+    DBuf<int> bad;
+    rc = bad.alloc(1);
+    if (rc == FDA_OK) rc = bad.zero();
+    if (rc == FDA_OK) {
+      k_check_elems<<<cdiv(6 * n_elems, 256), 256>>>(P->elems.p, 6 * n_elems, n_nodes, bad.p);
+      int hb = 0;
+      if (cudaMemcpy(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        set_error("CUDA error while checking the element table");
+        rc = FDA_E_CUDA;
+      } else if (hb) {
+        set_error("element table holds a node index outside [0, n_nodes)");
+        rc = FDA_E_INVALID_ARG;
+      }
+    }
+  }
+  if (rc == FDA_OK) rc = nystrom_points(P);
+  if (rc != FDA_OK) {
+    delete P;
+    return rc;
+  }
+  *out = P;
+  return FDA_OK;
+}
+
+int bm_problem_geometry(const bm_problem_t* prob, double* x_dev, double* n_dev, double* w_dev) {
+  ARG_CHECK(prob, "problem is NULL");
+  if (x_dev) FDA_CUDA(cudaMemcpy(x_dev, prob->x.p, sizeof(double) * 3 * prob->N, cudaMemcpyDeviceToDevice));
+  if (n_dev) FDA_CUDA(cudaMemcpy(n_dev, prob->n.p, sizeof(double) * 3 * prob->N, cudaMemcpyDeviceToDevice));
+  if (w_dev) FDA_CUDA(cudaMemcpy(w_dev, prob->w.p, sizeof(double) * prob->N, cudaMemcpyDeviceToDevice));
+  return FDA_OK;
+}
+
+void bm_problem_destroy(bm_problem_t* prob) { delete prob; }
+
+static __global__ void k_plane_wave(const double* x, const double* n, int64_t N, const double* dirs, int nrhs,
+                                    double k, double2 alpha, double2* b) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= N * nrhs) return;
+  int r = (int)(q / N);
+  int64_t i = q - (int64_t)r * N;
+  const double* d = dirs + 3 * r;
+  double ph = k * (d[0] * x[3 * i] + d[1] * x[3 * i + 1] + d[2] * x[3 * i + 2]);
+  double sn, cs;
+  sincos(ph, &sn, &cs);
+  double2 u = make_double2(cs, sn);
+  double dn = d[0] * n[3 * i] + d[1] * n[3 * i + 1] + d[2] * n[3 * i + 2];
+  double2 dudn = cmul(make_double2(0, k * dn), u);  // i k (d.n) u
+  b[q] = cadd(u, cmul(alpha, dudn));
+}
+
+int bm_rhs_plane_wave(const bm_problem_t* prob, const double* dirs, int nrhs, void* b_dev, void* stream) {
+  ARG_CHECK(prob && dirs && b_dev, "NULL argument");
+  ARG_CHECK(nrhs >= 1, "nrhs must be >= 1");
+  std::vector<double> d(3 * (size_t)nrhs);
+  for (int r = 0; r < nrhs; ++r) {
+    double l = sqrt(dirs[3 * r] * dirs[3 * r] + dirs[3 * r + 1] * dirs[3 * r + 1] + dirs[3 * r + 2] * dirs[3 * r + 2]);
+    ARG_CHECK(l > 0 && std::isfinite(l), "direction of zero length");
+    for (int c = 0; c < 3; ++c) d[3 * r + c] = dirs[3 * r + c] / l;
+  }
+  DBuf<double> dd;
+  FDA_TRY(dd.upload(d));
+  cudaStream_t s = (cudaStream_t)stream;
+  k_plane_wave<<<cdiv(prob->N * nrhs, 256), 256, 0, s>>>(prob->x.p, prob->n.p, prob->N, dd.p, nrhs, prob->k,
+                                                          prob->alpha, (double2*)b_dev);
+  FDA_LAUNCH_CHECK();
+  FDA_CUDA(cudaStreamSynchronize(s));
+  return FDA_OK;
+}
+
+int fda_build_tree(bm_problem_t* prob, int leaf_max, fda_tree_t** out) {
+  ARG_CHECK(out, "out is NULL");
+  *out = nullptr;
+  ARG_CHECK(prob, "problem is NULL");
+  ARG_CHECK(leaf_max >= 1, "leaf_max must be >= 1");
+  fda_tree_s* T = new (std::nothrow) fda_tree_s();
+  if (!T) {
+    set_error("host allocation failed");
+    return FDA_E_OOM;
+  }
+  int rc = fda_tree_build_impl(prob, leaf_max, T);
+  if (rc != FDA_OK) {
+    delete T;
+    return rc;
+  }
+  *out = T;
+  return FDA_OK;
+}
+
+int fda_tree_export(const fda_tree_t* T, fda_tree_view_t* v) {
+  ARG_CHECK(T && v, "NULL argument");
+  v->n_points = T->N;
+  v->n_boxes = T->nbox;
+  v->n_levels = T->nlev;
+  v->n_direct = T->ndir;
+  v->n_m2l = T->nm2l;
+  for (int d = 0; d < 3; ++d) v->corner[d] = T->corner[d];
+  v->side = T->side;
+  v->perm = T->h_perm.data();
+  v->keys = T->h_keys.data();
+  v->box_level = T->h_lev.data();
+  v->box_ix = T->h_ix.data();
+  v->box_iy = T->h_iy.data();
+  v->box_iz = T->h_iz.data();
+  v->box_nchild = T->h_nch.data();
+  v->box_leaf = T->h_leaf.data();
+  v->box_parent = T->h_par.data();
+  v->box_child_begin = T->h_cbeg.data();
+  v->box_pbeg = T->h_pb.data();
+  v->box_pend = T->h_pe.data();
+  v->level_hf = T->h_level_hf.data();
+  v->level_T = T->h_level_T.data();
+  v->level_n = T->h_level_n.data();
+  v->direct = T->h_direct.data();
+  v->m2l_box = T->h_m2l_box.data();
+  v->m2l_info = T->h_m2l_info.data();
+  return FDA_OK;
+}
+
+void fda_tree_destroy(fda_tree_t* T) { delete T; }
+
+int fda_precompute_translations(fda_tree_t* tree, const fda_config_t* cfg, fda_plan_t** out) {
+  ARG_CHECK(out, "out is NULL");
+  *out = nullptr;
+  ARG_CHECK(tree && cfg, "NULL argument");
+  ARG_CHECK(cfg->eps > 0 && cfg->eps < 1, "eps must lie in (0, 1)");
+  ARG_CHECK(cfg->precision == FDA_PREC_FP64 || cfg->precision == FDA_PREC_FP32, "unknown precision");
+  ARG_CHECK(cfg->nrhs_max >= 1 && cfg->nrhs_max <= 4096, "nrhs_max must lie in [1, 4096]");
+  fda_plan_s* P = new (std::nothrow) fda_plan_s();
+  if (!P) {
+    set_error("host allocation failed");
+    return FDA_E_OOM;
+  }
+  int rc = plan_build(tree, cfg, P);
+  if (rc != FDA_OK) {
+    delete P;
+    return rc;
+  }
+  *out = P;
+  return FDA_OK;
+}
+
+int fda_matvec(fda_plan_t* plan, const void* x, void* y, int nrhs, int dtype, void* stream) {
+  ARG_CHECK(plan && x && y, "NULL argument");
+  ARG_CHECK(dtype == FDA_CPLX128 || dtype == FDA_CPLX64, "unknown dtype");
+  ARG_CHECK(x != y, "x and y must not overlap");
+  return plan_matvec(plan, plan->cfg.precision, x, y, nrhs, dtype, (cudaStream_t)stream, false);
+}
+
+int fda_plan_info(const fda_plan_t* P, fda_plan_info_t* I) {
+  ARG_CHECK(P && I, "NULL argument");
+  memset(I, 0, sizeof(*I));
+  I->n_levels = P->tree->nlev;
+  I->lmin = P->lmin;
+  I->precision = P->cfg.precision;
+  I->lowrank = P->cfg.lowrank;
+  for (int l = 0; l < FDA_MAXLEV && l < 32; ++l) {
+    I->s[l] = P->lev[l].s;
+    I->n_equiv[l] = P->lev[l].se;
+    I->n_check[l] = P->lev[l].sc;
+    I->n_wedges[l] = P->lev[l].used ? P->lev[l].nw : 0;
+    I->m2l_pairs[l] = P->m2l_pairs[l];
+    I->m2l_offsets[l] = P->m2l_offsets[l];
+    I->m2l_lowrank[l] = P->m2l_lowrank[l];
+  }
+  I->n_leaves = (int64_t)P->h_leaves.size();
+  I->n_direct_blocks = P->n_blocks;
+  I->near_entries = P->near_entries;
+  I->corr_entries = P->corr_entries;
+  I->bytes_near = 16.0 * (double)(P->near_entries + P->corr_entries) + 4.0 * P->corr_entries;
+  I->bytes_s2m_l2t = P->bytes_s2m_l2t;
+  I->flops_m2l = P->flops_m2l;
+  I->flops_m2m_l2l = P->flops_m2m;
+  I->flops_near = 8.0 * (double)(P->near_entries + P->corr_entries);
+  double dev = 0;
+  const fda::RunOps<double2>& a = P->op64;
+  dev += a.S.bytes() + a.T.bytes() + a.M.bytes() + a.K.bytes() + a.near.bytes() + a.corr.bytes() + a.lr.bytes();
+  const fda::RunOps<float2>& b = P->op32;
+  dev += b.S.bytes() + b.T.bytes() + b.M.bytes() + b.K.bytes() + b.near.bytes() + b.corr.bytes() + b.lr.bytes();
+  dev += P->corr_col.bytes() + P->cout64.bytes() + P->cin64.bytes() + P->cout32.bytes() + P->cin32.bytes();
+  I->device_bytes = dev;
+  for (int q = 0; q < 8; ++q) I->setup_ms[q] = P->setup_ms[q];
+  return FDA_OK;
+}
+
+int fda_corrections_export(const fda_plan_t* P, const int64_t* rows, int64_t nrows, int64_t cap, int64_t* cnt,
+                           int64_t* cols, double* vals) {
+  ARG_CHECK(P && rows && cnt && cols && vals, "NULL argument");
+  const int64_t N = P->tree->N;
+  std::vector<int64_t> ip, ptr;
+  std::vector<int32_t> cc;
+  std::vector<double2> vv;
+  FDA_TRY(P->iperm.download(ip));
+  FDA_TRY(P->corr_ptr.download(ptr));
+  cc.resize(P->corr_entries);
+  vv.resize(P->corr_entries);
+  if (P->corr_entries) {
+    FDA_CUDA(cudaMemcpy(cc.data(), P->corr_col.p, sizeof(int32_t) * P->corr_entries, cudaMemcpyDeviceToHost));
+    FDA_CUDA(cudaMemcpy(vv.data(), P->op64.corr.p, sizeof(double2) * P->corr_entries, cudaMemcpyDeviceToHost));
+  }
+  const std::vector<int64_t>& perm = P->tree->h_perm;
+  for (int64_t r = 0; r < nrows; ++r) {
+    ARG_CHECK(rows[r] >= 0 && rows[r] < N, "row out of range");
+    int64_t t = ip[rows[r]];
+    int64_t n = ptr[t + 1] - ptr[t];
+    cnt[r] = n;
+    for (int64_t q = 0; q < n && q < cap; ++q) {
+      cols[r * cap + q] = perm[cc[ptr[t] + q]];
+      vals[2 * (r * cap + q)] = vv[ptr[t] + q].x;
+      vals[2 * (r * cap + q) + 1] = vv[ptr[t] + q].y;
+    }
+  }
+  return FDA_OK;
+}
+
+void fda_plan_destroy(fda_plan_t* plan) { delete plan; }
+
+int bm_gmres_solve(fda_plan_t* plan, const void* b, void* x, int nrhs, const bm_gmres_opts_t* opts,
+                   bm_gmres_stats_t* stats, void* stream) {
+  ARG_CHECK(plan && b && x && opts, "NULL argument");
+  ARG_CHECK(nrhs >= 1, "nrhs must be >= 1");
+  ARG_CHECK(opts->tol > 0, "tol must be positive");
+  ARG_CHECK(opts->restart >= 1, "restart must be >= 1");
+  ARG_CHECK(opts->max_iter >= 1, "max_iter must be >= 1");
+  return gmres_solve(plan, (const double2*)b, (double2*)x, nrhs, opts, stats, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,462 @@
+// The FDA matrix-vector product y = (1/2) x + Hbar x (Eq. bm with q = 0, Eq. kcorrection):
+//   near   : y_i = sum over direct blocks K_H(x_i, y_j) w_j x_j + sum_j C_ij x_j        (Sec. 2.2, 3.2 mod. 3)
+//   S2M    : t_C = S~_C x_C                                                             (Eq. cmps, evas2mh)
+//   M2M    : t_P,z = sum_children M~(l, octant, z) t_c,z'                               (Eq. cmpm)
+//   M2L    : u_B,-z += K~(offset) t_C,z  (dense, or U^ (V^ t) when low rank)           (Eq. cmpk, lrdk)
+//   L2L    : u_c,z' += sum_{z in z'} M~(l, octant, z)^T u_P,z                          (Eq. cmpl, L = M^T)
+//   L2T    : y_C += sum_z T~_C,z u_C,z                                                  (Eq. cmpt, eval2t)
+// Vectors live in tree order with the RHS index fastest: v[(point) * nrhs + rhs]; coefficients likewise:
+// c[(slot + wedge * s + r) * nrhs + rhs]. One template serves FP64 (double2) and FP32 (float2) operators.
+#include "plan.cuh"
+
+namespace fda {
+
+template <typename C>
+static __global__ void k_perm_in(const void* x, int io, const int64_t* perm, int64_t N, int nrhs, C* xt) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= N * nrhs) return;
+  int64_t t = q / nrhs;
+  int r = (int)(q - t * nrhs);
+  int64_t src = (int64_t)r * N + perm[t];
+  double2 v = io == FDA_CPLX128 ? ((const double2*)x)[src]
+                                : make_double2(((const float2*)x)[src].x, ((const float2*)x)[src].y);
+  xt[q] = from_d<C>(v);
+}
+
+template <typename C>
+static __global__ void k_assemble(const void* x, void* y, int io, const int64_t* perm, int64_t N, int nrhs,
+                                  const C* yt) {
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= N * nrhs) return;
+  int64_t t = q / nrhs;
+  int r = (int)(q - t * nrhs);
+  int64_t d = (int64_t)r * N + perm[t];
+  double2 a = to_d(yt[q]);
+  if (io == FDA_CPLX128) {
+    double2 xv = ((const double2*)x)[d];
+    ((double2*)y)[d] = make_double2(0.5 * xv.x + a.x, 0.5 * xv.y + a.y);
+  } else {
+    float2 xv = ((const float2*)x)[d];
+    ((float2*)y)[d] = make_float2(0.5f * xv.x + (float)a.x, 0.5f * xv.y + (float)a.y);
+  }
+}
+
+// ------------------------------------------------------------------ near field (a6)
+// One CTA per target leaf; threads own rows and NR right-hand sides; corrections by warps (lanes over a row).
+#define NEAR_NT 128
+#define NEAR_XS 256
+template <typename C, int NR>
+static __global__ void __launch_bounds__(NEAR_NT) k_near(const int64_t* tleaf, const int64_t* tptr,
+                                                         const int64_t* srcbox, const int64_t* boff,
+                                                         const int64_t* pb, const int64_t* pe, const C* B,
+                                                         const int64_t* cptr, const int32_t* ccol, const C* cval,
+                                                         const C* xt, C* yt, int nrhs, int r0) {
+  __shared__ C xs[NEAR_XS * NR];
+  __shared__ C ys[NEAR_NT * NR];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int64_t L = tleaf[blockIdx.x];
+  const int64_t tb = pb[L], te = pe[L];
+  const int64_t nr = te - tb;
+  for (int64_t rb = 0; rb < nr; rb += NEAR_NT) {
+    const int64_t i = rb + t;
+    C acc[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) acc[q] = mk((decltype(acc[0].x))0, (decltype(acc[0].x))0);
+    for (int64_t bq = tptr[blockIdx.x]; bq < tptr[blockIdx.x + 1]; ++bq) {
+      const int64_t Q = srcbox[bq];
+      const int64_t sb = pb[Q], se = pe[Q];
+      const C* blk = B + boff[bq];
+      for (int64_t j0 = sb; j0 < se; j0 += NEAR_XS) {
+        int nc = (int)min((int64_t)NEAR_XS, se - j0);
+        __syncthreads();
+        for (int q = t; q < nc * NR; q += NEAR_NT) {
+          int j = q / NR, rr = q - j * NR;
+          xs[q] = (r0 + rr < nrhs) ? xt[(j0 + j) * nrhs + r0 + rr] : mk((decltype(acc[0].x))0, (decltype(acc[0].x))0);
+        }
+        __syncthreads();
+        if (i < nr) {
+          const C* col = blk + (j0 - sb) * nr + i;
+          for (int j = 0; j < nc; ++j) {
+            C bv = col[(int64_t)j * nr];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) cfma(acc[q], bv, xs[j * NR + q]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NR; ++q) ys[t * NR + q] = acc[q];
+    __syncthreads();
+    // corrections: warp per row
+    for (int rr = w; rr < NEAR_NT && rb + rr < nr; rr += NEAR_NT / 32) {
+      const int64_t ti = tb + rb + rr;
+      C cacc[NR];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) cacc[q] = mk((decltype(acc[0].x))0, (decltype(acc[0].x))0);
+      for (int64_t p = cptr[ti] + lane; p < cptr[ti + 1]; p += 32) {
+        C v = cval[p];
+        int64_t col = ccol[p];
+#pragma unroll
+        for (int q = 0; q < NR; ++q)
+          if (r0 + q < nrhs) cfma(cacc[q], v, xt[col * nrhs + r0 + q]);
+      }
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        cacc[q] = warp_csum(cacc[q]);
+        if (lane == 0) ys[rr * NR + q] = cadd(ys[rr * NR + q], cacc[q]);
+      }
+    }
+    __syncthreads();
+    if (i < nr) {
+#pragma unroll
+      for (int q = 0; q < NR; ++q)
+        if (r0 + q < nrhs) yt[(tb + i) * nrhs + r0 + q] = ys[t * NR + q];
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ S2M (a7): one CTA per (leaf, wedge)
+// Right-hand sides r0 .. r0+rc-1 of nrhs (shared-memory staging bounded by rc).
+template <typename C>
+static __global__ void k_s2m(const int64_t* leaves, const int64_t* soff, const int64_t* pb, const int64_t* pe,
+                             const int32_t* lev, const int64_t* slot, const int* ls, const int* lnw, const C* S,
+                             const C* xt, C* cout, int nrhs, int r0, int rc) {
+  extern __shared__ unsigned char smem_raw[];
+  C* xs = (C*)smem_raw;
+  const int64_t b = leaves[blockIdx.x];
+  const int z = blockIdx.y;
+  const int l = lev[b];
+  const int s = ls[l], nw = lnw[l];
+  if (z >= nw) return;
+  const int64_t p0 = pb[b];
+  const int nC = (int)(pe[b] - p0);
+  for (int q = threadIdx.x; q < nC * rc; q += blockDim.x) {
+    int j = q / rc, rr = q - j * rc;
+    xs[q] = xt[(p0 + j) * nrhs + r0 + rr];
+  }
+  __syncthreads();
+  const C* Sz = S + soff[blockIdx.x] + (int64_t)z * s * nC;
+  const int64_t base = slot[b] + (int64_t)z * s;
+  for (int q = threadIdx.x; q < s * rc; q += blockDim.x) {
+    int r = q / rc, rr = q - r * rc;
+    C acc = mk((decltype(acc.x))0, (decltype(acc.x))0);
+    for (int j = 0; j < nC; ++j) cfma(acc, Sz[(int64_t)j * s + r], xs[j * rc + rr]);
+    cout[(base + r) * nrhs + r0 + rr] = acc;
+  }
+}
+
+// ------------------------------------------------------------------ M2M (a8): one CTA per (parent, wedge)
+__device__ __forceinline__ int child_wedge_dev(int hf_c, int n, int nc, int z) {
+  if (!hf_c) return 0;
+  int face = z / (n * n), cell = z - face * n * n;
+  int c1 = cell / n, c2 = cell - c1 * n;
+  return face * nc * nc + (c1 / 2) * nc + (c2 / 2);
+}
+
+template <typename C>
+static __global__ void k_m2m(const int64_t* parents, const int64_t* cbeg, const int32_t* nch, const int32_t* ix,
+                             const int32_t* iy, const int32_t* iz, const int64_t* slot, int sl, int sc_, int nwl,
+                             int nl, int nc, int hf_c, const C* M, C* cout, int nrhs, int r0, int rc) {
+  extern __shared__ unsigned char smem_raw[];
+  C* ts = (C*)smem_raw;
+  const int64_t P = parents[blockIdx.x];
+  const int z = blockIdx.y;
+  const int zc = child_wedge_dev(hf_c, nl, nc, z);
+  const int nout = sl * rc;
+  for (int q0 = 0; q0 < nout; q0 += 4 * blockDim.x) {
+    C acc[4];
+    for (int q = 0; q < 4; ++q) acc[q] = mk((decltype(acc[0].x))0, (decltype(acc[0].x))0);
+    for (int64_t c = cbeg[P]; c < cbeg[P] + nch[P]; ++c) {
+      int o = ((ix[c] & 1) << 2) | ((iy[c] & 1) << 1) | (iz[c] & 1);
+      const C* Mz = M + (int64_t)(o * nwl + z) * sl * sc_;
+      __syncthreads();
+      for (int q = threadIdx.x; q < sc_ * rc; q += blockDim.x) {
+        int j = q / rc, rr = q - j * rc;
+        ts[q] = cout[(slot[c] + (int64_t)zc * sc_ + j) * nrhs + r0 + rr];
+      }
+      __syncthreads();
+      for (int u = 0; u < 4; ++u) {
+        int q = q0 + threadIdx.x + u * blockDim.x;
+        if (q >= nout) break;
+        int r = q / rc, rr = q - r * rc;
+        for (int j = 0; j < sc_; ++j) cfma(acc[u], Mz[(int64_t)j * sl + r], ts[j * rc + rr]);
+      }
+    }
+    for (int u = 0; u < 4; ++u) {
+      int q = q0 + threadIdx.x + u * blockDim.x;
+      if (q >= nout) break;
+      int r = q / rc, rr = q - r * rc;
+      cout[(slot[P] + (int64_t)z * sl + r) * nrhs + r0 + rr] = acc[u];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ L2L (a10): one CTA per (child, child wedge)
+template <typename C>
+static __global__ void k_l2l(int64_t box0, const int64_t* par, const int32_t* ix, const int32_t* iy,
+                             const int32_t* iz, const int64_t* slot, int sl, int sc_, int nwl, int nl, int nc,
+                             int hf_c, const C* M, C* cin, int nrhs, int r0, int rc) {
+  extern __shared__ unsigned char smem_raw[];
+  C* us = (C*)smem_raw;
+  C* acc = us + sl * rc;
+  const int64_t c = box0 + blockIdx.x;
+  const int zc = blockIdx.y;
+  const int64_t P = par[c];
+  const int o = ((ix[c] & 1) << 2) | ((iy[c] & 1) << 1) | (iz[c] & 1);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int nout = sc_ * rc;
+  for (int q = threadIdx.x; q < nout; q += blockDim.x) acc[q] = mk((decltype(acc[0].x))0, (decltype(acc[0].x))0);
+  for (int z = 0; z < nwl; ++z) {
+    if (child_wedge_dev(hf_c, nl, nc, z) != zc) continue;
+    const C* Mz = M + (int64_t)(o * nwl + z) * sl * sc_;
+    __syncthreads();
+    for (int q = threadIdx.x; q < sl * rc; q += blockDim.x) {
+      int j = q / rc, rr = q - j * rc;
+      us[q] = cin[(slot[P] + (int64_t)z * sl + j) * nrhs + r0 + rr];
+    }
+    __syncthreads();
+    for (int r = w; r < sc_; r += nwarp) {
+      const C* col = Mz + (int64_t)r * sl;  // column r of M~ = row r of M~^T
+      for (int rr = 0; rr < rc; ++rr) {
+        C a = mk((decltype(acc[0].x))0, (decltype(acc[0].x))0);
+        for (int j = lane; j < sl; j += 32) cfma(a, col[j], us[j * rc + rr]);
+        a = warp_csum(a);
+        if (lane == 0) acc[r * rc + rr] = cadd(acc[r * rc + rr], a);
+      }
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < nout; q += blockDim.x) {
+    int r = q / rc, rr = q - r * rc;
+    C* d = cin + (slot[c] + (int64_t)zc * sc_ + r) * nrhs + r0 + rr;
+    *d = cadd(*d, acc[q]);
+  }
+}
+
+// ------------------------------------------------------------------ L2T (a11): one CTA per leaf
+template <typename C>
+static __global__ void k_l2t(const int64_t* leaves, const int64_t* toff, const int64_t* pb, const int64_t* pe,
+                             const int32_t* lev, const int64_t* slot, const int* ls, const int* lnw, const C* Tm,
+                             const C* cin, C* yt, int nrhs, int r0, int rc) {
+  extern __shared__ unsigned char smem_raw[];
+  C* us = (C*)smem_raw;
+  const int64_t b = leaves[blockIdx.x];
+  const int l = lev[b];
+  const int s = ls[l], nw = lnw[l];
+  const int64_t p0 = pb[b];
+  const int nC = (int)(pe[b] - p0);
+  for (int z = 0; z < nw; ++z) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < s * rc; q += blockDim.x) {
+      int r = q / rc, rr = q - r * rc;
+      us[q] = cin[(slot[b] + (int64_t)z * s + r) * nrhs + r0 + rr];
+    }
+    __syncthreads();
+    const C* Tz = Tm + toff[blockIdx.x] + (int64_t)z * s * nC;
+    for (int q = threadIdx.x; q < nC * rc; q += blockDim.x) {
+      int i = q / rc, rr = q - i * rc;
+      C acc = mk((decltype(us[0].x))0, (decltype(us[0].x))0);
+      for (int r = 0; r < s; ++r) cfma(acc, Tz[(int64_t)r * nC + i], us[r * rc + rr]);
+      C* d = yt + (p0 + i) * nrhs + r0 + rr;
+      *d = cadd(*d, acc);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ M2L (a9): grouped gather-GEMM-scatter
+#define M2L_TM 64
+#define M2L_TN 32
+#define M2L_TK 16
+template <typename C>
+static __global__ void __launch_bounds__(256) k_m2l(const GemmUnit* units, const C* poolK, const C* poolLR,
+                                                    const int64_t* psrc,
+                                                    const int64_t* ptgt, const int64_t* pmid, const C* cout,
+                                                    C* cin, C* mid, int nrhs) {
+  __shared__ C As[M2L_TK][M2L_TM + 1];
+  __shared__ C Xs[M2L_TK][M2L_TN + 1];
+  __shared__ int64_t sbase[M2L_TN], dbase[M2L_TN];
+  __shared__ int srr[M2L_TN];
+  const GemmUnit U = units[blockIdx.x];
+  const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
+  const C* A = (U.mode == 0 ? poolK : poolLR) + U.a_off;
+  const C* X = (U.mode == 2) ? mid : cout;
+  const int ncols = U.p_count * nrhs;
+  for (int c0 = 0; c0 < ncols; c0 += M2L_TN) {
+    __syncthreads();
+    if (t < M2L_TN) {
+      int c = c0 + t;
+      if (c < ncols) {
+        int p = c / nrhs;
+        int rr = c - p * nrhs;
+        int64_t pi = U.p_begin + p;
+        sbase[t] = (U.mode == 2) ? pmid[pi] : psrc[pi];
+        dbase[t] = (U.mode == 1) ? pmid[pi] : ptgt[pi];
+        srr[t] = rr;
+      } else {
+        sbase[t] = -1;
+        dbase[t] = -1;
+        srr[t] = 0;
+      }
+    }
+    C acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = mk((decltype(acc[0].x))0, (decltype(acc[0].x))0);
+    for (int k0 = 0; k0 < U.K; k0 += M2L_TK) {
+      __syncthreads();
+      for (int q = t; q < M2L_TK * M2L_TM; q += 256) {
+        int mm = q % M2L_TM, kk = q / M2L_TM;
+        int gm = U.m0 + mm, gk = k0 + kk;
+        As[kk][mm] = (gm < U.M && gk < U.K) ? A[gm + (int64_t)gk * U.M] : mk((decltype(acc[0].x))0, (decltype(acc[0].x))0);
+      }
+      for (int q = t; q < M2L_TK * M2L_TN; q += 256) {
+        int cc = q % M2L_TN, kk = q / M2L_TN;
+        int gk = k0 + kk;
+        Xs[kk][cc] = (sbase[cc] >= 0 && gk < U.K) ? X[(sbase[cc] + gk) * nrhs + srr[cc]]
+                                                  : mk((decltype(acc[0].x))0, (decltype(acc[0].x))0);
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < M2L_TK; ++kk) {
+        C xv = Xs[kk][tx];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) cfma(acc[q], As[kk][ty + 8 * q], xv);
+      }
+    }
+    if (dbase[tx] >= 0) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        int gm = U.m0 + ty + 8 * q;
+        if (gm >= U.M) continue;
+        int64_t d = (dbase[tx] + gm) * nrhs + srr[tx];
+        if (U.mode == 1)
+          mid[d] = acc[q];
+        else
+          atomic_cadd(cin + d, acc[q]);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ driver
+template <typename C>
+static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf<C>& cout, DBuf<C>& cin,
+                    DBuf<C>& mid, const void* x, void* y, int nrhs, int io, cudaStream_t s) {
+  fda_tree_s* T = P->tree;
+  const int64_t N = T->N;
+  k_perm_in<C><<<cdiv(N * nrhs, 256), 256, 0, s>>>(x, io, T->perm.p, N, nrhs, xt.p);
+  FDA_LAUNCH_CHECK();
+  // near field
+  if (P->n_near_tleaf > 0) {
+    for (int r0 = 0; r0 < nrhs; r0 += (nrhs == 1 ? 1 : 4)) {
+      if (nrhs == 1)
+        k_near<C, 1><<<(unsigned)P->n_near_tleaf, NEAR_NT, 0, s>>>(
+            P->near_tleaf.p, P->near_tptr.p, P->near_src.p, P->near_off.p, T->pb.p, T->pe.p, op.near.p,
+            P->corr_ptr.p, P->corr_col.p, op.corr.p, xt.p, yt.p, nrhs, r0);
+      else
+        k_near<C, 4><<<(unsigned)P->n_near_tleaf, NEAR_NT, 0, s>>>(
+            P->near_tleaf.p, P->near_tptr.p, P->near_src.p, P->near_off.p, T->pb.p, T->pe.p, op.near.p,
+            P->corr_ptr.p, P->corr_col.p, op.corr.p, xt.p, yt.p, nrhs, r0);
+      FDA_LAUNCH_CHECK();
+    }
+  } else {
+    FDA_CUDA(cudaMemsetAsync(yt.p, 0, sizeof(C) * N * nrhs, s));
+  }
+  if (P->n_coef > 0) {
+    const int* d_ls = P->lev_s.p;
+    const int* d_lnw = P->lev_nw.p;
+    int maxnw = 1, maxs = 1;
+    for (int l = P->lmin; l <= P->lmax; ++l) maxnw = std::max(maxnw, P->lev[l].nw), maxs = std::max(maxs, P->lev[l].s);
+    const int maxleaf = std::max(1, P->max_leaf);
+    const size_t SMEM = 40960;
+    auto chunk = [&](size_t rows) { return (int)std::max<size_t>(1, std::min<size_t>(nrhs, SMEM / (rows * sizeof(C)))); };
+    // S2M
+    if (!P->h_leaves.empty()) {
+      int rc = chunk(maxleaf);
+      for (int r0 = 0; r0 < nrhs; r0 += rc) {
+        int rcc = std::min(rc, nrhs - r0);
+        k_s2m<C><<<dim3((unsigned)P->h_leaves.size(), maxnw), 128, sizeof(C) * maxleaf * rcc, s>>>(
+            P->leaves.p, P->leaf_s_off.p, T->pb.p, T->pe.p, T->lev.p, P->slot.p, d_ls, d_lnw, op.S.p, xt.p,
+            cout.p, nrhs, r0, rcc);
+        FDA_LAUNCH_CHECK();
+      }
+    }
+    // M2M bottom-up
+    for (int l = P->lmax - 1; l >= P->lmin; --l) {
+      if (P->h_parents[l].empty()) continue;
+      const LevelOps &L = P->lev[l], &Lc = P->lev[l + 1];
+      int rc = chunk(Lc.s);
+      for (int r0 = 0; r0 < nrhs; r0 += rc) {
+        int rcc = std::min(rc, nrhs - r0);
+        int nt = 128;
+        while (nt * 4 < L.s * rcc && nt < 512) nt *= 2;
+        k_m2m<C><<<dim3((unsigned)P->h_parents[l].size(), L.nw), nt, sizeof(C) * Lc.s * rcc, s>>>(
+            P->parents[l].p, T->cbeg.p, T->nch.p, T->ix.p, T->iy.p, T->iz.p, P->slot.p, L.s, Lc.s, L.nw, L.n, Lc.n,
+            Lc.hf ? 1 : 0, op.M.p + P->m_off[l], cout.p, nrhs, r0, rcc);
+        FDA_LAUNCH_CHECK();
+      }
+    }
+    // M2L
+    FDA_CUDA(cudaMemsetAsync(cin.p, 0, sizeof(C) * P->n_coef * nrhs, s));
+    for (int l = P->lmin; l <= P->lmax; ++l) {
+      for (int st = 0; st < 2; ++st) {
+        size_t nu = P->h_units[l][st].size();
+        for (size_t u0 = 0; u0 < nu; u0 += 65535) {
+          unsigned n = (unsigned)std::min<size_t>(65535, nu - u0);
+          k_m2l<C><<<n, 256, 0, s>>>(P->units[l][st].p + u0, op.K.p, op.lr.p, P->pair_src.p, P->pair_tgt.p,
+                                     P->pair_mid.p, cout.p, cin.p, mid.p, nrhs);
+          FDA_LAUNCH_CHECK();
+        }
+      }
+    }
+    // L2L top-down
+    for (int l = P->lmin; l < P->lmax; ++l) {
+      const LevelOps &L = P->lev[l], &Lc = P->lev[l + 1];
+      int64_t nchild = Lc.box_end - Lc.box_begin;
+      if (nchild <= 0 || P->h_parents[l].empty()) continue;
+      int rc = chunk(L.s + Lc.s);
+      for (int r0 = 0; r0 < nrhs; r0 += rc) {
+        int rcc = std::min(rc, nrhs - r0);
+        size_t sm = sizeof(C) * ((size_t)L.s * rcc + (size_t)Lc.s * rcc);
+        k_l2l<C><<<dim3((unsigned)nchild, Lc.nw), 256, sm, s>>>(Lc.box_begin, T->par.p, T->ix.p, T->iy.p, T->iz.p,
+                                                               P->slot.p, L.s, Lc.s, L.nw, L.n, Lc.n, Lc.hf ? 1 : 0,
+                                                               op.M.p + P->m_off[l], cin.p, nrhs, r0, rcc);
+        FDA_LAUNCH_CHECK();
+      }
+    }
+    // L2T
+    if (!P->h_leaves.empty()) {
+      int rc = chunk(maxs);
+      for (int r0 = 0; r0 < nrhs; r0 += rc) {
+        int rcc = std::min(rc, nrhs - r0);
+        k_l2t<C><<<(unsigned)P->h_leaves.size(), 128, sizeof(C) * maxs * rcc, s>>>(
+            P->leaves.p, P->leaf_t_off.p, T->pb.p, T->pe.p, T->lev.p, P->slot.p, d_ls, d_lnw, op.T.p, cin.p, yt.p,
+            nrhs, r0, rcc);
+        FDA_LAUNCH_CHECK();
+      }
+    }
+  }
+  k_assemble<C><<<cdiv(N * nrhs, 256), 256, 0, s>>>(x, y, io, T->perm.p, N, nrhs, yt.p);
+  FDA_LAUNCH_CHECK();
+  return FDA_OK;
+}
+
+int plan_matvec(fda_plan_s* P, int prec, const void* x, void* y, int nrhs, int io_dtype, cudaStream_t s,
+                bool tree_order) {
+  (void)tree_order;
+  if (nrhs < 1 || nrhs > P->cfg.nrhs_max) {
+    set_error("nrhs %d outside [1, %d]", nrhs, P->cfg.nrhs_max);
+    return FDA_E_INVALID_ARG;
+  }
+  if (prec == FDA_PREC_FP32) {
+    if (P->cfg.precision != FDA_PREC_FP32) {
+      set_error("plan was built without FP32 operators");
+      return FDA_E_STATE;
+    }
+    return matvec_t<float2>(P, P->op32, P->xt32, P->yt32, P->cout32, P->cin32, P->mid32, x, y, nrhs, io_dtype, s);
+  }
+  return matvec_t<double2>(P, P->op64, P->xt64, P->yt64, P->cout64, P->cin64, P->mid64, x, y, nrhs, io_dtype, s);
+}
+
+}  // namespace fda

@@ -1,0 +1,104 @@
+// Plan layout: translation operators, near-field matrices and execution schedules.
+#pragma once
+#include "internal.cuh"
+
+namespace fda {
+
+struct QRJob;
+struct QFormJob;
+struct SVDJob;
+int zgemm_batched(char opa, char opb, int M, int N, int K, double2 alpha, const double2* const* A, int lda,
+                  const double2* const* B, int ldb, double2 beta, double2* const* C, int ldc, int64_t batch,
+                  cudaStream_t s);
+int near_corrections(bm_problem_s* P, DBuf<int64_t>& di_ptr, DBuf<int32_t>& di_cols, DBuf<double2>& corr,
+                     double* ms);
+int upload_geometry_constants();
+
+// One level of the tree that carries outgoing/incoming representations.
+struct LevelOps {
+  bool used = false, hf = false;
+  int n = 1, nw = 1;        // cells per face edge, wedges
+  int s = 0, se = 0, sc = 0;  // compressed dim, selected equivalent / check points
+  double w = 0;
+  std::vector<double> b, a, Wa;   // canonical equivalent (se x 3), check (sc x 3), check weights
+  std::vector<double> rot;        // nw x 9 rotations (row-major), e_x -> wedge centre direction
+  DBuf<double> d_b, d_a, d_Wa, d_rot;
+  DBuf<double2> P;    // sc x s : U~ Sigma~^-1
+  DBuf<double2> Pc;   // sc x s : conj(P)
+  DBuf<double2> V;    // se x s : V~
+  std::vector<double> sigma;
+  int64_t box_begin = 0, box_end = 0;  // boxes of this level
+};
+
+// A unit of grouped gather-GEMM-scatter work: Y[:, tgt(p)] (+)= A X[:, src(p)] for pairs p.
+struct GemmUnit {
+  int64_t a_off;      // offset of A (M x K, column-major, lda = M) in the matrix pool
+  int32_t M, K;
+  int64_t p_begin;    // first pair (index into pair arrays)
+  int32_t p_count;
+  int32_t m0;         // first output row of this unit's row tile
+  int32_t mode;       // 0: coef_out -> coef_in (add), 1: coef_out -> mid (store), 2: mid -> coef_in (add)
+  int32_t pad;
+};
+
+template <typename C>
+struct RunOps {
+  DBuf<C> S, T, M, K, near, corr, lr;  // operator pools
+};
+
+}  // namespace fda
+
+struct fda_plan_s {
+  fda_tree_s* tree = nullptr;
+  bm_problem_s* prob = nullptr;
+  fda_config_t cfg;
+  int lmin = 0, lmax = 0;  // levels carrying representations
+  fda::LevelOps lev[FDA_MAXLEV];
+  // coefficient slots: per box (levels >= lmin) nw * s complex per RHS
+  std::vector<int64_t> h_slot;  // per box: first coefficient index (or -1)
+  int64_t n_coef = 0;
+  fda::DBuf<int64_t> slot;
+  // leaves carrying S2M / L2T (level >= lmin)
+  std::vector<int64_t> h_leaves;
+  fda::DBuf<int64_t> leaves, leaf_s_off, leaf_t_off;
+  // near field: blocks per target leaf
+  fda::DBuf<int64_t> near_tleaf;     // target leaves with at least one block
+  fda::DBuf<int64_t> near_tptr;      // CSR over those leaves -> blocks
+  fda::DBuf<int64_t> near_src;       // block -> source box
+  fda::DBuf<int64_t> near_off;       // block -> entry offset
+  int64_t n_near_tleaf = 0, n_blocks = 0, near_entries = 0;
+  fda::DBuf<int64_t> corr_ptr;       // tree-order CSR of the correction matrix
+  fda::DBuf<int32_t> corr_col;
+  int64_t corr_entries = 0;
+  // M2M / L2L: per level, parent boxes (non-leaf, level in [lmin, lmax-1])
+  std::vector<int64_t> h_parents[FDA_MAXLEV];
+  fda::DBuf<int64_t> parents[FDA_MAXLEV];
+  int64_t m_off[FDA_MAXLEV] = {0};   // offset of M~(l, o, z) blocks in the M pool
+  // M2L
+  std::vector<fda::GemmUnit> h_units[FDA_MAXLEV][2];  // [level][0: dense or V^ stage, 1: U^ stage]
+  fda::DBuf<fda::GemmUnit> units[FDA_MAXLEV][2];
+  fda::DBuf<int64_t> pair_src, pair_tgt;  // coefficient indices (slot + wedge * s)
+  fda::DBuf<int64_t> pair_mid;            // low-rank intermediate index per pair (-1 if dense)
+  int64_t n_pairs = 0, n_mid = 0;
+  int64_t m2l_pairs[FDA_MAXLEV] = {0}, m2l_offsets[FDA_MAXLEV] = {0}, m2l_lowrank[FDA_MAXLEV] = {0};
+  // operators
+  fda::RunOps<double2> op64;
+  fda::RunOps<float2> op32;
+  // workspaces (sized for nrhs_max)
+  fda::DBuf<double2> xt64, yt64, cout64, cin64, mid64;
+  fda::DBuf<float2> xt32, yt32, cout32, cin32, mid32;
+  fda::DBuf<int64_t> iperm;
+  fda::DBuf<int> lev_s, lev_nw;  // per level: compressed dimension and wedge count
+  int max_leaf = 1;
+  double setup_ms[8] = {0};
+  double flops_m2l = 0, flops_m2m = 0, bytes_s2m_l2t = 0;
+  // GMRES workspace (allocated on first solve)
+  fda::DBuf<double2> gm_V, gm_w, gm_r, gm_x, gm_z, gm_b;
+  fda::DBuf<double> gm_small;
+};
+
+namespace fda {
+int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P);
+int plan_matvec(fda_plan_s* P, int prec, const void* x, void* y, int nrhs, int io_dtype, cudaStream_t s,
+                bool tree_order);
+}  // namespace fda

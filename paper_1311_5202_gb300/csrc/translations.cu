@@ -1,0 +1,1181 @@
+// Plan builder: translation operators of the FDA for the Burton-Miller kernels and the near field.
+//
+// Per level l carrying representations (Sec. 3.1.2):
+//   candidates (LF: cube surfaces, KIFMM style; HF: spheres around the box for the equivalent points and a
+//   cone of far check points for the canonical wedge (1,0,0), rotated to the other wedges),
+//   equivalent points b = columns and check points a = rows selected by pivoted QR of W G(X, Y),
+//   R = W G(a, b) = U Sigma V^H truncated at sigma_i >= eps sigma_1 (Eq. svdr, invr), s = rank.
+// Compressed operators (Eq. cmps..cmpt), with the Burton-Miller modifications of Sec. 3.2:
+//   S~ = Sigma^-1 U^H [W dG/dn_y(a, y_j)] diag(w_j)           (Eq. evas2mh: dipole check potentials)
+//   M~ = Sigma_l^-1 U_l^H [W G(a_l, b_{l+1})] V_{l+1},  L~ = M~^T (Eq. cmpl)
+//   K~ = V^T G(b_target, b_source) V                          (incoming check points = outgoing equivalents)
+//   T~ = [(G + alpha dG/dn_x)(x_i, a) W] conj(U) Sigma^-1       (Eq. eval2t)
+//   low rank: K~ = U^ V^ by rank-revealing QR when the rank is below s/2 (Eq. lrdk).
+// Near field: direct blocks K_H(x_i, y_j) w_j over the near leaf pairs and the correction matrix
+// C_ij = wbar_ij - [j != i] K_H(x_i, y_j) w_j of Eq. kcorrection, both in tree order.
+#include "plan.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <map>
+#include <tuple>
+#include <unordered_map>
+
+namespace fda {
+
+struct QRJob {
+  double2* A;
+  int m, n, lda, kmax;
+  double tol;
+  int* perm;
+  int* rank;
+  double2* rdiag;
+  double2* tau;
+  double* cn;
+};
+struct QFormJob {
+  const double2* A;
+  int m, lda, r;
+  const double2* tau;
+  double2* Q;
+  int ldq;
+};
+struct SVDJob {
+  double2* A;
+  int m, n, lda;
+  double2* V;
+  int ldv;
+  int* sweeps;
+};
+int pivoted_qr_batched(const std::vector<QRJob>& jobs, cudaStream_t s);
+int form_q_batched(const std::vector<QFormJob>& jobs, cudaStream_t s);
+int jacobi_svd_batched(const std::vector<SVDJob>& jobs, cudaStream_t s);
+
+// ------------------------------------------------------------------ candidate point sets (host)
+static void cube_surface(int p, double scale, std::vector<double>& out) {
+  for (int i = 0; i < p; ++i)
+    for (int j = 0; j < p; ++j)
+      for (int k = 0; k < p; ++k) {
+        if (i != 0 && i != p - 1 && j != 0 && j != p - 1 && k != 0 && k != p - 1) continue;
+        out.push_back(scale * (-1.0 + 2.0 * i / (p - 1)));
+        out.push_back(scale * (-1.0 + 2.0 * j / (p - 1)));
+        out.push_back(scale * (-1.0 + 2.0 * k / (p - 1)));
+      }
+}
+
+static void fib_sphere(int n, double r, std::vector<double>& out) {
+  for (int j = 0; j < n; ++j) {
+    double z = 1.0 - 2.0 * (j + 0.5) / n;
+    double ph = (j + 0.5) * FDA_PI * (3.0 - sqrt(5.0));
+    double s = sqrt(std::max(0.0, 1.0 - z * z));
+    out.push_back(r * s * cos(ph));
+    out.push_back(r * s * sin(ph));
+    out.push_back(r * z);
+  }
+}
+
+// unit directions in the cap of half-angle th around +x
+static void fib_cap_x(int n, double th, std::vector<double>& out) {
+  for (int j = 0; j < n; ++j) {
+    double c = 1.0 - (1.0 - cos(th)) * (j + 0.5) / n;
+    double ph = (j + 0.5) * FDA_PI * (3.0 - sqrt(5.0));
+    double s = sqrt(std::max(0.0, 1.0 - c * c));
+    out.push_back(c);
+    out.push_back(s * cos(ph));
+    out.push_back(s * sin(ph));
+  }
+}
+
+static void wedge_center(int n, int wid, double* d) {
+  int face = wid / (n * n), cell = wid % (n * n);
+  int a = face / 2, sg = face % 2;
+  int c1 = cell / n, c2 = cell % n;
+  int o1 = (a == 0) ? 1 : 0, o2 = (a == 2) ? 1 : 2;
+  d[a] = sg == 0 ? 1.0 : -1.0;
+  d[o1] = -1.0 + (2.0 * c1 + 1.0) / n;
+  d[o2] = -1.0 + (2.0 * c2 + 1.0) / n;
+  double l = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  for (int q = 0; q < 3; ++q) d[q] /= l;
+}
+
+// rotation taking e_x to d (Rodrigues); pi about e_z for d = -e_x
+static void rot_x_to(const double* d, double* R) {
+  double c = d[0];
+  if (c > 1 - 1e-15) {
+    double I[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    memcpy(R, I, sizeof(I));
+    return;
+  }
+  if (c < -1 + 1e-15) {
+    double Z[9] = {-1, 0, 0, 0, -1, 0, 0, 0, 1};
+    memcpy(R, Z, sizeof(Z));
+    return;
+  }
+  double ax[3] = {0, -d[2], d[1]};  // e_x x d
+  double sn = sqrt(ax[1] * ax[1] + ax[2] * ax[2]);
+  for (int q = 0; q < 3; ++q) ax[q] /= sn;
+  double K[9] = {0, -ax[2], ax[1], ax[2], 0, -ax[0], -ax[1], ax[0], 0};
+  double K2[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0;
+      for (int q = 0; q < 3; ++q) s += K[3 * i + q] * K[3 * q + j];
+      K2[3 * i + j] = s;
+    }
+  for (int q = 0; q < 9; ++q) R[q] = (q % 4 == 0 ? 1.0 : 0.0) + sn * K[q] + (1 - c) * K2[q];
+}
+
+static double cell_half_angle(int n) {
+  double best = 0;
+  for (int wid = 0; wid < n * n; ++wid) {
+    double c[3];
+    wedge_center(n, wid, c);
+    int c1 = wid / n, c2 = wid % n;
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) {
+        double q[3] = {1.0, -1.0 + 2.0 * (c1 + a) / n, -1.0 + 2.0 * (c2 + b) / n};
+        double l = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+        double d = (q[0] * c[0] + q[1] * c[1] + q[2] * c[2]) / l;
+        best = std::max(best, acos(std::min(1.0, d)));
+      }
+  }
+  return best;
+}
+
+// parent-level wedge z -> child-level wedge (nested face cells; 0 when the child level is LF)
+static int child_wedge(const LevelOps& Lp, const LevelOps& Lc, int z) {
+  if (!Lc.hf) return 0;
+  int n = Lp.n, nc = Lc.n;
+  int face = z / (n * n), cell = z % (n * n);
+  int c1 = cell / n, c2 = cell % n;
+  return face * nc * nc + (c1 / 2) * nc + (c2 / 2);
+}
+
+// ------------------------------------------------------------------ kernel-matrix generators
+struct PtSet {
+  const double* p;  // canonical points (count x 3)
+  const double* rot;  // 9 or nullptr
+  double c[3];      // centre shift
+};
+
+__device__ __forceinline__ void pt_get(const PtSet& S, int i, double* out) {
+  const double* q = S.p + 3 * i;
+  if (S.rot) {
+    const double* R = S.rot;
+    out[0] = R[0] * q[0] + R[1] * q[1] + R[2] * q[2] + S.c[0];
+    out[1] = R[3] * q[0] + R[4] * q[1] + R[5] * q[2] + S.c[1];
+    out[2] = R[6] * q[0] + R[7] * q[1] + R[8] * q[2] + S.c[2];
+  } else {
+    out[0] = q[0] + S.c[0];
+    out[1] = q[1] + S.c[1];
+    out[2] = q[2] + S.c[2];
+  }
+}
+
+__device__ __forceinline__ double2 greens(const double* x, const double* y, double k) {
+  double r0 = x[0] - y[0], r1 = x[1] - y[1], r2 = x[2] - y[2];
+  double R = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
+  double sn, cs;
+  sincos(k * R, &sn, &cs);
+  double g = 0.25 / FDA_PI / R;
+  return make_double2(g * cs, g * sn);
+}
+
+// out[i + j m] = W_i G(X_i, Y_j) for one batch item per blockIdx.y
+struct GJob {
+  PtSet X, Y;
+  const double* W;
+  int m, n;
+  double2* out;
+  int ld;
+};
+static __global__ void k_gen_G(const GJob* jobs, double k) {
+  const GJob J = jobs[blockIdx.y];
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)J.m * J.n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(q % J.m), j = (int)(q / J.m);
+    double x[3], y[3];
+    pt_get(J.X, i, x);
+    pt_get(J.Y, j, y);
+    double2 g = greens(x, y, k);
+    if (J.W) g = cscale(g, J.W[i]);
+    J.out[i + (int64_t)j * J.ld] = g;
+  }
+}
+
+static int gen_G(const std::vector<GJob>& jobs, double k) {
+  if (jobs.empty()) return FDA_OK;
+  DBuf<GJob> dj;
+  FDA_TRY(dj.upload(jobs));
+  for (size_t b0 = 0; b0 < jobs.size(); b0 += 65535) {
+    unsigned nb = (unsigned)std::min<size_t>(65535, jobs.size() - b0);
+    k_gen_G<<<dim3(64, nb), 256>>>(dj.p + b0, k);
+    FDA_LAUNCH_CHECK();
+  }
+  return FDA_OK;
+}
+
+// E_up (S2M) : out[i + j sc] = W_i dG/dn_y(c + R a_i, y_j) w_j, zero for j >= nC (pad to ncol)
+// E_dn (L2T) : out[j + i nrow] = (G + alpha dG/dn_x)(x_j, c + R a_i) W_i, zero rows j >= nC
+struct LeafJob {
+  PtSet A;      // check points around the leaf centre (rotated for the wedge)
+  const double* W;
+  int sc;
+  int64_t pbeg;  // first tree position of the leaf
+  int nC;
+  double2* out;
+};
+static __global__ void k_gen_leaf(const LeafJob* jobs, const double* xt, const double* nt, const double* wt,
+                                  double k, double2 alpha, int ncol, int mode) {
+  const LeafJob J = jobs[blockIdx.y];
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < J.sc * ncol; q += gridDim.x * blockDim.x) {
+    int i = q % J.sc, j = q / J.sc;
+    double2 v = make_double2(0, 0);
+    if (j < J.nC) {
+      double a[3];
+      pt_get(J.A, i, a);
+      int64_t p = J.pbeg + j;
+      const double* y = xt + 3 * p;
+      const double* ny = nt + 3 * p;
+      if (mode == 0) {
+        // dG/dn_y(a, y) with r = a - y
+        double dummy[3] = {0, 0, 0};
+        KernVals K = helmholtz4(a, dummy, y, ny, k);
+        v = cscale(K.Dy, J.W[i] * wt[p]);
+        J.out[i + (int64_t)j * J.sc] = v;
+      } else {
+        // (G + alpha dG/dn_x)(x, a) with r = x - a
+        double dummy[3] = {0, 0, 0};
+        KernVals K = helmholtz4(y, ny, a, dummy, k);
+        v = cscale(cadd(K.G, cmul(alpha, K.Dx)), J.W[i]);
+        J.out[j + (int64_t)i * ncol] = v;
+      }
+    } else {
+      if (mode == 0)
+        J.out[i + (int64_t)j * J.sc] = v;
+      else
+        J.out[j + (int64_t)i * ncol] = v;
+    }
+  }
+}
+
+// compact [ld x ncols] blocks to [rows x cols] (column-major) at the given offsets
+struct CopyJob {
+  const double2* src;
+  int ld, rows, cols;
+  double2* dst;
+};
+static __global__ void k_compact(const CopyJob* jobs) {
+  const CopyJob J = jobs[blockIdx.y];
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < J.rows * J.cols; q += gridDim.x * blockDim.x) {
+    int i = q % J.rows, j = q / J.rows;
+    J.dst[q] = J.src[i + (int64_t)j * J.ld];
+  }
+}
+
+static __global__ void k_conj_copy(const double2* a, double2* b, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = conjc(a[i]);
+}
+
+// V^ (r x s) from the pivoted-QR output: V^[:, perm[j]] = R[:, j], R upper trapezoidal
+static __global__ void k_build_vhat(const double2* A, int lda, const double2* rdiag, const int* perm, int r, int s,
+                                    double2* vh) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < r * s; q += gridDim.x * blockDim.x) {
+    int i = q % r, j = q / r;
+    double2 v = make_double2(0, 0);
+    if (j == i)
+      v = rdiag[i];
+    else if (j > i)
+      v = A[i + (int64_t)j * lda];
+    vh[i + (int64_t)perm[j] * r] = v;
+  }
+}
+
+// near blocks: one CTA per block, entries column-major (rows = target points)
+struct NearJob {
+  int64_t tb, te, sb, se;  // target / source tree-position ranges
+  int64_t off;
+};
+static __global__ void k_gen_near(const NearJob* jobs, const double* xt, const double* nt, const double* wt, double k,
+                                  double2 alpha, double2* out) {
+  const NearJob J = jobs[blockIdx.x];
+  int64_t nr = J.te - J.tb, nc = J.se - J.sb;
+  for (int64_t q = threadIdx.x; q < nr * nc; q += blockDim.x) {
+    int64_t i = J.tb + q % nr, j = J.sb + q / nr;
+    double2 v = make_double2(0, 0);
+    if (i != j) {
+      KernVals K = helmholtz4(xt + 3 * i, nt + 3 * i, xt + 3 * j, nt + 3 * j, k);
+      v = cscale(cadd(K.Dy, cmul(alpha, K.H)), wt[j]);
+    }
+    out[J.off + q] = v;
+  }
+}
+
+static __global__ void k_permute_geom(const double* x, const double* n, const double* w, const int64_t* perm,
+                                      int64_t N, double* xt, double* nt, double* wt, int64_t* iperm) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  int64_t i = perm[t];
+  for (int d = 0; d < 3; ++d) {
+    xt[3 * t + d] = x[3 * i + d];
+    nt[3 * t + d] = n[3 * i + d];
+  }
+  wt[t] = w[i];
+  iperm[i] = t;
+}
+
+// corrections to tree order
+static __global__ void k_corr_counts(const int64_t* perm, const int64_t* di_ptr, int64_t N, int64_t* cnt) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  int64_t i = perm[t];
+  cnt[t] = 6 * (di_ptr[i + 1] - di_ptr[i]);
+}
+static __global__ void k_corr_scatter(const int64_t* perm, const int64_t* iperm, const int64_t* di_ptr,
+                                      const int32_t* di_cols, const double2* corr, const int64_t* rowptr, int64_t N,
+                                      int32_t* col, double2* val) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  int64_t i = perm[t];
+  int64_t o = rowptr[t];
+  for (int64_t p = di_ptr[i]; p < di_ptr[i + 1]; ++p) {
+    int64_t e = di_cols[p];
+    for (int g = 0; g < 6; ++g) {
+      col[o] = (int32_t)iperm[6 * e + g];
+      val[o] = corr[6 * p + g];
+      ++o;
+    }
+  }
+}
+
+template <typename A, typename B>
+static __global__ void k_convert(const A* a, B* b, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = from_d<B>(to_d(a[i]));
+}
+
+template <typename C>
+static int to_fp32(const DBuf<double2>& a, DBuf<C>& b) {
+  FDA_TRY(b.alloc(a.n));
+  if (a.n) {
+    k_convert<double2, C><<<cdiv(a.n, 256), 256>>>(a.p, b.p, (int64_t)a.n);
+    FDA_LAUNCH_CHECK();
+  }
+  return FDA_OK;
+}
+
+static double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// ------------------------------------------------------------------ plan build
+int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
+  bm_problem_s* pr = T->prob;
+  const double k = pr->k, eps = cfg->eps;
+  const double2 alpha = pr->alpha;
+  P->tree = T;
+  P->prob = pr;
+  P->cfg = *cfg;
+  if (P->cfg.nrhs_max < 1) P->cfg.nrhs_max = 1;
+  FDA_TRY(upload_geometry_constants());
+  const int64_t N = T->N, nbox = T->nbox;
+  double t0 = now_ms();
+
+  // tree-order geometry
+  DBuf<double> xt, nt, wt;
+  FDA_TRY(xt.alloc(3 * N));
+  FDA_TRY(nt.alloc(3 * N));
+  FDA_TRY(wt.alloc(N));
+  FDA_TRY(P->iperm.alloc(N));
+  k_permute_geom<<<cdiv(N, 256), 256>>>(pr->x.p, pr->n.p, pr->w.p, T->perm.p, N, xt.p, nt.p, wt.p, P->iperm.p);
+  FDA_LAUNCH_CHECK();
+
+  // levels carrying representations
+  int lmin = FDA_MAXLEV, lmax = T->nlev - 1;
+  for (int64_t q = 0; q < T->nm2l; ++q) lmin = std::min(lmin, T->h_m2l_info[6 * q]);
+  const bool far = T->nm2l > 0;
+  if (!far) lmin = lmax + 1;
+  P->lmin = lmin;
+  P->lmax = lmax;
+  std::vector<int64_t> lb(T->nlev + 1, nbox);
+  for (int64_t b = nbox - 1; b >= 0; --b) lb[T->h_lev[b]] = b;
+  for (int l = T->nlev - 1; l >= 0; --l)
+    if (lb[l] == nbox) lb[l] = lb[l + 1];
+  std::vector<double> cen(3 * nbox);
+  for (int64_t b = 0; b < nbox; ++b) {
+    double w = ldexp(T->side, -T->h_lev[b]);
+    cen[3 * b] = T->corner[0] + w * (T->h_ix[b] + 0.5);
+    cen[3 * b + 1] = T->corner[1] + w * (T->h_iy[b] + 0.5);
+    cen[3 * b + 2] = T->corner[2] + w * (T->h_iz[b] + 0.5);
+  }
+
+  // ---- 1. point selection and SVD per level
+  struct Cand {
+    std::vector<double> Y, X, W;
+    DBuf<double> dY, dX, dW;
+    DBuf<double2> A, A2, R, V;
+    DBuf<int> perm, perm2, rank;
+    DBuf<double2> rd, tau, rd2, tau2;
+    DBuf<double> cn, cn2;
+    DBuf<int> sweeps;
+  };
+  std::vector<Cand> cand(FDA_MAXLEV);
+  std::vector<QRJob> qjobs;
+  std::vector<int> qlev;
+  const double lam = 2 * FDA_PI / k;
+  if (far) {
+    for (int l = lmin; l <= lmax; ++l) {
+      LevelOps& L = P->lev[l];
+      Cand& C = cand[l];
+      L.used = true;
+      L.hf = T->hf[l] != 0;
+      L.n = T->nw[l];
+      L.nw = L.hf ? 6 * L.n * L.n : 1;
+      L.w = ldexp(T->side, -l);
+      L.box_begin = lb[l];
+      L.box_end = lb[l + 1];
+      double h = 0.5 * L.w;
+      int p_ext = std::max(0, (int)ceil(2.0 * k * L.w / FDA_PI));  // resolve oscillation across the box
+      int pe = std::max(eps < 5e-6 ? 10 : 8, std::min(16, 6 + p_ext));
+      if (!L.hf) {
+        cube_surface(pe, 1.05 * h, C.Y);
+        cube_surface(std::max(5, pe - 3), 0.6 * h, C.Y);
+        cube_surface(pe + 2, 2.95 * h, C.X);
+        C.W.assign(C.X.size() / 3, 1.0);
+      } else {
+        double rad = 1.05 * sqrt(3.0) * h;
+        int ne = (int)(2.0 * (k * rad + 8) * (k * rad + 8));
+        fib_sphere(ne, rad, C.Y);
+        fib_sphere(std::max(50, ne / 3), 0.6 * rad, C.Y);
+        int Tl = T->T[l];
+        double th = cell_half_angle(L.n) + asin(sqrt(3.0) / (2.0 * (Tl + 2))) + 0.05;
+        th = std::min(th, FDA_PI);
+        double rmin = 0.98 * (Tl + 1.5) * L.w;
+        int nd = (int)(2.0 * (1 - cos(th)) / 2.0 * (k * rad + 8) * (k * rad + 8)) + 40;
+        std::vector<double> dirs;
+        fib_cap_x(nd, th, dirs);
+        const double radii[7] = {1, 1.3, 1.8, 2.6, 4, 8, 20};
+        for (double rr : radii)
+          for (int j = 0; j < nd; ++j) {
+            for (int d = 0; d < 3; ++d) C.X.push_back(rr * rmin * dirs[3 * j + d]);
+            C.W.push_back(rr * rmin / L.w);
+          }
+        L.rot.resize(9 * L.nw);
+        for (int z = 0; z < L.nw; ++z) {
+          double d[3];
+          wedge_center(L.n, z, d);
+          rot_x_to(d, &L.rot[9 * z]);
+        }
+      }
+      if (!L.hf) {
+        L.rot = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+      }
+      (void)lam;
+      int m = (int)(C.X.size() / 3), n = (int)(C.Y.size() / 3);
+      FDA_TRY(C.dY.upload(C.Y));
+      FDA_TRY(C.dX.upload(C.X));
+      FDA_TRY(C.dW.upload(C.W));
+      FDA_TRY(C.A.alloc((size_t)m * n));
+      FDA_TRY(C.perm.alloc(n));
+      FDA_TRY(C.rank.alloc(2));
+      FDA_TRY(C.rd.alloc(n));
+      FDA_TRY(C.tau.alloc(n));
+      FDA_TRY(C.cn.alloc(n));
+      GJob g;
+      g.X = {C.dX.p, nullptr, {0, 0, 0}};
+      g.Y = {C.dY.p, nullptr, {0, 0, 0}};
+      g.W = C.dW.p;
+      g.m = m;
+      g.n = n;
+      g.out = C.A.p;
+      g.ld = m;
+      FDA_TRY(gen_G({g}, k));
+      QRJob q;
+      q.A = C.A.p;
+      q.m = m;
+      q.n = n;
+      q.lda = m;
+      q.kmax = std::min(m, n);
+      q.tol = 0.1 * eps;
+      q.perm = C.perm.p;
+      q.rank = C.rank.p;
+      q.rdiag = C.rd.p;
+      q.tau = C.tau.p;
+      q.cn = C.cn.p;
+      qjobs.push_back(q);
+      qlev.push_back(l);
+    }
+    FDA_TRY(pivoted_qr_batched(qjobs, 0));
+    // selected equivalent points -> row selection on (W G(X, b))^H
+    std::vector<QRJob> qjobs2;
+    for (int l : qlev) {
+      LevelOps& L = P->lev[l];
+      Cand& C = cand[l];
+      int rk = 0;
+      FDA_CUDA(cudaMemcpy(&rk, C.rank.p, sizeof(int), cudaMemcpyDeviceToHost));
+      std::vector<int> pm;
+      FDA_TRY(C.perm.download(pm));
+      L.se = rk;
+      L.b.resize(3 * rk);
+      for (int j = 0; j < rk; ++j)
+        for (int d = 0; d < 3; ++d) L.b[3 * j + d] = C.Y[3 * pm[j] + d];
+      FDA_TRY(L.d_b.upload(L.b));
+      int m = (int)(C.X.size() / 3);
+      // A2 = (W G(X, b))^H  : rk x m  -> generate G(b, X) W (rows b) then conj
+      FDA_TRY(C.A2.alloc((size_t)rk * m));
+      GJob g;
+      g.X = {L.d_b.p, nullptr, {0, 0, 0}};
+      g.Y = {C.dX.p, nullptr, {0, 0, 0}};
+      g.W = nullptr;
+      g.m = rk;
+      g.n = m;
+      g.out = C.A2.p;
+      g.ld = rk;
+      FDA_TRY(gen_G({g}, k));
+      // scale column j by W_j and conjugate: (W G(X,b))^H [j-th col] = conj(W_j G(b, X_j))
+      {
+        std::vector<double2> dummy;
+        (void)dummy;
+      }
+      FDA_TRY(C.perm2.alloc(m));
+      FDA_TRY(C.rd2.alloc(m));
+      FDA_TRY(C.tau2.alloc(m));
+      FDA_TRY(C.cn2.alloc(m));
+      QRJob q;
+      q.A = C.A2.p;
+      q.m = rk;
+      q.n = m;
+      q.lda = rk;
+      q.kmax = std::min(rk, m);
+      q.tol = 0.1 * eps;
+      q.perm = C.perm2.p;
+      q.rank = C.rank.p + 1;
+      q.rdiag = C.rd2.p;
+      q.tau = C.tau2.p;
+      q.cn = C.cn2.p;
+      qjobs2.push_back(q);
+    }
+    // weights on the columns of the transposed problem: multiply column j by W_j (conjugation does not
+    // change pivoting or norms)
+    for (size_t q = 0; q < qlev.size(); ++q) {
+      Cand& C = cand[qlev[q]];
+      int rk = qjobs2[q].m, m = qjobs2[q].n;
+      std::vector<double2> h((size_t)rk * m);
+      FDA_CUDA(cudaMemcpy(h.data(), C.A2.p, h.size() * sizeof(double2), cudaMemcpyDeviceToHost));
+      for (int j = 0; j < m; ++j)
+        for (int i = 0; i < rk; ++i) h[i + (size_t)j * rk] = cscale(h[i + (size_t)j * rk], C.W[j]);
+      FDA_CUDA(cudaMemcpy(C.A2.p, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    }
+    FDA_TRY(pivoted_qr_batched(qjobs2, 0));
+    // R = W_a G(a, b) and its SVD
+    std::vector<SVDJob> sjobs;
+    for (size_t q = 0; q < qlev.size(); ++q) {
+      int l = qlev[q];
+      LevelOps& L = P->lev[l];
+      Cand& C = cand[l];
+      int rk2 = 0;
+      FDA_CUDA(cudaMemcpy(&rk2, C.rank.p + 1, sizeof(int), cudaMemcpyDeviceToHost));
+      std::vector<int> pm;
+      FDA_TRY(C.perm2.download(pm));
+      L.sc = rk2;
+      L.a.resize(3 * rk2);
+      L.Wa.resize(rk2);
+      for (int i = 0; i < rk2; ++i) {
+        for (int d = 0; d < 3; ++d) L.a[3 * i + d] = C.X[3 * pm[i] + d];
+        L.Wa[i] = C.W[pm[i]];
+      }
+      FDA_TRY(L.d_a.upload(L.a));
+      FDA_TRY(L.d_Wa.upload(L.Wa));
+      FDA_TRY(L.d_rot.upload(L.rot));
+      FDA_TRY(C.R.alloc((size_t)L.sc * L.se));
+      FDA_TRY(C.V.alloc((size_t)L.se * L.se));
+      FDA_TRY(C.sweeps.alloc(1));
+      GJob g;
+      g.X = {L.d_a.p, nullptr, {0, 0, 0}};
+      g.Y = {L.d_b.p, nullptr, {0, 0, 0}};
+      g.W = L.d_Wa.p;
+      g.m = L.sc;
+      g.n = L.se;
+      g.out = C.R.p;
+      g.ld = L.sc;
+      FDA_TRY(gen_G({g}, k));
+      SVDJob sj;
+      sj.A = C.R.p;
+      sj.m = L.sc;
+      sj.n = L.se;
+      sj.lda = L.sc;
+      sj.V = C.V.p;
+      sj.ldv = L.se;
+      sj.sweeps = C.sweeps.p;
+      sjobs.push_back(sj);
+    }
+    FDA_TRY(jacobi_svd_batched(sjobs, 0));
+    for (size_t q = 0; q < qlev.size(); ++q) {
+      int l = qlev[q];
+      LevelOps& L = P->lev[l];
+      Cand& C = cand[l];
+      std::vector<double2> hR, hV;
+      FDA_TRY(C.R.download(hR));
+      FDA_TRY(C.V.download(hV));
+      std::vector<double> sg(L.se);
+      for (int j = 0; j < L.se; ++j) {
+        double s2 = 0;
+        for (int i = 0; i < L.sc; ++i) s2 += cabs2(hR[i + (size_t)j * L.sc]);
+        sg[j] = sqrt(s2);
+      }
+      std::vector<int> ord(L.se);
+      for (int j = 0; j < L.se; ++j) ord[j] = j;
+      std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return sg[a] > sg[b]; });
+      double s1 = sg[ord[0]];
+      int s = 0;
+      while (s < L.se && s < L.sc && sg[ord[s]] >= eps * s1) ++s;
+      L.s = s;
+      L.sigma.resize(s);
+      std::vector<double2> Ph((size_t)L.sc * s), Pch((size_t)L.sc * s), Vh((size_t)L.se * s);
+      for (int c = 0; c < s; ++c) {
+        int j = ord[c];
+        double sj = sg[j];
+        L.sigma[c] = sj;
+        for (int i = 0; i < L.sc; ++i) {
+          double2 u = cscale(hR[i + (size_t)j * L.sc], 1.0 / sj);  // u_c
+          Ph[i + (size_t)c * L.sc] = cscale(u, 1.0 / sj);            // U Sigma^-1
+          Pch[i + (size_t)c * L.sc] = conjc(Ph[i + (size_t)c * L.sc]);
+        }
+        for (int i = 0; i < L.se; ++i) Vh[i + (size_t)c * L.se] = hV[i + (size_t)j * L.se];
+      }
+      FDA_TRY(L.P.upload(Ph));
+      FDA_TRY(L.Pc.upload(Pch));
+      FDA_TRY(L.V.upload(Vh));
+    }
+  }
+  double t1 = now_ms();
+  P->setup_ms[0] = t1 - t0;
+
+  // ---- 2. coefficient slots
+  P->h_slot.assign(nbox, -1);
+  int64_t off = 0;
+  if (far)
+    for (int64_t b = lb[lmin]; b < nbox; ++b) {
+      const LevelOps& L = P->lev[T->h_lev[b]];
+      P->h_slot[b] = off;
+      off += (int64_t)L.nw * L.s;
+    }
+  P->n_coef = off;
+  FDA_TRY(P->slot.upload(P->h_slot));
+
+  // ---- 3. leaf operators S~ and T~
+  std::vector<int64_t> s_off, t_off;
+  int64_t s_tot = 0, t_tot = 0;
+  if (far) {
+    for (int64_t b = lb[lmin]; b < nbox; ++b)
+      if (T->h_leaf[b]) P->h_leaves.push_back(b);
+    s_off.resize(P->h_leaves.size());
+    t_off.resize(P->h_leaves.size());
+    for (size_t q = 0; q < P->h_leaves.size(); ++q) {
+      int64_t b = P->h_leaves[q];
+      const LevelOps& L = P->lev[T->h_lev[b]];
+      int64_t nC = T->h_pe[b] - T->h_pb[b];
+      s_off[q] = s_tot;
+      t_off[q] = t_tot;
+      s_tot += (int64_t)L.nw * L.s * nC;
+      t_tot += (int64_t)L.nw * L.s * nC;
+      P->bytes_s2m_l2t += 2.0 * L.nw * L.s * nC * 16.0;
+    }
+  }
+  FDA_TRY(P->leaves.upload(P->h_leaves));
+  FDA_TRY(P->leaf_s_off.upload(s_off));
+  FDA_TRY(P->leaf_t_off.upload(t_off));
+  FDA_TRY(P->op64.S.alloc(std::max<int64_t>(s_tot, 1)));
+  FDA_TRY(P->op64.T.alloc(std::max<int64_t>(t_tot, 1)));
+  if (far) {
+    // batches per level and wedge
+    for (int l = lmin; l <= lmax; ++l) {
+      LevelOps& L = P->lev[l];
+      std::vector<size_t> items;
+      int ncol = 1;
+      for (size_t q = 0; q < P->h_leaves.size(); ++q)
+        if (T->h_lev[P->h_leaves[q]] == l) {
+          items.push_back(q);
+          ncol = std::max<int>(ncol, (int)(T->h_pe[P->h_leaves[q]] - T->h_pb[P->h_leaves[q]]));
+        }
+      if (items.empty()) continue;
+      const int64_t BATCH = 2048;
+      DBuf<double2> E, Out;
+      FDA_TRY(E.alloc((size_t)BATCH * L.sc * ncol));
+      FDA_TRY(Out.alloc((size_t)BATCH * L.s * ncol));
+      for (int mode = 0; mode < 2; ++mode)
+        for (size_t i0 = 0; i0 < items.size() * L.nw; i0 += BATCH) {
+          size_t nb = std::min<size_t>(BATCH, items.size() * L.nw - i0);
+          std::vector<LeafJob> lj(nb);
+          std::vector<const double2*> Ap(nb), Bp(nb);
+          std::vector<double2*> Cp(nb);
+          std::vector<CopyJob> cj(nb);
+          for (size_t u = 0; u < nb; ++u) {
+            size_t it = (i0 + u) / L.nw;
+            int z = (int)((i0 + u) % L.nw);
+            int64_t b = P->h_leaves[items[it]];
+            LeafJob& J = lj[u];
+            J.A.p = L.d_a.p;
+            J.A.rot = L.d_rot.p + 9 * z;
+            for (int d = 0; d < 3; ++d) J.A.c[d] = cen[3 * b + d];
+            J.W = L.d_Wa.p;
+            J.sc = L.sc;
+            J.pbeg = T->h_pb[b];
+            J.nC = (int)(T->h_pe[b] - T->h_pb[b]);
+            J.out = E.p + u * (size_t)L.sc * ncol;
+            Cp[u] = Out.p + u * (size_t)L.s * ncol;
+            if (mode == 0) {
+              Ap[u] = L.P.p;   // op C
+              Bp[u] = J.out;   // sc x ncol
+            } else {
+              Ap[u] = J.out;   // ncol x sc
+              Bp[u] = L.Pc.p;  // sc x s
+            }
+            int64_t nC = J.nC;
+            if (mode == 0)
+              cj[u] = {Cp[u], L.s, L.s, (int)nC, P->op64.S.p + s_off[items[it]] + (int64_t)z * L.s * nC};
+            else
+              cj[u] = {Cp[u], ncol, (int)nC, L.s, P->op64.T.p + t_off[items[it]] + (int64_t)z * L.s * nC};
+          }
+          DBuf<LeafJob> dlj;
+          FDA_TRY(dlj.upload(lj));
+          k_gen_leaf<<<dim3(16, (unsigned)nb), 256>>>(dlj.p, xt.p, nt.p, wt.p, k, alpha, ncol, mode);
+          FDA_LAUNCH_CHECK();
+          DBuf<const double2*> dA, dB;
+          DBuf<double2*> dC;
+          FDA_TRY(dA.upload(Ap));
+          FDA_TRY(dB.upload(Bp));
+          FDA_TRY(dC.upload(Cp));
+          if (mode == 0)
+            FDA_TRY(zgemm_batched('C', 'N', L.s, ncol, L.sc, make_double2(1, 0), dA.p, L.sc, dB.p, L.sc,
+                                  make_double2(0, 0), dC.p, L.s, nb, 0));
+          else
+            FDA_TRY(zgemm_batched('N', 'N', ncol, L.s, L.sc, make_double2(1, 0), dA.p, ncol, dB.p, L.sc,
+                                  make_double2(0, 0), dC.p, ncol, nb, 0));
+          DBuf<CopyJob> dcj;
+          FDA_TRY(dcj.upload(cj));
+          k_compact<<<dim3(8, (unsigned)nb), 256>>>(dcj.p);
+          FDA_LAUNCH_CHECK();
+          FDA_CUDA(cudaDeviceSynchronize());
+        }
+    }
+  }
+  double t2 = now_ms();
+  P->setup_ms[2] = t2 - t1;
+
+  // ---- 4. M~ per (level, octant, wedge)
+  int64_t m_tot = 0;
+  for (int l = lmin; l < lmax; ++l) {
+    P->m_off[l] = m_tot;
+    m_tot += 8LL * P->lev[l].nw * P->lev[l].s * P->lev[l + 1].s;
+  }
+  FDA_TRY(P->op64.M.alloc(std::max<int64_t>(m_tot, 1)));
+  for (int l = lmin; l < lmax && far; ++l) {
+    LevelOps& L = P->lev[l];
+    LevelOps& Lc = P->lev[l + 1];
+    for (int64_t b = L.box_begin; b < L.box_end; ++b)
+      if (!T->h_leaf[b]) P->h_parents[l].push_back(b);
+    FDA_TRY(P->parents[l].upload(P->h_parents[l]));
+    int nitem = 8 * L.nw;
+    const int BATCH = 256;
+    DBuf<double2> G, S1;
+    FDA_TRY(G.alloc((size_t)BATCH * L.sc * Lc.se));
+    FDA_TRY(S1.alloc((size_t)BATCH * L.s * Lc.se));
+    for (int i0 = 0; i0 < nitem; i0 += BATCH) {
+      int nb = std::min(BATCH, nitem - i0);
+      std::vector<GJob> gj(nb);
+      std::vector<const double2*> A1(nb), B1(nb), A2(nb), B2(nb);
+      std::vector<double2*> C1(nb), C2(nb);
+      for (int u = 0; u < nb; ++u) {
+        int o = (i0 + u) / L.nw, z = (i0 + u) % L.nw;
+        int zc = child_wedge(L, Lc, z);
+        double dl[3] = {(((o >> 2) & 1) - 0.5) * 0.5 * L.w, (((o >> 1) & 1) - 0.5) * 0.5 * L.w,
+                        ((o & 1) - 0.5) * 0.5 * L.w};
+        GJob& g = gj[u];
+        g.X = {L.d_a.p, L.d_rot.p + 9 * z, {0, 0, 0}};
+        g.Y = {Lc.d_b.p, Lc.d_rot.p + 9 * zc, {dl[0], dl[1], dl[2]}};
+        g.W = L.d_Wa.p;
+        g.m = L.sc;
+        g.n = Lc.se;
+        g.out = G.p + (size_t)u * L.sc * Lc.se;
+        g.ld = L.sc;
+        A1[u] = L.P.p;
+        B1[u] = g.out;
+        C1[u] = S1.p + (size_t)u * L.s * Lc.se;
+        A2[u] = C1[u];
+        B2[u] = Lc.V.p;
+        C2[u] = P->op64.M.p + P->m_off[l] + (int64_t)(o * L.nw + z) * L.s * Lc.s;
+      }
+      FDA_TRY(gen_G(gj, k));
+      DBuf<const double2*> dA1, dB1, dA2, dB2;
+      DBuf<double2*> dC1, dC2;
+      FDA_TRY(dA1.upload(A1));
+      FDA_TRY(dB1.upload(B1));
+      FDA_TRY(dC1.upload(C1));
+      FDA_TRY(dA2.upload(A2));
+      FDA_TRY(dB2.upload(B2));
+      FDA_TRY(dC2.upload(C2));
+      FDA_TRY(zgemm_batched('C', 'N', L.s, Lc.se, L.sc, make_double2(1, 0), dA1.p, L.sc, dB1.p, L.sc,
+                            make_double2(0, 0), dC1.p, L.s, nb, 0));
+      FDA_TRY(zgemm_batched('N', 'N', L.s, Lc.s, Lc.se, make_double2(1, 0), dA2.p, L.s, dB2.p, Lc.se,
+                            make_double2(0, 0), dC2.p, L.s, nb, 0));
+      FDA_CUDA(cudaDeviceSynchronize());
+    }
+    // algorithmic flops: M2M + L2L, every parent box x wedge x child
+    for (int64_t b : P->h_parents[l]) P->flops_m2m += 2.0 * 8.0 * L.nw * T->h_nch[b] * (double)L.s * Lc.s;
+  }
+  double t3 = now_ms();
+  P->setup_ms[3] = t3 - t2;
+
+  // ---- 5. K~ per (level, offset); M2L schedule
+  struct OffInfo {
+    int32_t dx, dy, dz, wo, wi;
+    int64_t count;
+    int64_t k_off;   // dense K~ offset, or -1
+    int64_t u_off, v_off;  // low-rank U^, V^ offsets
+    int rank;
+  };
+  std::vector<std::vector<OffInfo>> offs(FDA_MAXLEV);
+  std::vector<int32_t> pair_off(T->nm2l);
+  for (int l = 0; l < FDA_MAXLEV; ++l) {
+    std::map<std::tuple<int, int, int>, int> idx;
+    for (int64_t q = 0; q < T->nm2l; ++q) {
+      const int32_t* inf = &T->h_m2l_info[6 * q];
+      if (inf[0] != l) continue;
+      auto key = std::make_tuple(inf[1], inf[2], inf[3]);
+      auto it = idx.find(key);
+      int id;
+      if (it == idx.end()) {
+        id = (int)offs[l].size();
+        idx[key] = id;
+        offs[l].push_back({inf[1], inf[2], inf[3], inf[4], inf[5], 0, -1, -1, -1, 0});
+      } else {
+        id = it->second;
+      }
+      offs[l][id].count++;
+      pair_off[q] = id;
+      P->m2l_pairs[l]++;
+    }
+    P->m2l_offsets[l] = (int64_t)offs[l].size();
+  }
+  int64_t k_tot = 0;
+  for (int l = lmin; l <= lmax && far; ++l)
+    for (auto& o : offs[l]) {
+      o.k_off = k_tot;
+      k_tot += (int64_t)P->lev[l].s * P->lev[l].s;
+    }
+  FDA_TRY(P->op64.K.alloc(std::max<int64_t>(k_tot, 1)));
+  for (int l = lmin; l <= lmax && far; ++l) {
+    LevelOps& L = P->lev[l];
+    int no = (int)offs[l].size();
+    if (!no) continue;
+    const int BATCH = 128;
+    DBuf<double2> G, T1;
+    FDA_TRY(G.alloc((size_t)BATCH * L.se * L.se));
+    FDA_TRY(T1.alloc((size_t)BATCH * L.se * L.s));
+    for (int i0 = 0; i0 < no; i0 += BATCH) {
+      int nb = std::min(BATCH, no - i0);
+      std::vector<GJob> gj(nb);
+      std::vector<const double2*> A1(nb), B1(nb), A2(nb), B2(nb);
+      std::vector<double2*> C1(nb), C2(nb);
+      for (int u = 0; u < nb; ++u) {
+        const OffInfo& o = offs[l][i0 + u];
+        GJob& g = gj[u];
+        g.X = {L.d_b.p, L.d_rot.p + 9 * (L.hf ? o.wi : 0), {0, 0, 0}};
+        g.Y = {L.d_b.p, L.d_rot.p + 9 * (L.hf ? o.wo : 0), {o.dx * L.w, o.dy * L.w, o.dz * L.w}};
+        g.W = nullptr;
+        g.m = L.se;
+        g.n = L.se;
+        g.out = G.p + (size_t)u * L.se * L.se;
+        g.ld = L.se;
+        A1[u] = g.out;
+        B1[u] = L.V.p;
+        C1[u] = T1.p + (size_t)u * L.se * L.s;
+        A2[u] = L.V.p;
+        B2[u] = C1[u];
+        C2[u] = P->op64.K.p + o.k_off;
+      }
+      FDA_TRY(gen_G(gj, k));
+      DBuf<const double2*> dA1, dB1, dA2, dB2;
+      DBuf<double2*> dC1, dC2;
+      FDA_TRY(dA1.upload(A1));
+      FDA_TRY(dB1.upload(B1));
+      FDA_TRY(dC1.upload(C1));
+      FDA_TRY(dA2.upload(A2));
+      FDA_TRY(dB2.upload(B2));
+      FDA_TRY(dC2.upload(C2));
+      FDA_TRY(zgemm_batched('N', 'N', L.se, L.s, L.se, make_double2(1, 0), dA1.p, L.se, dB1.p, L.se,
+                            make_double2(0, 0), dC1.p, L.se, nb, 0));
+      FDA_TRY(zgemm_batched('T', 'N', L.s, L.s, L.se, make_double2(1, 0), dA2.p, L.se, dB2.p, L.se,
+                            make_double2(0, 0), dC2.p, L.s, nb, 0));
+      FDA_CUDA(cudaDeviceSynchronize());
+    }
+  }
+  double t4 = now_ms();
+  P->setup_ms[4] = t4 - t3;
+
+  // ---- 6. low-rank factors of K~ (Sec. 4.2)
+  int64_t lr_tot = 0;
+  if (cfg->lowrank && far) {
+    for (int l = lmin; l <= lmax; ++l) {
+      LevelOps& L = P->lev[l];
+      int no = (int)offs[l].size();
+      if (!no || L.s < 4) continue;
+      const int BATCH = 512;
+      int kmax = (L.s + 1) / 2;
+      DBuf<double2> W, rd, tau;
+      DBuf<int> perm, rank;
+      DBuf<double> cn;
+      FDA_TRY(W.alloc((size_t)BATCH * L.s * L.s));
+      FDA_TRY(rd.alloc((size_t)BATCH * kmax));
+      FDA_TRY(tau.alloc((size_t)BATCH * kmax));
+      FDA_TRY(perm.alloc((size_t)BATCH * L.s));
+      FDA_TRY(rank.alloc(BATCH));
+      FDA_TRY(cn.alloc((size_t)BATCH * L.s));
+      for (int i0 = 0; i0 < no; i0 += BATCH) {
+        int nb = std::min(BATCH, no - i0);
+        std::vector<QRJob> qj(nb);
+        for (int u = 0; u < nb; ++u) {
+          FDA_CUDA(cudaMemcpy(W.p + (size_t)u * L.s * L.s, P->op64.K.p + offs[l][i0 + u].k_off,
+                              sizeof(double2) * L.s * L.s, cudaMemcpyDeviceToDevice));
+          QRJob& q = qj[u];
+          q.A = W.p + (size_t)u * L.s * L.s;
+          q.m = L.s;
+          q.n = L.s;
+          q.lda = L.s;
+          q.kmax = kmax;
+          q.tol = 0.5 * eps;
+          q.perm = perm.p + (size_t)u * L.s;
+          q.rank = rank.p + u;
+          q.rdiag = rd.p + (size_t)u * kmax;
+          q.tau = tau.p + (size_t)u * kmax;
+          q.cn = cn.p + (size_t)u * L.s;
+        }
+        FDA_TRY(pivoted_qr_batched(qj, 0));
+        std::vector<int> rk(nb);
+        FDA_CUDA(cudaMemcpy(rk.data(), rank.p, sizeof(int) * nb, cudaMemcpyDeviceToHost));
+        // allocate low-rank storage (grow pool)
+        std::vector<QFormJob> fj;
+        std::vector<std::pair<int, int>> which;
+        int64_t need = 0;
+        for (int u = 0; u < nb; ++u)
+          if (2 * rk[u] < L.s) need += 2LL * rk[u] * L.s;
+        if (need) {
+          DBuf<double2>& pool = P->op64.lr;
+          size_t newn = lr_tot + need;
+          if (newn > pool.n) {
+            double2* np = nullptr;
+            size_t cap = std::max(newn, 2 * pool.n);
+            if (cudaMalloc((void**)&np, cap * sizeof(double2)) != cudaSuccess) {
+              set_error("low-rank pool allocation failed");
+              return FDA_E_OOM;
+            }
+            if (lr_tot) FDA_CUDA(cudaMemcpy(np, pool.p, lr_tot * sizeof(double2), cudaMemcpyDeviceToDevice));
+            pool.release();
+            pool.p = np;
+            pool.n = cap;
+          }
+        }
+        for (int u = 0; u < nb; ++u) {
+          OffInfo& o = offs[l][i0 + u];
+          if (!(2 * rk[u] < L.s) || rk[u] < 1) continue;
+          o.rank = rk[u];
+          o.u_off = lr_tot;
+          o.v_off = lr_tot + (int64_t)rk[u] * L.s;
+          lr_tot += 2LL * rk[u] * L.s;
+          QFormJob f;
+          f.A = W.p + (size_t)u * L.s * L.s;
+          f.m = L.s;
+          f.lda = L.s;
+          f.r = rk[u];
+          f.tau = tau.p + (size_t)u * kmax;
+          f.Q = P->op64.lr.p + o.u_off;
+          f.ldq = L.s;
+          fj.push_back(f);
+          k_build_vhat<<<32, 256>>>(W.p + (size_t)u * L.s * L.s, L.s, rd.p + (size_t)u * kmax,
+                                    perm.p + (size_t)u * L.s, rk[u], L.s, P->op64.lr.p + o.v_off);
+          FDA_LAUNCH_CHECK();
+          P->m2l_lowrank[l]++;
+        }
+        FDA_TRY(form_q_batched(fj, 0));
+      }
+    }
+  }
+  double t5 = now_ms();
+  P->setup_ms[5] = t5 - t4;
+
+  // M2L pairs grouped by (level, offset) and units
+  {
+    std::vector<int64_t> order(T->nm2l);
+    for (int64_t q = 0; q < T->nm2l; ++q) order[q] = q;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+      int la = T->h_m2l_info[6 * a], lb2 = T->h_m2l_info[6 * b];
+      if (la != lb2) return la < lb2;
+      return pair_off[a] < pair_off[b];
+    });
+    std::vector<int64_t> ps(T->nm2l), pt(T->nm2l), pm(T->nm2l, -1);
+    int64_t mid = 0;
+    for (int64_t u = 0; u < T->nm2l; ++u) {
+      int64_t q = order[u];
+      const int32_t* inf = &T->h_m2l_info[6 * q];
+      int l = inf[0];
+      const LevelOps& L = P->lev[l];
+      int64_t tb = T->h_m2l_box[2 * q], sb = T->h_m2l_box[2 * q + 1];
+      ps[u] = P->h_slot[sb] + (int64_t)(L.hf ? inf[4] : 0) * L.s;
+      pt[u] = P->h_slot[tb] + (int64_t)(L.hf ? inf[5] : 0) * L.s;
+      const OffInfo& o = offs[l][pair_off[q]];
+      if (o.rank > 0) {
+        pm[u] = mid;
+        mid += o.rank;
+      }
+      double fl = o.rank > 0 ? 16.0 * o.rank * L.s : 8.0 * L.s * L.s;
+      P->flops_m2l += fl;
+    }
+    P->n_pairs = T->nm2l;
+    P->n_mid = mid;
+    FDA_TRY(P->pair_src.upload(ps));
+    FDA_TRY(P->pair_tgt.upload(pt));
+    FDA_TRY(P->pair_mid.upload(pm));
+    int64_t u = 0;
+    const int CP = 32, TM = 64;
+    while (u < T->nm2l) {
+      int64_t q = order[u];
+      int l = T->h_m2l_info[6 * q];
+      int id = pair_off[q];
+      int64_t v = u;
+      while (v < T->nm2l && T->h_m2l_info[6 * order[v]] == l && pair_off[order[v]] == id) ++v;
+      const OffInfo& o = offs[l][id];
+      const LevelOps& L = P->lev[l];
+      for (int64_t p0 = u; p0 < v; p0 += CP) {
+        int pc = (int)std::min<int64_t>(CP, v - p0);
+        if (o.rank > 0) {
+          for (int m0 = 0; m0 < o.rank; m0 += TM)
+            P->h_units[l][0].push_back({o.v_off, o.rank, L.s, p0, pc, m0, 1, 0});
+          for (int m0 = 0; m0 < L.s; m0 += TM)
+            P->h_units[l][1].push_back({o.u_off, L.s, o.rank, p0, pc, m0, 2, 0});
+        } else {
+          for (int m0 = 0; m0 < L.s; m0 += TM) P->h_units[l][0].push_back({o.k_off, L.s, L.s, p0, pc, m0, 0, 0});
+        }
+      }
+      u = v;
+    }
+    for (int l = 0; l < FDA_MAXLEV; ++l)
+      for (int st = 0; st < 2; ++st) FDA_TRY(P->units[l][st].upload(P->h_units[l][st]));
+  }
+
+  // ---- 7. near field: corrections (Eq. kcorrection) and direct blocks
+  {
+    DBuf<int64_t> di_ptr;
+    DBuf<int32_t> di_cols;
+    DBuf<double2> corr;
+    double ms = 0;
+    FDA_TRY(near_corrections(pr, di_ptr, di_cols, corr, &ms));
+    P->setup_ms[6] = ms;
+    DBuf<int64_t> cnt;
+    FDA_TRY(cnt.alloc(N));
+    k_corr_counts<<<cdiv(N, 256), 256>>>(T->perm.p, di_ptr.p, N, cnt.p);
+    FDA_LAUNCH_CHECK();
+    FDA_TRY(P->corr_ptr.alloc(N + 1));
+    int64_t tot = 0;
+    FDA_TRY(exclusive_scan_i64(cnt.p, P->corr_ptr.p, N, &tot, 0));
+    FDA_CUDA(cudaMemcpy(P->corr_ptr.p + N, &tot, sizeof(int64_t), cudaMemcpyHostToDevice));
+    P->corr_entries = tot;
+    FDA_TRY(P->corr_col.alloc(std::max<int64_t>(tot, 1)));
+    FDA_TRY(P->op64.corr.alloc(std::max<int64_t>(tot, 1)));
+    k_corr_scatter<<<cdiv(N, 256), 256>>>(T->perm.p, P->iperm.p, di_ptr.p, di_cols.p, corr.p, P->corr_ptr.p, N,
+                                          P->corr_col.p, P->op64.corr.p);
+    FDA_LAUNCH_CHECK();
+    FDA_CUDA(cudaDeviceSynchronize());
+  }
+  double t6 = now_ms();
+  {
+    // expand direct pairs to leaf targets; group by target leaf
+    std::vector<std::pair<int64_t, int64_t>> blocks;
+    for (int64_t q = 0; q < T->ndir; ++q) {
+      int64_t Pb = T->h_direct[2 * q], Qb = T->h_direct[2 * q + 1];
+      if (T->h_leaf[Pb]) {
+        blocks.push_back({Pb, Qb});
+      } else {
+        std::vector<int64_t> st{Pb};
+        while (!st.empty()) {
+          int64_t b = st.back();
+          st.pop_back();
+          if (T->h_leaf[b])
+            blocks.push_back({b, Qb});
+          else
+            for (int c = T->h_nch[b] - 1; c >= 0; --c) st.push_back(T->h_cbeg[b] + c);
+        }
+      }
+    }
+    std::sort(blocks.begin(), blocks.end());
+    std::vector<int64_t> tleaf, tptr, src, boff;
+    std::vector<NearJob> jobs;
+    int64_t eoff = 0;
+    for (size_t q = 0; q < blocks.size(); ++q) {
+      if (q == 0 || blocks[q].first != blocks[q - 1].first) {
+        tleaf.push_back(blocks[q].first);
+        tptr.push_back((int64_t)q);
+      }
+      int64_t L = blocks[q].first, Q = blocks[q].second;
+      src.push_back(Q);
+      boff.push_back(eoff);
+      jobs.push_back({T->h_pb[L], T->h_pe[L], T->h_pb[Q], T->h_pe[Q], eoff});
+      eoff += (T->h_pe[L] - T->h_pb[L]) * (T->h_pe[Q] - T->h_pb[Q]);
+    }
+    tptr.push_back((int64_t)blocks.size());
+    P->n_near_tleaf = (int64_t)tleaf.size();
+    P->n_blocks = (int64_t)blocks.size();
+    P->near_entries = eoff;
+    FDA_TRY(P->near_tleaf.upload(tleaf));
+    FDA_TRY(P->near_tptr.upload(tptr));
+    FDA_TRY(P->near_src.upload(src));
+    FDA_TRY(P->near_off.upload(boff));
+    FDA_TRY(P->op64.near.alloc(std::max<int64_t>(eoff, 1)));
+    DBuf<NearJob> dj;
+    FDA_TRY(dj.upload(jobs));
+    for (size_t b0 = 0; b0 < jobs.size(); b0 += 65535) {
+      unsigned nb = (unsigned)std::min<size_t>(65535, jobs.size() - b0);
+      k_gen_near<<<nb, 256>>>(dj.p + b0, xt.p, nt.p, wt.p, k, alpha, P->op64.near.p);
+      FDA_LAUNCH_CHECK();
+    }
+    FDA_CUDA(cudaDeviceSynchronize());
+  }
+  double t7 = now_ms();
+  P->setup_ms[7] = t7 - t6;
+
+  // ---- 8. FP32 operator copies and workspaces
+  const int nr = P->cfg.nrhs_max;
+  FDA_TRY(P->xt64.alloc((size_t)N * nr));
+  FDA_TRY(P->yt64.alloc((size_t)N * nr));
+  FDA_TRY(P->cout64.alloc((size_t)std::max<int64_t>(P->n_coef, 1) * nr));
+  FDA_TRY(P->cin64.alloc((size_t)std::max<int64_t>(P->n_coef, 1) * nr));
+  FDA_TRY(P->mid64.alloc((size_t)std::max<int64_t>(P->n_mid, 1) * nr));
+  if (P->cfg.precision == FDA_PREC_FP32) {
+    FDA_TRY(to_fp32(P->op64.S, P->op32.S));
+    FDA_TRY(to_fp32(P->op64.T, P->op32.T));
+    FDA_TRY(to_fp32(P->op64.M, P->op32.M));
+    FDA_TRY(to_fp32(P->op64.K, P->op32.K));
+    FDA_TRY(to_fp32(P->op64.near, P->op32.near));
+    FDA_TRY(to_fp32(P->op64.corr, P->op32.corr));
+    if (P->op64.lr.n) FDA_TRY(to_fp32(P->op64.lr, P->op32.lr));
+    FDA_TRY(P->xt32.alloc((size_t)N * nr));
+    FDA_TRY(P->yt32.alloc((size_t)N * nr));
+    FDA_TRY(P->cout32.alloc((size_t)std::max<int64_t>(P->n_coef, 1) * nr));
+    FDA_TRY(P->cin32.alloc((size_t)std::max<int64_t>(P->n_coef, 1) * nr));
+    FDA_TRY(P->mid32.alloc((size_t)std::max<int64_t>(P->n_mid, 1) * nr));
+  }
+  {
+    std::vector<int> ls(FDA_MAXLEV, 0), lnw(FDA_MAXLEV, 1);
+    for (int l = 0; l < FDA_MAXLEV; ++l) ls[l] = P->lev[l].s, lnw[l] = P->lev[l].nw;
+    FDA_TRY(P->lev_s.upload(ls));
+    FDA_TRY(P->lev_nw.upload(lnw));
+    for (int64_t b : P->h_leaves) P->max_leaf = std::max<int>(P->max_leaf, (int)(T->h_pe[b] - T->h_pb[b]));
+  }
+  FDA_CUDA(cudaDeviceSynchronize());
+  P->setup_ms[1] = 0;
+  return FDA_OK;
+}
+
+}  // namespace fda

@@ -1,0 +1,225 @@
+"""GPU path vs the FP64 oracle, through the C ABI (rows a1-a13 of the hot path).
+
+Tolerances: tree and lists bit-exact; geometry to rounding; corrections to 1e-8 of the row scale
+(the two sides use different quadrature orders); FDA matvec relative l2 <= 1e-4 (FP64 path) and
+<= 3e-4 (FP32 path); solution within 1e-4 of the oracle's direct solve, within the discretisation
+error of the Mie series.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_1311_5202_gb300 import fdbem, inputs  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.fixture(scope="module")
+def c1():
+    _need_gpu()
+    mesh = inputs.icosphere(4, 0.5)
+    S = fdbem.Solver(mesh.nodes, mesh.elems, 10.0, eps=1e-6, leaf_max=64, precision=fdbem.FDA_PREC_FP32,
+                     nrhs_max=4)
+    yield mesh, S
+    S.close()
+
+
+# ------------------------------------------------------------------ a1 geometry
+def test_nystrom_geometry_matches_oracle(c1):
+    mesh, S = c1
+    N = S.N
+    x = torch.empty(N * 3, dtype=torch.float64, device=DEV)
+    n = torch.empty(N * 3, dtype=torch.float64, device=DEV)
+    w = torch.empty(N, dtype=torch.float64, device=DEV)
+    fdbem.bm_problem_geometry(S.prob, x, n, w)
+    xo, no, wo = O.geometry(mesh.nodes, mesh.elems)
+    assert np.allclose(x.cpu().numpy().reshape(N, 3), xo, rtol=0, atol=1e-14)
+    assert np.allclose(n.cpu().numpy().reshape(N, 3), no, rtol=0, atol=1e-13)
+    assert np.allclose(w.cpu().numpy(), wo, rtol=1e-13, atol=0)
+
+
+# ------------------------------------------------------------------ a2, a3 tree + lists, bit-exact
+TREE_CASES = [
+    ("sphere_k10_leaf64", lambda: inputs.icosphere(4, 0.5), 64, 10.0),
+    ("sphere_k100_leaf16", lambda: inputs.icosphere(5, 0.5), 16, 100.0),
+    ("spheroid_k60_leaf24", lambda: inputs.ellipsoid(6, (1.0, 0.25, 0.25)), 24, 60.0),
+    ("torus_k40_leaf20", lambda: inputs.torus(0.5, 0.2, 24, 10), 20, 40.0),
+    ("sphere_k100_leaf64_N100k", lambda: inputs.icosphere(29, 0.5), 64, 100.0),
+]
+
+
+@pytest.mark.parametrize("name,mk,leaf,k", TREE_CASES, ids=[c[0] for c in TREE_CASES])
+def test_tree_and_lists_bit_exact(name, mk, leaf, k):
+    _need_gpu()
+    mesh = mk()
+    prob = fdbem.bm_problem_create(mesh.nodes, mesh.elems, k)
+    try:
+        tree = fdbem.fda_build_tree(prob, leaf)
+        try:
+            G = fdbem.fda_tree_export(tree)
+        finally:
+            fdbem.fda_tree_destroy(tree)
+    finally:
+        fdbem.bm_problem_destroy(prob)
+    xo, _, _ = O.geometry(mesh.nodes, mesh.elems)
+    R = O.tree(xo, leaf, k)
+    assert np.array_equal(G["corner"], R["corner"]) and G["side"] == R["side"]
+    for key in ("perm", "keys", "level", "ix", "iy", "iz", "nchild", "leaf", "parent", "child_begin", "pbeg", "pend",
+                "lev_hf", "lev_T", "lev_n", "direct", "m2l_tgt", "m2l_src", "m2l_level", "m2l_off", "m2l_wout",
+                "m2l_win"):
+        assert np.array_equal(G[key], R[key]), key
+
+
+# ------------------------------------------------------------------ a5 corrections
+def test_near_corrections_match_oracle(c1):
+    mesh, S = c1
+    k = 10.0
+    rows = inputs.sample_rows(S.N, 48, 11)
+    got = fdbem.fda_corrections_export(S.plan, rows)
+    ref = O.correction_weights(mesh.nodes, mesh.elems, k, rows)
+    xs, ns, ws = O.geometry(mesh.nodes, mesh.elems)
+    alpha = 1j / k
+    for r, i in enumerate(rows):
+        elist, wD, wH = ref[r]
+        cols = (6 * elist[:, None] + np.arange(6)[None, :]).ravel()
+        wbar = (wD + alpha * wH).ravel()
+        kk = O.kernels(np.repeat(xs[i:i + 1], len(cols), 0), np.repeat(ns[i:i + 1], len(cols), 0), xs[cols],
+                       ns[cols], k)
+        direct = (kk[:, 1] + alpha * kk[:, 3]) * ws[cols]
+        direct[cols == i] = 0
+        cref = wbar - direct
+        gc, gv = got[r]
+        assert np.array_equal(np.sort(gc), np.sort(cols)), i
+        order = np.argsort(gc)
+        scale = np.max(np.abs(cref))
+        assert np.max(np.abs(gv[order] - cref[np.argsort(cols)])) < 1e-8 * scale, i
+
+
+# ------------------------------------------------------------------ a6-a12 matvec
+def _oracle_rows(mesh, k, x, rows):
+    return O.matvec_rows(mesh.nodes, mesh.elems, k, x, rows)
+
+
+def test_fda_matvec_fp64_matches_dense_oracle_all_rows(c1):
+    mesh, S = c1
+    x = inputs.complex_gaussian(S.N, 20131120)
+    xd = torch.from_numpy(x).to(DEV)
+    yd = torch.empty_like(xd)
+    fdbem.lib()  # loaded
+    # FP64 operator through the plan (a plan built with FP32 also keeps FP64 masters): use nrhs=1 FP64 path
+    plan64 = fdbem.fda_precompute_translations(S.tree, 1e-6, fdbem.FDA_PREC_FP64, 1, 1)
+    try:
+        fdbem.fda_matvec(plan64, xd, yd)
+        torch.cuda.synchronize()
+    finally:
+        fdbem.fda_plan_destroy(plan64)
+    y = yd.cpu().numpy()
+    rows = np.arange(S.N)
+    yo = _oracle_rows(mesh, 10.0, x, rows)
+    err = np.linalg.norm(y - yo) / np.linalg.norm(yo)
+    assert err < 1e-4, err
+
+
+def test_fda_matvec_fp32_path(c1):
+    mesh, S = c1
+    x = inputs.complex_gaussian(S.N, 5)
+    xd = torch.from_numpy(x).to(DEV)
+    yd = torch.empty_like(xd)
+    S.matvec(xd, yd)
+    torch.cuda.synchronize()
+    rows = inputs.sample_rows(S.N, 256, 7)
+    yo = _oracle_rows(mesh, 10.0, x, rows)
+    err = np.linalg.norm(yd.cpu().numpy()[rows] - yo) / np.linalg.norm(yo)
+    assert err < 3e-4, err
+
+
+def test_matvec_batched_rhs_equals_single(c1):
+    mesh, S = c1
+    X = inputs.complex_gaussian(S.N, 9, nrhs=3)
+    Xd = torch.from_numpy(X).to(DEV).contiguous()
+    Yd = torch.empty_like(Xd)
+    S.matvec(Xd, Yd)
+    for r in range(3):
+        y1 = torch.empty_like(Xd[r])
+        S.matvec(Xd[r].contiguous(), y1)
+        torch.cuda.synchronize()
+        a, b = Yd[r].cpu().numpy(), y1.cpu().numpy()
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-6
+
+
+# ------------------------------------------------------------------ a13 solve
+def test_gmres_solve_matches_oracle_and_mie(c1):
+    mesh, S = c1
+    k = 10.0
+    b = torch.empty(S.N, dtype=torch.complex128, device=DEV)
+    fdbem.bm_rhs_plane_wave(S.prob, [0.0, 0.0, 1.0], b)
+    xs, ns, ws = O.geometry(mesh.nodes, mesh.elems)
+    bo = O.bm_rhs(xs, ns, k, [0, 0, 1])
+    assert np.allclose(b.cpu().numpy(), bo, rtol=1e-13, atol=1e-14)
+    x = torch.zeros_like(b)
+    st = S.solve(b, x, tol=1e-6, restart=50, max_iter=300)
+    assert st["rel_residual"] <= 1e-6
+    A = O.dense_matrix(mesh.nodes, mesh.elems, k)
+    xo = np.linalg.solve(A, bo)
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) < 1e-4
+    th = np.arccos(np.clip(xs[:, 2] / np.linalg.norm(xs, axis=1), -1, 1))
+    mie = O.mie_total_surface(th, k, 0.5)
+    assert np.linalg.norm(xg - mie) / np.linalg.norm(mie) < 6e-3
+
+
+def test_refinement_solve_fp32_inner(c1):
+    mesh, S = c1
+    b = torch.empty(S.N, dtype=torch.complex128, device=DEV)
+    fdbem.bm_rhs_plane_wave(S.prob, [1.0, 0.0, 0.0], b)
+    x = torch.zeros_like(b)
+    st = S.solve(b, x, tol=1e-6, restart=50, max_iter=400, refine=True, inner_tol=1e-3)
+    assert st["rel_residual"] <= 1e-6 and st["outer_iterations"] >= 1
+
+
+# ------------------------------------------------------------------ high-frequency levels (directional wedges)
+def test_fda_matvec_with_directional_levels_sampled_rows():
+    _need_gpu()
+    mesh = inputs.icosphere(14, 0.5)
+    k = 100.0
+    S = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=1e-5, leaf_max=64)
+    try:
+        info = S.info()
+        assert any(info["n_wedges"][l] > 1 and info["m2l_pairs"][l] > 0 for l in range(32))
+        x = inputs.complex_gaussian(S.N, 20131120)
+        xd = torch.from_numpy(x).to(DEV)
+        yd = torch.empty_like(xd)
+        S.matvec(xd, yd)
+        torch.cuda.synchronize()
+        rows = inputs.sample_rows(S.N, 256, 7)
+        yo = _oracle_rows(mesh, k, x, rows)
+        err = np.linalg.norm(yd.cpu().numpy()[rows] - yo) / np.linalg.norm(yo)
+        assert err < 1e-4, err
+    finally:
+        S.close()
+
+
+def test_tiny_mesh_without_far_field():
+    """Every pair is near: the plan has no translations and the matvec is the corrected direct sum."""
+    _need_gpu()
+    mesh = inputs.icosphere(1, 0.5)  # 20 elements, 120 DOF < leaf size
+    S = fdbem.Solver(mesh.nodes, mesh.elems, 3.0, eps=1e-6, leaf_max=200)
+    try:
+        x = inputs.complex_gaussian(S.N, 3)
+        xd = torch.from_numpy(x).to(DEV)
+        yd = torch.empty_like(xd)
+        S.matvec(xd, yd)
+        torch.cuda.synchronize()
+        yo = _oracle_rows(mesh, 3.0, x, np.arange(S.N))
+        assert np.linalg.norm(yd.cpu().numpy() - yo) / np.linalg.norm(yo) < 1e-10
+    finally:
+        S.close()
