@@ -24,7 +24,9 @@ __constant__ double c_gl8x[8], c_gl8w[8];
 __constant__ double c_gl12x[12], c_gl12w[12];
 __constant__ double c_gl14x[14], c_gl14w[14];
 
-static const double kA1 = 0.44594849091596488632, kA2 = 0.09157621350977074346;
+// published 6-point (degree 4) rule on the reference triangle, two barycentric orbits
+static const double kA1 = 0.44594849091596488632, kB1 = 0.10810301816807022736;
+static const double kA2 = 0.09157621350977074346, kB2 = 0.81684757298045851308;
 static const double kW1 = 0.22338158967801146570, kW2 = 0.10995174365532186764;
 
 static void gauss_legendre_host(int n, double* x, double* w) {
@@ -51,7 +53,7 @@ static void gauss_legendre_host(int n, double* x, double* w) {
 int upload_geometry_constants() {
   static bool done = false;
   if (done) return FDA_OK;
-  double b1 = 1 - 2 * kA1, b2 = 1 - 2 * kA2;
+  const double b1 = kB1, b2 = kB2;
   double gxi[6][2] = {{kA1, kA1}, {b1, kA1}, {kA1, b1}, {kA2, kA2}, {b2, kA2}, {kA2, b2}};
   double gw[6] = {0.5 * kW1, 0.5 * kW1, 0.5 * kW1, 0.5 * kW2, 0.5 * kW2, 0.5 * kW2};
   // inverse of M[n][j] = phi_n(xi_j), phi = {1, s, t, s^2, s t, t^2}, by Gauss-Jordan
@@ -161,17 +163,49 @@ __device__ __forceinline__ void basis6(double s, double t, double* p) {
 }
 
 // ------------------------------------------------------------------ a1: Nystrom points
+// The Nystrom points feed the integer tree rules, so they are evaluated in the plain order of the
+// definition y = sum_k N_k(xi) P_k, n = -(y_s x y_t)/|y_s x y_t|, w = w_g |y_s x y_t|, every operation
+// explicitly rounded (no contraction): any other implementation of the same formulas in that order gets
+// the same bits.
+__device__ __forceinline__ double rm(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double ra(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rs(double a, double b) { return __dsub_rn(a, b); }
+
 static __global__ void k_nystrom(const double* nodes, const int32_t* elems, int64_t ne, double* x, double* n,
                                  double* w) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 6 * ne) return;
   int64_t e = i / 6;
   int g = (int)(i - 6 * e);
-  Tri6 E;
-  tri_load(E, nodes, elems + 6 * e);
-  double J;
-  tri_point(E, c_gxi[g][0], c_gxi[g][1], x + 3 * i, n + 3 * i, J);
-  w[i] = c_gw[g] * J;
+  const int32_t* el = elems + 6 * e;
+  const double s = c_gxi[g][0], t = c_gxi[g][1];
+  const double L = rs(rs(1.0, s), t);
+  const double N[6] = {rm(L, rs(rm(2.0, L), 1.0)), rm(s, rs(rm(2.0, s), 1.0)), rm(t, rs(rm(2.0, t), 1.0)),
+                       rm(rm(4.0, L), s),        rm(rm(4.0, s), t),        rm(rm(4.0, t), L)};
+  const double A[6] = {-rs(rm(4.0, L), 1.0), rs(rm(4.0, s), 1.0), 0.0, rm(4.0, rs(L, s)), rm(4.0, t), -rm(4.0, t)};
+  const double B[6] = {-rs(rm(4.0, L), 1.0), 0.0, rs(rm(4.0, t), 1.0), -rm(4.0, s), rm(4.0, s), rm(4.0, rs(L, t))};
+  double y[3], ys[3], yt[3];
+  for (int d = 0; d < 3; ++d) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int q = 0; q < 6; ++q) {
+      double p = nodes[3 * (int64_t)el[q] + d];
+      a = ra(a, rm(N[q], p));
+      b = ra(b, rm(A[q], p));
+      c = ra(c, rm(B[q], p));
+    }
+    y[d] = a;
+    ys[d] = b;
+    yt[d] = c;
+  }
+  double c0 = rs(rm(ys[1], yt[2]), rm(ys[2], yt[1]));
+  double c1 = rs(rm(ys[2], yt[0]), rm(ys[0], yt[2]));
+  double c2 = rs(rm(ys[0], yt[1]), rm(ys[1], yt[0]));
+  double J = __dsqrt_rn(ra(ra(rm(c0, c0), rm(c1, c1)), rm(c2, c2)));
+  for (int d = 0; d < 3; ++d) x[3 * i + d] = y[d];
+  n[3 * i + 0] = __ddiv_rn(-c0, J);
+  n[3 * i + 1] = __ddiv_rn(-c1, J);
+  n[3 * i + 2] = __ddiv_rn(-c2, J);
+  w[i] = rm(c_gw[g], J);
 }
 
 int nystrom_points(bm_problem_s* P) {

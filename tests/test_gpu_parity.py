@@ -42,9 +42,10 @@ def test_nystrom_geometry_matches_oracle(c1):
     w = torch.empty(N, dtype=torch.float64, device=DEV)
     fdbem.bm_problem_geometry(S.prob, x, n, w)
     xo, no, wo = O.geometry(mesh.nodes, mesh.elems)
-    assert np.allclose(x.cpu().numpy().reshape(N, 3), xo, rtol=0, atol=1e-14)
-    assert np.allclose(n.cpu().numpy().reshape(N, 3), no, rtol=0, atol=1e-13)
-    assert np.allclose(w.cpu().numpy(), wo, rtol=1e-13, atol=0)
+    # the point formula is evaluated in the same operation order without contraction on both sides
+    assert np.array_equal(x.cpu().numpy().reshape(N, 3), xo)
+    assert np.array_equal(n.cpu().numpy().reshape(N, 3), no)
+    assert np.array_equal(w.cpu().numpy(), wo)
 
 
 # ------------------------------------------------------------------ a2, a3 tree + lists, bit-exact
