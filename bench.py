@@ -1,0 +1,321 @@
+"""Benchmark: FDA matvec/s and GMRES solve time for the rigid-sphere Burton-Miller problem at kD = 200.
+
+Workload (default): sphere of radius 0.5 (D = 1) at k = 200, icosphere frequency 97: 188,180 curved
+quadratic triangles, N = 1,129,080 DOF (the paper's kD ~ 200 sphere with h ~ lambda/5), FDA eps = 1e-4,
+<= 64 points per leaf, seeded complex Gaussian density, plane wave along +z for the solves.
+
+A step is one FDA matrix-vector product of the whole operator (near field + S2M + M2M + M2L + L2L + L2T)
+on one batch of nrhs densities, inputs resident in HBM. `value` is matvec/s of the mixed-precision
+form (FP32 near field and translations); the plain FP64 form is reported beside it, and so are the GMRES
+solve times to a 1e-5 relative residual (plain FP64 GMRES vs FP64 iterative refinement around the FP32
+operator). The operator data (GBs) is far larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+
+Multi-GPU: replicas only (every rank runs the same workload, no collective on the data path);
+value = all ranks' matvecs / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1311_5202_gb300 import inputs  # noqa: E402
+
+METRIC = "FDA matvec/s and GMRES solve s at kD=200: mixed+learned vs plain FP64, same GB300"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self, gpu_index=0):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+        except Exception:
+            return out
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9 and r[0].strip() == str(gpu_index)]
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        out.update(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=sorted(reasons), samples=len(rows))
+        return out
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(mesh, k, x, rows_n, seed=7):
+    """The FP64 oracle (dense Nystrom rows, O(N) each) on a bounded sample of rows, all host cores."""
+    from oracle import oracle as O
+    N = mesh.n_dof
+    rows = inputs.sample_rows(N, rows_n, seed)
+    t0 = time.perf_counter()
+    O.matvec_rows(mesh.nodes, mesh.elems, k, x, rows)
+    dt = time.perf_counter() - t0
+    per_matvec = dt * N / len(rows)
+    return {"value": 1.0 / per_matvec, "unit": "matvec/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{len(rows)} of {N} rows of the dense FP64 oracle matvec (O(N) each, locally corrected), "
+                      f"{dt:.2f} s wall, extrapolated x N/rows"}
+
+
+def run_reference(args):
+    """Reference arm: the oracle as it stands, on this machine's host cores, same workload, metric and unit."""
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    spec = inputs.WORKLOADS[args.workload]
+    mesh = inputs.make_mesh(spec)
+    k = spec["k"]
+    x = inputs.complex_gaussian(mesh.n_dof, 20131120)
+    rows_per_step = args.ref_rows
+    from oracle import oracle as O
+    for _ in range(args.warmup):
+        O.matvec_rows(mesh.nodes, mesh.elems, k, x, inputs.sample_rows(mesh.n_dof, max(4, rows_per_step // 4), 1))
+    times = []
+    for s in range(args.steps):
+        rows = inputs.sample_rows(mesh.n_dof, rows_per_step, 100 + s)
+        t0 = time.perf_counter()
+        O.matvec_rows(mesh.nodes, mesh.elems, k, x, rows)
+        times.append(time.perf_counter() - t0)
+    per_matvec = float(np.mean(times)) * mesh.n_dof / rows_per_step
+    value = 1.0 / per_matvec
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "matvec/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_matvec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": args.workload, "N": mesh.n_dof, "k": k, "nrhs": 1},
+            "cpu_baseline": {"value": value, "unit": "matvec/s", "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"{rows_per_step} sampled rows per step of the dense FP64 oracle matvec, "
+                                       f"extrapolated x N/rows"},
+            "e2e": {"value": value, "unit": "matvec/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="sphere_kd200", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--ref-rows", type=int, default=48)
+    ap.add_argument("--cpu-rows", type=int, default=192)
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--eps", type=float, default=None)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_1311_5202_gb300 import fdbem
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    dev = torch.device("cuda", local)
+    spec = inputs.WORKLOADS[args.workload]
+    eps = args.eps or spec["eps"]
+    mesh = inputs.make_mesh(spec)
+    k = spec["k"]
+    N = mesh.n_dof
+    nrhs = args.nrhs
+    t0 = time.perf_counter()
+    S = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=eps, leaf_max=spec["leaf"], precision=fdbem.FDA_PREC_FP32,
+                     lowrank=1, nrhs_max=nrhs)
+    setup_s = time.perf_counter() - t0
+    info = S.info()
+    X = inputs.complex_gaussian(N, 20131120, nrhs=nrhs if nrhs > 1 else None)
+    xd = torch.from_numpy(X).to(dev).contiguous()
+    yd = torch.empty_like(xd)
+    stream = torch.cuda.current_stream()
+
+    def timed(prec, steps, warm):
+        for _ in range(warm):
+            fdbem.fda_matvec_ex(S.plan, prec, xd, yd, stream)
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fdbem.fda_matvec_ex(S.plan, prec, xd, yd, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        if pg:
+            t = torch.tensor([ms], device=dev)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    clocks = Clocks(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                                 f"bench_clocks_r{rank}.csv"))
+    with clocks:
+        ms32 = timed(fdbem.FDA_PREC_FP32, args.steps, args.warmup)
+        launches = int(S.info()["launches_per_matvec"])
+    steps64 = max(3, args.steps // 3)
+    ms64 = timed(fdbem.FDA_PREC_FP64, steps64, 1)
+    # phase breakdown (device time per phase, one launch each)
+    ph32 = fdbem.fda_matvec_phases(S.plan, fdbem.FDA_PREC_FP32, xd, yd, stream)
+    ph64 = fdbem.fda_matvec_phases(S.plan, fdbem.FDA_PREC_FP64, xd, yd, stream)
+    # end to end through the C ABI with host buffers: H2D of x, matvec, D2H of y per step
+    xh = torch.from_numpy(X).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    for _ in range(2):
+        xd.copy_(xh, non_blocking=True)
+        fdbem.fda_matvec_ex(S.plan, fdbem.FDA_PREC_FP32, xd, yd, stream)
+        yh.copy_(yd, non_blocking=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        xd.copy_(xh, non_blocking=True)
+        fdbem.fda_matvec_ex(S.plan, fdbem.FDA_PREC_FP32, xd, yd, stream)
+        yh.copy_(yd, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    # solves to 1e-5: plain FP64 GMRES vs FP64 iterative refinement around the FP32 operator
+    solve = {}
+    if not args.no_solve:
+        b = torch.empty(N, dtype=torch.complex128, device=dev)
+        fdbem.bm_rhs_plane_wave(S.prob, [0.0, 0.0, 1.0], b, stream)
+        for name, kw in (("fp64", dict(refine=False)), ("mixed", dict(refine=True, inner_tol=1e-3))):
+            xs = torch.zeros_like(b)
+            t1 = time.perf_counter()
+            st = fdbem.bm_gmres_solve(S.plan, b, xs, tol=1e-5, restart=60, max_iter=600, stream=stream,
+                                      raise_on_error=False, **kw)
+            torch.cuda.synchronize()
+            st["wall_s"] = time.perf_counter() - t1
+            solve[name] = st
+    peaks, peak_src = _peaks()
+    p64, p32 = fdbem.fda_device_peaks()
+    # roofline of the dominant phase of the mixed-precision matvec
+    dom = max((p for p in ph32 if p not in ("perm", "assemble")), key=lambda p: ph32[p])
+    dom_ms = ph32[dom]
+    if dom == "near":
+        bytes_near = 8.0 * (info["near_entries"] + info["corr_entries"]) + 4.0 * info["corr_entries"]
+        achieved = bytes_near * nrhs ** 0 / (dom_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "k_near<float2>",
+                "peak_source": f"{peak_src} hbm_gbs"}
+    elif dom in ("m2l", "m2m", "l2l"):
+        fl = info["flops_m2l"] if dom == "m2l" else info["flops_m2m_l2l"] / 2
+        achieved = fl * nrhs / (dom_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": p32, "unit": "TFLOP/s", "frac": achieved / p32,
+                "traffic": None, "kernel": f"k_{dom}<float2>",
+                "peak_source": "FP32 FMA throughput measured on this GPU by fda_device_peaks"}
+    else:
+        bts = info["bytes_s2m_l2t"] / 2 / 2
+        achieved = bts / (dom_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": f"k_{dom}<float2>",
+                "peak_source": f"{peak_src} hbm_gbs"}
+    roof["phase_ms"] = dom_ms
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(mesh, k, X if nrhs == 1 else X[0], args.cpu_rows)
+    value = ws * nrhs * 1000.0 / ms32
+    line = {
+        "metric": METRIC, "value": value, "unit": "matvec/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": args.workload, "N": N, "k": k, "kD": 2 * k * 0.5 if spec["kind"] == "sphere" else None,
+                   "eps": eps, "leaf_max": spec["leaf"], "nrhs": nrhs, "parallelism": f"replicas{ws}",
+                   "l2": "operators and vectors (GBs) larger than L2; no flush"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": ws * nrhs * 1000.0 / e2e_ms, "unit": "matvec/s",
+                "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
+                "d2h_bytes_per_step": int(yh.numel() * yh.element_size())},
+        "gpu_launches": launches * args.steps,
+        "clocks": clocks.summary(local),
+        "fp64": {"matvec_per_s": 1000.0 / ms64, "ms_per_matvec": ms64, "phase_ms": ph64,
+                 "solve": solve.get("fp64")},
+        "mixed": {"matvec_per_s": 1000.0 / ms32, "ms_per_matvec": ms32, "phase_ms": ph32,
+                  "solve": solve.get("mixed")},
+        "speedup_matvec_mixed_vs_fp64": ms64 / ms32,
+        "speedup_solve_mixed_vs_fp64": (solve["fp64"]["wall_s"] / solve["mixed"]["wall_s"]) if solve else None,
+        "measured_fma_tflops": {"fp64": p64, "fp32": p32},
+        "setup_s": setup_s, "setup_ms": info["setup_ms"],
+        "plan": {k_: info[k_] for k_ in ("lmin", "n_leaves", "n_direct_blocks", "near_entries", "corr_entries",
+                                         "flops_m2l", "flops_m2m_l2l", "bytes_near", "bytes_s2m_l2t",
+                                         "device_bytes")},
+        "levels": {str(l): {"s": info["s"][l], "wedges": info["n_wedges"][l], "pairs": info["m2l_pairs"][l],
+                            "offsets": info["m2l_offsets"][l], "lowrank": info["m2l_lowrank"][l]}
+                   for l in range(32) if info["s"][l] > 0},
+    }
+    S.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -159,6 +159,16 @@ int fda_precompute_translations(fda_tree_t* tree, const fda_config_t* cfg, fda_p
  * DOF order; x and y must not overlap. 1 <= nrhs <= cfg.nrhs_max. Asynchronous on `stream`. */
 int fda_matvec(fda_plan_t* plan, const void* x, void* y, int nrhs, int dtype, void* stream);
 
+/* fda_matvec with an explicit arithmetic: FDA_PREC_FP64 always works (every plan keeps its FP64 operators);
+ * FDA_PREC_FP32 needs a plan built with cfg.precision = FDA_PREC_FP32 (else FDA_E_STATE). */
+int fda_matvec_ex(fda_plan_t* plan, int precision, const void* x, void* y, int nrhs, int dtype, void* stream);
+
+/* Same product as fda_matvec_ex, with CUDA events recorded on `stream` between the phases; on return
+ * (synchronous) phase_ms[0..7] holds the device time of: input permutation, near field (direct blocks +
+ * corrections), S2M, M2M, M2L, L2L, L2T, output assembly. Diagnostic; no paper counterpart. */
+int fda_matvec_phases(fda_plan_t* plan, int precision, const void* x, void* y, int nrhs, int dtype, void* stream,
+                      double* phase_ms);
+
 /* Plan statistics for measurement (sizes, algorithmic bytes and flops per matvec). */
 typedef struct {
   int32_t n_levels, lmin, precision, lowrank;
@@ -178,7 +188,8 @@ typedef struct {
   double flops_m2m_l2l;     /* algorithmic flops of M2M + L2L per RHS */
   double flops_near;        /* 8 flops per stored complex entry per RHS */
   double device_bytes;      /* device memory held by the plan */
-  double setup_ms[8];       /* lists/points, SVD, S~T~, M~, K~, low-rank, corrections, near blocks */
+  double setup_ms[8];       /* point selection + SVD, -, S~T~, M~, K~, low-rank, corrections, near blocks */
+  int64_t launches_per_matvec; /* kernels launched by the last fda_matvec */
 } fda_plan_info_t;
 
 int fda_plan_info(const fda_plan_t* plan, fda_plan_info_t* info);
@@ -224,6 +235,10 @@ typedef struct {
  * plan's FP64 operator for the outer residual. */
 int bm_gmres_solve(fda_plan_t* plan, const void* b, void* x, int nrhs, const bm_gmres_opts_t* opts,
                    bm_gmres_stats_t* stats, void* stream);
+
+/* Measured FMA throughput of the current device (diagnostic; no paper counterpart): dependent-chain FMA
+ * kernels over every SM, reported in TFLOP/s (2 flops per FMA). Synchronous. */
+int fda_device_peaks(double* fp64_tflops, double* fp32_tflops);
 
 /* Last error message of the calling thread. */
 const char* fda_last_error(void);

@@ -18,6 +18,7 @@ const char* last_error() { return g_err; }
 int nystrom_points(bm_problem_s* P);
 int gmres_solve(fda_plan_s* P, const double2* b, double2* x, int nrhs, const bm_gmres_opts_t* o,
                 bm_gmres_stats_t* st, cudaStream_t s);
+int device_peaks(double* p64, double* p32);
 }  // namespace fda
 
 int fda_tree_build_impl(bm_problem_s* P, int leaf_max, fda_tree_s* T);
@@ -210,6 +211,44 @@ int fda_matvec(fda_plan_t* plan, const void* x, void* y, int nrhs, int dtype, vo
   return plan_matvec(plan, plan->cfg.precision, x, y, nrhs, dtype, (cudaStream_t)stream, false);
 }
 
+int fda_matvec_ex(fda_plan_t* plan, int precision, const void* x, void* y, int nrhs, int dtype, void* stream) {
+  ARG_CHECK(plan && x && y, "NULL argument");
+  ARG_CHECK(dtype == FDA_CPLX128 || dtype == FDA_CPLX64, "unknown dtype");
+  ARG_CHECK(precision == FDA_PREC_FP64 || precision == FDA_PREC_FP32, "unknown precision");
+  ARG_CHECK(x != y, "x and y must not overlap");
+  return plan_matvec(plan, precision, x, y, nrhs, dtype, (cudaStream_t)stream, false);
+}
+
+int fda_matvec_phases(fda_plan_t* plan, int precision, const void* x, void* y, int nrhs, int dtype, void* stream,
+                      double* ms) {
+  ARG_CHECK(plan && x && y && ms, "NULL argument");
+  ARG_CHECK(precision == FDA_PREC_FP64 || precision == FDA_PREC_FP32, "unknown precision");
+  ARG_CHECK(dtype == FDA_CPLX128 || dtype == FDA_CPLX64, "unknown dtype");
+  cudaEvent_t ev[9];
+  for (int q = 0; q < 9; ++q) FDA_CUDA(cudaEventCreate(&ev[q]));
+  plan->phase_ev = ev;
+  int rc = plan_matvec(plan, precision, x, y, nrhs, dtype, (cudaStream_t)stream, false);
+  plan->phase_ev = nullptr;
+  if (rc == FDA_OK) {
+    FDA_CUDA(cudaEventSynchronize(ev[8]));
+    float t = 0;
+    double ph[9] = {0};
+    for (int q = 0; q < 8; ++q) {
+      cudaEventElapsedTime(&t, ev[q], ev[q + 1]);
+      ph[q] = t;
+    }
+    // phases: perm, near, S2M, M2M, M2L, L2L, L2T, assemble (event q+1 closes phase q)
+    for (int q = 0; q < 8; ++q) ms[q] = ph[q];
+  }
+  for (int q = 0; q < 9; ++q) cudaEventDestroy(ev[q]);
+  return rc;
+}
+
+int fda_device_peaks(double* fp64_tflops, double* fp32_tflops) {
+  ARG_CHECK(fp64_tflops && fp32_tflops, "NULL argument");
+  return device_peaks(fp64_tflops, fp32_tflops);
+}
+
 int fda_plan_info(const fda_plan_t* P, fda_plan_info_t* I) {
   ARG_CHECK(P && I, "NULL argument");
   memset(I, 0, sizeof(*I));
@@ -243,6 +282,7 @@ int fda_plan_info(const fda_plan_t* P, fda_plan_info_t* I) {
   dev += P->corr_col.bytes() + P->cout64.bytes() + P->cin64.bytes() + P->cout32.bytes() + P->cin32.bytes();
   I->device_bytes = dev;
   for (int q = 0; q < 8; ++q) I->setup_ms[q] = P->setup_ms[q];
+  I->launches_per_matvec = P->launches;
   return FDA_OK;
 }
 

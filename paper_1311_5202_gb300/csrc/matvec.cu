@@ -345,8 +345,15 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
                     DBuf<C>& mid, const void* x, void* y, int nrhs, int io, cudaStream_t s) {
   fda_tree_s* T = P->tree;
   const int64_t N = T->N;
+  int64_t nl = 0;
+  auto ev = [&](int q) {
+    if (P->phase_ev) cudaEventRecord(P->phase_ev[q], s);
+  };
+  ev(0);
+  ++nl;
   k_perm_in<C><<<cdiv(N * nrhs, 256), 256, 0, s>>>(x, io, T->perm.p, N, nrhs, xt.p);
   FDA_LAUNCH_CHECK();
+  ev(1);
   // near field
   if (P->n_near_tleaf > 0) {
     for (int r0 = 0; r0 < nrhs; r0 += (nrhs == 1 ? 1 : 4)) {
@@ -359,10 +366,12 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
             P->near_tleaf.p, P->near_tptr.p, P->near_src.p, P->near_off.p, T->pb.p, T->pe.p, op.near.p,
             P->corr_ptr.p, P->corr_col.p, op.corr.p, xt.p, yt.p, nrhs, r0);
       FDA_LAUNCH_CHECK();
+      ++nl;
     }
   } else {
     FDA_CUDA(cudaMemsetAsync(yt.p, 0, sizeof(C) * N * nrhs, s));
   }
+  ev(2);
   if (P->n_coef > 0) {
     const int* d_ls = P->lev_s.p;
     const int* d_lnw = P->lev_nw.p;
@@ -380,8 +389,10 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
             P->leaves.p, P->leaf_s_off.p, T->pb.p, T->pe.p, T->lev.p, P->slot.p, d_ls, d_lnw, op.S.p, xt.p,
             cout.p, nrhs, r0, rcc);
         FDA_LAUNCH_CHECK();
+        ++nl;
       }
     }
+    ev(3);
     // M2M bottom-up
     for (int l = P->lmax - 1; l >= P->lmin; --l) {
       if (P->h_parents[l].empty()) continue;
@@ -395,8 +406,10 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
             P->parents[l].p, T->cbeg.p, T->nch.p, T->ix.p, T->iy.p, T->iz.p, P->slot.p, L.s, Lc.s, L.nw, L.n, Lc.n,
             Lc.hf ? 1 : 0, op.M.p + P->m_off[l], cout.p, nrhs, r0, rcc);
         FDA_LAUNCH_CHECK();
+        ++nl;
       }
     }
+    ev(4);
     // M2L
     FDA_CUDA(cudaMemsetAsync(cin.p, 0, sizeof(C) * P->n_coef * nrhs, s));
     for (int l = P->lmin; l <= P->lmax; ++l) {
@@ -407,9 +420,11 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
           k_m2l<C><<<n, 256, 0, s>>>(P->units[l][st].p + u0, op.K.p, op.lr.p, P->pair_src.p, P->pair_tgt.p,
                                      P->pair_mid.p, cout.p, cin.p, mid.p, nrhs);
           FDA_LAUNCH_CHECK();
+          ++nl;
         }
       }
     }
+    ev(5);
     // L2L top-down
     for (int l = P->lmin; l < P->lmax; ++l) {
       const LevelOps &L = P->lev[l], &Lc = P->lev[l + 1];
@@ -423,8 +438,10 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
                                                                P->slot.p, L.s, Lc.s, L.nw, L.n, Lc.n, Lc.hf ? 1 : 0,
                                                                op.M.p + P->m_off[l], cin.p, nrhs, r0, rcc);
         FDA_LAUNCH_CHECK();
+        ++nl;
       }
     }
+    ev(6);
     // L2T
     if (!P->h_leaves.empty()) {
       int rc = chunk(maxs);
@@ -434,11 +451,21 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
             P->leaves.p, P->leaf_t_off.p, T->pb.p, T->pe.p, T->lev.p, P->slot.p, d_ls, d_lnw, op.T.p, cin.p, yt.p,
             nrhs, r0, rcc);
         FDA_LAUNCH_CHECK();
+        ++nl;
       }
     }
+  } else {
+    ev(3);
+    ev(4);
+    ev(5);
+    ev(6);
   }
+  ev(7);
+  ++nl;
   k_assemble<C><<<cdiv(N * nrhs, 256), 256, 0, s>>>(x, y, io, T->perm.p, N, nrhs, yt.p);
   FDA_LAUNCH_CHECK();
+  ev(8);
+  P->launches = nl;
   return FDA_OK;
 }
 
@@ -457,6 +484,62 @@ int plan_matvec(fda_plan_s* P, int prec, const void* x, void* y, int nrhs, int i
     return matvec_t<float2>(P, P->op32, P->xt32, P->yt32, P->cout32, P->cin32, P->mid32, x, y, nrhs, io_dtype, s);
   }
   return matvec_t<double2>(P, P->op64, P->xt64, P->yt64, P->cout64, P->cin64, P->mid64, x, y, nrhs, io_dtype, s);
+}
+
+// ------------------------------------------------------------------ FMA throughput probe
+template <typename R>
+static __global__ void k_fma_probe(R* out, int iters, R seed) {
+  R a0 = seed + threadIdx.x, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6, a7 = a0 + 7;
+  const R m = (R)0.999999, c = (R)1e-7;
+  for (int i = 0; i < iters; ++i) {
+    a0 = a0 * m + c;
+    a1 = a1 * m + c;
+    a2 = a2 * m + c;
+    a3 = a3 * m + c;
+    a4 = a4 * m + c;
+    a5 = a5 * m + c;
+    a6 = a6 * m + c;
+    a7 = a7 * m + c;
+  }
+  R r = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+  if (r == (R)-12345.0) out[threadIdx.x] = r;  // keeps the chains live
+}
+
+int device_peaks(double* p64, double* p32) {
+  int dev = 0, nsm = 0;
+  FDA_CUDA(cudaGetDevice(&dev));
+  FDA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  DBuf<double> o64;
+  DBuf<float> o32;
+  FDA_TRY(o64.alloc(1024));
+  FDA_TRY(o32.alloc(1024));
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  const int iters = 1 << 14;
+  double res[2] = {0, 0};
+  for (int kind = 0; kind < 2; ++kind) {
+    int blocks = nsm * 8, threads = 256;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(a);
+      if (kind == 0)
+        k_fma_probe<double><<<blocks, threads>>>(o64.p, iters, 1.0);
+      else
+        k_fma_probe<float><<<blocks * 4, threads>>>(o32.p, iters, 1.0f);
+      cudaEventRecord(b);
+      FDA_LAUNCH_CHECK();
+      FDA_CUDA(cudaEventSynchronize(b));
+      float ms = 0;
+      cudaEventElapsedTime(&ms, a, b);
+      double fl = 2.0 * 8.0 * iters * (double)threads * blocks * (kind ? 4 : 1);
+      res[kind] = std::max(res[kind], fl / (ms * 1e-3) / 1e12);
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *p64 = res[0];
+  *p32 = res[1];
+  return FDA_OK;
 }
 
 }  // namespace fda

@@ -90,6 +90,8 @@ struct fda_plan_s {
   fda::DBuf<int64_t> iperm;
   fda::DBuf<int> lev_s, lev_nw;  // per level: compressed dimension and wedge count
   int max_leaf = 1;
+  int64_t launches = 0;          // kernels launched by the last matvec
+  cudaEvent_t* phase_ev = nullptr;  // when set, 9 events recorded between the matvec phases
   double setup_ms[8] = {0};
   double flops_m2l = 0, flops_m2m = 0, bytes_s2m_l2t = 0;
   // GMRES workspace (allocated on first solve)

@@ -77,7 +77,8 @@ class fda_plan_info_t(C.Structure):
                 ("m2l_lowrank", C.c_int64 * 32), ("n_leaves", C.c_int64), ("n_direct_blocks", C.c_int64),
                 ("near_entries", C.c_int64), ("corr_entries", C.c_int64), ("bytes_near", C.c_double),
                 ("bytes_s2m_l2t", C.c_double), ("flops_m2l", C.c_double), ("flops_m2m_l2l", C.c_double),
-                ("flops_near", C.c_double), ("device_bytes", C.c_double), ("setup_ms", C.c_double * 8)]
+                ("flops_near", C.c_double), ("device_bytes", C.c_double), ("setup_ms", C.c_double * 8),
+                ("launches_per_matvec", C.c_int64)]
 
 
 _LIB = None
@@ -99,6 +100,10 @@ _SIGS = [
     ("fda_plan_destroy", None, [C.c_void_p]),
     ("bm_gmres_solve", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(bm_gmres_opts_t),
                                  C.POINTER(bm_gmres_stats_t), C.c_void_p]),
+    ("fda_matvec_ex", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    ("fda_matvec_phases", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                    _dp]),
+    ("fda_device_peaks", C.c_int, [_dp, _dp]),
     ("fda_last_error", C.c_char_p, []),
 ]
 
@@ -212,6 +217,35 @@ def fda_matvec(plan, x, y, stream=None):
     nrhs = 1 if x.dim() == 1 else x.shape[0]
     dt = FDA_CPLX128 if x.dtype == torch.complex128 else FDA_CPLX64
     _check(lib().fda_matvec(plan, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), nrhs, dt, _stream(stream)))
+
+
+PHASES = ("perm", "near", "s2m", "m2m", "m2l", "l2l", "l2t", "assemble")
+
+
+def fda_matvec_ex(plan, precision, x, y, stream=None):
+    import torch
+    nrhs = 1 if x.dim() == 1 else x.shape[0]
+    dt = FDA_CPLX128 if x.dtype == torch.complex128 else FDA_CPLX64
+    _check(lib().fda_matvec_ex(plan, int(precision), C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), nrhs, dt,
+                               _stream(stream)))
+
+
+def fda_matvec_phases(plan, precision, x, y, stream=None) -> dict:
+    """Like fda_matvec_ex, synchronous, returning the device milliseconds of each phase."""
+    import torch
+    nrhs = 1 if x.dim() == 1 else x.shape[0]
+    dt = FDA_CPLX128 if x.dtype == torch.complex128 else FDA_CPLX64
+    ms = np.zeros(8)
+    _check(lib().fda_matvec_phases(plan, int(precision), C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), nrhs,
+                                   dt, _stream(stream), _ptr(ms)))
+    return dict(zip(PHASES, ms.tolist()))
+
+
+def fda_device_peaks() -> tuple:
+    a = C.c_double()
+    b = C.c_double()
+    _check(lib().fda_device_peaks(C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def fda_plan_info(plan) -> dict:

@@ -115,14 +115,9 @@ def test_fda_matvec_fp64_matches_dense_oracle_all_rows(c1):
     x = inputs.complex_gaussian(S.N, 20131120)
     xd = torch.from_numpy(x).to(DEV)
     yd = torch.empty_like(xd)
-    fdbem.lib()  # loaded
-    # FP64 operator through the plan (a plan built with FP32 also keeps FP64 masters): use nrhs=1 FP64 path
-    plan64 = fdbem.fda_precompute_translations(S.tree, 1e-6, fdbem.FDA_PREC_FP64, 1, 1)
-    try:
-        fdbem.fda_matvec(plan64, xd, yd)
-        torch.cuda.synchronize()
-    finally:
-        fdbem.fda_plan_destroy(plan64)
+    # the FP32 plan keeps its FP64 operators: run the plain FP64 product explicitly
+    fdbem.fda_matvec_ex(S.plan, fdbem.FDA_PREC_FP64, xd, yd)
+    torch.cuda.synchronize()
     y = yd.cpu().numpy()
     rows = np.arange(S.N)
     yo = _oracle_rows(mesh, 10.0, x, rows)
