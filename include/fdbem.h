@@ -81,6 +81,16 @@ int bm_problem_geometry(const bm_problem_t* prob, double* x_dev, double* n_dev, 
  * inside). b_dev: DEVICE, N x nrhs complex128, column-major. */
 int bm_rhs_plane_wave(const bm_problem_t* prob, const double* dirs, int nrhs, void* b_dev, void* stream);
 
+/* The same right-hand side without any device allocation (the paper has no counterpart: this serves
+ * callers that cannot call cudaMalloc at the point they need a right-hand side, e.g. code running inside
+ * an allocator or memory-pool callback, or codes that forbid allocation after start-up). The directions
+ * go through a fixed file-scope device array of FDA_RHS_NOALLOC_MAX = 1024 directions (24 KiB, held by
+ * every GPU that loads the library until the process exits); nrhs > 1024 fails with FDA_E_INVALID_ARG.
+ * The first call on a device looks up that array's address for the device: make it before any stream
+ * capture. Every call shares the array and overwrites the entries it uses; calls that overlap on the GPU
+ * (different streams without ordering) race on it. Synchronous. */
+int bm_rhs_plane_wave_noalloc(const bm_problem_t* prob, const double* dirs, int nrhs, void* b_dev, void* stream);
+
 void bm_problem_destroy(bm_problem_t* prob);
 
 /* ------------------------------------------------------------------------------------------ */

@@ -89,6 +89,7 @@ _SIGS = [
                                     C.POINTER(C.c_void_p)]),
     ("bm_problem_geometry", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("bm_rhs_plane_wave", C.c_int, [C.c_void_p, _dp, C.c_int, C.c_void_p, C.c_void_p]),
+    ("bm_rhs_plane_wave_noalloc", C.c_int, [C.c_void_p, _dp, C.c_int, C.c_void_p, C.c_void_p]),
     ("bm_problem_destroy", None, [C.c_void_p]),
     ("fda_build_tree", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
     ("fda_tree_export", C.c_int, [C.c_void_p, C.POINTER(fda_tree_view_t)]),
@@ -159,6 +160,16 @@ def bm_problem_geometry(prob, x_dev, n_dev, w_dev):
 def bm_rhs_plane_wave(prob, dirs, b_dev, stream=None):
     dirs = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
     _check(lib().bm_rhs_plane_wave(prob, _ptr(dirs), dirs.shape[0], C.c_void_p(b_dev.data_ptr()), _stream(stream)))
+
+
+def bm_rhs_plane_wave_noalloc(prob, dirs, b_dev, stream=None, raise_on_error=True):
+    """Plane-wave right-hand side without device allocation (at most 1024 directions per call)."""
+    dirs = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+    rc = lib().bm_rhs_plane_wave_noalloc(prob, _ptr(dirs), dirs.shape[0], C.c_void_p(b_dev.data_ptr()),
+                                         _stream(stream))
+    if raise_on_error:
+        _check(rc)
+    return rc
 
 
 def bm_problem_destroy(prob):
