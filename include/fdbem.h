@@ -204,7 +204,8 @@ typedef struct {
 
 int fda_plan_info(const fda_plan_t* plan, fda_plan_info_t* info);
 
-/* Export the correction matrix of Eq. kcorrection for tests: for rows[r] (DOF indices, host),
+/* Export the correction matrix of Eq. kcorrection for tests (recomputed on the GPU with the plan's
+ * kernels, since the plan folds most entries into its direct blocks): for rows[r] (DOF indices, host),
  * fills cnt[r] (host) and, up to cap entries per row, cols[r*cap + q] (DOF index, host) and
  * vals[2*(r*cap + q)] (complex, host) with C_ij = wbar_ij - [j != i] K_H(x_i, y_j) w_j.
  * Synchronous. */

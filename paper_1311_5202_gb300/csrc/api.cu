@@ -290,27 +290,27 @@ int fda_corrections_export(const fda_plan_t* P, const int64_t* rows, int64_t nro
                            int64_t* cols, double* vals) {
   ARG_CHECK(P && rows && cnt && cols && vals, "NULL argument");
   const int64_t N = P->tree->N;
-  std::vector<int64_t> ip, ptr;
-  std::vector<int32_t> cc;
-  std::vector<double2> vv;
-  FDA_TRY(P->iperm.download(ip));
-  FDA_TRY(P->corr_ptr.download(ptr));
-  cc.resize(P->corr_entries);
-  vv.resize(P->corr_entries);
-  if (P->corr_entries) {
-    FDA_CUDA(cudaMemcpy(cc.data(), P->corr_col.p, sizeof(int32_t) * P->corr_entries, cudaMemcpyDeviceToHost));
-    FDA_CUDA(cudaMemcpy(vv.data(), P->op64.corr.p, sizeof(double2) * P->corr_entries, cudaMemcpyDeviceToHost));
-  }
-  const std::vector<int64_t>& perm = P->tree->h_perm;
+  for (int64_t r = 0; r < nrows; ++r) ARG_CHECK(rows[r] >= 0 && rows[r] < N, "row out of range");
+  // the plan folds most corrections into its direct blocks, so recompute them (same kernels) for export
+  DBuf<int64_t> di_ptr;
+  DBuf<int32_t> di_cols;
+  DBuf<double2> corr;
+  FDA_TRY(near_corrections(P->prob, di_ptr, di_cols, corr, nullptr));
   for (int64_t r = 0; r < nrows; ++r) {
-    ARG_CHECK(rows[r] >= 0 && rows[r] < N, "row out of range");
-    int64_t t = ip[rows[r]];
-    int64_t n = ptr[t + 1] - ptr[t];
-    cnt[r] = n;
-    for (int64_t q = 0; q < n && q < cap; ++q) {
-      cols[r * cap + q] = perm[cc[ptr[t] + q]];
-      vals[2 * (r * cap + q)] = vv[ptr[t] + q].x;
-      vals[2 * (r * cap + q) + 1] = vv[ptr[t] + q].y;
+    int64_t rp[2];
+    FDA_CUDA(cudaMemcpy(rp, di_ptr.p + rows[r], 2 * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    int64_t ne = rp[1] - rp[0];
+    std::vector<int32_t> el(ne);
+    std::vector<double2> v(6 * ne);
+    if (ne) {
+      FDA_CUDA(cudaMemcpy(el.data(), di_cols.p + rp[0], sizeof(int32_t) * ne, cudaMemcpyDeviceToHost));
+      FDA_CUDA(cudaMemcpy(v.data(), corr.p + 6 * rp[0], sizeof(double2) * 6 * ne, cudaMemcpyDeviceToHost));
+    }
+    cnt[r] = 6 * ne;
+    for (int64_t q = 0; q < 6 * ne && q < cap; ++q) {
+      cols[r * cap + q] = 6 * (int64_t)el[q / 6] + q % 6;
+      vals[2 * (r * cap + q)] = v[q].x;
+      vals[2 * (r * cap + q) + 1] = v[q].y;
     }
   }
   return FDA_OK;

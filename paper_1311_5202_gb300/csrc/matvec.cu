@@ -42,78 +42,114 @@ static __global__ void k_assemble(const void* x, void* y, int io, const int64_t*
 }
 
 // ------------------------------------------------------------------ near field (a6)
-// One CTA per target leaf; threads own rows and NR right-hand sides; corrections by warps (lanes over a row).
-#define NEAR_NT 128
-#define NEAR_XS 256
+// One CTA per target leaf. The leaf's direct blocks are one contiguous column-major matrix (nr rows, one
+// column per source point, blocks in order); its source densities are gathered into shared memory in
+// column order, then G = NT / nr thread groups stream the matrix linearly (group g takes columns
+// g, g + G, ...; consecutive threads read consecutive entries) and are summed per row. The correction
+// entries left over after merging into the blocks (columns outside the leaf's near field) follow, one warp
+// per row. Right-hand sides r0 .. r0+rc-1 (rc <= NR).
+#define NEAR_NT 256
+#define NEAR_CAP 2048
 template <typename C, int NR>
 static __global__ void __launch_bounds__(NEAR_NT) k_near(const int64_t* tleaf, const int64_t* tptr,
                                                          const int64_t* srcbox, const int64_t* boff,
-                                                         const int64_t* pb, const int64_t* pe, const C* B,
-                                                         const int64_t* cptr, const int32_t* ccol, const C* cval,
-                                                         const C* xt, C* yt, int nrhs, int r0) {
-  __shared__ C xs[NEAR_XS * NR];
-  __shared__ C ys[NEAR_NT * NR];
+                                                         const int64_t* coff, const int64_t* pb, const int64_t* pe,
+                                                         const C* B, const int64_t* cptr, const int32_t* ccol,
+                                                         const C* cval, const C* xt, C* yt, int nrhs, int r0,
+                                                         int rc) {
+  extern __shared__ unsigned char smem_raw[];
+  C* xs = (C*)smem_raw;              // NEAR_CAP * NR
+  C* red = xs + NEAR_CAP * NR;       // NEAR_NT * NR
+  typedef decltype(xs[0].x) R;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int64_t L = tleaf[blockIdx.x];
-  const int64_t tb = pb[L], te = pe[L];
-  const int64_t nr = te - tb;
-  for (int64_t rb = 0; rb < nr; rb += NEAR_NT) {
-    const int64_t i = rb + t;
+  const int64_t tb = pb[L];
+  const int nr = (int)(pe[L] - tb);
+  const int64_t q0 = tptr[blockIdx.x], q1 = tptr[blockIdx.x + 1];
+  const int64_t ncol = coff[q1 - 1] + (pe[srcbox[q1 - 1]] - pb[srcbox[q1 - 1]]);
+  const C* base = B + boff[q0];
+  for (int rb = 0; rb < nr; rb += NEAR_NT) {
+    const int nrr = min(NEAR_NT, nr - rb);
+    const int G = NEAR_NT / nrr;
+    const int i = t % nrr, g = t / nrr;
+    const bool act = g < G;
     C acc[NR];
 #pragma unroll
-    for (int q = 0; q < NR; ++q) acc[q] = mk((decltype(acc[0].x))0, (decltype(acc[0].x))0);
-    for (int64_t bq = tptr[blockIdx.x]; bq < tptr[blockIdx.x + 1]; ++bq) {
-      const int64_t Q = srcbox[bq];
-      const int64_t sb = pb[Q], se = pe[Q];
-      const C* blk = B + boff[bq];
-      for (int64_t j0 = sb; j0 < se; j0 += NEAR_XS) {
-        int nc = (int)min((int64_t)NEAR_XS, se - j0);
-        __syncthreads();
-        for (int q = t; q < nc * NR; q += NEAR_NT) {
-          int j = q / NR, rr = q - j * NR;
-          xs[q] = (r0 + rr < nrhs) ? xt[(j0 + j) * nrhs + r0 + rr] : mk((decltype(acc[0].x))0, (decltype(acc[0].x))0);
-        }
-        __syncthreads();
-        if (i < nr) {
-          const C* col = blk + (j0 - sb) * nr + i;
-          for (int j = 0; j < nc; ++j) {
-            C bv = col[(int64_t)j * nr];
+    for (int q = 0; q < NR; ++q) acc[q] = mk((R)0, (R)0);
+    for (int64_t c0 = 0; c0 < ncol; c0 += NEAR_CAP) {
+      const int nc = (int)min((int64_t)NEAR_CAP, ncol - c0);
+      __syncthreads();
+      // gather x for columns [c0, c0 + nc): walk the blocks overlapping this chunk
+      for (int64_t q = q0; q < q1; ++q) {
+        int64_t cb = coff[q], sb = pb[srcbox[q]], ce = cb + (pe[srcbox[q]] - sb);
+        int64_t lo = max(cb, c0), hi = min(ce, c0 + nc);
+        for (int64_t c = lo + t; c < hi; c += NEAR_NT) {
+          const C* xp = xt + (sb + (c - cb)) * nrhs + r0;
 #pragma unroll
-            for (int q = 0; q < NR; ++q) cfma(acc[q], bv, xs[j * NR + q]);
+          for (int rr = 0; rr < NR; ++rr) xs[(c - c0) * NR + rr] = (rr < rc) ? xp[rr] : mk((R)0, (R)0);
+        }
+      }
+      __syncthreads();
+      if (act) {
+        const C* col = base + (c0 + g) * nr + rb + i;
+        const int64_t stride = (int64_t)G * nr;
+        int c = g;
+        for (; c + 3 * G < nc; c += 4 * G) {
+          C b0 = col[0], b1 = col[stride], b2 = col[2 * stride], b3 = col[3 * stride];
+#pragma unroll
+          for (int q = 0; q < NR; ++q) {
+            cfma(acc[q], b0, xs[c * NR + q]);
+            cfma(acc[q], b1, xs[(c + G) * NR + q]);
+            cfma(acc[q], b2, xs[(c + 2 * G) * NR + q]);
+            cfma(acc[q], b3, xs[(c + 3 * G) * NR + q]);
           }
+          col += 4 * stride;
+        }
+        for (; c < nc; c += G) {
+          C bv = col[0];
+#pragma unroll
+          for (int q = 0; q < NR; ++q) cfma(acc[q], bv, xs[c * NR + q]);
+          col += stride;
         }
       }
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < NR; ++q) ys[t * NR + q] = acc[q];
+    for (int q = 0; q < NR; ++q) red[t * NR + q] = act ? acc[q] : mk((R)0, (R)0);
     __syncthreads();
-    // corrections: warp per row
-    for (int rr = w; rr < NEAR_NT && rb + rr < nr; rr += NEAR_NT / 32) {
-      const int64_t ti = tb + rb + rr;
+    if (t < nrr) {
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        C s = red[t * NR + q];
+        for (int gg = 1; gg < G; ++gg) s = cadd(s, red[(gg * nrr + t) * NR + q]);
+        red[t * NR + q] = s;
+      }
+    }
+    __syncthreads();
+    // residual corrections: warp per row, lanes over the row's entries
+    for (int r = w; r < nrr; r += NEAR_NT / 32) {
+      const int64_t ti = tb + rb + r;
       C cacc[NR];
 #pragma unroll
-      for (int q = 0; q < NR; ++q) cacc[q] = mk((decltype(acc[0].x))0, (decltype(acc[0].x))0);
+      for (int q = 0; q < NR; ++q) cacc[q] = mk((R)0, (R)0);
       for (int64_t p = cptr[ti] + lane; p < cptr[ti + 1]; p += 32) {
         C v = cval[p];
-        int64_t col = ccol[p];
+        const C* xp = xt + (int64_t)ccol[p] * nrhs + r0;
 #pragma unroll
         for (int q = 0; q < NR; ++q)
-          if (r0 + q < nrhs) cfma(cacc[q], v, xt[col * nrhs + r0 + q]);
+          if (q < rc) cfma(cacc[q], v, xp[q]);
       }
 #pragma unroll
       for (int q = 0; q < NR; ++q) {
         cacc[q] = warp_csum(cacc[q]);
-        if (lane == 0) ys[rr * NR + q] = cadd(ys[rr * NR + q], cacc[q]);
+        if (lane == 0) red[r * NR + q] = cadd(red[r * NR + q], cacc[q]);
       }
     }
     __syncthreads();
-    if (i < nr) {
-#pragma unroll
-      for (int q = 0; q < NR; ++q)
-        if (r0 + q < nrhs) yt[(tb + i) * nrhs + r0 + q] = ys[t * NR + q];
+    for (int q = t; q < nrr * rc; q += NEAR_NT) {
+      int r = q / rc, rr = q - r * rc;
+      yt[(tb + rb + r) * nrhs + r0 + rr] = red[r * NR + rr];
     }
-    __syncthreads();
   }
 }
 
@@ -356,15 +392,26 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
   ev(1);
   // near field
   if (P->n_near_tleaf > 0) {
-    for (int r0 = 0; r0 < nrhs; r0 += (nrhs == 1 ? 1 : 4)) {
-      if (nrhs == 1)
-        k_near<C, 1><<<(unsigned)P->n_near_tleaf, NEAR_NT, 0, s>>>(
-            P->near_tleaf.p, P->near_tptr.p, P->near_src.p, P->near_off.p, T->pb.p, T->pe.p, op.near.p,
-            P->corr_ptr.p, P->corr_col.p, op.corr.p, xt.p, yt.p, nrhs, r0);
+    static bool attr_set = false;
+    if (!attr_set) {
+      FDA_CUDA(cudaFuncSetAttribute(k_near<double2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(sizeof(double2) * (NEAR_CAP + NEAR_NT) * 4)));
+      FDA_CUDA(cudaFuncSetAttribute(k_near<float2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(sizeof(float2) * (NEAR_CAP + NEAR_NT) * 4)));
+      attr_set = true;
+    }
+    const int NR = nrhs == 1 ? 1 : 4;
+    for (int r0 = 0; r0 < nrhs; r0 += NR) {
+      int rc = std::min(NR, nrhs - r0);
+      size_t sm = sizeof(C) * (size_t)(NEAR_CAP + NEAR_NT) * NR;
+      if (NR == 1)
+        k_near<C, 1><<<(unsigned)P->n_near_tleaf, NEAR_NT, sm, s>>>(
+            P->near_tleaf.p, P->near_tptr.p, P->near_src.p, P->near_off.p, P->near_coff.p, T->pb.p, T->pe.p,
+            op.near.p, P->corr_ptr.p, P->corr_col.p, op.corr.p, xt.p, yt.p, nrhs, r0, rc);
       else
-        k_near<C, 4><<<(unsigned)P->n_near_tleaf, NEAR_NT, 0, s>>>(
-            P->near_tleaf.p, P->near_tptr.p, P->near_src.p, P->near_off.p, T->pb.p, T->pe.p, op.near.p,
-            P->corr_ptr.p, P->corr_col.p, op.corr.p, xt.p, yt.p, nrhs, r0);
+        k_near<C, 4><<<(unsigned)P->n_near_tleaf, NEAR_NT, sm, s>>>(
+            P->near_tleaf.p, P->near_tptr.p, P->near_src.p, P->near_off.p, P->near_coff.p, T->pb.p, T->pe.p,
+            op.near.p, P->corr_ptr.p, P->corr_col.p, op.corr.p, xt.p, yt.p, nrhs, r0, rc);
       FDA_LAUNCH_CHECK();
       ++nl;
     }

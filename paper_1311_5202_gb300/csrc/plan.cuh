@@ -66,6 +66,8 @@ struct fda_plan_s {
   fda::DBuf<int64_t> near_tptr;      // CSR over those leaves -> blocks
   fda::DBuf<int64_t> near_src;       // block -> source box
   fda::DBuf<int64_t> near_off;       // block -> entry offset
+  fda::DBuf<int64_t> near_coff;      // block -> first column within its target leaf's matrix
+  int64_t corr_merged = 0;           // correction entries folded into the direct blocks
   int64_t n_near_tleaf = 0, n_blocks = 0, near_entries = 0;
   fda::DBuf<int64_t> corr_ptr;       // tree-order CSR of the correction matrix
   fda::DBuf<int32_t> corr_col;

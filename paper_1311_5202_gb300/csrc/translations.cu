@@ -349,6 +349,50 @@ static __global__ void k_corr_scatter(const int64_t* perm, const int64_t* iperm,
   }
 }
 
+// Fold correction entries whose column lies in the row's direct blocks into those blocks; flag the rest.
+static __global__ void k_merge_corr(const int64_t* cptr, const int32_t* ccol, const double2* cval,
+                                    const int32_t* row_leaf, const int64_t* tleaf, const int64_t* tptr,
+                                    const int64_t* srcbox, const int64_t* boff, const int64_t* pb, const int64_t* pe,
+                                    int64_t N, double2* near, int64_t* keep_cnt, int8_t* keep) {
+  int64_t ti = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (ti >= N) return;
+  int u = row_leaf[ti];
+  int64_t kept = 0;
+  for (int64_t p = cptr[ti]; p < cptr[ti + 1]; ++p) {
+    int64_t j = ccol[p];
+    bool done = false;
+    if (u >= 0) {
+      int64_t L = tleaf[u], tb = pb[L], nr = pe[L] - tb;
+      for (int64_t q = tptr[u]; q < tptr[u + 1]; ++q) {
+        int64_t Q = srcbox[q], sb = pb[Q], se = pe[Q];
+        if (j >= sb && j < se) {
+          int64_t idx = boff[q] + (j - sb) * nr + (ti - tb);
+          near[idx] = cadd(near[idx], cval[p]);
+          done = true;
+          break;
+        }
+      }
+    }
+    keep[p] = done ? 0 : 1;
+    kept += done ? 0 : 1;
+  }
+  keep_cnt[ti] = kept;
+}
+
+static __global__ void k_compact_corr(const int64_t* cptr, const int32_t* ccol, const double2* cval,
+                                      const int8_t* keep, const int64_t* nptr, int64_t N, int32_t* ncol,
+                                      double2* nval) {
+  int64_t ti = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (ti >= N) return;
+  int64_t o = nptr[ti];
+  for (int64_t p = cptr[ti]; p < cptr[ti + 1]; ++p)
+    if (keep[p]) {
+      ncol[o] = ccol[p];
+      nval[o] = cval[p];
+      ++o;
+    }
+}
+
 template <typename A, typename B>
 static __global__ void k_convert(const A* a, B* b, int64_t n) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1110,17 +1154,20 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
       }
     }
     std::sort(blocks.begin(), blocks.end());
-    std::vector<int64_t> tleaf, tptr, src, boff;
+    std::vector<int64_t> tleaf, tptr, src, boff, coff;
     std::vector<NearJob> jobs;
-    int64_t eoff = 0;
+    int64_t eoff = 0, ccur = 0;
     for (size_t q = 0; q < blocks.size(); ++q) {
       if (q == 0 || blocks[q].first != blocks[q - 1].first) {
         tleaf.push_back(blocks[q].first);
         tptr.push_back((int64_t)q);
+        ccur = 0;
       }
       int64_t L = blocks[q].first, Q = blocks[q].second;
       src.push_back(Q);
       boff.push_back(eoff);
+      coff.push_back(ccur);
+      ccur += T->h_pe[Q] - T->h_pb[Q];
       jobs.push_back({T->h_pb[L], T->h_pe[L], T->h_pb[Q], T->h_pe[Q], eoff});
       eoff += (T->h_pe[L] - T->h_pb[L]) * (T->h_pe[Q] - T->h_pb[Q]);
     }
@@ -1132,6 +1179,7 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
     FDA_TRY(P->near_tptr.upload(tptr));
     FDA_TRY(P->near_src.upload(src));
     FDA_TRY(P->near_off.upload(boff));
+    FDA_TRY(P->near_coff.upload(coff));
     FDA_TRY(P->op64.near.alloc(std::max<int64_t>(eoff, 1)));
     DBuf<NearJob> dj;
     FDA_TRY(dj.upload(jobs));
@@ -1141,6 +1189,40 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
       FDA_LAUNCH_CHECK();
     }
     FDA_CUDA(cudaDeviceSynchronize());
+    // fold the corrections that fall inside a row's direct blocks into the blocks
+    std::vector<int32_t> row_leaf(N, -1);
+    for (size_t u = 0; u < tleaf.size(); ++u)
+      for (int64_t ti = T->h_pb[tleaf[u]]; ti < T->h_pe[tleaf[u]]; ++ti) row_leaf[ti] = (int32_t)u;
+    DBuf<int32_t> d_row_leaf;
+    FDA_TRY(d_row_leaf.upload(row_leaf));
+    DBuf<int64_t> keep_cnt, nptr;
+    DBuf<int8_t> keep;
+    FDA_TRY(keep_cnt.alloc(N));
+    FDA_TRY(keep.alloc(std::max<int64_t>(P->corr_entries, 1)));
+    k_merge_corr<<<cdiv(N, 128), 128>>>(P->corr_ptr.p, P->corr_col.p, P->op64.corr.p, d_row_leaf.p, P->near_tleaf.p,
+                                        P->near_tptr.p, P->near_src.p, P->near_off.p, T->pb.p, T->pe.p, N,
+                                        P->op64.near.p, keep_cnt.p, keep.p);
+    FDA_LAUNCH_CHECK();
+    FDA_TRY(nptr.alloc(N + 1));
+    int64_t kept = 0;
+    FDA_TRY(exclusive_scan_i64(keep_cnt.p, nptr.p, N, &kept, 0));
+    FDA_CUDA(cudaMemcpy(nptr.p + N, &kept, sizeof(int64_t), cudaMemcpyHostToDevice));
+    DBuf<int32_t> ncol;
+    DBuf<double2> nval;
+    FDA_TRY(ncol.alloc(std::max<int64_t>(kept, 1)));
+    FDA_TRY(nval.alloc(std::max<int64_t>(kept, 1)));
+    k_compact_corr<<<cdiv(N, 128), 128>>>(P->corr_ptr.p, P->corr_col.p, P->op64.corr.p, keep.p, nptr.p, N, ncol.p,
+                                          nval.p);
+    FDA_LAUNCH_CHECK();
+    FDA_CUDA(cudaDeviceSynchronize());
+    P->corr_merged = P->corr_entries - kept;
+    P->corr_entries = kept;
+    std::swap(P->corr_ptr.p, nptr.p);
+    std::swap(P->corr_ptr.n, nptr.n);
+    std::swap(P->corr_col.p, ncol.p);
+    std::swap(P->corr_col.n, ncol.n);
+    std::swap(P->op64.corr.p, nval.p);
+    std::swap(P->op64.corr.n, nval.n);
   }
   double t7 = now_ms();
   P->setup_ms[7] = t7 - t6;

@@ -183,6 +183,8 @@ WORKLOADS = {
     "sphere_kd10": dict(kind="sphere", m=4, radius=0.5, k=10.0, eps=1e-6, leaf=64),
     # sphere a=0.5, kD=100, 16820 elements, 100920 DOF
     "sphere_kd100": dict(kind="sphere", m=29, radius=0.5, k=100.0, eps=1e-4, leaf=64),
+    # sphere a=0.5, kD=60, 8000 elements, 48000 DOF (profiling-sized: a few GB on the device)
+    "sphere_kd60": dict(kind="sphere", m=20, radius=0.5, k=60.0, eps=1e-4, leaf=64),
     # sphere a=0.5, kD=200, 188180 elements, 1129080 DOF (h ~ lambda/5)
     "sphere_kd200": dict(kind="sphere", m=97, radius=0.5, k=200.0, eps=1e-4, leaf=64),
     # prolate spheroid (1, .25, .25), kD=200, 67280 elements, 403680 DOF
