@@ -161,6 +161,7 @@ def main():
     ap.add_argument("--no-alt", action="store_true", help="skip the alpha = -i/k solves")
     ap.add_argument("--full-solve", action="store_true", help="also the plain FP64 solve at alpha = i/k (long)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip training/using the learned preconditioner")
     ap.add_argument("--eps", type=float, default=None)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -273,6 +274,29 @@ def main():
         setup2 = time.perf_counter() - t2
         solve_alt = solves(S2, [("fp64", dict(refine=False)), ("mixed", dict(refine=True, inner_tol=1e-3))], 100, 2000)
         solve_alt["setup_s"] = setup2
+        if not args.no_learned:
+            # learned leaf-block preconditioner: trained on seeded random ellipsoids (kD 20-40, 12k DOF each)
+            # from the method's own GMRES solves, then flexible GMRES inside the mixed solve
+            from paper_1311_5202_gb300 import precond as PCm
+            t3 = time.perf_counter()
+            train = [(inputs.ellipsoid(10, ax), kk) for ax, kk in
+                     inputs.random_ellipsoid_params(3, seed=1, kd_range=(20.0, 40.0))]
+            net, tinfo = PCm.build_trained(train, alpha_sign=-1, hidden=32, epochs=20, dirs_per_mesh=6)
+            train_s = time.perf_counter() - t3
+            pc = fdbem.bm_precond_create(S2.plan)
+            b = torch.empty(N, dtype=torch.complex128, device=dev)
+            fdbem.bm_rhs_plane_wave(S2.prob, [0.0, 0.0, 1.0], b, stream)
+            xs = torch.zeros_like(b)
+            t4 = time.perf_counter()
+            st = fdbem.bm_fgmres_solve(S2.plan, pc, net, b, xs, tol=1e-5, restart=100, max_iter=2000, refine=True,
+                                       inner_tol=1e-3, stream=stream, raise_on_error=False)
+            torch.cuda.synchronize()
+            st["wall_s"] = time.perf_counter() - t4
+            st["train_s"] = train_s
+            st["training"] = tinfo
+            solve_alt["mixed_learned"] = st
+            fdbem.bm_precond_destroy(pc)
+            fdbem.bm_net_destroy(net)
         S2.close()
     peaks, peak_src = _peaks()
     p64, p32 = fdbem.fda_device_peaks()
@@ -323,6 +347,8 @@ def main():
         "solve_alpha_minus_i_over_k": solve_alt,
         "speedup_solve_mixed_vs_fp64": (solve_alt["fp64"]["wall_s"] / solve_alt["mixed"]["wall_s"])
         if solve_alt else None,
+        "speedup_solve_mixed_learned_vs_fp64": (solve_alt["fp64"]["wall_s"] / solve_alt["mixed_learned"]["wall_s"])
+        if solve_alt.get("mixed_learned") else None,
         "measured_fma_tflops": {"fp64": p64, "fp32": p32},
         "setup_s": setup_s, "setup_ms": info["setup_ms"],
         "plan": {k_: info[k_] for k_ in ("lmin", "n_leaves", "n_direct_blocks", "near_entries", "corr_entries",

@@ -251,6 +251,46 @@ int bm_gmres_solve(fda_plan_t* plan, const void* b, void* x, int nrhs, const bm_
  * kernels over every SM, reported in TFLOP/s (2 flops per FMA). Synchronous. */
 int fda_device_peaks(double* fp64_tflops, double* fp32_tflops);
 
+/* ------------------------------------------------------------------------------------------ */
+/* Learned leaf-block preconditioner for flexible GMRES (no paper counterpart; the method's own */
+/* GMRES solves supply its training pairs).                                                    */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct bm_net_s bm_net_t;
+typedef struct bm_precond_s bm_precond_t;
+
+/* Network 6 -> hidden -> hidden -> 4 (tanh), FP32 on the device, seeded splitmix64 initialisation; the
+ * output layer starts at the identity preconditioner (z = r). 1 <= hidden <= 64. */
+int bm_net_create(int hidden, uint64_t seed, bm_net_t** out);
+/* Copy the parameters to get_host and/or from set_host (either may be NULL); *nparam = parameter count.
+ * Layout: W1 (hidden x 6, row-major), b1, W2 (hidden x hidden), b2, W3 (4 x hidden), b3. Synchronous. */
+int bm_net_params(bm_net_t* net, float* get_host, const float* set_host, int* nparam);
+void bm_net_destroy(bm_net_t* net);
+
+/* Per-leaf inverses of A_LL = (1/2) I + near-field self block (FP64 Gauss-Jordan, stored FP32) for the
+ * plan's leaves of at most 64 points. The plan must outlive the preconditioner. Synchronous. */
+int bm_precond_create(fda_plan_t* plan, bm_precond_t** out);
+void bm_precond_destroy(bm_precond_t* precond);
+
+/* z = M(r): per point z_i = w1_i r_i + w2_i y_i, y_L = A_LL^-1 r_L, (w1, w2) = net(r_i / s_L, y_i / s_L,
+ * mean_L(y) / s_L), s_L the leaf's mean residual. r, z: DEVICE, N complex128, user order. Synchronous. */
+int bm_precond_apply(bm_precond_t* precond, bm_net_t* net, const void* r, void* z, void* stream);
+
+/* One training step on npairs residual/correction pairs (r_q, e_q), DEVICE N x npairs complex128 user
+ * order: loss = mean_q |M(r_q) - e_q|^2 / |e_q|^2, gradient by the backward kernels, then an Adam update
+ * with learning rate lr (lr <= 0: gradient only). *loss and grad_host (nparam floats, may be NULL) report
+ * the loss and gradient before the update. Synchronous. */
+int bm_precond_train_step(bm_precond_t* precond, bm_net_t* net, const void* r, const void* e, int npairs, double lr,
+                          double* loss, float* grad_host, void* stream);
+
+/* Training pair from a GMRES iterate: r = b - A x (FP64 operator) and e = xstar - x. All DEVICE, N
+ * complex128, user order; r and e must not alias the inputs. Synchronous. */
+int bm_residual_pair(fda_plan_t* plan, const void* b, const void* xstar, const void* x, void* r, void* e,
+                     void* stream);
+
+/* Flexible GMRES (right preconditioner M above) with the options and results of bm_gmres_solve. */
+int bm_fgmres_solve(fda_plan_t* plan, bm_precond_t* precond, bm_net_t* net, const void* b, void* x, int nrhs,
+                    const bm_gmres_opts_t* opts, bm_gmres_stats_t* stats, void* stream);
+
 /* Last error message of the calling thread. */
 const char* fda_last_error(void);
 

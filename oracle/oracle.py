@@ -401,3 +401,74 @@ def tree(points, leaf_max, k):
 
 def wedge_of(n, d):
     return int(lib().orc_wedge_of(int(n), int(d[0]), int(d[1]), int(d[2])))
+
+
+# ------------------------------------------------------------------------------------------------
+# Learned leaf-block preconditioner: the network, written out plainly in FP64 (the GPU trains it in FP32)
+# ------------------------------------------------------------------------------------------------
+def net_layout(H):
+    W1 = 0
+    b1 = W1 + 6 * H
+    W2 = b1 + H
+    b2 = W2 + H * H
+    W3 = b2 + H
+    b3 = W3 + 4 * H
+    return dict(W1=W1, b1=b1, W2=W2, b2=b2, W3=W3, b3=b3, n=b3 + 4)
+
+
+def net_unpack(w, H):
+    L = net_layout(H)
+    w = np.asarray(w, dtype=np.float64)
+    return (w[L["W1"]:L["b1"]].reshape(H, 6), w[L["b1"]:L["W2"]], w[L["W2"]:L["b2"]].reshape(H, H),
+            w[L["b2"]:L["W3"]], w[L["W3"]:L["b3"]].reshape(4, H), w[L["b3"]:L["n"]])
+
+
+def leaf_features(r, y, segments):
+    """Per point: u = r/s_L, v = y/s_L and mean_L(v), s_L = leaf mean of r (RMS of r when the mean is below
+    1e-3 RMS). segments: list of index arrays (one per leaf). Returns (features (N,6), s per point)."""
+    N = len(r)
+    f = np.zeros((N, 6))
+    s_pt = np.ones(N, dtype=np.complex128)
+    for idx in segments:
+        rr, yy = r[idx], y[idx]
+        mr = rr.mean()
+        rms = np.sqrt(np.mean(np.abs(rr) ** 2))
+        s = mr if (abs(mr) > 1e-3 * rms and abs(mr) > 0) else complex(rms if rms > 0 else 1.0)
+        u, v = rr / s, yy / s
+        mv = v.mean()
+        f[idx, 0], f[idx, 1], f[idx, 2], f[idx, 3] = u.real, u.imag, v.real, v.imag
+        f[idx, 4], f[idx, 5] = mv.real, mv.imag
+        s_pt[idx] = s
+    return f, s_pt
+
+
+def net_loss_grad(w, H, r, y, e, segments):
+    """Loss |z - e|^2 / |e|^2 with z_i = (o0 + i o1) r_i + (o2 + i o3) y_i, o = net(features_i), and its gradient
+    with respect to the parameters (plain backpropagation). Points outside every segment do not contribute."""
+    W1, b1, W2, b2, W3, b3 = net_unpack(w, H)
+    f, _ = leaf_features(r, y, segments)
+    mask = np.zeros(len(r), dtype=bool)
+    for idx in segments:
+        mask[idx] = True
+    a1 = f @ W1.T + b1
+    h1 = np.tanh(a1)
+    a2 = h1 @ W2.T + b2
+    h2 = np.tanh(a2)
+    o = h2 @ W3.T + b3
+    z = (o[:, 0] + 1j * o[:, 1]) * r + (o[:, 2] + 1j * o[:, 3]) * y
+    E = np.sum(np.abs(e) ** 2)
+    d = (z - e) * mask
+    loss = np.sum(np.abs(d) ** 2) / E
+    gz = 2.0 * d / E  # dL/dRe z + i dL/dIm z
+    go = np.stack([np.real(np.conj(gz) * r), np.real(np.conj(gz) * 1j * r), np.real(np.conj(gz) * y),
+                   np.real(np.conj(gz) * 1j * y)], axis=1)
+    gW3 = go.T @ h2
+    gb3 = go.sum(0)
+    dh2 = (go @ W3) * (1 - h2 ** 2)
+    gW2 = dh2.T @ h1
+    gb2 = dh2.sum(0)
+    dh1 = (dh2 @ W2) * (1 - h1 ** 2)
+    gW1 = dh1.T @ f
+    gb1 = dh1.sum(0)
+    g = np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3.ravel(), gb3])
+    return loss, g

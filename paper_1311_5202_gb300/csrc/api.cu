@@ -17,7 +17,7 @@ const char* last_error() { return g_err; }
 
 int nystrom_points(bm_problem_s* P);
 int gmres_solve(fda_plan_s* P, const double2* b, double2* x, int nrhs, const bm_gmres_opts_t* o,
-                bm_gmres_stats_t* st, cudaStream_t s);
+                bm_gmres_stats_t* st, cudaStream_t s, bm_precond_s* pc, bm_net_s* net);
 int device_peaks(double* p64, double* p32);
 }  // namespace fda
 
@@ -325,7 +325,8 @@ int bm_gmres_solve(fda_plan_t* plan, const void* b, void* x, int nrhs, const bm_
   ARG_CHECK(opts->tol > 0, "tol must be positive");
   ARG_CHECK(opts->restart >= 1, "restart must be >= 1");
   ARG_CHECK(opts->max_iter >= 1, "max_iter must be >= 1");
-  return gmres_solve(plan, (const double2*)b, (double2*)x, nrhs, opts, stats, (cudaStream_t)stream);
+  return gmres_solve(plan, (const double2*)b, (double2*)x, nrhs, opts, stats, (cudaStream_t)stream, nullptr, nullptr);
 }
+
 
 }  // extern "C"

@@ -12,6 +12,8 @@ namespace fda {
 
 typedef std::complex<double> zc;
 
+int precond_apply(bm_precond_s* Pc, bm_net_s* net, const double2* r, double2* z, cudaStream_t s);
+
 #define GM_NB 256
 // partial[q * nb + blk] = sum_i conj(V_q[i]) w[i]
 static __global__ void k_multidot(const double2* V, int64_t ldv, int nv, const double2* w, int64_t N,
@@ -110,6 +112,8 @@ static __global__ void k_norm_final(const double* partial, int nb, double* out) 
 
 struct GmCtx {
   fda_plan_s* P;
+  bm_precond_s* pc = nullptr;  // flexible GMRES right preconditioner (optional)
+  bm_net_s* net = nullptr;
   cudaStream_t s;
   int64_t N;
   int nb;
@@ -155,6 +159,9 @@ static int gmres_core(GmCtx& C, int prec, const double2* b, double2* x, double t
   if (P->gm_V.n < (size_t)(m + 1) * N) FDA_TRY(P->gm_V.alloc((size_t)(m + 1) * N));
   if (P->gm_w.n < (size_t)N) FDA_TRY(P->gm_w.alloc(N));
   if (P->gm_r.n < (size_t)N) FDA_TRY(P->gm_r.alloc(N));
+  const bool flex = C.pc != nullptr;
+  if (flex && P->gm_x.n < (size_t)m * N) FDA_TRY(P->gm_x.alloc((size_t)m * N));
+  double2* Z = flex ? P->gm_x.p : nullptr;  // z_j = M(v_j)
   double2* V = P->gm_V.p;
   double2* w = P->gm_w.p;
   double2* r = P->gm_r.p;
@@ -214,7 +221,12 @@ static int gmres_core(GmCtx& C, int prec, const double2* b, double2* x, double t
     g[0] = beta;
     int j = 0;
     for (; j < m && it < maxit; ++j) {
-      FDA_TRY(apply_A(C, prec, V + (int64_t)j * N, w));
+      if (flex) {
+        FDA_TRY(precond_apply(C.pc, C.net, V + (int64_t)j * N, Z + (int64_t)j * N, C.s));
+        FDA_TRY(apply_A(C, prec, Z + (int64_t)j * N, w));
+      } else {
+        FDA_TRY(apply_A(C, prec, V + (int64_t)j * N, w));
+      }
       ++it;
       FDA_CUDA(cudaMemsetAsync(C.hacc.p, 0, sizeof(double2) * (j + 1), C.s));
       for (int pass = 0; pass < 2; ++pass) {
@@ -269,17 +281,19 @@ static int gmres_core(GmCtx& C, int prec, const double2* b, double2* x, double t
     }
     for (int q = 0; q < kk; ++q) hy[q] = make_double2(y[q].real(), y[q].imag());
     FDA_CUDA(cudaMemcpyAsync(C.h.p, hy.data(), sizeof(double2) * kk, cudaMemcpyHostToDevice, C.s));
-    k_add_combo<<<cdiv(N, 256), 256, 0, C.s>>>(x, V, N, C.h.p, kk, N);
+    k_add_combo<<<cdiv(N, 256), 256, 0, C.s>>>(x, flex ? Z : V, N, C.h.p, kk, N);
     FDA_LAUNCH_CHECK();
     x0_zero = false;
   }
 }
 
 int gmres_solve(fda_plan_s* P, const double2* b, double2* x, int nrhs, const bm_gmres_opts_t* o,
-                bm_gmres_stats_t* st, cudaStream_t s) {
+                bm_gmres_stats_t* st, cudaStream_t s, bm_precond_s* pc, bm_net_s* net) {
   auto t0 = std::chrono::steady_clock::now();
   GmCtx C;
   C.P = P;
+  C.pc = pc;
+  C.net = net;
   C.s = s;
   C.N = P->tree->N;
   C.nb = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (C.N + GM_NB - 1) / GM_NB));

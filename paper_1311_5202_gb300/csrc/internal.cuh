@@ -4,6 +4,9 @@
 
 #define FDA_MAXLEV 22
 
+struct bm_net_s;
+struct bm_precond_s;
+
 struct bm_problem_s {
   int64_t ne = 0, N = 0, nn = 0;
   double k = 0;

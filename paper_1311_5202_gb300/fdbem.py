@@ -105,6 +105,18 @@ _SIGS = [
     ("fda_matvec_phases", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                     _dp]),
     ("fda_device_peaks", C.c_int, [_dp, _dp]),
+    ("bm_net_create", C.c_int, [C.c_int, C.c_uint64, C.POINTER(C.c_void_p)]),
+    ("bm_net_params", C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_int)]),
+    ("bm_net_destroy", None, [C.c_void_p]),
+    ("bm_precond_create", C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("bm_precond_destroy", None, [C.c_void_p]),
+    ("bm_precond_apply", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("bm_precond_train_step", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
+                                        _dp, C.POINTER(C.c_float), C.c_void_p]),
+    ("bm_residual_pair", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p]),
+    ("bm_fgmres_solve", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                  C.POINTER(bm_gmres_opts_t), C.POINTER(bm_gmres_stats_t), C.c_void_p]),
     ("fda_last_error", C.c_char_p, []),
 ]
 
@@ -302,6 +314,86 @@ def bm_gmres_solve(plan, b, x, tol=1e-6, restart=50, max_iter=1000, x0_given=Fal
     nrhs = 1 if b.dim() == 1 else b.shape[0]
     rc = lib().bm_gmres_solve(plan, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), nrhs, C.byref(o),
                               C.byref(st), _stream(stream))
+    stats = dict(iterations=st.iterations, outer_iterations=st.outer_iterations, rel_residual=st.rel_residual,
+                 ms_total=st.ms_total, ms_matvec=st.ms_matvec, status=st.status)
+    if raise_on_error:
+        _check(rc)
+    return stats
+
+
+def bm_net_create(hidden=32, seed=1):
+    h = C.c_void_p()
+    _check(lib().bm_net_create(int(hidden), int(seed), C.byref(h)))
+    return h
+
+
+def bm_net_params(net, set_values=None):
+    """Return the parameters (float32 numpy); optionally set them first."""
+    n = C.c_int()
+    _check(lib().bm_net_params(net, None, None, C.byref(n)))
+    if set_values is not None:
+        sv = np.ascontiguousarray(set_values, dtype=np.float32)
+        assert sv.size == n.value
+        _check(lib().bm_net_params(net, None, sv.ctypes.data_as(C.POINTER(C.c_float)), C.byref(n)))
+    out = np.zeros(n.value, dtype=np.float32)
+    _check(lib().bm_net_params(net, out.ctypes.data_as(C.POINTER(C.c_float)), None, C.byref(n)))
+    return out
+
+
+def bm_net_destroy(net):
+    lib().bm_net_destroy(net)
+
+
+def bm_precond_create(plan):
+    h = C.c_void_p()
+    _check(lib().bm_precond_create(plan, C.byref(h)))
+    return h
+
+
+def bm_precond_destroy(pc):
+    lib().bm_precond_destroy(pc)
+
+
+def bm_precond_apply(pc, net, r, z, stream=None):
+    _check(lib().bm_precond_apply(pc, net, C.c_void_p(r.data_ptr()), C.c_void_p(z.data_ptr()), _stream(stream)))
+
+
+def bm_precond_train_step(pc, net, R, E, lr=1e-3, want_grad=False, stream=None):
+    """R, E: (npairs, N) complex128 device tensors. Returns (loss, grad or None)."""
+    npairs = 1 if R.dim() == 1 else R.shape[0]
+    loss = C.c_double()
+    g = None
+    gp = None
+    if want_grad:
+        n = C.c_int()
+        _check(lib().bm_net_params(net, None, None, C.byref(n)))
+        g = np.zeros(n.value, dtype=np.float32)
+        gp = g.ctypes.data_as(C.POINTER(C.c_float))
+    _check(lib().bm_precond_train_step(pc, net, C.c_void_p(R.data_ptr()), C.c_void_p(E.data_ptr()), npairs,
+                                       float(lr), C.byref(loss), gp, _stream(stream)))
+    return loss.value, g
+
+
+def bm_residual_pair(plan, b, xstar, x, r, e, stream=None):
+    _check(lib().bm_residual_pair(plan, C.c_void_p(b.data_ptr()), C.c_void_p(xstar.data_ptr()),
+                                  C.c_void_p(x.data_ptr()), C.c_void_p(r.data_ptr()), C.c_void_p(e.data_ptr()),
+                                  _stream(stream)))
+
+
+def bm_fgmres_solve(plan, pc, net, b, x, tol=1e-6, restart=50, max_iter=1000, x0_given=False, refine=False,
+                    inner_restart=0, inner_tol=1e-4, stream=None, raise_on_error=True):
+    o = bm_gmres_opts_t()
+    o.tol = float(tol)
+    o.restart = int(restart)
+    o.max_iter = int(max_iter)
+    o.x0_given = int(bool(x0_given))
+    o.refine = int(bool(refine))
+    o.inner_restart = int(inner_restart)
+    o.inner_tol = float(inner_tol)
+    st = bm_gmres_stats_t()
+    nrhs = 1 if b.dim() == 1 else b.shape[0]
+    rc = lib().bm_fgmres_solve(plan, pc, net, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), nrhs,
+                               C.byref(o), C.byref(st), _stream(stream))
     stats = dict(iterations=st.iterations, outer_iterations=st.outer_iterations, rel_residual=st.rel_residual,
                  ms_total=st.ms_total, ms_matvec=st.ms_matvec, status=st.status)
     if raise_on_error:

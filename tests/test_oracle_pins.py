@@ -319,3 +319,48 @@ def test_rigid_sphere_solve_matches_mie(sphere_c1):
     th = np.arccos(np.clip(xs[:, 2] / np.linalg.norm(xs, axis=1), -1, 1))
     u = O.mie_total_surface(th, k, a)
     assert np.linalg.norm(xd - u) / np.linalg.norm(u) < 6e-3
+
+
+# ---------------------------------------------------------------- learned preconditioner network
+def test_network_gradient_matches_finite_differences():
+    """The oracle's plain backpropagation of the preconditioner loss agrees with central differences."""
+    rng = np.random.default_rng(3)
+    H = 8
+    N = 60
+    segs = [np.arange(0, 25), np.arange(25, 60)]
+    r = rng.normal(size=N) + 1j * rng.normal(size=N)
+    y = rng.normal(size=N) + 1j * rng.normal(size=N)
+    e = rng.normal(size=N) + 1j * rng.normal(size=N)
+    nW = O.net_layout(H)["n"]
+    w = rng.normal(size=nW) * 0.5
+    loss, g = O.net_loss_grad(w, H, r, y, e, segs)
+    h = 1e-6
+    for q in rng.choice(nW, size=25, replace=False):
+        wp, wm = w.copy(), w.copy()
+        wp[q] += h
+        wm[q] -= h
+        fd = (O.net_loss_grad(wp, H, r, y, e, segs)[0] - O.net_loss_grad(wm, H, r, y, e, segs)[0]) / (2 * h)
+        assert abs(fd - g[q]) < 1e-6 * max(1.0, abs(fd)), q
+
+
+def test_network_identity_start_and_scaling():
+    """With the identity output layer z = r for any input, and the loss is invariant to a common complex
+    scaling of (r, y, e) (features are normalised by the leaf mean)."""
+    rng = np.random.default_rng(4)
+    H = 6
+    L = O.net_layout(H)
+    w = rng.normal(size=L["n"])
+    w[L["W3"]:L["b3"]] = 0.0
+    w[L["b3"]:L["n"]] = [1, 0, 0, 0]
+    N = 30
+    segs = [np.arange(N)]
+    r = rng.normal(size=N) + 1j * rng.normal(size=N)
+    y = rng.normal(size=N) + 1j * rng.normal(size=N)
+    loss, _ = O.net_loss_grad(w, H, r, y, r, segs)
+    assert loss < 1e-28
+    w2 = rng.normal(size=L["n"]) * 0.3
+    e = rng.normal(size=N) + 1j * rng.normal(size=N)
+    c = 2.5 * np.exp(0.7j)
+    l1, _ = O.net_loss_grad(w2, H, r, y, e, segs)
+    l2, _ = O.net_loss_grad(w2, H, c * r, c * y, c * e, segs)
+    assert abs(l1 - l2) < 1e-12 * l1
