@@ -147,7 +147,9 @@ typedef struct {
   int precision;     /* FDA_PREC_FP64 or FDA_PREC_FP32: arithmetic of fda_matvec */
   int lowrank;       /* 1: factor compressed M2L matrices K~ = U^ V^ when rank < s/2 (Sec. 4.2) */
   int nrhs_max;      /* largest nrhs fda_matvec / bm_gmres_solve will be called with (>= 1) */
-  int reserved[5];
+  int m2l_tensor;    /* FP32 plans: M2L (and its low-rank stages) on the tensor cores (tcgen05, TF32):
+                        0 = FP32 FMA, 1 = TF32, 2 = 3xTF32 split (FP32-level accuracy) */
+  int reserved[4];
 } fda_config_t;
 
 /* Build every translation operator and the near-field matrices on the GPU (FP64 masters):
@@ -290,6 +292,11 @@ int bm_residual_pair(fda_plan_t* plan, const void* b, const void* xstar, const v
 /* Flexible GMRES (right preconditioner M above) with the options and results of bm_gmres_solve. */
 int bm_fgmres_solve(fda_plan_t* plan, bm_precond_t* precond, bm_net_t* net, const void* b, void* x, int nrhs,
                     const bm_gmres_opts_t* opts, bm_gmres_stats_t* stats, void* stream);
+
+/* Self-test of the tensor-core M2L kernel (diagnostic; no paper counterpart): one complex 64 x K
+ * product (K <= 1024) against an FP64 host product; *max_rel_err is the largest entrywise error relative to
+ * the sum of |a||x| over the row, *wait_failed is 1 when a bounded device wait gave up. Synchronous. */
+int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_failed);
 
 /* Last error message of the calling thread. */
 const char* fda_last_error(void);

@@ -1,0 +1,338 @@
+// M2L on the 5th-generation tensor cores (tcgen05, kind::tf32, accumulators in TMEM).
+//
+// A complex product y = A x (A: M x K, column-major complex) is one real GEMM on interleaved (re, im)
+// storage: with A^ the 2x2 real block expansion [[Ar, -Ai], [Ai, Ar]] of every entry, rows 2i / 2i+1 of
+// A^ x^ are the real / imaginary parts of y_i, and x^ is the complex vector read as 2K reals. Each CTA
+// computes one 128-row tile of A^ (64 complex rows) against up to 64 gathered columns (pairs x RHS):
+// the A^ tile is expanded on the fly, both operands are staged in shared memory in the canonical K-major
+// layout without swizzle (8-row x 16-byte core matrices), one thread issues tcgen05.mma (K = 8 per
+// instruction) and commits to an mbarrier, and the accumulator (128 lanes x 64 FP32 columns) is read back
+// with tcgen05.ld and scattered with atomics. With split = 1 every operand is split into TF32 hi + lo and
+// three products (hi hi + hi lo + lo hi) keep FP32 accuracy. Every wait is bounded: a wait that gives up
+// sets an error flag, and the kernel still releases its TMEM.
+#include "plan.cuh"
+
+namespace fda {
+
+#define TC_M 128       // real rows per tile (64 complex rows)
+#define TC_N 64        // real GEMM columns per tile (pairs x RHS)
+#define TC_KC 32       // real K per stage (16 complex)
+#define TC_NT 128      // threads per CTA (4 warps: one TMEM lane quadrant each)
+#define TC_WAIT_LIMIT (1 << 24)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// canonical K-major no-swizzle offset (bytes) of element (row, k) in a tile with kc real K columns
+__device__ __forceinline__ uint32_t kmaj_off(int row, int k, int kc) {
+  return (uint32_t)((row & 7) * 16 + (row >> 3) * (kc / 4) * 128 + (k & 3) * 4 + (k >> 2) * 128);
+}
+
+// shared-memory matrix descriptor: start address, leading (K-direction) and stride (8-row) byte offsets,
+// version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// instruction descriptor: D F32, A and B TF32, both K-major, N and M dimensions
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// bounded wait on the mbarrier phase; returns false when the limit is hit
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t a = smem_u32(bar);
+  for (int it = 0; it < TC_WAIT_LIMIT; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// Shared memory: [A hi | A lo | B hi | B lo] tiles + mbarrier + TMEM address holder
+struct TcSmem {
+  alignas(128) float a_hi[TC_M * TC_KC];
+  alignas(128) float a_lo[TC_M * TC_KC];
+  alignas(128) float b_hi[TC_N * TC_KC];
+  alignas(128) float b_lo[TC_N * TC_KC];
+  alignas(8) uint64_t bar;
+  uint32_t tmem;
+  int64_t sbase[TC_N], dbase[TC_N];
+  int srr[TC_N];
+};
+
+// Grouped gather-GEMM-scatter on the tensor cores; same units and modes as the SIMT k_m2l
+// (0: coef_out -> coef_in add, 1: coef_out -> mid store, 2: mid -> coef_in add). FP32 operands.
+template <int SPLIT>
+static __global__ void __launch_bounds__(TC_NT) k_m2l_tc(const GemmUnit* units, const float2* poolK,
+                                                         const float2* poolLR, const int64_t* psrc,
+                                                         const int64_t* ptgt, const int64_t* pmid,
+                                                         const float2* cout, float2* cin, float2* mid, int nrhs,
+                                                         int* err) {
+  extern __shared__ unsigned char smem_raw[];
+  TcSmem& S = *reinterpret_cast<TcSmem*>((((uintptr_t)smem_raw) + 127) & ~(uintptr_t)127);
+  const GemmUnit U = units[blockIdx.x];
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const float2* A = (U.mode == 0 ? poolK : poolLR) + U.a_off;
+  const float2* X = (U.mode == 2) ? mid : cout;
+  if (w == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
+                 "r"(TC_N));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (t == 0) {
+    mbar_init(&S.bar, 1);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = S.tmem;
+  const int ncols = U.p_count * nrhs;
+  const int Kr = 2 * U.K;  // real K
+  uint32_t phase = 0;
+  bool ok = true;
+  constexpr uint32_t IDESC = idesc_tf32(TC_M, TC_N);
+  for (int c0 = 0; c0 < ncols && ok; c0 += TC_N) {
+    if (t < TC_N) {
+      int c = c0 + t;
+      if (c < ncols) {
+        int p = c / nrhs, rr = c - p * nrhs;
+        int64_t pi = U.p_begin + p;
+        S.sbase[t] = (U.mode == 2) ? pmid[pi] : psrc[pi];
+        S.dbase[t] = (U.mode == 1) ? pmid[pi] : ptgt[pi];
+        S.srr[t] = rr;
+      } else {
+        S.sbase[t] = -1;
+        S.dbase[t] = -1;
+        S.srr[t] = 0;
+      }
+    }
+    __syncthreads();
+    int acc = 0;
+    for (int k0 = 0; k0 < Kr && ok; k0 += TC_KC) {
+      // A^ tile: complex rows m0 + i (i < 64), complex columns k0/2 + j (j < 16) -> 2x2 real blocks
+      for (int q = t; q < 64 * (TC_KC / 2); q += TC_NT) {
+        int i = q & 63, j = q >> 6;
+        int gi = U.m0 + i, gj = k0 / 2 + j;
+        float2 a = (gi < U.M && gj < U.K) ? A[gi + (int64_t)gj * U.M] : make_float2(0.f, 0.f);
+        float v[4] = {a.x, -a.y, a.y, a.x};  // (2i,2j), (2i,2j+1), (2i+1,2j), (2i+1,2j+1)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          int row = 2 * i + (u >> 1), col = 2 * j + (u & 1);
+          uint32_t off = kmaj_off(row, col, TC_KC) / 4;
+          float hi = tf32_round(v[u]);
+          S.a_hi[off] = hi;
+          if (SPLIT) S.a_lo[off] = tf32_round(v[u] - hi);
+        }
+      }
+      // B tile: gathered columns, K-major (each column's 16 complex = 32 reals contiguous in K)
+      for (int q = t; q < TC_N * (TC_KC / 2); q += TC_NT) {
+        int n = q % TC_N, j = q / TC_N;
+        int gj = k0 / 2 + j;
+        float2 x = (S.sbase[n] >= 0 && gj < U.K) ? X[(S.sbase[n] + gj) * nrhs + S.srr[n]] : make_float2(0.f, 0.f);
+        float v[2] = {x.x, x.y};
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          uint32_t off = kmaj_off(n, 2 * j + u, TC_KC) / 4;
+          float hi = tf32_round(v[u]);
+          S.b_hi[off] = hi;
+          if (SPLIT) S.b_lo[off] = tf32_round(v[u] - hi);
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (t == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t lbo = 128, sbo = (TC_KC / 4) * 128;
+#pragma unroll
+        for (int s = 0; s < TC_KC / 8; ++s) {
+          uint32_t ks = s * 256;  // two K-adjacent core matrices per instruction
+          uint64_t ah = smem_desc(smem_u32(S.a_hi) + ks, lbo, sbo);
+          uint64_t bh = smem_desc(smem_u32(S.b_hi) + ks, lbo, sbo);
+          tc_mma(tmem, ah, bh, IDESC, acc | (s > 0));
+          if (SPLIT) {
+            uint64_t al = smem_desc(smem_u32(S.a_lo) + ks, lbo, sbo);
+            uint64_t bl = smem_desc(smem_u32(S.b_lo) + ks, lbo, sbo);
+            tc_mma(tmem, ah, bl, IDESC, 1);
+            tc_mma(tmem, al, bh, IDESC, 1);
+          }
+        }
+        tc_commit(&S.bar);
+      }
+      acc = 1;
+      // every thread waits (bounded) for the MMAs before the tiles are overwritten; the outcome is made
+      // uniform across the CTA so that every thread leaves the loops together
+      bool mine = mbar_wait(&S.bar, phase);
+      ok = __syncthreads_and(mine ? 1 : 0) != 0;
+      if (!ok) {
+        if (t == 0) atomicExch(err, 1);
+        mbar_wait(&S.bar, phase);  // second bounded wait for the MMAs still in flight
+      }
+      phase ^= 1;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok && acc) {
+      // epilogue: warp w reads TMEM lanes 32w..32w+31 (real rows), 64 columns
+      const int row = 32 * w + lane;
+      const int ci = U.m0 + (row >> 1);
+      const int part = row & 1;
+#pragma unroll
+      for (int h = 0; h < TC_N / 32; ++h) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * w) << 16) + 32 * h, v);
+        if (ci < U.M) {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            int n = 32 * h + q;
+            if (S.dbase[n] < 0) continue;
+            int64_t d = (S.dbase[n] + ci) * nrhs + S.srr[n];
+            float* dst = (U.mode == 1) ? (float*)(mid + d) : (float*)(cin + d);
+            if (U.mode == 1)
+              dst[part] = v[q];
+            else
+              atomicAdd(dst + part, v[q]);
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  if (w == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N));
+  }
+}
+
+size_t m2l_tc_smem() { return sizeof(TcSmem) + 128; }
+
+int m2l_tc_launch(const GemmUnit* units, size_t nunits, const float2* poolK, const float2* poolLR,
+                  const int64_t* psrc, const int64_t* ptgt, const int64_t* pmid, const float2* cout, float2* cin,
+                  float2* mid, int nrhs, int split, int* err, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    FDA_CUDA(cudaFuncSetAttribute(k_m2l_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m2l_tc_smem()));
+    FDA_CUDA(cudaFuncSetAttribute(k_m2l_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m2l_tc_smem()));
+    attr = true;
+  }
+  for (size_t u0 = 0; u0 < nunits; u0 += 65535) {
+    unsigned n = (unsigned)std::min<size_t>(65535, nunits - u0);
+    if (split)
+      k_m2l_tc<1><<<n, TC_NT, m2l_tc_smem(), s>>>(units + u0, poolK, poolLR, psrc, ptgt, pmid, cout, cin, mid, nrhs,
+                                                   err);
+    else
+      k_m2l_tc<0><<<n, TC_NT, m2l_tc_smem(), s>>>(units + u0, poolK, poolLR, psrc, ptgt, pmid, cout, cin, mid, nrhs,
+                                                   err);
+    FDA_LAUNCH_CHECK();
+  }
+  return FDA_OK;
+}
+
+}  // namespace fda
+
+using namespace fda;
+
+// Self-test of the tensor-core path: one complex 64 x K product against FP32 FMA on the same data.
+extern "C" int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_failed) {
+  if (K < 1 || K > 1024 || !max_rel_err || !wait_failed) {
+    set_error("bad arguments");
+    return FDA_E_INVALID_ARG;
+  }
+  const int M = 64, P = 64;
+  std::vector<float2> hA((size_t)M * K), hX((size_t)K * P);
+  uint64_t st = 12345;
+  auto rnd = [&]() {
+    st = st * 6364136223846793005ull + 1442695040888963407ull;
+    return (float)((double)(st >> 11) / 9007199254740992.0 * 2.0 - 1.0);
+  };
+  for (auto& a : hA) a = make_float2(rnd(), rnd());
+  for (auto& x : hX) x = make_float2(rnd(), rnd());
+  DBuf<float2> dA, dX, dY, dmid;
+  DBuf<int64_t> src, tgt, pm;
+  DBuf<GemmUnit> du;
+  DBuf<int> err;
+  std::vector<int64_t> hs(P), ht(P), hm(P, -1);
+  for (int p = 0; p < P; ++p) hs[p] = (int64_t)p * K, ht[p] = (int64_t)p * M;
+  FDA_TRY(dA.upload(hA));
+  FDA_TRY(dX.upload(hX));
+  FDA_TRY(dY.alloc((size_t)M * P));
+  FDA_TRY(dY.zero());
+  FDA_TRY(dmid.alloc(1));
+  FDA_TRY(src.upload(hs));
+  FDA_TRY(tgt.upload(ht));
+  FDA_TRY(pm.upload(hm));
+  GemmUnit u{0, M, K, 0, P, 0, 0, 0};
+  FDA_TRY(du.upload(&u, 1));
+  FDA_TRY(err.alloc(1));
+  FDA_TRY(err.zero());
+  FDA_TRY(m2l_tc_launch(du.p, 1, dA.p, dA.p, src.p, tgt.p, pm.p, dX.p, dY.p, dmid.p, 1, split, err.p, 0));
+  FDA_CUDA(cudaDeviceSynchronize());
+  std::vector<float2> hY;
+  FDA_TRY(dY.download(hY));
+  int he = 0;
+  FDA_CUDA(cudaMemcpy(&he, err.p, sizeof(int), cudaMemcpyDeviceToHost));
+  double worst = 0;
+  for (int p = 0; p < P; ++p)
+    for (int i = 0; i < M; ++i) {
+      double rr = 0, ri = 0, nrm = 0;
+      for (int k = 0; k < K; ++k) {
+        float2 a = hA[i + (size_t)k * M], x = hX[(size_t)p * K + k];
+        rr += (double)a.x * x.x - (double)a.y * x.y;
+        ri += (double)a.x * x.y + (double)a.y * x.x;
+        nrm += sqrt(((double)a.x * a.x + (double)a.y * a.y) * ((double)x.x * x.x + (double)x.y * x.y));
+      }
+      float2 y = hY[(size_t)p * M + i];
+      double e = sqrt((y.x - rr) * (y.x - rr) + (y.y - ri) * (y.y - ri)) / nrm;
+      worst = std::max(worst, e);
+    }
+  *max_rel_err = worst;
+  *wait_failed = he;
+  return FDA_OK;
+}

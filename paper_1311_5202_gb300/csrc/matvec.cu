@@ -9,7 +9,13 @@
 // c[(slot + wedge * s + r) * nrhs + rhs]. One template serves FP64 (double2) and FP32 (float2) operators.
 #include "plan.cuh"
 
+#include <type_traits>
+
 namespace fda {
+
+int m2l_tc_launch(const GemmUnit* units, size_t nunits, const float2* poolK, const float2* poolLR,
+                  const int64_t* psrc, const int64_t* ptgt, const int64_t* pmid, const float2* cout, float2* cin,
+                  float2* mid, int nrhs, int split, int* err, cudaStream_t s);
 
 template <typename C>
 static __global__ void k_perm_in(const void* x, int io, const int64_t* perm, int64_t N, int nrhs, C* xt) {
@@ -462,6 +468,13 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
     for (int l = P->lmin; l <= P->lmax; ++l) {
       for (int st = 0; st < 2; ++st) {
         size_t nu = P->h_units[l][st].size();
+        if (nu && std::is_same<C, float2>::value && P->cfg.m2l_tensor > 0) {
+          FDA_TRY(m2l_tc_launch(P->units[l][st].p, nu, (const float2*)op.K.p, (const float2*)op.lr.p,
+                                P->pair_src.p, P->pair_tgt.p, P->pair_mid.p, (const float2*)cout.p, (float2*)cin.p,
+                                (float2*)mid.p, nrhs, P->cfg.m2l_tensor == 2 ? 1 : 0, P->tc_err.p, s));
+          nl += (int64_t)((nu + 65534) / 65535);
+          continue;
+        }
         for (size_t u0 = 0; u0 < nu; u0 += 65535) {
           unsigned n = (unsigned)std::min<size_t>(65535, nu - u0);
           k_m2l<C><<<n, 256, 0, s>>>(P->units[l][st].p + u0, op.K.p, op.lr.p, P->pair_src.p, P->pair_tgt.p,

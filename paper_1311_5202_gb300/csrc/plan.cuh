@@ -93,6 +93,7 @@ struct fda_plan_s {
   fda::DBuf<int> lev_s, lev_nw;  // per level: compressed dimension and wedge count
   int max_leaf = 1;
   int64_t launches = 0;          // kernels launched by the last matvec
+  fda::DBuf<int> tc_err;         // set by a tensor-core kernel whose bounded wait gave up
   cudaEvent_t* phase_ev = nullptr;  // when set, 9 events recorded between the matvec phases
   double setup_ms[8] = {0};
   double flops_m2l = 0, flops_m2m = 0, bytes_s2m_l2t = 0;

@@ -1083,7 +1083,7 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
     FDA_TRY(P->pair_tgt.upload(pt));
     FDA_TRY(P->pair_mid.upload(pm));
     int64_t u = 0;
-    const int CP = 32, TM = 64;
+    const int CP = 64, TM = 64;
     while (u < T->nm2l) {
       int64_t q = order[u];
       int l = T->h_m2l_info[6 * q];
@@ -1229,6 +1229,8 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
 
   // ---- 8. FP32 operator copies and workspaces
   const int nr = P->cfg.nrhs_max;
+  FDA_TRY(P->tc_err.alloc(1));
+  FDA_TRY(P->tc_err.zero());
   FDA_TRY(P->xt64.alloc((size_t)N * nr));
   FDA_TRY(P->yt64.alloc((size_t)N * nr));
   FDA_TRY(P->cout64.alloc((size_t)std::max<int64_t>(P->n_coef, 1) * nr));

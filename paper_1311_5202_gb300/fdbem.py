@@ -39,7 +39,7 @@ class FdaError(RuntimeError):
 
 class fda_config_t(C.Structure):
     _fields_ = [("eps", C.c_double), ("precision", C.c_int), ("lowrank", C.c_int), ("nrhs_max", C.c_int),
-                ("reserved", C.c_int * 5)]
+                ("m2l_tensor", C.c_int), ("reserved", C.c_int * 4)]
 
 
 class bm_gmres_opts_t(C.Structure):
@@ -117,6 +117,7 @@ _SIGS = [
                                    C.c_void_p]),
     ("bm_fgmres_solve", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                   C.POINTER(bm_gmres_opts_t), C.POINTER(bm_gmres_stats_t), C.c_void_p]),
+    ("fda_tc_selftest", C.c_int, [C.c_int, C.c_int, _dp, C.POINTER(C.c_int)]),
     ("fda_last_error", C.c_char_p, []),
 ]
 
@@ -222,12 +223,13 @@ def fda_tree_destroy(tree):
     lib().fda_tree_destroy(tree)
 
 
-def fda_precompute_translations(tree, eps, precision=FDA_PREC_FP64, lowrank=1, nrhs_max=1):
+def fda_precompute_translations(tree, eps, precision=FDA_PREC_FP64, lowrank=1, nrhs_max=1, m2l_tensor=0):
     cfg = fda_config_t()
     cfg.eps = float(eps)
     cfg.precision = int(precision)
     cfg.lowrank = int(lowrank)
     cfg.nrhs_max = int(nrhs_max)
+    cfg.m2l_tensor = int(m2l_tensor)
     h = C.c_void_p()
     _check(lib().fda_precompute_translations(tree, C.byref(cfg), C.byref(h)))
     return h
@@ -401,6 +403,13 @@ def bm_fgmres_solve(plan, pc, net, b, x, tol=1e-6, restart=50, max_iter=1000, x0
     return stats
 
 
+def fda_tc_selftest(K=64, split=0):
+    e = C.c_double()
+    wf = C.c_int()
+    _check(lib().fda_tc_selftest(int(K), int(split), C.byref(e), C.byref(wf)))
+    return e.value, wf.value
+
+
 def fda_last_error() -> str:
     return lib().fda_last_error().decode(errors="replace")
 
@@ -410,11 +419,11 @@ class Solver:
     """Problem + tree + plan with ordered destruction."""
 
     def __init__(self, nodes, elems, k, eps=1e-4, leaf_max=64, precision=FDA_PREC_FP64, lowrank=1, nrhs_max=1,
-                 alpha=None):
+                 alpha=None, m2l_tensor=0):
         self.k = float(k)
         self.prob = bm_problem_create(nodes, elems, k, alpha)
         self.tree = fda_build_tree(self.prob, leaf_max)
-        self.plan = fda_precompute_translations(self.tree, eps, precision, lowrank, nrhs_max)
+        self.plan = fda_precompute_translations(self.tree, eps, precision, lowrank, nrhs_max, m2l_tensor)
         self.N = 6 * int(np.asarray(elems).shape[0])
 
     def matvec(self, x, y, stream=None):

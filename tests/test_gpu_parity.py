@@ -219,3 +219,38 @@ def test_tiny_mesh_without_far_field():
         assert np.linalg.norm(yd.cpu().numpy() - yo) / np.linalg.norm(yo) < 1e-10
     finally:
         S.close()
+
+
+# ------------------------------------------------------------------ tensor-core M2L (tcgen05)
+@pytest.mark.parametrize("split", [0, 1])
+def test_tensor_core_selftest(split):
+    """One complex 64 x K product on the tensor cores against an FP64 host product (TF32: ~1e-4 of the row
+    scale; 3xTF32 split: FP32 level)."""
+    _need_gpu()
+    for K in (16, 111, 222):
+        err, wait_failed = fdbem.fda_tc_selftest(K, split)
+        assert wait_failed == 0
+        assert err < (1e-3 if split == 0 else 5e-6), (K, err)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_fda_matvec_tensor_core_m2l(mode):
+    """FP32 plan with M2L on the tensor cores (TF32, or 3xTF32 split) against the dense oracle (<= 3e-4)."""
+    _need_gpu()
+    mesh = inputs.icosphere(8, 0.5)
+    k = 20.0
+    S = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=1e-5, leaf_max=64, precision=fdbem.FDA_PREC_FP32,
+                     m2l_tensor=mode, nrhs_max=2)
+    try:
+        x = inputs.complex_gaussian(S.N, 5, nrhs=2)
+        xd = torch.from_numpy(x).to(DEV).contiguous()
+        yd = torch.empty_like(xd)
+        S.matvec(xd, yd)
+        torch.cuda.synchronize()
+        rows = inputs.sample_rows(S.N, 200, 7)
+        for r in range(2):
+            yo = _oracle_rows(mesh, k, x[r], rows)
+            err = np.linalg.norm(yd[r].cpu().numpy()[rows] - yo) / np.linalg.norm(yo)
+            assert err < 3e-4, (mode, r, err)
+    finally:
+        S.close()
