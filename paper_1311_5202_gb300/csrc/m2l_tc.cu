@@ -95,39 +95,53 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-// Shared memory: [A hi | A lo | B hi | B lo] tiles + mbarrier + TMEM address holder
+#define TC_MT 4      // row tiles per CTA (up to 256 complex rows)
+
+// Shared memory per pipeline buffer: A^ tiles (TC_MT x 128 x KC), B tile (64 x KC), hi and (split) lo parts
+template <int KC, int MTC, int SPLIT>
+struct TcBuf {
+  alignas(128) float a_hi[MTC][TC_M * KC];
+  alignas(128) float a_lo[MTC][SPLIT ? TC_M * KC : 4];
+  alignas(128) float b_hi[TC_N * KC];
+  alignas(128) float b_lo[SPLIT ? TC_N * KC : 4];
+};
+template <int KC, int MTC, int SPLIT>
 struct TcSmem {
-  alignas(128) float a_hi[TC_M * TC_KC];
-  alignas(128) float a_lo[TC_M * TC_KC];
-  alignas(128) float b_hi[TC_N * TC_KC];
-  alignas(128) float b_lo[TC_N * TC_KC];
-  alignas(8) uint64_t bar;
+  TcBuf<KC, MTC, SPLIT> buf[2];
+  alignas(8) uint64_t bar[2];
   uint32_t tmem;
   int64_t sbase[TC_N], dbase[TC_N];
   int srr[TC_N];
 };
 
-// Grouped gather-GEMM-scatter on the tensor cores; same units and modes as the SIMT k_m2l
-// (0: coef_out -> coef_in add, 1: coef_out -> mid store, 2: mid -> coef_in add). FP32 operands.
-template <int SPLIT>
+// Grouped gather-GEMM-scatter on the tensor cores; same units and modes as the FMA k_m2l
+// (0: coef_out -> coef_in add, 1: coef_out -> mid store, 2: mid -> coef_in add). A unit covers output rows
+// [m0, min(M, m0 + 256)); its gathered columns are staged once per K-chunk and reused by every row tile.
+// Two shared-memory buffers: the loads of chunk k+1 overlap the MMAs of chunk k.
+template <int SPLIT, int MTC>
 static __global__ void __launch_bounds__(TC_NT) k_m2l_tc(const GemmUnit* units, const float2* poolK,
                                                          const float2* poolLR, const int64_t* psrc,
                                                          const int64_t* ptgt, const int64_t* pmid,
                                                          const float2* cout, float2* cin, float2* mid, int nrhs,
                                                          int* err) {
+  constexpr int KC = SPLIT ? 16 : 32;  // real K per chunk
   extern __shared__ unsigned char smem_raw[];
-  TcSmem& S = *reinterpret_cast<TcSmem*>((((uintptr_t)smem_raw) + 127) & ~(uintptr_t)127);
+  typedef TcSmem<KC, MTC, SPLIT> Sm;
+  Sm& S = *reinterpret_cast<Sm*>((((uintptr_t)smem_raw) + 127) & ~(uintptr_t)127);
   const GemmUnit U = units[blockIdx.x];
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   const float2* A = (U.mode == 0 ? poolK : poolLR) + U.a_off;
   const float2* X = (U.mode == 2) ? mid : cout;
+  const int rows = min(U.M - U.m0, 64 * MTC);  // complex rows of this unit
+  const int MT = (rows + 63) / 64;
   if (w == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
-                 "r"(TC_N));
+                 "r"(TC_N * (MTC < 2 ? 2 : MTC)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (t == 0) {
-    mbar_init(&S.bar, 1);
+    mbar_init(&S.bar[0], 1);
+    mbar_init(&S.bar[1], 1);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -135,10 +149,53 @@ static __global__ void __launch_bounds__(TC_NT) k_m2l_tc(const GemmUnit* units, 
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = S.tmem;
   const int ncols = U.p_count * nrhs;
-  const int Kr = 2 * U.K;  // real K
-  uint32_t phase = 0;
+  const int Kr = 2 * U.K;
+  const int nk = (Kr + KC - 1) / KC;
+  uint32_t ph[2] = {0, 0};
   bool ok = true;
   constexpr uint32_t IDESC = idesc_tf32(TC_M, TC_N);
+
+  auto load_chunk = [&](int kc, TcBuf<KC, MTC, SPLIT>& B) {
+    const int k0 = kc * KC;
+    for (int mt = 0; mt < MT; ++mt)
+      for (int q = t; q < 64 * (KC / 2); q += TC_NT) {
+        int i = q & 63, j = q >> 6;
+        int gi = U.m0 + 64 * mt + i, gj = k0 / 2 + j;
+        float2 a = (gi < U.M && gj < U.K) ? A[gi + (int64_t)gj * U.M] : make_float2(0.f, 0.f);
+        float v[4] = {a.x, -a.y, a.y, a.x};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          uint32_t off = kmaj_off(2 * i + (u >> 1), 2 * j + (u & 1), KC) / 4;
+          float hi = tf32_round(v[u]);
+          B.a_hi[mt][off] = hi;
+          if (SPLIT) B.a_lo[mt][off] = tf32_round(v[u] - hi);
+        }
+      }
+    for (int q = t; q < TC_N * (KC / 2); q += TC_NT) {
+      int j = q % (KC / 2), n = q / (KC / 2);
+      int gj = k0 / 2 + j;
+      float2 x = (S.sbase[n] >= 0 && gj < U.K) ? X[(S.sbase[n] + gj) * nrhs + S.srr[n]] : make_float2(0.f, 0.f);
+      float v[2] = {x.x, x.y};
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        uint32_t off = kmaj_off(n, 2 * j + u, KC) / 4;
+        float hi = tf32_round(v[u]);
+        B.b_hi[off] = hi;
+        if (SPLIT) B.b_lo[off] = tf32_round(v[u] - hi);
+      }
+    }
+  };
+  auto wait_uniform = [&](int b) {
+    bool mine = mbar_wait(&S.bar[b], ph[b]);
+    bool all = __syncthreads_and(mine ? 1 : 0) != 0;
+    if (!all) {
+      if (t == 0) atomicExch(err, 1);
+      mbar_wait(&S.bar[b], ph[b]);  // second bounded wait for the MMAs still in flight
+    }
+    ph[b] ^= 1;
+    return all;
+  };
+
   for (int c0 = 0; c0 < ncols && ok; c0 += TC_N) {
     if (t < TC_N) {
       int c = c0 + t;
@@ -155,89 +212,73 @@ static __global__ void __launch_bounds__(TC_NT) k_m2l_tc(const GemmUnit* units, 
       }
     }
     __syncthreads();
-    int acc = 0;
-    for (int k0 = 0; k0 < Kr && ok; k0 += TC_KC) {
-      // A^ tile: complex rows m0 + i (i < 64), complex columns k0/2 + j (j < 16) -> 2x2 real blocks
-      for (int q = t; q < 64 * (TC_KC / 2); q += TC_NT) {
-        int i = q & 63, j = q >> 6;
-        int gi = U.m0 + i, gj = k0 / 2 + j;
-        float2 a = (gi < U.M && gj < U.K) ? A[gi + (int64_t)gj * U.M] : make_float2(0.f, 0.f);
-        float v[4] = {a.x, -a.y, a.y, a.x};  // (2i,2j), (2i,2j+1), (2i+1,2j), (2i+1,2j+1)
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          int row = 2 * i + (u >> 1), col = 2 * j + (u & 1);
-          uint32_t off = kmaj_off(row, col, TC_KC) / 4;
-          float hi = tf32_round(v[u]);
-          S.a_hi[off] = hi;
-          if (SPLIT) S.a_lo[off] = tf32_round(v[u] - hi);
-        }
-      }
-      // B tile: gathered columns, K-major (each column's 16 complex = 32 reals contiguous in K)
-      for (int q = t; q < TC_N * (TC_KC / 2); q += TC_NT) {
-        int n = q % TC_N, j = q / TC_N;
-        int gj = k0 / 2 + j;
-        float2 x = (S.sbase[n] >= 0 && gj < U.K) ? X[(S.sbase[n] + gj) * nrhs + S.srr[n]] : make_float2(0.f, 0.f);
-        float v[2] = {x.x, x.y};
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          uint32_t off = kmaj_off(n, 2 * j + u, TC_KC) / 4;
-          float hi = tf32_round(v[u]);
-          S.b_hi[off] = hi;
-          if (SPLIT) S.b_lo[off] = tf32_round(v[u] - hi);
-        }
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
+    load_chunk(0, S.buf[0]);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    bool pending[2] = {false, false};
+    for (int kc = 0; kc < nk; ++kc) {
+      const int b = kc & 1;
       if (t == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t lbo = 128, sbo = (TC_KC / 4) * 128;
+        const uint32_t lbo = 128, sbo = (KC / 4) * 128;
+        for (int mt = 0; mt < MT; ++mt) {
+          const uint32_t dt = tmem + 64 * mt;
 #pragma unroll
-        for (int s = 0; s < TC_KC / 8; ++s) {
-          uint32_t ks = s * 256;  // two K-adjacent core matrices per instruction
-          uint64_t ah = smem_desc(smem_u32(S.a_hi) + ks, lbo, sbo);
-          uint64_t bh = smem_desc(smem_u32(S.b_hi) + ks, lbo, sbo);
-          tc_mma(tmem, ah, bh, IDESC, acc | (s > 0));
-          if (SPLIT) {
-            uint64_t al = smem_desc(smem_u32(S.a_lo) + ks, lbo, sbo);
-            uint64_t bl = smem_desc(smem_u32(S.b_lo) + ks, lbo, sbo);
-            tc_mma(tmem, ah, bl, IDESC, 1);
-            tc_mma(tmem, al, bh, IDESC, 1);
+          for (int s8 = 0; s8 < KC / 8; ++s8) {
+            uint32_t ks = s8 * 256;
+            uint64_t ah = smem_desc(smem_u32(S.buf[b].a_hi[mt]) + ks, lbo, sbo);
+            uint64_t bh = smem_desc(smem_u32(S.buf[b].b_hi) + ks, lbo, sbo);
+            tc_mma(dt, ah, bh, IDESC, (kc > 0 || s8 > 0) ? 1 : 0);
+            if (SPLIT) {
+              uint64_t al = smem_desc(smem_u32(S.buf[b].a_lo[mt]) + ks, lbo, sbo);
+              uint64_t bl = smem_desc(smem_u32(S.buf[b].b_lo) + ks, lbo, sbo);
+              tc_mma(dt, ah, bl, IDESC, 1);
+              tc_mma(dt, al, bh, IDESC, 1);
+            }
           }
         }
-        tc_commit(&S.bar);
+        tc_commit(&S.bar[b]);
       }
-      acc = 1;
-      // every thread waits (bounded) for the MMAs before the tiles are overwritten; the outcome is made
-      // uniform across the CTA so that every thread leaves the loops together
-      bool mine = mbar_wait(&S.bar, phase);
-      ok = __syncthreads_and(mine ? 1 : 0) != 0;
-      if (!ok) {
-        if (t == 0) atomicExch(err, 1);
-        mbar_wait(&S.bar, phase);  // second bounded wait for the MMAs still in flight
+      pending[b] = true;
+      if (kc + 1 < nk) {
+        const int nb = b ^ 1;
+        if (pending[nb]) {  // chunk kc-1 used buffer nb: its MMAs must finish before it is overwritten
+          ok = wait_uniform(nb);
+          pending[nb] = false;
+          if (!ok) break;
+        }
+        load_chunk(kc + 1, S.buf[nb]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       }
-      phase ^= 1;
+      __syncthreads();
     }
+    for (int b = 0; b < 2; ++b)
+      if (pending[b]) {
+        bool r = wait_uniform(b);
+        ok = ok && r;
+      }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok && acc) {
-      // epilogue: warp w reads TMEM lanes 32w..32w+31 (real rows), 64 columns
-      const int row = 32 * w + lane;
-      const int ci = U.m0 + (row >> 1);
-      const int part = row & 1;
+    if (ok) {
+      const int row = 32 * w + lane;  // real row within a tile
+#pragma unroll 1
+      for (int mt = 0; mt < MT; ++mt) {
+        const int ci = U.m0 + 64 * mt + (row >> 1);
+        const int part = row & 1;
 #pragma unroll
-      for (int h = 0; h < TC_N / 32; ++h) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * w) << 16) + 32 * h, v);
-        if (ci < U.M) {
+        for (int h = 0; h < TC_N / 32; ++h) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(32 * w) << 16) + 64 * mt + 32 * h, v);
+          if (ci < U.M) {
 #pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            int n = 32 * h + q;
-            if (S.dbase[n] < 0) continue;
-            int64_t d = (S.dbase[n] + ci) * nrhs + S.srr[n];
-            float* dst = (U.mode == 1) ? (float*)(mid + d) : (float*)(cin + d);
-            if (U.mode == 1)
-              dst[part] = v[q];
-            else
-              atomicAdd(dst + part, v[q]);
+            for (int q = 0; q < 32; ++q) {
+              int n = 32 * h + q;
+              if (S.dbase[n] < 0) continue;
+              int64_t d = (S.dbase[n] + ci) * nrhs + S.srr[n];
+              if (U.mode == 1)
+                ((float*)(mid + d))[part] = v[q];
+              else
+                atomicAdd(((float*)(cin + d)) + part, v[q]);
+            }
           }
         }
       }
@@ -247,32 +288,50 @@ static __global__ void __launch_bounds__(TC_NT) k_m2l_tc(const GemmUnit* units, 
   }
   if (w == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N * (MTC < 2 ? 2 : MTC)));
   }
 }
 
-size_t m2l_tc_smem() { return sizeof(TcSmem) + 128; }
+template <int SPLIT, int MTC>
+static size_t tc_smem() {
+  return sizeof(TcSmem<SPLIT ? 16 : 32, MTC, SPLIT>) + 128;
+}
 
-int m2l_tc_launch(const GemmUnit* units, size_t nunits, const float2* poolK, const float2* poolLR,
-                  const int64_t* psrc, const int64_t* ptgt, const int64_t* pmid, const float2* cout, float2* cin,
-                  float2* mid, int nrhs, int split, int* err, cudaStream_t s) {
+template <int SPLIT, int MTC>
+static int tc_launch(const GemmUnit* units, size_t nunits, const float2* poolK, const float2* poolLR,
+                     const int64_t* psrc, const int64_t* ptgt, const int64_t* pmid, const float2* cout, float2* cin,
+                     float2* mid, int nrhs, int* err, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    FDA_CUDA(cudaFuncSetAttribute(k_m2l_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m2l_tc_smem()));
-    FDA_CUDA(cudaFuncSetAttribute(k_m2l_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m2l_tc_smem()));
+    FDA_CUDA(cudaFuncSetAttribute(k_m2l_tc<SPLIT, MTC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tc_smem<SPLIT, MTC>()));
     attr = true;
   }
   for (size_t u0 = 0; u0 < nunits; u0 += 65535) {
     unsigned n = (unsigned)std::min<size_t>(65535, nunits - u0);
-    if (split)
-      k_m2l_tc<1><<<n, TC_NT, m2l_tc_smem(), s>>>(units + u0, poolK, poolLR, psrc, ptgt, pmid, cout, cin, mid, nrhs,
-                                                   err);
-    else
-      k_m2l_tc<0><<<n, TC_NT, m2l_tc_smem(), s>>>(units + u0, poolK, poolLR, psrc, ptgt, pmid, cout, cin, mid, nrhs,
-                                                   err);
+    k_m2l_tc<SPLIT, MTC><<<n, TC_NT, tc_smem<SPLIT, MTC>(), s>>>(units + u0, poolK, poolLR, psrc, ptgt, pmid, cout,
+                                                                 cin, mid, nrhs, err);
     FDA_LAUNCH_CHECK();
   }
   return FDA_OK;
+}
+
+// max_rows: the largest number of complex output rows any unit of this launch covers (<= 256)
+int m2l_tc_launch(const GemmUnit* units, size_t nunits, const float2* poolK, const float2* poolLR,
+                  const int64_t* psrc, const int64_t* ptgt, const int64_t* pmid, const float2* cout, float2* cin,
+                  float2* mid, int nrhs, int split, int max_rows, int* err, cudaStream_t s) {
+  int mt = (max_rows + 63) / 64;
+#define TCL(S_, M_) return tc_launch<S_, M_>(units, nunits, poolK, poolLR, psrc, ptgt, pmid, cout, cin, mid, nrhs, err, s)
+  if (split) {
+    if (mt <= 1) TCL(1, 1);
+    if (mt <= 2) TCL(1, 2);
+    TCL(1, 4);
+  } else {
+    if (mt <= 1) TCL(0, 1);
+    if (mt <= 2) TCL(0, 2);
+    TCL(0, 4);
+  }
+#undef TCL
 }
 
 }  // namespace fda
@@ -312,7 +371,7 @@ extern "C" int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_
   FDA_TRY(du.upload(&u, 1));
   FDA_TRY(err.alloc(1));
   FDA_TRY(err.zero());
-  FDA_TRY(m2l_tc_launch(du.p, 1, dA.p, dA.p, src.p, tgt.p, pm.p, dX.p, dY.p, dmid.p, 1, split, err.p, 0));
+  FDA_TRY(m2l_tc_launch(du.p, 1, dA.p, dA.p, src.p, tgt.p, pm.p, dX.p, dY.p, dmid.p, 1, split, M, err.p, 0));
   FDA_CUDA(cudaDeviceSynchronize());
   std::vector<float2> hY;
   FDA_TRY(dY.download(hY));

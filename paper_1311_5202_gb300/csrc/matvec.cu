@@ -15,7 +15,7 @@ namespace fda {
 
 int m2l_tc_launch(const GemmUnit* units, size_t nunits, const float2* poolK, const float2* poolLR,
                   const int64_t* psrc, const int64_t* ptgt, const int64_t* pmid, const float2* cout, float2* cin,
-                  float2* mid, int nrhs, int split, int* err, cudaStream_t s);
+                  float2* mid, int nrhs, int split, int max_rows, int* err, cudaStream_t s);
 
 template <typename C>
 static __global__ void k_perm_in(const void* x, int io, const int64_t* perm, int64_t N, int nrhs, C* xt) {
@@ -468,11 +468,13 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
     for (int l = P->lmin; l <= P->lmax; ++l) {
       for (int st = 0; st < 2; ++st) {
         size_t nu = P->h_units[l][st].size();
-        if (nu && std::is_same<C, float2>::value && P->cfg.m2l_tensor > 0) {
-          FDA_TRY(m2l_tc_launch(P->units[l][st].p, nu, (const float2*)op.K.p, (const float2*)op.lr.p,
+        size_t ntu = P->h_tc_units[l][st].size();
+        if (ntu && std::is_same<C, float2>::value && P->cfg.m2l_tensor > 0) {
+          FDA_TRY(m2l_tc_launch(P->tc_units[l][st].p, ntu, (const float2*)op.K.p, (const float2*)op.lr.p,
                                 P->pair_src.p, P->pair_tgt.p, P->pair_mid.p, (const float2*)cout.p, (float2*)cin.p,
-                                (float2*)mid.p, nrhs, P->cfg.m2l_tensor == 2 ? 1 : 0, P->tc_err.p, s));
-          nl += (int64_t)((nu + 65534) / 65535);
+                                (float2*)mid.p, nrhs, P->cfg.m2l_tensor == 2 ? 1 : 0, P->tc_max_rows[l][st],
+                                P->tc_err.p, s));
+          nl += (int64_t)((ntu + 65534) / 65535);
           continue;
         }
         for (size_t u0 = 0; u0 < nu; u0 += 65535) {

@@ -79,6 +79,10 @@ struct fda_plan_s {
   // M2L
   std::vector<fda::GemmUnit> h_units[FDA_MAXLEV][2];  // [level][0: dense or V^ stage, 1: U^ stage]
   fda::DBuf<fda::GemmUnit> units[FDA_MAXLEV][2];
+  // tensor-core units: one per (group, pair chunk, block of up to 256 output rows)
+  std::vector<fda::GemmUnit> h_tc_units[FDA_MAXLEV][2];
+  fda::DBuf<fda::GemmUnit> tc_units[FDA_MAXLEV][2];
+  int tc_max_rows[FDA_MAXLEV][2] = {{0}};
   fda::DBuf<int64_t> pair_src, pair_tgt;  // coefficient indices (slot + wedge * s)
   fda::DBuf<int64_t> pair_mid;            // low-rank intermediate index per pair (-1 if dense)
   int64_t n_pairs = 0, n_mid = 0;

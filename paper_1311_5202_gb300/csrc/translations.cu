@@ -1094,6 +1094,22 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
       const LevelOps& L = P->lev[l];
       for (int64_t p0 = u; p0 < v; p0 += CP) {
         int pc = (int)std::min<int64_t>(CP, v - p0);
+        // tensor-core units: up to 256 output rows each
+        if (o.rank > 0) {
+          for (int m0 = 0; m0 < o.rank; m0 += 256) {
+            P->h_tc_units[l][0].push_back({o.v_off, o.rank, L.s, p0, pc, m0, 1, 0});
+            P->tc_max_rows[l][0] = std::max(P->tc_max_rows[l][0], std::min(256, o.rank - m0));
+          }
+          for (int m0 = 0; m0 < L.s; m0 += 256) {
+            P->h_tc_units[l][1].push_back({o.u_off, L.s, o.rank, p0, pc, m0, 2, 0});
+            P->tc_max_rows[l][1] = std::max(P->tc_max_rows[l][1], std::min(256, L.s - m0));
+          }
+        } else {
+          for (int m0 = 0; m0 < L.s; m0 += 256) {
+            P->h_tc_units[l][0].push_back({o.k_off, L.s, L.s, p0, pc, m0, 0, 0});
+            P->tc_max_rows[l][0] = std::max(P->tc_max_rows[l][0], std::min(256, L.s - m0));
+          }
+        }
         if (o.rank > 0) {
           for (int m0 = 0; m0 < o.rank; m0 += TM)
             P->h_units[l][0].push_back({o.v_off, o.rank, L.s, p0, pc, m0, 1, 0});
@@ -1106,7 +1122,10 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
       u = v;
     }
     for (int l = 0; l < FDA_MAXLEV; ++l)
-      for (int st = 0; st < 2; ++st) FDA_TRY(P->units[l][st].upload(P->h_units[l][st]));
+      for (int st = 0; st < 2; ++st) {
+        FDA_TRY(P->units[l][st].upload(P->h_units[l][st]));
+        FDA_TRY(P->tc_units[l][st].upload(P->h_tc_units[l][st]));
+      }
   }
 
   // ---- 7. near field: corrections (Eq. kcorrection) and direct blocks
