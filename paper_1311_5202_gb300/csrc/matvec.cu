@@ -18,6 +18,10 @@ int m2l_tc_launch(const GemmUnit* units, size_t nunits, const float2* poolK, con
                   float2* mid, int nrhs, int split, int max_rows, int* err, cudaStream_t s);
 
 template <typename C>
+int near_stream(fda_plan_s* P, const C* B, const C* cval, const C* xt, C* yt, int nrhs, cudaStream_t s,
+                int64_t* launches);
+
+template <typename C>
 static __global__ void k_perm_in(const void* x, int io, const int64_t* perm, int64_t N, int nrhs, C* xt) {
   int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= N * nrhs) return;
@@ -397,7 +401,9 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
   FDA_LAUNCH_CHECK();
   ev(1);
   // near field
-  if (P->n_near_tleaf > 0) {
+  if (P->n_near_tleaf > 0 && P->near_max_nr <= 256) {
+    FDA_TRY(near_stream<C>(P, op.near.p, op.corr.p, xt.p, yt.p, nrhs, s, &nl));
+  } else if (P->n_near_tleaf > 0) {
     static bool attr_set = false;
     if (!attr_set) {
       FDA_CUDA(cudaFuncSetAttribute(k_near<double2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,

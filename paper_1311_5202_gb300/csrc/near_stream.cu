@@ -1,0 +1,317 @@
+// Near-field apply (the direct and corrected near sum of Eq. kcorrection) as a bulk-copy stream.
+//
+// Every target leaf's direct blocks form one contiguous column-major matrix (rows: the leaf's points,
+// columns: the points of its direct source boxes), 4-entry aligned in HBM. A persistent grid of CTAs
+// (two per SM) owns balanced, contiguous ranges of target leaves. In each CTA one producer thread walks
+// the leaves' matrices chunk by chunk (whole columns, <= 16 KB) and issues cp.async.bulk copies into a
+// ring of four shared-memory stages, each guarded by a "full" mbarrier (transaction bytes) and an
+// "empty" mbarrier (one arrival per consumer warp). Eight consumer warps gather the leaf's source
+// densities into shared memory once per column window (one index per column, a single parallel pass),
+// then read each landed stage: thread (i, g) takes row i and columns g, g + G, ... (G = 256 / rows), so
+// consecutive threads read consecutive shared-memory words. Group partial sums are reduced per row; the
+// correction entries that fall outside the leaf's direct blocks (a CSR per row, one contiguous range per
+// leaf) are spread over all consumer threads and summed per row in shared memory. Every wait is bounded: a wait that gives up sets the error flag, the kernel runs to its end
+// without touching other memory, and the producer still waits (bounded) for its own copies in flight.
+#include "plan.cuh"
+
+namespace fda {
+
+#define NS_STAGES 4
+#define NS_STAGE_BYTES 16384
+#define NS_CONS 256            // consumer threads (8 warps)
+#define NS_NT (NS_CONS + 32)   // + one producer warp
+#define NS_WAIT_LIMIT (1 << 24)
+
+__device__ __forceinline__ uint32_t ns_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool ns_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = ns_smem(bar);
+  for (int it = 0; it < NS_WAIT_LIMIT; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void ns_arrive(uint64_t* bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(ns_smem(bar)) : "memory");
+}
+
+__device__ __forceinline__ void ns_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(ns_smem(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16), completion on an mbarrier
+__device__ __forceinline__ void ns_bulk(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   ns_smem(dst)),
+               "l"(src), "r"(bytes), "r"(ns_smem(bar))
+               : "memory");
+}
+
+// barrier among the consumer warps only (the producer warp never joins it)
+__device__ __forceinline__ void ns_cons_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NS_CONS) : "memory"); }
+
+template <typename C, int NR>
+struct NsLayout {
+  static constexpr int E = sizeof(C);
+  static constexpr int XBYTES = (E * NR >= 64) ? 16384 : 32768;
+  static constexpr int XW = (XBYTES / (NR * E)) & ~1;  // columns per density window (even)
+  static constexpr size_t ring = (size_t)NS_STAGES * NS_STAGE_BYTES;
+  static constexpr size_t xs = ring;
+  static constexpr size_t red = xs + (size_t)XW * NR * E;
+  static constexpr size_t cor = red + (size_t)NS_CONS * NR * E;
+  static constexpr size_t crow = cor + (size_t)NS_CONS * NR * E;
+  static constexpr size_t bars = crow + (NS_CONS + 8) * sizeof(int);
+  static constexpr size_t total = bars + 2 * NS_STAGES * sizeof(uint64_t) + 128;  // + alignment slack
+};
+
+// columns per chunk: whole columns, an even count, at most one stage
+__device__ __forceinline__ int ns_cpc(int nr, int E) { return max(2, (NS_STAGE_BYTES / (nr * E)) & ~1); }
+
+template <typename C, int NR>
+static __global__ void __launch_bounds__(NS_NT, 2) k_near_stream(
+    const int32_t* part, const int64_t* tleaf, const int64_t* pb, const int64_t* pe, const int64_t* nbase,
+    const int32_t* ncolv, const int64_t* xbase, const int32_t* xcol, const C* B, const int64_t* cptr,
+    const int32_t* ccol, const C* cval, const C* xt, C* yt, int nrhs, int r0, int rc, int* err) {
+  typedef NsLayout<C, NR> Ly;
+  typedef decltype(xt[0].x) R;
+  constexpr int E = Ly::E, XW = Ly::XW;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm = (unsigned char*)((((uintptr_t)smem_raw) + 127) & ~(uintptr_t)127);
+  unsigned char* ring = sm;
+  C* xs = (C*)(sm + Ly::xs);
+  C* red = (C*)(sm + Ly::red);
+  C* cor = (C*)(sm + Ly::cor);
+  int* crow = (int*)(sm + Ly::crow);
+  uint64_t* full = (uint64_t*)(sm + Ly::bars);
+  uint64_t* empty = full + NS_STAGES;
+  const int t = threadIdx.x;
+  if (t == 0) {
+    for (int s = 0; s < NS_STAGES; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(ns_smem(&full[s])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(ns_smem(&empty[s])), "r"(NS_CONS / 32));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  const int u0 = part[blockIdx.x], u1 = part[blockIdx.x + 1];
+
+  if (t >= NS_CONS) {
+    // ---------------- producer
+    if (t == NS_CONS) {
+      int it = 0;
+      bool ok = true;
+      for (int u = u0; u < u1 && ok; ++u) {
+        const int64_t L = tleaf[u];
+        const int nr = (int)(pe[L] - pb[L]);
+        const int ncol = ncolv[u];
+        const unsigned char* src = (const unsigned char*)(B + nbase[u]);
+        const int cpc = ns_cpc(nr, E);
+        for (int c = 0; c < ncol;) {
+          const int wend = min(ncol, (c / XW + 1) * XW);
+          const int cc = min(cpc, wend - c);
+          const int st = it % NS_STAGES;
+          if (it >= NS_STAGES && !ns_wait(&empty[st], ((it / NS_STAGES) - 1) & 1)) {
+            atomicExch(err, 1);
+            ok = false;
+            break;
+          }
+          const uint32_t bytes = (uint32_t)(((int64_t)cc * nr * E + 15) & ~(int64_t)15);
+          ns_expect_tx(&full[st], bytes);
+          ns_bulk(ring + (size_t)st * NS_STAGE_BYTES, src + (int64_t)c * nr * E, bytes, &full[st]);
+          c += cc;
+          ++it;
+        }
+      }
+      // the last fill of every stage has landed before the CTA's shared memory is released
+      for (int j = max(0, it - NS_STAGES); j < it; ++j) ns_wait(&full[j % NS_STAGES], (j / NS_STAGES) & 1);
+    }
+    return;
+  }
+
+  // ---------------- consumers
+  const int lane = t & 31;
+  int it = 0;
+  bool failed = false;
+  for (int u = u0; u < u1; ++u) {
+    const int64_t L = tleaf[u];
+    const int64_t tb = pb[L];
+    const int nr = (int)(pe[L] - tb);
+    const int ncol = ncolv[u];
+    const int64_t xb = xbase[u];
+    const int cpc = ns_cpc(nr, E);
+    const int G = NS_CONS / nr;
+    const int i = t % nr, g = t / nr;
+    const bool act = g < G;
+    // correction entries outside the direct blocks. A leaf's rows are consecutive, so its entries are one
+    // CSR range: every thread takes entries, finds the row by binary search over the leaf's row pointers
+    // and adds into shared memory (one parallel pass instead of a chain per row).
+    const int64_t cb = cptr[tb];
+    for (int q = t; q <= nr; q += NS_CONS) crow[q] = (int)(cptr[tb + q] - cb);
+    for (int q = t; q < nr * NR; q += NS_CONS) cor[q] = mk((R)0, (R)0);
+    ns_cons_sync();
+    const int ncor = crow[nr];
+    for (int e0 = 0; e0 < ncor; e0 += 4 * NS_CONS) {
+      // all loads first (4 entries per thread), then the density gathers, then per-entry products
+      C v[4];
+      int col[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int e = e0 + j * NS_CONS + t;
+        v[j] = e < ncor ? cval[cb + e] : mk((R)0, (R)0);
+        col[j] = e < ncor ? ccol[cb + e] : 0;
+      }
+      C xv[4][NR];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int q = 0; q < NR; ++q)
+          xv[j][q] = (e0 + j * NS_CONS + t < ncor && q < rc) ? xt[(int64_t)col[j] * nrhs + r0 + q] : mk((R)0, (R)0);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int e = e0 + j * NS_CONS + t;
+        int row = -1;  // largest r with crow[r] <= e (rows are non-decreasing along the lanes)
+        if (e < ncor) {
+          int lo = 0, hi = nr;
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (crow[mid] <= e) lo = mid; else hi = mid;
+          }
+          row = lo;
+        }
+        C a[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          a[q] = mk((R)0, (R)0);
+          cfma(a[q], v[j], xv[j][q]);
+        }
+        // segmented inclusive scan over lanes of equal row; the last lane of each segment holds its sum
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const int ro = __shfl_up_sync(0xffffffffu, row, off);
+#pragma unroll
+          for (int q = 0; q < NR; ++q) {
+            const R ax = __shfl_up_sync(0xffffffffu, a[q].x, off);
+            const R ay = __shfl_up_sync(0xffffffffu, a[q].y, off);
+            if (lane >= off && ro == row) {
+              a[q].x += ax;
+              a[q].y += ay;
+            }
+          }
+        }
+        const int rn = __shfl_down_sync(0xffffffffu, row, 1);
+        if (row >= 0 && (lane == 31 || rn != row)) {
+#pragma unroll
+          for (int q = 0; q < NR; ++q)
+            if (q < rc) {
+              atomicAdd(&cor[row * NR + q].x, a[q].x);
+              atomicAdd(&cor[row * NR + q].y, a[q].y);
+            }
+        }
+      }
+    }
+    C acc[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) acc[q] = mk((R)0, (R)0);
+    for (int wb = 0; wb < ncol; wb += XW) {
+      const int we = min(ncol, wb + XW);
+      ns_cons_sync();  // readers of the previous window are done
+      for (int c = wb + t; c < we; c += NS_CONS) {
+        const C* xp = xt + (int64_t)xcol[xb + c] * nrhs + r0;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) xs[(c - wb) * NR + q] = (q < rc) ? xp[q] : mk((R)0, (R)0);
+      }
+      ns_cons_sync();
+      for (int c = wb; c < we;) {
+        const int cc = min(cpc, we - c);
+        const int st = it % NS_STAGES;
+        if (!failed && !ns_wait(&full[st], (it / NS_STAGES) & 1)) {
+          failed = true;
+          atomicExch(err, 1);
+        }
+        if (!failed && act) {
+          const C* Bs = (const C*)(ring + (size_t)st * NS_STAGE_BYTES) + i;
+          const C* xw = xs + (c - wb) * NR;
+          int cl = g;
+          for (; cl + 3 * G < cc; cl += 4 * G) {
+            const C b0 = Bs[cl * nr], b1 = Bs[(cl + G) * nr], b2 = Bs[(cl + 2 * G) * nr], b3 = Bs[(cl + 3 * G) * nr];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
+              cfma(acc[q], b0, xw[cl * NR + q]);
+              cfma(acc[q], b1, xw[(cl + G) * NR + q]);
+              cfma(acc[q], b2, xw[(cl + 2 * G) * NR + q]);
+              cfma(acc[q], b3, xw[(cl + 3 * G) * NR + q]);
+            }
+          }
+          for (; cl < cc; cl += G) {
+            const C bv = Bs[cl * nr];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) cfma(acc[q], bv, xw[cl * NR + q]);
+          }
+        }
+        __syncwarp();
+        if (lane == 0) ns_arrive(&empty[st]);
+        c += cc;
+        ++it;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NR; ++q) red[t * NR + q] = act ? acc[q] : mk((R)0, (R)0);
+    ns_cons_sync();
+    for (int q = t; q < nr * rc; q += NS_CONS) {
+      const int r = q / rc, rr = q - r * rc;
+      C s = cor[r * NR + rr];
+      for (int gg = 0; gg < G; ++gg) s = cadd(s, red[(gg * nr + r) * NR + rr]);
+      yt[(tb + r) * nrhs + r0 + rr] = s;
+    }
+    ns_cons_sync();  // red and cor are rewritten by the next leaf
+  }
+}
+
+template <typename C, int NR>
+static int near_stream_t(fda_plan_s* P, const C* B, const C* cval, const C* xt, C* yt, int nrhs, cudaStream_t s,
+                         int64_t* launches) {
+  typedef NsLayout<C, NR> Ly;
+  static bool attr = false;
+  if (!attr) {
+    FDA_CUDA(cudaFuncSetAttribute(k_near_stream<C, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Ly::total));
+    attr = true;
+  }
+  fda_tree_s* T = P->tree;
+  for (int r0 = 0; r0 < nrhs; r0 += NR) {
+    const int rc = std::min(NR, nrhs - r0);
+    k_near_stream<C, NR><<<(unsigned)P->near_grid, NS_NT, Ly::total, s>>>(
+        P->near_part.p, P->near_tleaf.p, T->pb.p, T->pe.p, P->near_nbase.p, P->near_ncol.p, P->near_xbase.p,
+        P->near_xcol.p, B, P->corr_ptr.p, P->corr_col.p, cval, xt, yt, nrhs, r0, rc, P->tc_err.p);
+    FDA_LAUNCH_CHECK();
+    ++*launches;
+  }
+  return FDA_OK;
+}
+
+template <typename C>
+int near_stream(fda_plan_s* P, const C* B, const C* cval, const C* xt, C* yt, int nrhs, cudaStream_t s,
+                int64_t* launches) {
+  if (P->near_max_nr > NS_CONS) {
+    set_error("near-field stream needs leaves of at most %d points (got %d)", NS_CONS, P->near_max_nr);
+    return FDA_E_INVALID_ARG;
+  }
+  if (nrhs == 1) return near_stream_t<C, 1>(P, B, cval, xt, yt, nrhs, s, launches);
+  return near_stream_t<C, 4>(P, B, cval, xt, yt, nrhs, s, launches);
+}
+
+template int near_stream<float2>(fda_plan_s*, const float2*, const float2*, const float2*, float2*, int,
+                                 cudaStream_t, int64_t*);
+template int near_stream<double2>(fda_plan_s*, const double2*, const double2*, const double2*, double2*, int,
+                                  cudaStream_t, int64_t*);
+
+}  // namespace fda

@@ -67,6 +67,12 @@ struct fda_plan_s {
   fda::DBuf<int64_t> near_src;       // block -> source box
   fda::DBuf<int64_t> near_off;       // block -> entry offset
   fda::DBuf<int64_t> near_coff;      // block -> first column within its target leaf's matrix
+  fda::DBuf<int64_t> near_nbase;     // target leaf -> first entry of its matrix (4-entry aligned)
+  fda::DBuf<int32_t> near_ncol;      // target leaf -> number of columns
+  fda::DBuf<int64_t> near_xbase;     // target leaf -> first entry of its column list in near_xcol
+  fda::DBuf<int32_t> near_xcol;      // column -> tree position of its source point
+  fda::DBuf<int32_t> near_part;      // persistent CTA -> first target leaf (grid + 1 entries)
+  int near_grid = 0, near_max_nr = 0;
   int64_t corr_merged = 0;           // correction entries folded into the direct blocks
   int64_t n_near_tleaf = 0, n_blocks = 0, near_entries = 0;
   fda::DBuf<int64_t> corr_ptr;       // tree-order CSR of the correction matrix

@@ -1173,33 +1173,77 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
       }
     }
     std::sort(blocks.begin(), blocks.end());
-    std::vector<int64_t> tleaf, tptr, src, boff, coff;
+    // Each target leaf's blocks form one column-major matrix whose first entry is 4-entry aligned (32 B in
+    // FP32), so the streaming kernel can fetch it with bulk copies; the gaps are zero.
+    std::vector<int64_t> tleaf, tptr, src, boff, coff, nbase, xbase;
+    std::vector<int32_t> ncolv, xcol;
     std::vector<NearJob> jobs;
-    int64_t eoff = 0, ccur = 0;
+    int64_t eoff = 0, ccur = 0, entries = 0;
+    int max_nr = 0;
     for (size_t q = 0; q < blocks.size(); ++q) {
-      if (q == 0 || blocks[q].first != blocks[q - 1].first) {
-        tleaf.push_back(blocks[q].first);
-        tptr.push_back((int64_t)q);
-        ccur = 0;
-      }
       int64_t L = blocks[q].first, Q = blocks[q].second;
+      if (q == 0 || L != blocks[q - 1].first) {
+        if (q > 0) ncolv.push_back((int32_t)ccur);
+        eoff = (eoff + 3) & ~(int64_t)3;
+        tleaf.push_back(L);
+        tptr.push_back((int64_t)q);
+        nbase.push_back(eoff);
+        xbase.push_back((int64_t)xcol.size());
+        ccur = 0;
+        max_nr = std::max(max_nr, (int)(T->h_pe[L] - T->h_pb[L]));
+      }
       src.push_back(Q);
       boff.push_back(eoff);
       coff.push_back(ccur);
+      for (int64_t j = T->h_pb[Q]; j < T->h_pe[Q]; ++j) xcol.push_back((int32_t)j);
       ccur += T->h_pe[Q] - T->h_pb[Q];
       jobs.push_back({T->h_pb[L], T->h_pe[L], T->h_pb[Q], T->h_pe[Q], eoff});
-      eoff += (T->h_pe[L] - T->h_pb[L]) * (T->h_pe[Q] - T->h_pb[Q]);
+      int64_t ne = (T->h_pe[L] - T->h_pb[L]) * (T->h_pe[Q] - T->h_pb[Q]);
+      eoff += ne;
+      entries += ne;
     }
+    if (!blocks.empty()) ncolv.push_back((int32_t)ccur);
     tptr.push_back((int64_t)blocks.size());
+    xbase.push_back((int64_t)xcol.size());
+    const int64_t alloc_entries = ((eoff + 3) & ~(int64_t)3) + 4;
     P->n_near_tleaf = (int64_t)tleaf.size();
     P->n_blocks = (int64_t)blocks.size();
-    P->near_entries = eoff;
+    P->near_entries = entries;
+    P->near_max_nr = max_nr;
+    // balanced partition of the target leaves over the streaming kernel's persistent CTAs
+    {
+      int dev = 0, nsm = 1;
+      FDA_CUDA(cudaGetDevice(&dev));
+      FDA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+      const int64_t nt = (int64_t)tleaf.size();
+      int grid = (int)std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)nsm, nt));
+      std::vector<int64_t> cost(nt + 1, 0);
+      for (int64_t u = 0; u < nt; ++u) {
+        int64_t nr = T->h_pe[tleaf[u]] - T->h_pb[tleaf[u]];
+        cost[u + 1] = cost[u] + nr * ncolv[u] + 64 * nr + 256;  // entries + per-row and per-leaf overheads
+      }
+      std::vector<int32_t> part(grid + 1, 0);
+      int64_t u = 0;
+      for (int b = 1; b < grid; ++b) {
+        int64_t target = cost[nt] * b / grid;
+        while (u < nt && cost[u + 1] <= target) ++u;
+        part[b] = (int32_t)u;
+      }
+      part[grid] = (int32_t)nt;
+      P->near_grid = grid;
+      FDA_TRY(P->near_part.upload(part));
+    }
     FDA_TRY(P->near_tleaf.upload(tleaf));
     FDA_TRY(P->near_tptr.upload(tptr));
     FDA_TRY(P->near_src.upload(src));
     FDA_TRY(P->near_off.upload(boff));
     FDA_TRY(P->near_coff.upload(coff));
-    FDA_TRY(P->op64.near.alloc(std::max<int64_t>(eoff, 1)));
+    FDA_TRY(P->near_nbase.upload(nbase));
+    FDA_TRY(P->near_ncol.upload(ncolv));
+    FDA_TRY(P->near_xbase.upload(xbase));
+    FDA_TRY(P->near_xcol.upload(xcol));
+    FDA_TRY(P->op64.near.alloc(alloc_entries));
+    FDA_TRY(P->op64.near.zero());
     DBuf<NearJob> dj;
     FDA_TRY(dj.upload(jobs));
     for (size_t b0 = 0; b0 < jobs.size(); b0 += 65535) {
