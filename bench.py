@@ -163,6 +163,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip training/using the learned preconditioner")
     ap.add_argument("--eps", type=float, default=None)
+    ap.add_argument("--m2l-tensor", type=int, default=1, choices=[0, 1, 2],
+                    help="M2L of the FP32 form: 0 FP32 FMA, 1 TF32 tensor cores, 2 3xTF32 tensor cores")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -186,7 +188,7 @@ def main():
     nrhs = args.nrhs
     t0 = time.perf_counter()
     S = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=eps, leaf_max=spec["leaf"], precision=fdbem.FDA_PREC_FP32,
-                     lowrank=1, nrhs_max=nrhs)
+                     lowrank=1, nrhs_max=nrhs, m2l_tensor=args.m2l_tensor)
     setup_s = time.perf_counter() - t0
     info = S.info()
     X = inputs.complex_gaussian(N, 20131120, nrhs=nrhs if nrhs > 1 else None)
@@ -270,7 +272,7 @@ def main():
         # coupling alpha = -i/k: clustered spectrum, the iteration counts the paper reports
         t2 = time.perf_counter()
         S2 = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=eps, leaf_max=spec["leaf"], precision=fdbem.FDA_PREC_FP32,
-                          lowrank=1, nrhs_max=1, alpha=-1j / k)
+                          lowrank=1, nrhs_max=1, alpha=-1j / k, m2l_tensor=args.m2l_tensor)
         setup2 = time.perf_counter() - t2
         solve_alt = solves(S2, [("fp64", dict(refine=False)), ("mixed", dict(refine=True, inner_tol=1e-3))], 100, 2000)
         solve_alt["setup_s"] = setup2
@@ -301,14 +303,21 @@ def main():
     peaks, peak_src = _peaks()
     p64, p32 = fdbem.fda_device_peaks()
     # roofline of the dominant phase of the mixed-precision matvec
+    tf32_peak = peaks["bf16_tflops"] * 1.1 / 2.25  # measured bf16 x the nominal TF32/BF16 ratio
+    bytes_near = 8.0 * (info["near_entries"] + info["corr_entries"]) + 4.0 * info["corr_entries"]
+    near_gbs = bytes_near * nrhs / (ph32["near"] * 1e-3) / 1e9 if nrhs == 1 else None
     dom = max((p for p in ph32 if p not in ("perm", "assemble")), key=lambda p: ph32[p])
     dom_ms = ph32[dom]
     if dom == "near":
-        bytes_near = 8.0 * (info["near_entries"] + info["corr_entries"]) + 4.0 * info["corr_entries"]
-        achieved = bytes_near * nrhs ** 0 / (dom_ms * 1e-3) / 1e9
+        achieved = bytes_near / (dom_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "k_near<float2>",
-                "peak_source": f"{peak_src} hbm_gbs"}
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "k_near_stream<float2, 1>",
+                "peak_source": f"{peak_src} hbm_gbs (copy, burst)"}
+    elif dom == "m2l" and args.m2l_tensor == 1:
+        achieved = info["flops_m2l"] * nrhs / (dom_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
+                "frac": achieved / tf32_peak, "traffic": None, "kernel": "k_m2l_tc3 (TF32 tcgen05)",
+                "peak_source": f"{peak_src} bf16_tflops x 1.1/2.25 (nominal TF32/BF16)"}
     elif dom in ("m2l", "m2m", "l2l"):
         fl = info["flops_m2l"] if dom == "m2l" else info["flops_m2m_l2l"] / 2
         achieved = fl * nrhs / (dom_ms * 1e-3) / 1e12
@@ -343,6 +352,10 @@ def main():
         "fp64": {"matvec_per_s": 1000.0 / ms64, "ms_per_matvec": ms64, "phase_ms": ph64},
         "mixed": {"matvec_per_s": 1000.0 / ms32, "ms_per_matvec": ms32, "phase_ms": ph32},
         "speedup_matvec_mixed_vs_fp64": ms64 / ms32,
+        "near_field": {"kernel": "k_near_stream<float2, 1>", "ms": ph32["near"], "achieved_gbs": near_gbs,
+                       "peak_gbs": peaks["hbm_gbs"], "frac": near_gbs / peaks["hbm_gbs"] if near_gbs else None,
+                       "algorithmic_bytes": bytes_near},
+        "m2l_tensor": args.m2l_tensor,
         "solve_alpha_i_over_k": solve,
         "solve_alpha_minus_i_over_k": solve_alt,
         "speedup_solve_mixed_vs_fp64": (solve_alt["fp64"]["wall_s"] / solve_alt["mixed"]["wall_s"])
@@ -355,7 +368,9 @@ def main():
                                          "flops_m2l", "flops_m2m_l2l", "bytes_near", "bytes_s2m_l2t",
                                          "device_bytes")},
         "levels": {str(l): {"s": info["s"][l], "wedges": info["n_wedges"][l], "pairs": info["m2l_pairs"][l],
-                            "offsets": info["m2l_offsets"][l], "lowrank": info["m2l_lowrank"][l]}
+                            "offsets": info["m2l_offsets"][l], "lowrank": info["m2l_lowrank"][l],
+                            "m2l_gflops": info["m2l_flops_lev"][l] / 1e9,
+                            "m2l_op_bytes_fp32": info["m2l_op_bytes_lev"][l] / 2}
                    for l in range(32) if info["s"][l] > 0},
     }
     if rank == 0:

@@ -148,7 +148,9 @@ typedef struct {
   int lowrank;       /* 1: factor compressed M2L matrices K~ = U^ V^ when rank < s/2 (Sec. 4.2) */
   int nrhs_max;      /* largest nrhs fda_matvec / bm_gmres_solve will be called with (>= 1) */
   int m2l_tensor;    /* FP32 plans: M2L (and its low-rank stages) on the tensor cores (tcgen05, TF32):
-                        0 = FP32 FMA, 1 = TF32, 2 = 3xTF32 split (FP32-level accuracy) */
+                        0 = FP32 FMA; 1 = TF32 with operators pre-expanded at plan time into their
+                        shared-memory images (extra device memory about twice the FP32 M2L operators;
+                        levels with s > 256 keep the FMA kernel); 2 = 3xTF32 split (FP32-level accuracy) */
   int reserved[4];
 } fda_config_t;
 
@@ -202,6 +204,8 @@ typedef struct {
   double device_bytes;      /* device memory held by the plan */
   double setup_ms[8];       /* point selection + SVD, -, S~T~, M~, K~, low-rank, corrections, near blocks */
   int64_t launches_per_matvec; /* kernels launched by the last fda_matvec */
+  double m2l_flops_lev[32];    /* algorithmic M2L flops per level per RHS */
+  double m2l_op_bytes_lev[32]; /* FP64 bytes of the stored M2L operators per level (K~, or U^ and V^) */
 } fda_plan_info_t;
 
 int fda_plan_info(const fda_plan_t* plan, fda_plan_info_t* info);
@@ -293,9 +297,12 @@ int bm_residual_pair(fda_plan_t* plan, const void* b, const void* xstar, const v
 int bm_fgmres_solve(fda_plan_t* plan, bm_precond_t* precond, bm_net_t* net, const void* b, void* x, int nrhs,
                     const bm_gmres_opts_t* opts, bm_gmres_stats_t* stats, void* stream);
 
-/* Self-test of the tensor-core M2L kernel (diagnostic; no paper counterpart): one complex 64 x K
- * product (K <= 1024) against an FP64 host product; *max_rel_err is the largest entrywise error relative to
- * the sum of |a||x| over the row, *wait_failed is 1 when a bounded device wait gave up. Synchronous. */
+/* Self-test of the tensor-core M2L kernels (diagnostic; no paper counterpart): one complex M x K operator
+ * (K <= 1024) applied to P gathered columns, against an FP64 host product of the same FP32 data.
+ * split = 0: TF32 with operands expanded in the kernel (M = 64, P = 64); 1: 3xTF32 split (M = 64, P = 64);
+ * 2: TF32 with the pre-expanded operator image of the m2l_tensor = 1 form (M = min(256, K), P = 100).
+ * *max_rel_err is the largest entrywise error relative to the sum of |a||x| over the row, *wait_failed is 1
+ * when a bounded device wait gave up. Synchronous. */
 int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_failed);
 
 /* Last error message of the calling thread. */

@@ -273,6 +273,10 @@ int fda_plan_info(const fda_plan_t* P, fda_plan_info_t* I) {
   I->bytes_near = 16.0 * (double)(P->near_entries + P->corr_entries) + 4.0 * P->corr_entries;
   I->bytes_s2m_l2t = P->bytes_s2m_l2t;
   I->flops_m2l = P->flops_m2l;
+  for (int l = 0; l < 32; ++l) {
+    I->m2l_flops_lev[l] = l < FDA_MAXLEV ? P->m2l_flops_lev[l] : 0.0;
+    I->m2l_op_bytes_lev[l] = l < FDA_MAXLEV ? P->m2l_op_bytes_lev[l] : 0.0;
+  }
   I->flops_m2m_l2l = P->flops_m2m;
   I->flops_near = 8.0 * (double)(P->near_entries + P->corr_entries);
   double dev = 0;
@@ -280,6 +284,7 @@ int fda_plan_info(const fda_plan_t* P, fda_plan_info_t* I) {
   dev += a.S.bytes() + a.T.bytes() + a.M.bytes() + a.K.bytes() + a.near.bytes() + a.corr.bytes() + a.lr.bytes();
   const fda::RunOps<float2>& b = P->op32;
   dev += b.S.bytes() + b.T.bytes() + b.M.bytes() + b.K.bytes() + b.near.bytes() + b.corr.bytes() + b.lr.bytes();
+  dev += P->tc_img.bytes();
   dev += P->corr_col.bytes() + P->cout64.bytes() + P->cin64.bytes() + P->cout32.bytes() + P->cin32.bytes();
   I->device_bytes = dev;
   for (int q = 0; q < 8; ++q) I->setup_ms[q] = P->setup_ms[q];

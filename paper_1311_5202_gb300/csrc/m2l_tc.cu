@@ -12,13 +12,21 @@
 // sets an error flag, and the kernel still releases its TMEM.
 #include "plan.cuh"
 
+#include <vector>
+
 namespace fda {
+
+struct TcImgJob {
+  const double2* src;  // M x K complex, column-major (lda = M)
+  int M, K;
+  int64_t img_off;     // first float of the image
+};
 
 #define TC_M 128       // real rows per tile (64 complex rows)
 #define TC_N 64        // real GEMM columns per tile (pairs x RHS)
 #define TC_KC 32       // real K per stage (16 complex)
 #define TC_NT 128      // threads per CTA (4 warps: one TMEM lane quadrant each)
-#define TC_WAIT_LIMIT (1 << 24)
+#define TC_WAIT_NS 1000000000ull  // 1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -53,10 +61,17 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-// bounded wait on the mbarrier phase; returns false when the limit is hit
+__device__ __forceinline__ uint64_t tc_clock_ns() {
+  uint64_t v;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(v));
+  return v;
+}
+
+// wait on the mbarrier phase with a wall-clock bound (TC_WAIT_NS); returns false when it gives up
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   uint32_t a = smem_u32(bar);
-  for (int it = 0; it < TC_WAIT_LIMIT; ++it) {
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -64,8 +79,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (ok) return true;
+    if (it == 0) t0 = tc_clock_ns();
+    else if ((it & 255) == 0 && tc_clock_ns() - t0 > TC_WAIT_NS) return false;
   }
-  return false;
 }
 
 __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int acc) {
@@ -334,17 +350,324 @@ int m2l_tc_launch(const GemmUnit* units, size_t nunits, const float2* poolK, con
 #undef TCL
 }
 
+
+// ================================================================== TF32 form with pre-expanded operators
+// Each operator (K~, or U^ and V^) is expanded once at plan time into the exact shared-memory image the
+// MMA reads: per 128-row tile and per 32-wide real K chunk, the canonical K-major no-swizzle layout
+// (8-row groups of 1 KB), rounded to TF32, with only the 8-row groups that hold rows stored. A unit is
+// one operator with up to 128 pairs and covers all its output rows (up to MTC tiles, accumulators in
+// TMEM). Per K chunk, one thread copies the operator tiles with cp.async.bulk (completion on an
+// mbarrier with transaction bytes) while all threads gather the pairs' source coefficients with 8-byte
+// cp.async (zero fill past K); NST chunks are in flight. The MMA issuer commits each chunk to a
+// per-stage mbarrier that frees its buffers. Epilogue: warp w reads TMEM lane quadrant w % 4 and half of
+// the columns; lanes hold consecutive real rows, and after a lane-pair exchange every lane owns one complex
+// value, so a warp updates 16 consecutive complex coefficients of each of two columns per instruction
+// (8-byte atomics, or stores into the low-rank intermediate).
+
+__device__ __forceinline__ int tc3_ng(int M, int mt) { return (min(128, 2 * M - 128 * mt) + 7) / 8; }
+
+int64_t tc3_image_floats(int M, int K) {
+  const int MT = (2 * M + 127) / 128, nk = (2 * K + 31) / 32;
+  const int last = (std::min(128, 2 * M - 128 * (MT - 1)) + 7) / 8;
+  return (int64_t)(MT - 1) * nk * 16 * 256 + (int64_t)nk * last * 256;
+}
+
+static __global__ void k_tc3_image(const TcImgJob* jobs, float* img) {
+  const TcImgJob J = jobs[blockIdx.y];
+  const int MT = (2 * J.M + 127) / 128, nk = (2 * J.K + 31) / 32;
+  const int64_t full_tile = (int64_t)nk * 16 * 256;
+  const int last_ng = tc3_ng(J.M, MT - 1);
+  const int64_t total = (int64_t)(MT - 1) * full_tile + (int64_t)nk * last_ng * 256;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int mt = (int)(q / full_tile < (int64_t)(MT - 1) ? q / full_tile : (int64_t)(MT - 1));
+    const int64_t rem = q - mt * full_tile;
+    const int ng = (mt < MT - 1) ? 16 : last_ng;
+    const int kc = (int)(rem / (ng * 256));
+    const int o = (int)(rem - (int64_t)kc * ng * 256);
+    const int grp = o >> 8, within = o & 255;
+    const int row = grp * 8 + ((within & 31) >> 2);
+    const int kk = (within >> 5) * 4 + (within & 3);
+    const int j = 128 * mt + row, kr = 32 * kc + kk;
+    const int i = j >> 1, kx = kr >> 1;
+    float val = 0.f;
+    if (i < J.M && kx < J.K) {
+      const double2 a = J.src[i + (int64_t)kx * J.M];
+      const double v = (j & 1) == 0 ? ((kr & 1) == 0 ? a.x : -a.y) : ((kr & 1) == 0 ? a.y : a.x);
+      val = tf32_round((float)v);
+    }
+    img[J.img_off + q] = val;
+  }
+}
+
+int tc3_build_images(const std::vector<TcImgJob>& jobs, float* img) {
+  if (jobs.empty()) return FDA_OK;
+  DBuf<TcImgJob> dj;
+  FDA_TRY(dj.upload(jobs));
+  for (size_t b0 = 0; b0 < jobs.size(); b0 += 65535) {
+    unsigned nb = (unsigned)std::min<size_t>(65535, jobs.size() - b0);
+    k_tc3_image<<<dim3(16, nb), 256>>>(dj.p + b0, img);
+    FDA_LAUNCH_CHECK();
+  }
+  FDA_CUDA(cudaDeviceSynchronize());
+  return FDA_OK;
+}
+
+__device__ __forceinline__ void tc3_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tc3_bulk(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc3_cp8(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void tc3_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void tc3_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+#define TC3_KC 32
+#define TC3_NT 256
+
+// complex-pair epilogue helper: lanes 2i (real part) and 2i+1 (imaginary part) hold row i of columns
+// c and c + 1; after one exchange the even lane owns column c and the odd lane column c + 1, each as a
+// complex value (one 8-byte update per lane instead of two 4-byte ones)
+__device__ __forceinline__ float2 tc_pair(const float* v, int c, int part) {
+  const float send = part == 0 ? v[c + 1] : v[c];
+  const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
+  return part == 0 ? make_float2(v[c], recv) : make_float2(recv, v[c + 1]);
+}
+
+template <int MTC, int N, int NST>
+struct Tc3Smem {
+  alignas(1024) float a[NST][MTC][128 * TC3_KC];
+  alignas(1024) float b[NST][N * TC3_KC];
+  alignas(8) uint64_t afull[NST];
+  uint64_t mdone[NST];
+  uint32_t tmem;
+  int64_t sbase[N], dbase[N];
+  int srr[N];
+};
+
+// One CTA per unit (operator, up to 128 pairs); all its output rows (up to MTC tiles) in TMEM. Per K chunk,
+// thread 0 copies the operator tiles with cp.async.bulk while all threads gather the pairs' coefficients
+// with 8-byte cp.async; NST chunks in flight.
+template <int MTC, int N, int NST>
+static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units, const float* img,
+                                                          const int64_t* psrc, const int64_t* ptgt,
+                                                          const int64_t* pmid, const float2* cout, float2* cin,
+                                                          float2* mid, int nrhs, int* err) {
+  typedef Tc3Smem<MTC, N, NST> Sm;
+  extern __shared__ unsigned char smem_raw[];
+  Sm& S = *reinterpret_cast<Sm*>((((uintptr_t)smem_raw) + 1023) & ~(uintptr_t)1023);
+  constexpr int TCOLS = MTC * N;
+  constexpr uint32_t IDESC = idesc_tf32(128, N);
+  const GemmUnit U = units[blockIdx.x];
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const float2* X = (U.mode == 2) ? mid : cout;
+  const int MT = min(MTC, (2 * U.M + 127) / 128);
+  const int nk = (2 * U.K + TC3_KC - 1) / TC3_KC;
+  const float* A = img + U.a_off;
+  if (w == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
+                 "r"(TCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (t == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(&S.afull[s], 1);
+      mbar_init(&S.mdone[s], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = S.tmem;
+  uint32_t ph_a[NST], ph_m[NST];
+#pragma unroll
+  for (int s = 0; s < NST; ++s) ph_a[s] = ph_m[s] = 0;
+  bool ok = true;
+  // every thread takes the same branch: the wait result is made uniform across the CTA
+  auto wait_mdone = [&](int s) {
+    bool mine = mbar_wait(&S.mdone[s], ph_m[s]);
+    bool all = __syncthreads_and(mine ? 1 : 0) != 0;
+    if (!all) {
+      if (t == 0) atomicExch(err, 1);
+      mbar_wait(&S.mdone[s], ph_m[s]);  // second bounded wait for MMAs still in flight
+    }
+    ph_m[s] ^= 1;
+    return all;
+  };
+  const int n_lo = (lane >> 1) & 7, j_lo = (lane & 1) | (((lane >> 4) & 1) << 1);
+  auto issue = [&](int kc) {
+    const int s = kc % NST;
+    if (t == 0) {
+      uint32_t bytes = 0;
+      for (int mt = 0; mt < MT; ++mt) bytes += (uint32_t)tc3_ng(U.M, mt) * 1024u;
+      tc3_expect_tx(&S.afull[s], bytes);
+      for (int mt = 0; mt < MT; ++mt) {
+        const int ng = tc3_ng(U.M, mt);
+        tc3_bulk(S.a[s][mt], A + (int64_t)16 * mt * nk * 256 + (int64_t)kc * ng * 256, (uint32_t)ng * 1024u,
+                 &S.afull[s]);
+      }
+    }
+    const uint32_t bbase = smem_u32(S.b[s]);
+    for (int r = w; r < (N / 8) * 4; r += TC3_NT / 32) {
+      const int n = (r >> 2) * 8 + n_lo, j = (r & 3) * 4 + j_lo;
+      if (S.sbase[n] < 0) continue;  // unused column: its results are never read
+      const int gj = kc * (TC3_KC / 2) + j;
+      const bool in = gj < U.K;
+      const float2* src = in ? X + (S.sbase[n] + gj) * nrhs + S.srr[n] : X;
+      tc3_cp8(bbase + kmaj_off(n, 2 * j, TC3_KC), src, in ? 8u : 0u);
+    }
+    tc3_commit_group();
+  };
+
+  const int ncols = U.p_count * nrhs;
+  for (int c0 = 0; c0 < ncols && ok; c0 += N) {
+    if (t < N) {
+      const int c = c0 + t;
+      if (c < ncols) {
+        const int p = c / nrhs, rr = c - p * nrhs;
+        const int64_t pi = U.p_begin + p;
+        S.sbase[t] = (U.mode == 2) ? pmid[pi] : psrc[pi];
+        S.dbase[t] = (U.mode == 1) ? pmid[pi] : ptgt[pi];
+        S.srr[t] = rr;
+      } else {
+        S.sbase[t] = -1;
+        S.dbase[t] = -1;
+        S.srr[t] = 0;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NST - 1; ++j) {
+      if (j < nk)
+        issue(j);
+      else
+        tc3_commit_group();
+    }
+    for (int kc = 0; kc < nk; ++kc) {
+      const int j = kc + NST - 1;
+      if (j < nk) {
+        if (j >= NST) ok = wait_mdone(j % NST) && ok;  // MMAs of chunk j - NST released this stage
+        issue(j);
+      } else {
+        tc3_commit_group();
+      }
+      tc3_wait_group<NST - 1>();  // this thread's copies of chunk kc have landed
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (t == 0) {
+        const int s = kc % NST;
+        if (!mbar_wait(&S.afull[s], ph_a[s])) atomicExch(err, 1);
+        ph_a[s] ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t lbo = 128, sbo = (TC3_KC / 4) * 128;
+        for (int mt = 0; mt < MT; ++mt) {
+#pragma unroll
+          for (int s8 = 0; s8 < TC3_KC / 8; ++s8) {
+            const uint64_t ad = smem_desc(smem_u32(S.a[s][mt]) + s8 * 256, lbo, sbo);
+            const uint64_t bd = smem_desc(smem_u32(S.b[s]) + s8 * 256, lbo, sbo);
+            tc_mma(tmem + N * mt, ad, bd, IDESC, (kc > 0 || s8 > 0) ? 1 : 0);
+          }
+        }
+        tc_commit(&S.mdone[s]);
+      }
+    }
+    for (int c = max(0, nk - NST); c < nk; ++c) ok = wait_mdone(c % NST) && ok;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      const int q4 = w & 3, half = w >> 2;
+      const int row = 32 * q4 + lane;  // real row within a tile
+      const int part = row & 1;
+#pragma unroll 1
+      for (int mt = 0; mt < MT; ++mt) {
+        const int ci = 64 * mt + (row >> 1);
+#pragma unroll 1
+        for (int h = 0; h < N / 64; ++h) {
+          const int col0 = half * (N / 2) + 32 * h;
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(N * mt + col0), v);
+#pragma unroll
+          for (int q = 0; q < 32; q += 2) {
+            const float2 val = tc_pair(v, q, part);
+            const int n = col0 + q + part;
+            const int64_t db = S.dbase[n];
+            if (db < 0 || ci >= U.M) continue;
+            const int64_t d = (db + ci) * nrhs + S.srr[n];
+            if (U.mode == 1)
+              mid[d] = val;
+            else
+              atomicAdd(cin + d, val);
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  if (w == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
+  }
+}
+
+template <int MTC, int N, int NST>
+static int tc3_launch_t(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc,
+                        const int64_t* ptgt, const int64_t* pmid, const float2* cout, float2* cin, float2* mid,
+                        int nrhs, int* err, cudaStream_t s) {
+  const size_t smem = sizeof(Tc3Smem<MTC, N, NST>) + 1024;
+  static bool attr = false;
+  if (!attr) {
+    FDA_CUDA(cudaFuncSetAttribute(k_m2l_tc3<MTC, N, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  for (size_t u0 = 0; u0 < nunits; u0 += 65535) {
+    unsigned n = (unsigned)std::min<size_t>(65535, nunits - u0);
+    k_m2l_tc3<MTC, N, NST><<<n, TC3_NT, smem, s>>>(units + u0, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, err);
+    FDA_LAUNCH_CHECK();
+  }
+  return FDA_OK;
+}
+
+// max_mt: the largest number of 128-row tiles of any unit of this launch (1..4)
+int m2l_tc3_launch(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc, const int64_t* ptgt,
+                   const int64_t* pmid, const float2* cout, float2* cin, float2* mid, int nrhs, int max_mt, int* err,
+                   cudaStream_t s) {
+  if (max_mt < 1 || max_mt > 4) {
+    set_error("tensor-core M2L supports at most 256 complex output rows (got %d tiles)", max_mt);
+    return FDA_E_INVALID_ARG;
+  }
+  if (nunits == 0) return FDA_OK;
+  if (max_mt == 1) return tc3_launch_t<1, 128, 3>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, err, s);
+  if (max_mt == 2) return tc3_launch_t<2, 128, 2>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, err, s);
+  return tc3_launch_t<4, 64, 2>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, err, s);
+}
+
 }  // namespace fda
 
 using namespace fda;
 
-// Self-test of the tensor-core path: one complex 64 x K product against FP32 FMA on the same data.
+// Self-test of the tensor-core path: one complex M x K product applied to P gathered columns, against an FP64
+// host product of the same FP32 data. split 0: TF32 (M = 64, P = 64); 1: 3xTF32 split (M = 64, P = 64);
+// 2: TF32 with the pre-expanded operator image (M = min(256, K), P = 100).
 extern "C" int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_failed) {
-  if (K < 1 || K > 1024 || !max_rel_err || !wait_failed) {
+  if (K < 1 || K > 1024 || split < 0 || split > 2 || !max_rel_err || !wait_failed) {
     set_error("bad arguments");
     return FDA_E_INVALID_ARG;
   }
-  const int M = 64, P = 64;
+  const int M = split == 2 ? std::min(256, K) : 64, P = split == 2 ? 100 : 64;
   std::vector<float2> hA((size_t)M * K), hX((size_t)K * P);
   uint64_t st = 12345;
   auto rnd = [&]() {
@@ -367,12 +690,26 @@ extern "C" int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_
   FDA_TRY(src.upload(hs));
   FDA_TRY(tgt.upload(ht));
   FDA_TRY(pm.upload(hm));
-  GemmUnit u{0, M, K, 0, P, 0, 0, 0};
-  FDA_TRY(du.upload(&u, 1));
   FDA_TRY(err.alloc(1));
   FDA_TRY(err.zero());
-  FDA_TRY(m2l_tc_launch(du.p, 1, dA.p, dA.p, src.p, tgt.p, pm.p, dX.p, dY.p, dmid.p, 1, split, M, err.p, 0));
-  FDA_CUDA(cudaDeviceSynchronize());
+  if (split == 2) {
+    std::vector<double2> hA64(hA.size());
+    for (size_t q = 0; q < hA.size(); ++q) hA64[q] = make_double2(hA[q].x, hA[q].y);
+    DBuf<double2> dA64;
+    DBuf<float> img;
+    FDA_TRY(dA64.upload(hA64));
+    FDA_TRY(img.alloc((size_t)tc3_image_floats(M, K)));
+    FDA_TRY(tc3_build_images({TcImgJob{dA64.p, M, K, 0}}, img.p));
+    GemmUnit u{0, M, K, 0, P, 0, 0, 0};
+    FDA_TRY(du.upload(&u, 1));
+    FDA_TRY(m2l_tc3_launch(du.p, 1, img.p, src.p, tgt.p, pm.p, dX.p, dY.p, dmid.p, 1, (2 * M + 127) / 128, err.p, 0));
+    FDA_CUDA(cudaDeviceSynchronize());
+  } else {
+    GemmUnit u{0, M, K, 0, P, 0, 0, 0};
+    FDA_TRY(du.upload(&u, 1));
+    FDA_TRY(m2l_tc_launch(du.p, 1, dA.p, dA.p, src.p, tgt.p, pm.p, dX.p, dY.p, dmid.p, 1, split, M, err.p, 0));
+    FDA_CUDA(cudaDeviceSynchronize());
+  }
   std::vector<float2> hY;
   FDA_TRY(dY.download(hY));
   int he = 0;

@@ -13,6 +13,9 @@
 
 namespace fda {
 
+int m2l_tc3_launch(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc, const int64_t* ptgt,
+                   const int64_t* pmid, const float2* cout, float2* cin, float2* mid, int nrhs, int max_mt, int* err,
+                   cudaStream_t s);
 int m2l_tc_launch(const GemmUnit* units, size_t nunits, const float2* poolK, const float2* poolLR,
                   const int64_t* psrc, const int64_t* ptgt, const int64_t* pmid, const float2* cout, float2* cin,
                   float2* mid, int nrhs, int split, int max_rows, int* err, cudaStream_t s);
@@ -475,6 +478,14 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
       for (int st = 0; st < 2; ++st) {
         size_t nu = P->h_units[l][st].size();
         size_t ntu = P->h_tc_units[l][st].size();
+        size_t n3 = P->h_tc3_units[l][st].size();
+        if (n3 && std::is_same<C, float2>::value && P->cfg.m2l_tensor == 1 && P->tc3_mt[l][st] <= 4) {
+          FDA_TRY(m2l_tc3_launch(P->tc3_units[l][st].p, n3, P->tc_img.p, P->pair_src.p, P->pair_tgt.p,
+                                 P->pair_mid.p, (const float2*)cout.p, (float2*)cin.p, (float2*)mid.p, nrhs,
+                                 P->tc3_mt[l][st], P->tc_err.p, s));
+          nl += (int64_t)((n3 + 65534) / 65535);
+          continue;
+        }
         if (ntu && std::is_same<C, float2>::value && P->cfg.m2l_tensor > 0) {
           FDA_TRY(m2l_tc_launch(P->tc_units[l][st].p, ntu, (const float2*)op.K.p, (const float2*)op.lr.p,
                                 P->pair_src.p, P->pair_tgt.p, P->pair_mid.p, (const float2*)cout.p, (float2*)cin.p,

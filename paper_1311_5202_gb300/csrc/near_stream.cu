@@ -20,13 +20,15 @@ namespace fda {
 #define NS_STAGE_BYTES 16384
 #define NS_CONS 256            // consumer threads (8 warps)
 #define NS_NT (NS_CONS + 32)   // + one producer warp
-#define NS_WAIT_LIMIT (1 << 24)
+#define NS_WAIT_NS 1000000000ull  // 1 s
 
 __device__ __forceinline__ uint32_t ns_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// wait on the mbarrier phase with a wall-clock bound of 1 s; returns false when it gives up
 __device__ __forceinline__ bool ns_wait(uint64_t* bar, uint32_t parity) {
   const uint32_t a = ns_smem(bar);
-  for (int it = 0; it < NS_WAIT_LIMIT; ++it) {
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -34,8 +36,11 @@ __device__ __forceinline__ bool ns_wait(uint64_t* bar, uint32_t parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (ok) return true;
+    uint64_t now;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(now));
+    if (it == 0) t0 = now;
+    else if (now - t0 > NS_WAIT_NS) return false;
   }
-  return false;
 }
 
 __device__ __forceinline__ void ns_arrive(uint64_t* bar) {

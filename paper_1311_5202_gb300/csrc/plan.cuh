@@ -89,6 +89,11 @@ struct fda_plan_s {
   std::vector<fda::GemmUnit> h_tc_units[FDA_MAXLEV][2];
   fda::DBuf<fda::GemmUnit> tc_units[FDA_MAXLEV][2];
   int tc_max_rows[FDA_MAXLEV][2] = {{0}};
+  // TF32 tensor-core form: operator images (canonical shared-memory layout) and units of up to 128 pairs
+  fda::DBuf<float> tc_img;
+  std::vector<fda::GemmUnit> h_tc3_units[FDA_MAXLEV][2];
+  fda::DBuf<fda::GemmUnit> tc3_units[FDA_MAXLEV][2];
+  int tc3_mt[FDA_MAXLEV][2] = {{0}};  // largest number of 128-row tiles of a unit
   fda::DBuf<int64_t> pair_src, pair_tgt;  // coefficient indices (slot + wedge * s)
   fda::DBuf<int64_t> pair_mid;            // low-rank intermediate index per pair (-1 if dense)
   int64_t n_pairs = 0, n_mid = 0;
@@ -107,6 +112,7 @@ struct fda_plan_s {
   cudaEvent_t* phase_ev = nullptr;  // when set, 9 events recorded between the matvec phases
   double setup_ms[8] = {0};
   double flops_m2l = 0, flops_m2m = 0, bytes_s2m_l2t = 0;
+  double m2l_flops_lev[FDA_MAXLEV] = {0}, m2l_op_bytes_lev[FDA_MAXLEV] = {0};
   // GMRES workspace (allocated on first solve)
   fda::DBuf<double2> gm_V, gm_w, gm_r, gm_x, gm_z, gm_b;
   fda::DBuf<double> gm_small;

@@ -16,6 +16,7 @@
 #include "plan.cuh"
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <map>
 #include <tuple>
@@ -48,6 +49,13 @@ struct SVDJob {
   int* sweeps;
 };
 int pivoted_qr_batched(const std::vector<QRJob>& jobs, cudaStream_t s);
+struct TcImgJob {
+  const double2* src;  // M x K complex, column-major (lda = M)
+  int M, K;
+  int64_t img_off;     // first float of the image
+};
+int64_t tc3_image_floats(int M, int K);
+int tc3_build_images(const std::vector<TcImgJob>& jobs, float* img);
 int form_q_batched(const std::vector<QFormJob>& jobs, cudaStream_t s);
 int jacobi_svd_batched(const std::vector<SVDJob>& jobs, cudaStream_t s);
 
@@ -1076,7 +1084,11 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
       }
       double fl = o.rank > 0 ? 16.0 * o.rank * L.s : 8.0 * L.s * L.s;
       P->flops_m2l += fl;
+      P->m2l_flops_lev[l] += fl;
     }
+    for (int l = 0; l < FDA_MAXLEV; ++l)
+      for (const OffInfo& o : offs[l])
+        P->m2l_op_bytes_lev[l] += 16.0 * (o.rank > 0 ? 2.0 * o.rank * P->lev[l].s : (double)P->lev[l].s * P->lev[l].s);
     P->n_pairs = T->nm2l;
     P->n_mid = mid;
     FDA_TRY(P->pair_src.upload(ps));
@@ -1126,6 +1138,59 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
         FDA_TRY(P->units[l][st].upload(P->h_units[l][st]));
         FDA_TRY(P->tc_units[l][st].upload(P->h_tc_units[l][st]));
       }
+    // tensor-core (TF32) form: every operator pre-expanded into its shared-memory image, units of up to
+    // 128 pairs that cover all output rows
+    if (P->cfg.m2l_tensor == 1 && P->cfg.precision == FDA_PREC_FP32) {
+      std::vector<TcImgJob> jobs;
+      int64_t img_tot = 0;
+      std::vector<std::vector<std::array<int64_t, 3>>> img_of(FDA_MAXLEV);  // (k, v, u) image offsets
+      for (int l = lmin; l <= lmax && far; ++l) {
+        img_of[l].resize(offs[l].size());
+        const int sl = P->lev[l].s;
+        for (size_t i = 0; i < offs[l].size(); ++i) {
+          const OffInfo& o = offs[l][i];
+          auto add = [&](const double2* src, int M, int K) {
+            int64_t off = img_tot;
+            jobs.push_back({src, M, K, off});
+            img_tot += tc3_image_floats(M, K);
+            return off;
+          };
+          if (o.rank > 0) {
+            img_of[l][i] = {-1, add(P->op64.lr.p + o.v_off, o.rank, sl), add(P->op64.lr.p + o.u_off, sl, o.rank)};
+          } else {
+            img_of[l][i] = {add(P->op64.K.p + o.k_off, sl, sl), -1, -1};
+          }
+        }
+      }
+      FDA_TRY(P->tc_img.alloc(std::max<int64_t>(img_tot, 1)));
+      FDA_TRY(tc3_build_images(jobs, P->tc_img.p));
+      const int CP3 = 128;
+      int64_t u3 = 0;
+      while (u3 < T->nm2l) {
+        int64_t q = order[u3];
+        int l = T->h_m2l_info[6 * q];
+        int id = pair_off[q];
+        int64_t v = u3;
+        while (v < T->nm2l && T->h_m2l_info[6 * order[v]] == l && pair_off[order[v]] == id) ++v;
+        const OffInfo& o = offs[l][id];
+        const int sl = P->lev[l].s;
+        for (int64_t p0 = u3; p0 < v; p0 += CP3) {
+          int pc = (int)std::min<int64_t>(CP3, v - p0);
+          if (o.rank > 0) {
+            P->h_tc3_units[l][0].push_back({img_of[l][id][1], o.rank, sl, p0, pc, 0, 1, 0});
+            P->h_tc3_units[l][1].push_back({img_of[l][id][2], sl, o.rank, p0, pc, 0, 2, 0});
+            P->tc3_mt[l][0] = std::max(P->tc3_mt[l][0], (2 * o.rank + 127) / 128);
+            P->tc3_mt[l][1] = std::max(P->tc3_mt[l][1], (2 * sl + 127) / 128);
+          } else {
+            P->h_tc3_units[l][0].push_back({img_of[l][id][0], sl, sl, p0, pc, 0, 0, 0});
+            P->tc3_mt[l][0] = std::max(P->tc3_mt[l][0], (2 * sl + 127) / 128);
+          }
+        }
+        u3 = v;
+      }
+      for (int l = 0; l < FDA_MAXLEV; ++l)
+        for (int st = 0; st < 2; ++st) FDA_TRY(P->tc3_units[l][st].upload(P->h_tc3_units[l][st]));
+    }
   }
 
   // ---- 7. near field: corrections (Eq. kcorrection) and direct blocks

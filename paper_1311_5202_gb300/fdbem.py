@@ -78,7 +78,8 @@ class fda_plan_info_t(C.Structure):
                 ("near_entries", C.c_int64), ("corr_entries", C.c_int64), ("bytes_near", C.c_double),
                 ("bytes_s2m_l2t", C.c_double), ("flops_m2l", C.c_double), ("flops_m2m_l2l", C.c_double),
                 ("flops_near", C.c_double), ("device_bytes", C.c_double), ("setup_ms", C.c_double * 8),
-                ("launches_per_matvec", C.c_int64)]
+                ("launches_per_matvec", C.c_int64), ("m2l_flops_lev", C.c_double * 32),
+                ("m2l_op_bytes_lev", C.c_double * 32)]
 
 
 _LIB = None

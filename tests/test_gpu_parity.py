@@ -222,20 +222,22 @@ def test_tiny_mesh_without_far_field():
 
 
 # ------------------------------------------------------------------ tensor-core M2L (tcgen05)
-@pytest.mark.parametrize("split", [0, 1])
+@pytest.mark.parametrize("split", [0, 1, 2])
 def test_tensor_core_selftest(split):
-    """One complex 64 x K product on the tensor cores against an FP64 host product (TF32: ~1e-4 of the row
-    scale; 3xTF32 split: FP32 level)."""
+    """A complex operator applied to gathered columns on the tensor cores against an FP64 host product (TF32:
+    ~1e-4 of the row scale; 3xTF32 split: FP32 level). split 2 is the pre-expanded-image kernel with
+    M = min(256, K) rows: K = 8, 37 (one 128-row tile, ragged K), 111 (two tiles), 222 (four tiles)."""
     _need_gpu()
-    for K in (16, 111, 222):
+    for K in ((16, 111, 222) if split < 2 else (8, 37, 111, 222)):
         err, wait_failed = fdbem.fda_tc_selftest(K, split)
         assert wait_failed == 0
-        assert err < (1e-3 if split == 0 else 5e-6), (K, err)
+        assert err < (1e-3 if split != 1 else 5e-6), (K, err)
 
 
 @pytest.mark.parametrize("mode", [1, 2])
 def test_fda_matvec_tensor_core_m2l(mode):
-    """FP32 plan with M2L on the tensor cores (TF32, or 3xTF32 split) against the dense oracle (<= 3e-4)."""
+    """FP32 plan with M2L on the tensor cores (TF32 from pre-expanded operator images, or 3xTF32 split)
+    against the dense oracle (<= 3e-4), two right-hand sides."""
     _need_gpu()
     mesh = inputs.icosphere(8, 0.5)
     k = 20.0
