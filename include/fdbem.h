@@ -177,6 +177,39 @@ int fda_matvec(fda_plan_t* plan, const void* x, void* y, int nrhs, int dtype, vo
  * FDA_PREC_FP32 needs a plan built with cfg.precision = FDA_PREC_FP32 (else FDA_E_STATE). */
 int fda_matvec_ex(fda_plan_t* plan, int precision, const void* x, void* y, int nrhs, int dtype, void* stream);
 
+/* Autotuner (no paper counterpart). For an FP32 plan and a batch width nrhs (1..nrhs_max), times on the
+ * plan's own operators every M2L (level, stage) with the FP32 FMA kernel and with the plan's tensor-core
+ * kernel (m2l_tensor 1 or 2), and for nrhs >= 12 the near field at 4 and 16 right-hand sides per pass over
+ * the near-field matrices; the plan keeps the faster variant of each for all later products. Synchronous;
+ * overwrites the plan's internal workspaces only. report (HOST) receives the timings and choices.
+ * Errors: FDA_E_INVALID_ARG, FDA_E_STATE (FP64-only plan), FDA_E_OOM, FDA_E_CUDA. */
+typedef struct {
+  int32_t entries;        /* (level, stage) rows filled below */
+  int32_t level[64];
+  int32_t stage[64];      /* 0: dense K~ or V^ stage, 1: U^ stage */
+  double ms_fma[64];      /* FP32 FMA kernel, best of 3 */
+  double ms_tensor[64];   /* tensor-core kernel, best of 3 (-1 when the plan holds none) */
+  int32_t chosen[64];     /* 0: FMA kernel, 1: tensor-core kernel */
+  double near_ms[2];      /* near field at 4 and 16 right-hand sides per pass (nrhs >= 12; else 0) */
+  int32_t near_rhs_per_pass;
+  int32_t reserved[7];
+} fda_tune_report_t;
+int fda_autotune(fda_plan_t* plan, int nrhs, void* stream, fda_tune_report_t* report);
+
+/* CUDA-graph form of one product (the batched matvec of many incident directions replayed without
+ * per-kernel launch cost; no paper counterpart). fda_matvec_graph_create runs the product once on `stream`
+ * (synchronously; a null stream means an internal one for the capture), then captures the same product for
+ * these exact x, y (DEVICE, as fda_matvec_ex), nrhs, dtype and precision into a graph. fda_graph_launch
+ * replays it on any stream: the caller refreshes x in place and reads y after the replay; the graph keeps
+ * pointers to x, y and the plan, which must stay alive. fda_graph_nodes returns its kernel/memset node
+ * count. Errors: FDA_E_INVALID_ARG, FDA_E_CUDA (capture or instantiation refused). */
+typedef struct fda_graph_s fda_graph_t;
+int fda_matvec_graph_create(fda_plan_t* plan, int precision, const void* x, void* y, int nrhs, int dtype,
+                            void* stream, fda_graph_t** out);
+int fda_graph_launch(fda_graph_t* g, void* stream);
+int fda_graph_nodes(const fda_graph_t* g, int64_t* nodes);
+void fda_graph_destroy(fda_graph_t* g);
+
 /* Same product as fda_matvec_ex, with CUDA events recorded on `stream` between the phases; on return
  * (synchronous) phase_ms[0..7] holds the device time of: input permutation, near field (direct blocks +
  * corrections), S2M, M2M, M2L, L2L, L2T, output assembly. Diagnostic; no paper counterpart. */
@@ -249,7 +282,10 @@ typedef struct {
  * N x nrhs complex128, user DOF order. Synchronous (it reads back the Givens residual estimate
  * once per iteration). Returns FDA_E_NOT_CONVERGED / FDA_E_BREAKDOWN / FDA_E_NAN with x holding
  * the best iterate. The refine = 1 form needs a plan built with FDA_PREC_FP32 and uses the
- * plan's FP64 operator for the outer residual. */
+ * plan's FP64 operator for the outer residual. With nrhs > 1 the columns advance in lockstep: every
+ * step applies the operator once to the N x nrhs block (nrhs <= the plan's nrhs_max), each column keeps
+ * its own Arnoldi basis and Givens rotations, and a column stops extending its basis once its own residual
+ * estimate meets tol; stats->iterations then counts block steps and rel_residual is the worst column. */
 int bm_gmres_solve(fda_plan_t* plan, const void* b, void* x, int nrhs, const bm_gmres_opts_t* opts,
                    bm_gmres_stats_t* stats, void* stream);
 

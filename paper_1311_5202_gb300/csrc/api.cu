@@ -220,6 +220,94 @@ int fda_matvec_ex(fda_plan_t* plan, int precision, const void* x, void* y, int n
   return plan_matvec(plan, precision, x, y, nrhs, dtype, (cudaStream_t)stream, false);
 }
 
+int fda_autotune(fda_plan_t* plan, int nrhs, void* stream, fda_tune_report_t* report) {
+  ARG_CHECK(plan && report, "NULL argument");
+  ARG_CHECK(nrhs >= 1 && nrhs <= plan->cfg.nrhs_max, "nrhs outside [1, nrhs_max]");
+  if (plan->cfg.precision != FDA_PREC_FP32) {
+    set_error("autotuning needs a plan built with FDA_PREC_FP32");
+    return FDA_E_STATE;
+  }
+  return autotune(plan, nrhs, (cudaStream_t)stream, report);
+}
+
+struct fda_graph_s {
+  fda_plan_s* plan = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+int fda_matvec_graph_create(fda_plan_t* plan, int precision, const void* x, void* y, int nrhs, int dtype,
+                            void* stream, fda_graph_t** out) {
+  ARG_CHECK(plan && x && y && out, "NULL argument");
+  ARG_CHECK(dtype == FDA_CPLX128 || dtype == FDA_CPLX64, "unknown dtype");
+  ARG_CHECK(precision == FDA_PREC_FP64 || precision == FDA_PREC_FP32, "unknown precision");
+  ARG_CHECK(x != y, "x and y must not overlap");
+  *out = nullptr;
+  // capture needs a stream other than the legacy default one
+  cudaStream_t s = (cudaStream_t)stream, own = nullptr;
+  if (!s) {
+    FDA_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+    s = own;
+  }
+  auto done = [&](int rc) {
+    if (own) cudaStreamDestroy(own);
+    return rc;
+  };
+  // one ordinary product first: one-time kernel attributes are set outside the capture
+  int rc = plan_matvec(plan, precision, x, y, nrhs, dtype, s, false);
+  if (rc != FDA_OK) return done(rc);
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    set_error("matvec before capture failed");
+    return done(FDA_E_CUDA);
+  }
+  fda_graph_s* G = new fda_graph_s;
+  G->plan = plan;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    delete G;
+    set_error("cudaStreamBeginCapture failed");
+    return done(FDA_E_CUDA);
+  }
+  rc = plan_matvec(plan, precision, x, y, nrhs, dtype, s, false);
+  cudaError_t e = cudaStreamEndCapture(s, &G->graph);
+  if (rc == FDA_OK && e != cudaSuccess) {
+    set_error("cudaStreamEndCapture: %s", cudaGetErrorString(e));
+    rc = FDA_E_CUDA;
+  }
+  if (rc == FDA_OK && cudaGraphInstantiate(&G->exec, G->graph, 0) != cudaSuccess) {
+    set_error("cudaGraphInstantiate failed");
+    rc = FDA_E_CUDA;
+  }
+  if (rc != FDA_OK) {
+    if (G->graph) cudaGraphDestroy(G->graph);
+    delete G;
+    cudaGetLastError();
+    return done(rc);
+  }
+  *out = G;
+  return done(FDA_OK);
+}
+
+int fda_graph_launch(fda_graph_t* g, void* stream) {
+  ARG_CHECK(g && g->exec, "NULL graph");
+  FDA_CUDA(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+  return FDA_OK;
+}
+
+int fda_graph_nodes(const fda_graph_t* g, int64_t* nodes) {
+  ARG_CHECK(g && nodes, "NULL argument");
+  size_t n = 0;
+  FDA_CUDA(cudaGraphGetNodes(g->graph, nullptr, &n));
+  *nodes = (int64_t)n;
+  return FDA_OK;
+}
+
+void fda_graph_destroy(fda_graph_t* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+}
+
 int fda_matvec_phases(fda_plan_t* plan, int precision, const void* x, void* y, int nrhs, int dtype, void* stream,
                       double* ms) {
   ARG_CHECK(plan && x && y && ms, "NULL argument");

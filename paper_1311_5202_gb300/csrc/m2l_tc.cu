@@ -466,8 +466,10 @@ static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units
   typedef Tc3Smem<MTC, N, NST> Sm;
   extern __shared__ unsigned char smem_raw[];
   Sm& S = *reinterpret_cast<Sm*>((((uintptr_t)smem_raw) + 1023) & ~(uintptr_t)1023);
-  constexpr int TCOLS = MTC * N;
+  constexpr int TCOLS = MTC * N < 32 ? 32 : MTC * N;
   constexpr uint32_t IDESC = idesc_tf32(128, N);
+  // refill distance: chunk kc + D is issued at step kc into the stage that served chunk kc + D - NST
+  constexpr int D = NST - 1;
   const GemmUnit U = units[blockIdx.x];
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   const float2* X = (U.mode == 2) ? mid : cout;
@@ -549,21 +551,21 @@ static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < NST - 1; ++j) {
+    for (int j = 0; j < D; ++j) {
       if (j < nk)
         issue(j);
       else
         tc3_commit_group();
     }
     for (int kc = 0; kc < nk; ++kc) {
-      const int j = kc + NST - 1;
+      const int j = kc + D;
       if (j < nk) {
-        if (j >= NST) ok = wait_mdone(j % NST) && ok;  // MMAs of chunk j - NST released this stage
+        if (j >= NST) ok = wait_mdone(j % NST) && ok;  // MMAs of chunk j - NST (<= kc - 1) released this stage
         issue(j);
       } else {
         tc3_commit_group();
       }
-      tc3_wait_group<NST - 1>();  // this thread's copies of chunk kc have landed
+      tc3_wait_group<D>();  // this thread's copies of chunk kc have landed
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       if (t == 0) {

@@ -9,6 +9,8 @@
 // c[(slot + wedge * s + r) * nrhs + rhs]. One template serves FP64 (double2) and FP32 (float2) operators.
 #include "plan.cuh"
 
+#include <cstring>
+#include <functional>
 #include <type_traits>
 
 namespace fda {
@@ -389,6 +391,46 @@ static __global__ void __launch_bounds__(256) k_m2l(const GemmUnit* units, const
 }
 
 // ------------------------------------------------------------------ driver
+// M2L kernel variants of one (level, stage): 0 = FP32/FP64 FMA, 1 = TF32 from pre-expanded operator images,
+// 2 = TF32 or 3xTF32 with operands expanded in the kernel (plan option m2l_tensor = 2)
+int m2l_variant(const fda_plan_s* P, int l, int st) {
+  if (P->m2l_choice[l][st] >= 0) return P->m2l_choice[l][st];
+  if (P->cfg.m2l_tensor == 1 && !P->h_tc3_units[l][st].empty() && P->tc3_mt[l][st] <= 4) return 1;
+  if (P->cfg.m2l_tensor == 2 && !P->h_tc_units[l][st].empty()) return 2;
+  return 0;
+}
+
+template <typename C>
+int m2l_stage(fda_plan_s* P, RunOps<C>& op, DBuf<C>& cout, DBuf<C>& cin, DBuf<C>& mid, int l, int st, int variant,
+              int nrhs, cudaStream_t s, int64_t* nl) {
+  const bool f32 = std::is_same<C, float2>::value;
+  if (variant == 1 && f32 && !P->h_tc3_units[l][st].empty()) {
+    const size_t n3 = P->h_tc3_units[l][st].size();
+    FDA_TRY(m2l_tc3_launch(P->tc3_units[l][st].p, n3, P->tc_img.p, P->pair_src.p, P->pair_tgt.p, P->pair_mid.p,
+                           (const float2*)cout.p, (float2*)cin.p, (float2*)mid.p, nrhs, P->tc3_mt[l][st], P->tc_err.p,
+                           s));
+    *nl += (int64_t)((n3 + 65534) / 65535);
+    return FDA_OK;
+  }
+  if (variant == 2 && f32 && !P->h_tc_units[l][st].empty()) {
+    const size_t ntu = P->h_tc_units[l][st].size();
+    FDA_TRY(m2l_tc_launch(P->tc_units[l][st].p, ntu, (const float2*)op.K.p, (const float2*)op.lr.p, P->pair_src.p,
+                          P->pair_tgt.p, P->pair_mid.p, (const float2*)cout.p, (float2*)cin.p, (float2*)mid.p, nrhs,
+                          P->cfg.m2l_tensor == 2 ? 1 : 0, P->tc_max_rows[l][st], P->tc_err.p, s));
+    *nl += (int64_t)((ntu + 65534) / 65535);
+    return FDA_OK;
+  }
+  const size_t nu = P->h_units[l][st].size();
+  for (size_t u0 = 0; u0 < nu; u0 += 65535) {
+    unsigned n = (unsigned)std::min<size_t>(65535, nu - u0);
+    k_m2l<C><<<n, 256, 0, s>>>(P->units[l][st].p + u0, op.K.p, op.lr.p, P->pair_src.p, P->pair_tgt.p, P->pair_mid.p,
+                               cout.p, cin.p, mid.p, nrhs);
+    FDA_LAUNCH_CHECK();
+    ++*nl;
+  }
+  return FDA_OK;
+}
+
 template <typename C>
 static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf<C>& cout, DBuf<C>& cin,
                     DBuf<C>& mid, const void* x, void* y, int nrhs, int io, cudaStream_t s) {
@@ -474,35 +516,8 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
     ev(4);
     // M2L
     FDA_CUDA(cudaMemsetAsync(cin.p, 0, sizeof(C) * P->n_coef * nrhs, s));
-    for (int l = P->lmin; l <= P->lmax; ++l) {
-      for (int st = 0; st < 2; ++st) {
-        size_t nu = P->h_units[l][st].size();
-        size_t ntu = P->h_tc_units[l][st].size();
-        size_t n3 = P->h_tc3_units[l][st].size();
-        if (n3 && std::is_same<C, float2>::value && P->cfg.m2l_tensor == 1 && P->tc3_mt[l][st] <= 4) {
-          FDA_TRY(m2l_tc3_launch(P->tc3_units[l][st].p, n3, P->tc_img.p, P->pair_src.p, P->pair_tgt.p,
-                                 P->pair_mid.p, (const float2*)cout.p, (float2*)cin.p, (float2*)mid.p, nrhs,
-                                 P->tc3_mt[l][st], P->tc_err.p, s));
-          nl += (int64_t)((n3 + 65534) / 65535);
-          continue;
-        }
-        if (ntu && std::is_same<C, float2>::value && P->cfg.m2l_tensor > 0) {
-          FDA_TRY(m2l_tc_launch(P->tc_units[l][st].p, ntu, (const float2*)op.K.p, (const float2*)op.lr.p,
-                                P->pair_src.p, P->pair_tgt.p, P->pair_mid.p, (const float2*)cout.p, (float2*)cin.p,
-                                (float2*)mid.p, nrhs, P->cfg.m2l_tensor == 2 ? 1 : 0, P->tc_max_rows[l][st],
-                                P->tc_err.p, s));
-          nl += (int64_t)((ntu + 65534) / 65535);
-          continue;
-        }
-        for (size_t u0 = 0; u0 < nu; u0 += 65535) {
-          unsigned n = (unsigned)std::min<size_t>(65535, nu - u0);
-          k_m2l<C><<<n, 256, 0, s>>>(P->units[l][st].p + u0, op.K.p, op.lr.p, P->pair_src.p, P->pair_tgt.p,
-                                     P->pair_mid.p, cout.p, cin.p, mid.p, nrhs);
-          FDA_LAUNCH_CHECK();
-          ++nl;
-        }
-      }
-    }
+    for (int l = P->lmin; l <= P->lmax; ++l)
+      for (int st = 0; st < 2; ++st) FDA_TRY(m2l_stage<C>(P, op, cout, cin, mid, l, st, m2l_variant(P, l, st), nrhs, s, &nl));
     ev(5);
     // L2L top-down
     for (int l = P->lmin; l < P->lmax; ++l) {
@@ -563,6 +578,85 @@ int plan_matvec(fda_plan_s* P, int prec, const void* x, void* y, int nrhs, int i
     return matvec_t<float2>(P, P->op32, P->xt32, P->yt32, P->cout32, P->cin32, P->mid32, x, y, nrhs, io_dtype, s);
   }
   return matvec_t<double2>(P, P->op64, P->xt64, P->yt64, P->cout64, P->cin64, P->mid64, x, y, nrhs, io_dtype, s);
+}
+
+// ------------------------------------------------------------------ autotuner
+// Times, on the plan's own data and for the given batch width, every M2L (level, stage) with the FP32 FMA
+// kernel and with the tensor-core kernel the plan holds, and for wide batches the near field at 4 and 16
+// right-hand sides per pass; the plan then keeps the faster variant of each.
+static int time_ms(cudaStream_t s, const std::function<int()>& f, int reps, double* best) {
+  cudaEvent_t a, b;
+  FDA_CUDA(cudaEventCreate(&a));
+  FDA_CUDA(cudaEventCreate(&b));
+  *best = 1e300;
+  int rc = FDA_OK;
+  for (int r = 0; r < reps && rc == FDA_OK; ++r) {
+    cudaEventRecord(a, s);
+    rc = f();
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float t = 0;
+    cudaEventElapsedTime(&t, a, b);
+    *best = std::min(*best, (double)t);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return rc;
+}
+
+int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
+  memset(R, 0, sizeof(*R));
+  const int64_t N = P->tree->N;
+  DBuf<float2> x, y;
+  FDA_TRY(x.alloc((size_t)N * nrhs));
+  FDA_TRY(y.alloc((size_t)N * nrhs));
+  FDA_TRY(x.zero(s));
+  for (int l = 0; l < FDA_MAXLEV; ++l) P->m2l_choice[l][0] = P->m2l_choice[l][1] = -1;
+  P->near_wide = -1;
+  FDA_TRY(plan_matvec(P, FDA_PREC_FP32, x.p, y.p, nrhs, FDA_CPLX64, s, false));  // workspaces hold valid data
+  FDA_CUDA(cudaStreamSynchronize(s));
+  int64_t nl = 0;
+  int e = 0;
+  for (int l = P->lmin; l <= P->lmax && P->n_coef > 0; ++l)
+    for (int st = 0; st < 2; ++st) {
+      if (P->h_units[l][st].empty() || e >= 64) continue;
+      const int tv = m2l_variant(P, l, st);  // the plan's tensor-core variant, if any
+      double t0 = 0, t1 = -1;
+      FDA_TRY(time_ms(s, [&]() { return m2l_stage<float2>(P, P->op32, P->cout32, P->cin32, P->mid32, l, st, 0, nrhs, s,
+                                                          &nl); },
+                      3, &t0));
+      if (tv != 0)
+        FDA_TRY(time_ms(s, [&]() { return m2l_stage<float2>(P, P->op32, P->cout32, P->cin32, P->mid32, l, st, tv, nrhs,
+                                                            s, &nl); },
+                        3, &t1));
+      R->level[e] = l;
+      R->stage[e] = st;
+      R->ms_fma[e] = t0;
+      R->ms_tensor[e] = t1;
+      const int pick = (tv != 0 && t1 < t0) ? tv : 0;
+      R->chosen[e] = pick ? 1 : 0;
+      P->m2l_choice[l][st] = pick;
+      ++e;
+    }
+  R->entries = e;
+  if (nrhs >= 12 && P->n_near_tleaf > 0 && P->near_max_nr <= 256) {
+    double tn[2];
+    for (int wide = 0; wide < 2; ++wide) {
+      P->near_wide = wide;
+      FDA_TRY(time_ms(s, [&]() { return near_stream<float2>(P, P->op32.near.p, P->op32.corr.p, P->xt32.p, P->yt32.p,
+                                                            nrhs, s, &nl); },
+                      2, &tn[wide]));
+    }
+    R->near_ms[0] = tn[0];
+    R->near_ms[1] = tn[1];
+    P->near_wide = tn[1] < tn[0] ? 1 : 0;
+    R->near_rhs_per_pass = P->near_wide ? 16 : 4;
+  } else {
+    R->near_rhs_per_pass = nrhs == 1 ? 1 : 4;
+  }
+  FDA_TRY(plan_matvec(P, FDA_PREC_FP32, x.p, y.p, nrhs, FDA_CPLX64, s, false));
+  FDA_CUDA(cudaStreamSynchronize(s));
+  return FDA_OK;
 }
 
 // ------------------------------------------------------------------ FMA throughput probe

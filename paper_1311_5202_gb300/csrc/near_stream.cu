@@ -2,9 +2,9 @@
 //
 // Every target leaf's direct blocks form one contiguous column-major matrix (rows: the leaf's points,
 // columns: the points of its direct source boxes), 4-entry aligned in HBM. A persistent grid of CTAs
-// (two per SM) owns balanced, contiguous ranges of target leaves. In each CTA one producer thread walks
+// (three per SM) owns balanced, contiguous ranges of target leaves. In each CTA one producer thread walks
 // the leaves' matrices chunk by chunk (whole columns, <= 16 KB) and issues cp.async.bulk copies into a
-// ring of four shared-memory stages, each guarded by a "full" mbarrier (transaction bytes) and an
+// ring of shared-memory stages (three, or four for batches), each guarded by a "full" mbarrier (transaction bytes) and an
 // "empty" mbarrier (one arrival per consumer warp). Eight consumer warps gather the leaf's source
 // densities into shared memory once per column window (one index per column, a single parallel pass),
 // then read each landed stage: thread (i, g) takes row i and columns g, g + G, ... (G = 256 / rows), so
@@ -16,7 +16,6 @@
 
 namespace fda {
 
-#define NS_STAGES 4
 #define NS_STAGE_BYTES 16384
 #define NS_CONS 256            // consumer threads (8 warps)
 #define NS_NT (NS_CONS + 32)   // + one producer warp
@@ -64,31 +63,34 @@ __device__ __forceinline__ void ns_bulk(void* dst, const void* src, uint32_t byt
 // barrier among the consumer warps only (the producer warp never joins it)
 __device__ __forceinline__ void ns_cons_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NS_CONS) : "memory"); }
 
+// single right-hand side: three CTAs per SM (3-stage ring, 16 KB density window); batches: fewer, larger CTAs
 template <typename C, int NR>
 struct NsLayout {
   static constexpr int E = sizeof(C);
-  static constexpr int XBYTES = (E * NR >= 64) ? 16384 : 32768;
+  static constexpr int STAGES = NR == 1 ? 3 : 4;
+  static constexpr int MINB = NR == 1 ? 3 : (NR <= 4 ? 2 : 1);
+  static constexpr int XBYTES = (NR == 1 || E * NR >= 64) ? 16384 : 32768;
   static constexpr int XW = (XBYTES / (NR * E)) & ~1;  // columns per density window (even)
-  static constexpr size_t ring = (size_t)NS_STAGES * NS_STAGE_BYTES;
+  static constexpr size_t ring = (size_t)STAGES * NS_STAGE_BYTES;
   static constexpr size_t xs = ring;
   static constexpr size_t red = xs + (size_t)XW * NR * E;
   static constexpr size_t cor = red + (size_t)NS_CONS * NR * E;
   static constexpr size_t crow = cor + (size_t)NS_CONS * NR * E;
   static constexpr size_t bars = crow + (NS_CONS + 8) * sizeof(int);
-  static constexpr size_t total = bars + 2 * NS_STAGES * sizeof(uint64_t) + 128;  // + alignment slack
+  static constexpr size_t total = bars + 2 * STAGES * sizeof(uint64_t) + 128;  // + alignment slack
 };
 
 // columns per chunk: whole columns, an even count, at most one stage
 __device__ __forceinline__ int ns_cpc(int nr, int E) { return max(2, (NS_STAGE_BYTES / (nr * E)) & ~1); }
 
 template <typename C, int NR>
-static __global__ void __launch_bounds__(NS_NT, 2) k_near_stream(
+static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR>::MINB) k_near_stream(
     const int32_t* part, const int64_t* tleaf, const int64_t* pb, const int64_t* pe, const int64_t* nbase,
     const int32_t* ncolv, const int64_t* xbase, const int32_t* xcol, const C* B, const int64_t* cptr,
     const int32_t* ccol, const C* cval, const C* xt, C* yt, int nrhs, int r0, int rc, int* err) {
   typedef NsLayout<C, NR> Ly;
   typedef decltype(xt[0].x) R;
-  constexpr int E = Ly::E, XW = Ly::XW;
+  constexpr int E = Ly::E, XW = Ly::XW, NS_STAGES = Ly::STAGES;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)((((uintptr_t)smem_raw) + 127) & ~(uintptr_t)127);
   unsigned char* ring = sm;
@@ -165,24 +167,25 @@ static __global__ void __launch_bounds__(NS_NT, 2) k_near_stream(
     for (int q = t; q < nr * NR; q += NS_CONS) cor[q] = mk((R)0, (R)0);
     ns_cons_sync();
     const int ncor = crow[nr];
-    for (int e0 = 0; e0 < ncor; e0 += 4 * NS_CONS) {
-      // all loads first (4 entries per thread), then the density gathers, then per-entry products
-      C v[4];
-      int col[4];
+    constexpr int CE = NR <= 4 ? 4 : 1;  // correction entries per thread and pass (register budget)
+    for (int e0 = 0; e0 < ncor; e0 += CE * NS_CONS) {
+      // all loads first (CE entries per thread), then the density gathers, then per-entry products
+      C v[CE];
+      int col[CE];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < CE; ++j) {
         const int e = e0 + j * NS_CONS + t;
         v[j] = e < ncor ? cval[cb + e] : mk((R)0, (R)0);
         col[j] = e < ncor ? ccol[cb + e] : 0;
       }
-      C xv[4][NR];
+      C xv[CE][NR];
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
+      for (int j = 0; j < CE; ++j)
 #pragma unroll
         for (int q = 0; q < NR; ++q)
           xv[j][q] = (e0 + j * NS_CONS + t < ncor && q < rc) ? xt[(int64_t)col[j] * nrhs + r0 + q] : mk((R)0, (R)0);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < CE; ++j) {
         const int e = e0 + j * NS_CONS + t;
         int row = -1;  // largest r with crow[r] <= e (rows are non-decreasing along the lanes)
         if (e < ncor) {
@@ -310,8 +313,10 @@ int near_stream(fda_plan_s* P, const C* B, const C* cval, const C* xt, C* yt, in
     set_error("near-field stream needs leaves of at most %d points (got %d)", NS_CONS, P->near_max_nr);
     return FDA_E_INVALID_ARG;
   }
+  // right-hand sides per pass over the matrix: 1, 4, or 16 for wide batches (each pass streams it once)
   if (nrhs == 1) return near_stream_t<C, 1>(P, B, cval, xt, yt, nrhs, s, launches);
-  return near_stream_t<C, 4>(P, B, cval, xt, yt, nrhs, s, launches);
+  if (nrhs < 12 || P->near_wide == 0) return near_stream_t<C, 4>(P, B, cval, xt, yt, nrhs, s, launches);
+  return near_stream_t<C, 16>(P, B, cval, xt, yt, nrhs, s, launches);
 }
 
 template int near_stream<float2>(fda_plan_s*, const float2*, const float2*, const float2*, float2*, int,

@@ -49,6 +49,9 @@ struct RunOps {
 }  // namespace fda
 
 struct fda_plan_s {
+  fda_plan_s() {
+    for (int l = 0; l < FDA_MAXLEV; ++l) m2l_choice[l][0] = m2l_choice[l][1] = -1;
+  }
   fda_tree_s* tree = nullptr;
   bm_problem_s* prob = nullptr;
   fda_config_t cfg;
@@ -94,6 +97,8 @@ struct fda_plan_s {
   std::vector<fda::GemmUnit> h_tc3_units[FDA_MAXLEV][2];
   fda::DBuf<fda::GemmUnit> tc3_units[FDA_MAXLEV][2];
   int tc3_mt[FDA_MAXLEV][2] = {{0}};  // largest number of 128-row tiles of a unit
+  int m2l_choice[FDA_MAXLEV][2];      // autotuned M2L kernel per (level, stage), -1: from the plan options
+  int near_wide = -1;                 // autotuned right-hand sides per near-field pass for wide batches
   fda::DBuf<int64_t> pair_src, pair_tgt;  // coefficient indices (slot + wedge * s)
   fda::DBuf<int64_t> pair_mid;            // low-rank intermediate index per pair (-1 if dense)
   int64_t n_pairs = 0, n_mid = 0;
@@ -122,4 +127,5 @@ namespace fda {
 int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P);
 int plan_matvec(fda_plan_s* P, int prec, const void* x, void* y, int nrhs, int io_dtype, cudaStream_t s,
                 bool tree_order);
+int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R);
 }  // namespace fda

@@ -1281,7 +1281,7 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
       FDA_CUDA(cudaGetDevice(&dev));
       FDA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
       const int64_t nt = (int64_t)tleaf.size();
-      int grid = (int)std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)nsm, nt));
+      int grid = (int)std::max<int64_t>(1, std::min<int64_t>(3 * (int64_t)nsm, nt));
       std::vector<int64_t> cost(nt + 1, 0);
       for (int64_t u = 0; u < nt; ++u) {
         int64_t nr = T->h_pe[tleaf[u]] - T->h_pb[tleaf[u]];

@@ -70,6 +70,12 @@ class fda_tree_view_t(C.Structure):
                 ("m2l_info", _i32p)]
 
 
+class fda_tune_report_t(C.Structure):
+    _fields_ = [("entries", C.c_int32), ("level", C.c_int32 * 64), ("stage", C.c_int32 * 64),
+                ("ms_fma", C.c_double * 64), ("ms_tensor", C.c_double * 64), ("chosen", C.c_int32 * 64),
+                ("near_ms", C.c_double * 2), ("near_rhs_per_pass", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
 class fda_plan_info_t(C.Structure):
     _fields_ = [("n_levels", C.c_int32), ("lmin", C.c_int32), ("precision", C.c_int32), ("lowrank", C.c_int32),
                 ("s", C.c_int32 * 32), ("n_equiv", C.c_int32 * 32), ("n_check", C.c_int32 * 32),
@@ -98,6 +104,12 @@ _SIGS = [
     ("fda_precompute_translations", C.c_int, [C.c_void_p, C.POINTER(fda_config_t), C.POINTER(C.c_void_p)]),
     ("fda_matvec", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     ("fda_plan_info", C.c_int, [C.c_void_p, C.POINTER(fda_plan_info_t)]),
+    ("fda_matvec_graph_create", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                          C.POINTER(C.c_void_p)]),
+    ("fda_graph_launch", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("fda_autotune", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(fda_tune_report_t)]),
+    ("fda_graph_nodes", C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    ("fda_graph_destroy", None, [C.c_void_p]),
     ("fda_corrections_export", C.c_int, [C.c_void_p, _i64p, C.c_int64, C.c_int64, _i64p, _i64p, _dp]),
     ("fda_plan_destroy", None, [C.c_void_p]),
     ("bm_gmres_solve", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(bm_gmres_opts_t),
@@ -272,6 +284,40 @@ def fda_device_peaks() -> tuple:
     b = C.c_double()
     _check(lib().fda_device_peaks(C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def fda_matvec_graph_create(plan, precision, x, y, stream=None):
+    """Capture one product y = A x (fixed x, y tensors) into a CUDA graph; returns the graph handle."""
+    import torch
+    nrhs = 1 if x.dim() == 1 else x.shape[0]
+    dt = FDA_CPLX128 if x.dtype == torch.complex128 else FDA_CPLX64
+    g = C.c_void_p()
+    _check(lib().fda_matvec_graph_create(plan, int(precision), C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                         nrhs, dt, _stream(stream), C.byref(g)))
+    return g
+
+
+def fda_autotune(plan, nrhs=1, stream=None) -> dict:
+    """Pick the faster M2L kernel per (level, stage), and the near-field batch width, for this nrhs."""
+    R = fda_tune_report_t()
+    _check(lib().fda_autotune(plan, int(nrhs), _stream(stream), C.byref(R)))
+    rows = [dict(level=R.level[e], stage=R.stage[e], ms_fma=R.ms_fma[e], ms_tensor=R.ms_tensor[e],
+                 chosen="tensor" if R.chosen[e] else "fma") for e in range(R.entries)]
+    return dict(m2l=rows, near_ms=list(R.near_ms), near_rhs_per_pass=R.near_rhs_per_pass)
+
+
+def fda_graph_launch(g, stream=None):
+    _check(lib().fda_graph_launch(g, _stream(stream)))
+
+
+def fda_graph_nodes(g) -> int:
+    n = C.c_int64()
+    _check(lib().fda_graph_nodes(g, C.byref(n)))
+    return int(n.value)
+
+
+def fda_graph_destroy(g):
+    lib().fda_graph_destroy(g)
 
 
 def fda_plan_info(plan) -> dict:

@@ -256,3 +256,85 @@ def test_fda_matvec_tensor_core_m2l(mode):
             assert err < 3e-4, (mode, r, err)
     finally:
         S.close()
+
+
+# ------------------------------------------------------------------ lockstep block GMRES (several directions)
+@pytest.mark.parametrize("refine", [False, True])
+def test_block_gmres_several_directions_match_oracle(refine):
+    """Three incident directions solved together (one block matvec per step, a Krylov space per column):
+    every column meets the residual and matches the dense oracle solve of its own right-hand side."""
+    _need_gpu()
+    mesh = inputs.icosphere(4, 0.5)
+    k = 10.0
+    dirs = np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0], [0.0, 0.6, 0.8]])
+    S = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=1e-6, leaf_max=64,
+                     precision=fdbem.FDA_PREC_FP32 if refine else fdbem.FDA_PREC_FP64, nrhs_max=3)
+    try:
+        b = torch.empty((3, S.N), dtype=torch.complex128, device=DEV)
+        fdbem.bm_rhs_plane_wave(S.prob, dirs, b)
+        x = torch.zeros_like(b)
+        st = S.solve(b, x, tol=1e-6, restart=40, max_iter=400, refine=refine, inner_tol=1e-3)
+        assert st["status"] == 0 and st["rel_residual"] <= 1e-6
+        xs, ns, ws = O.geometry(mesh.nodes, mesh.elems)
+        A = O.dense_matrix(mesh.nodes, mesh.elems, k)
+        for c in range(3):
+            xo = np.linalg.solve(A, O.bm_rhs(xs, ns, k, dirs[c]))
+            xg = x[c].cpu().numpy()
+            assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) < 1e-4, c
+    finally:
+        S.close()
+
+
+# ------------------------------------------------------------------ CUDA-graph replay and the autotuner
+def test_graph_replay_equals_direct_matvec():
+    """A captured product replayed twice (x refreshed in place) equals the direct product of the same x."""
+    _need_gpu()
+    mesh = inputs.icosphere(6, 0.5)
+    S = fdbem.Solver(mesh.nodes, mesh.elems, 20.0, eps=1e-5, leaf_max=64, precision=fdbem.FDA_PREC_FP32,
+                     m2l_tensor=1, nrhs_max=4)
+    try:
+        xd = torch.empty((4, S.N), dtype=torch.complex64, device=DEV)
+        yd = torch.empty_like(xd)
+        g = fdbem.fda_matvec_graph_create(S.plan, fdbem.FDA_PREC_FP32, xd, yd)
+        try:
+            assert fdbem.fda_graph_nodes(g) > 10
+            for seed in (3, 4):
+                x = torch.from_numpy(inputs.complex_gaussian(S.N, seed, nrhs=4).astype(np.complex64)).to(DEV)
+                xd.copy_(x)
+                fdbem.fda_graph_launch(g)
+                torch.cuda.synchronize()
+                yr = torch.empty_like(yd)
+                fdbem.fda_matvec_ex(S.plan, fdbem.FDA_PREC_FP32, x, yr)
+                torch.cuda.synchronize()
+                err = (torch.linalg.norm(yd - yr) / torch.linalg.norm(yr)).item()
+                assert err < 1e-5, err  # same kernels; only the order of atomic additions differs
+        finally:
+            fdbem.fda_graph_destroy(g)
+    finally:
+        S.close()
+
+
+def test_autotuner_choices_keep_parity():
+    """The autotuner times both M2L kernels per (level, stage) and the near-field batch width; the tuned
+    plan still meets the mixed-precision bar against the oracle."""
+    _need_gpu()
+    mesh = inputs.icosphere(8, 0.5)
+    k = 20.0
+    S = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=1e-5, leaf_max=64, precision=fdbem.FDA_PREC_FP32,
+                     m2l_tensor=1, nrhs_max=16)
+    try:
+        rep = fdbem.fda_autotune(S.plan, 16)
+        assert rep["m2l"] and all(r["ms_fma"] > 0 and r["ms_tensor"] > 0 for r in rep["m2l"])
+        assert rep["near_rhs_per_pass"] in (4, 16) and min(rep["near_ms"]) > 0
+        x = inputs.complex_gaussian(S.N, 9, nrhs=16)
+        xd = torch.from_numpy(x).to(DEV).contiguous()
+        yd = torch.empty_like(xd)
+        fdbem.fda_matvec_ex(S.plan, fdbem.FDA_PREC_FP32, xd, yd)
+        torch.cuda.synchronize()
+        rows = inputs.sample_rows(S.N, 100, 7)
+        for r in (0, 15):
+            yo = _oracle_rows(mesh, k, x[r], rows)
+            err = np.linalg.norm(yd[r].cpu().numpy()[rows] - yo) / np.linalg.norm(yo)
+            assert err < 3e-4, (r, err)
+    finally:
+        S.close()
