@@ -139,7 +139,7 @@ static __global__ void __launch_bounds__(TC_NT) k_m2l_tc(const GemmUnit* units, 
                                                          const float2* poolLR, const int64_t* psrc,
                                                          const int64_t* ptgt, const int64_t* pmid,
                                                          const float2* cout, float2* cin, float2* mid, int nrhs,
-                                                         int* err) {
+                                                         int64_t ldc, int64_t ldm, int* err) {
   constexpr int KC = SPLIT ? 16 : 32;  // real K per chunk
   extern __shared__ unsigned char smem_raw[];
   typedef TcSmem<KC, MTC, SPLIT> Sm;
@@ -148,6 +148,7 @@ static __global__ void __launch_bounds__(TC_NT) k_m2l_tc(const GemmUnit* units, 
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   const float2* A = (U.mode == 0 ? poolK : poolLR) + U.a_off;
   const float2* X = (U.mode == 2) ? mid : cout;
+  const int64_t lds = (U.mode == 2) ? ldm : ldc, ldd = (U.mode == 1) ? ldm : ldc;  // right-hand-side strides
   const int rows = min(U.M - U.m0, 64 * MTC);  // complex rows of this unit
   const int MT = (rows + 63) / 64;
   if (w == 0) {
@@ -190,7 +191,7 @@ static __global__ void __launch_bounds__(TC_NT) k_m2l_tc(const GemmUnit* units, 
     for (int q = t; q < TC_N * (KC / 2); q += TC_NT) {
       int j = q % (KC / 2), n = q / (KC / 2);
       int gj = k0 / 2 + j;
-      float2 x = (S.sbase[n] >= 0 && gj < U.K) ? X[(S.sbase[n] + gj) * nrhs + S.srr[n]] : make_float2(0.f, 0.f);
+      float2 x = (S.sbase[n] >= 0 && gj < U.K) ? X[(int64_t)S.srr[n] * lds + S.sbase[n] + gj] : make_float2(0.f, 0.f);
       float v[2] = {x.x, x.y};
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
@@ -289,7 +290,7 @@ static __global__ void __launch_bounds__(TC_NT) k_m2l_tc(const GemmUnit* units, 
             for (int q = 0; q < 32; ++q) {
               int n = 32 * h + q;
               if (S.dbase[n] < 0) continue;
-              int64_t d = (S.dbase[n] + ci) * nrhs + S.srr[n];
+              int64_t d = (int64_t)S.srr[n] * ldd + S.dbase[n] + ci;
               if (U.mode == 1)
                 ((float*)(mid + d))[part] = v[q];
               else
@@ -316,7 +317,7 @@ static size_t tc_smem() {
 template <int SPLIT, int MTC>
 static int tc_launch(const GemmUnit* units, size_t nunits, const float2* poolK, const float2* poolLR,
                      const int64_t* psrc, const int64_t* ptgt, const int64_t* pmid, const float2* cout, float2* cin,
-                     float2* mid, int nrhs, int* err, cudaStream_t s) {
+                     float2* mid, int nrhs, int64_t ldc, int64_t ldm, int* err, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     FDA_CUDA(cudaFuncSetAttribute(k_m2l_tc<SPLIT, MTC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -326,7 +327,7 @@ static int tc_launch(const GemmUnit* units, size_t nunits, const float2* poolK, 
   for (size_t u0 = 0; u0 < nunits; u0 += 65535) {
     unsigned n = (unsigned)std::min<size_t>(65535, nunits - u0);
     k_m2l_tc<SPLIT, MTC><<<n, TC_NT, tc_smem<SPLIT, MTC>(), s>>>(units + u0, poolK, poolLR, psrc, ptgt, pmid, cout,
-                                                                 cin, mid, nrhs, err);
+                                                                 cin, mid, nrhs, ldc, ldm, err);
     FDA_LAUNCH_CHECK();
   }
   return FDA_OK;
@@ -335,9 +336,10 @@ static int tc_launch(const GemmUnit* units, size_t nunits, const float2* poolK, 
 // max_rows: the largest number of complex output rows any unit of this launch covers (<= 256)
 int m2l_tc_launch(const GemmUnit* units, size_t nunits, const float2* poolK, const float2* poolLR,
                   const int64_t* psrc, const int64_t* ptgt, const int64_t* pmid, const float2* cout, float2* cin,
-                  float2* mid, int nrhs, int split, int max_rows, int* err, cudaStream_t s) {
+                  float2* mid, int nrhs, int64_t ldc, int64_t ldm, int split, int max_rows, int* err, cudaStream_t s) {
   int mt = (max_rows + 63) / 64;
-#define TCL(S_, M_) return tc_launch<S_, M_>(units, nunits, poolK, poolLR, psrc, ptgt, pmid, cout, cin, mid, nrhs, err, s)
+#define TCL(S_, M_) \
+  return tc_launch<S_, M_>(units, nunits, poolK, poolLR, psrc, ptgt, pmid, cout, cin, mid, nrhs, ldc, ldm, err, s)
   if (split) {
     if (mt <= 1) TCL(1, 1);
     if (mt <= 2) TCL(1, 2);
@@ -462,7 +464,7 @@ template <int MTC, int N, int NST>
 static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units, const float* img,
                                                           const int64_t* psrc, const int64_t* ptgt,
                                                           const int64_t* pmid, const float2* cout, float2* cin,
-                                                          float2* mid, int nrhs, int* err) {
+                                                          float2* mid, int nrhs, int64_t ldc, int64_t ldm, int* err) {
   typedef Tc3Smem<MTC, N, NST> Sm;
   extern __shared__ unsigned char smem_raw[];
   Sm& S = *reinterpret_cast<Sm*>((((uintptr_t)smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -473,6 +475,7 @@ static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units
   const GemmUnit U = units[blockIdx.x];
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   const float2* X = (U.mode == 2) ? mid : cout;
+  const int64_t lds = (U.mode == 2) ? ldm : ldc, ldd = (U.mode == 1) ? ldm : ldc;  // right-hand-side strides
   const int MT = min(MTC, (2 * U.M + 127) / 128);
   const int nk = (2 * U.K + TC3_KC - 1) / TC3_KC;
   const float* A = img + U.a_off;
@@ -527,7 +530,7 @@ static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units
       if (S.sbase[n] < 0) continue;  // unused column: its results are never read
       const int gj = kc * (TC3_KC / 2) + j;
       const bool in = gj < U.K;
-      const float2* src = in ? X + (S.sbase[n] + gj) * nrhs + S.srr[n] : X;
+      const float2* src = in ? X + (int64_t)S.srr[n] * lds + S.sbase[n] + gj : X;
       tc3_cp8(bbase + kmaj_off(n, 2 * j, TC3_KC), src, in ? 8u : 0u);
     }
     tc3_commit_group();
@@ -605,7 +608,7 @@ static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units
             const int n = col0 + q + part;
             const int64_t db = S.dbase[n];
             if (db < 0 || ci >= U.M) continue;
-            const int64_t d = (db + ci) * nrhs + S.srr[n];
+            const int64_t d = (int64_t)S.srr[n] * ldd + db + ci;
             if (U.mode == 1)
               mid[d] = val;
             else
@@ -628,7 +631,7 @@ static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units
 template <int MTC, int N, int NST>
 static int tc3_launch_t(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc,
                         const int64_t* ptgt, const int64_t* pmid, const float2* cout, float2* cin, float2* mid,
-                        int nrhs, int* err, cudaStream_t s) {
+                        int nrhs, int64_t ldc, int64_t ldm, int* err, cudaStream_t s) {
   const size_t smem = sizeof(Tc3Smem<MTC, N, NST>) + 1024;
   static bool attr = false;
   if (!attr) {
@@ -637,7 +640,8 @@ static int tc3_launch_t(const GemmUnit* units, size_t nunits, const float* img, 
   }
   for (size_t u0 = 0; u0 < nunits; u0 += 65535) {
     unsigned n = (unsigned)std::min<size_t>(65535, nunits - u0);
-    k_m2l_tc3<MTC, N, NST><<<n, TC3_NT, smem, s>>>(units + u0, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, err);
+    k_m2l_tc3<MTC, N, NST><<<n, TC3_NT, smem, s>>>(units + u0, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, ldc, ldm,
+                                                   err);
     FDA_LAUNCH_CHECK();
   }
   return FDA_OK;
@@ -645,16 +649,16 @@ static int tc3_launch_t(const GemmUnit* units, size_t nunits, const float* img, 
 
 // max_mt: the largest number of 128-row tiles of any unit of this launch (1..4)
 int m2l_tc3_launch(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc, const int64_t* ptgt,
-                   const int64_t* pmid, const float2* cout, float2* cin, float2* mid, int nrhs, int max_mt, int* err,
-                   cudaStream_t s) {
+                   const int64_t* pmid, const float2* cout, float2* cin, float2* mid, int nrhs, int64_t ldc,
+                   int64_t ldm, int max_mt, int* err, cudaStream_t s) {
   if (max_mt < 1 || max_mt > 4) {
     set_error("tensor-core M2L supports at most 256 complex output rows (got %d tiles)", max_mt);
     return FDA_E_INVALID_ARG;
   }
   if (nunits == 0) return FDA_OK;
-  if (max_mt == 1) return tc3_launch_t<1, 128, 3>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, err, s);
-  if (max_mt == 2) return tc3_launch_t<2, 128, 2>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, err, s);
-  return tc3_launch_t<4, 64, 2>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, err, s);
+  if (max_mt == 1) return tc3_launch_t<1, 128, 3>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, ldc, ldm, err, s);
+  if (max_mt == 2) return tc3_launch_t<2, 128, 2>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, ldc, ldm, err, s);
+  return tc3_launch_t<4, 64, 2>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, ldc, ldm, err, s);
 }
 
 }  // namespace fda
@@ -704,12 +708,13 @@ extern "C" int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_
     FDA_TRY(tc3_build_images({TcImgJob{dA64.p, M, K, 0}}, img.p));
     GemmUnit u{0, M, K, 0, P, 0, 0, 0};
     FDA_TRY(du.upload(&u, 1));
-    FDA_TRY(m2l_tc3_launch(du.p, 1, img.p, src.p, tgt.p, pm.p, dX.p, dY.p, dmid.p, 1, (2 * M + 127) / 128, err.p, 0));
+    FDA_TRY(m2l_tc3_launch(du.p, 1, img.p, src.p, tgt.p, pm.p, dX.p, dY.p, dmid.p, 1, 0, 0, (2 * M + 127) / 128, err.p,
+                           0));
     FDA_CUDA(cudaDeviceSynchronize());
   } else {
     GemmUnit u{0, M, K, 0, P, 0, 0, 0};
     FDA_TRY(du.upload(&u, 1));
-    FDA_TRY(m2l_tc_launch(du.p, 1, dA.p, dA.p, src.p, tgt.p, pm.p, dX.p, dY.p, dmid.p, 1, split, M, err.p, 0));
+    FDA_TRY(m2l_tc_launch(du.p, 1, dA.p, dA.p, src.p, tgt.p, pm.p, dX.p, dY.p, dmid.p, 1, 0, 0, split, M, err.p, 0));
     FDA_CUDA(cudaDeviceSynchronize());
   }
   std::vector<float2> hY;

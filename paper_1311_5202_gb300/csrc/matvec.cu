@@ -5,8 +5,9 @@
 //   M2L    : u_B,-z += K~(offset) t_C,z  (dense, or U^ (V^ t) when low rank)           (Eq. cmpk, lrdk)
 //   L2L    : u_c,z' += sum_{z in z'} M~(l, octant, z)^T u_P,z                          (Eq. cmpl, L = M^T)
 //   L2T    : y_C += sum_z T~_C,z u_C,z                                                  (Eq. cmpt, eval2t)
-// Vectors live in tree order with the RHS index fastest: v[(point) * nrhs + rhs]; coefficients likewise:
-// c[(slot + wedge * s + r) * nrhs + rhs]. One template serves FP64 (double2) and FP32 (float2) operators.
+// Vectors live in tree order with the RHS index fastest: v[(point) * nrhs + rhs]; coefficients (outgoing,
+// incoming, low-rank intermediate) are right-hand-side major: c[rhs * n + slot + wedge * s + r], so that
+// the gathers and scatters of a translation stay contiguous for every right-hand side. One template serves FP64 (double2) and FP32 (float2) operators.
 #include "plan.cuh"
 
 #include <cstring>
@@ -16,11 +17,11 @@
 namespace fda {
 
 int m2l_tc3_launch(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc, const int64_t* ptgt,
-                   const int64_t* pmid, const float2* cout, float2* cin, float2* mid, int nrhs, int max_mt, int* err,
-                   cudaStream_t s);
+                   const int64_t* pmid, const float2* cout, float2* cin, float2* mid, int nrhs, int64_t ldc,
+                   int64_t ldm, int max_mt, int* err, cudaStream_t s);
 int m2l_tc_launch(const GemmUnit* units, size_t nunits, const float2* poolK, const float2* poolLR,
                   const int64_t* psrc, const int64_t* ptgt, const int64_t* pmid, const float2* cout, float2* cin,
-                  float2* mid, int nrhs, int split, int max_rows, int* err, cudaStream_t s);
+                  float2* mid, int nrhs, int64_t ldc, int64_t ldm, int split, int max_rows, int* err, cudaStream_t s);
 
 template <typename C>
 int near_stream(fda_plan_s* P, const C* B, const C* cval, const C* xt, C* yt, int nrhs, cudaStream_t s,
@@ -173,7 +174,7 @@ static __global__ void __launch_bounds__(NEAR_NT) k_near(const int64_t* tleaf, c
 template <typename C>
 static __global__ void k_s2m(const int64_t* leaves, const int64_t* soff, const int64_t* pb, const int64_t* pe,
                              const int32_t* lev, const int64_t* slot, const int* ls, const int* lnw, const C* S,
-                             const C* xt, C* cout, int nrhs, int r0, int rc) {
+                             const C* xt, C* cout, int nrhs, int64_t ldc, int r0, int rc) {
   extern __shared__ unsigned char smem_raw[];
   C* xs = (C*)smem_raw;
   const int64_t b = leaves[blockIdx.x];
@@ -191,10 +192,10 @@ static __global__ void k_s2m(const int64_t* leaves, const int64_t* soff, const i
   const C* Sz = S + soff[blockIdx.x] + (int64_t)z * s * nC;
   const int64_t base = slot[b] + (int64_t)z * s;
   for (int q = threadIdx.x; q < s * rc; q += blockDim.x) {
-    int r = q / rc, rr = q - r * rc;
+    int rr = q / s, r = q - rr * s;
     C acc = mk((decltype(acc.x))0, (decltype(acc.x))0);
     for (int j = 0; j < nC; ++j) cfma(acc, Sz[(int64_t)j * s + r], xs[j * rc + rr]);
-    cout[(base + r) * nrhs + r0 + rr] = acc;
+    cout[(int64_t)(r0 + rr) * ldc + base + r] = acc;
   }
 }
 
@@ -209,7 +210,7 @@ __device__ __forceinline__ int child_wedge_dev(int hf_c, int n, int nc, int z) {
 template <typename C>
 static __global__ void k_m2m(const int64_t* parents, const int64_t* cbeg, const int32_t* nch, const int32_t* ix,
                              const int32_t* iy, const int32_t* iz, const int64_t* slot, int sl, int sc_, int nwl,
-                             int nl, int nc, int hf_c, const C* M, C* cout, int nrhs, int r0, int rc) {
+                             int nl, int nc, int hf_c, const C* M, C* cout, int nrhs, int64_t ldc, int r0, int rc) {
   extern __shared__ unsigned char smem_raw[];
   C* ts = (C*)smem_raw;
   const int64_t P = parents[blockIdx.x];
@@ -224,22 +225,22 @@ static __global__ void k_m2m(const int64_t* parents, const int64_t* cbeg, const 
       const C* Mz = M + (int64_t)(o * nwl + z) * sl * sc_;
       __syncthreads();
       for (int q = threadIdx.x; q < sc_ * rc; q += blockDim.x) {
-        int j = q / rc, rr = q - j * rc;
-        ts[q] = cout[(slot[c] + (int64_t)zc * sc_ + j) * nrhs + r0 + rr];
+        int rr = q / sc_, j = q - rr * sc_;
+        ts[q] = cout[(int64_t)(r0 + rr) * ldc + slot[c] + (int64_t)zc * sc_ + j];
       }
       __syncthreads();
       for (int u = 0; u < 4; ++u) {
         int q = q0 + threadIdx.x + u * blockDim.x;
         if (q >= nout) break;
-        int r = q / rc, rr = q - r * rc;
-        for (int j = 0; j < sc_; ++j) cfma(acc[u], Mz[(int64_t)j * sl + r], ts[j * rc + rr]);
+        int rr = q / sl, r = q - rr * sl;
+        for (int j = 0; j < sc_; ++j) cfma(acc[u], Mz[(int64_t)j * sl + r], ts[rr * sc_ + j]);
       }
     }
     for (int u = 0; u < 4; ++u) {
       int q = q0 + threadIdx.x + u * blockDim.x;
       if (q >= nout) break;
-      int r = q / rc, rr = q - r * rc;
-      cout[(slot[P] + (int64_t)z * sl + r) * nrhs + r0 + rr] = acc[u];
+      int rr = q / sl, r = q - rr * sl;
+      cout[(int64_t)(r0 + rr) * ldc + slot[P] + (int64_t)z * sl + r] = acc[u];
     }
   }
 }
@@ -248,10 +249,10 @@ static __global__ void k_m2m(const int64_t* parents, const int64_t* cbeg, const 
 template <typename C>
 static __global__ void k_l2l(int64_t box0, const int64_t* par, const int32_t* ix, const int32_t* iy,
                              const int32_t* iz, const int64_t* slot, int sl, int sc_, int nwl, int nl, int nc,
-                             int hf_c, const C* M, C* cin, int nrhs, int r0, int rc) {
+                             int hf_c, const C* M, C* cin, int nrhs, int64_t ldc, int r0, int rc) {
   extern __shared__ unsigned char smem_raw[];
-  C* us = (C*)smem_raw;
-  C* acc = us + sl * rc;
+  C* us = (C*)smem_raw;   // [rr][j], parent wedge coefficients
+  C* acc = us + sl * rc;  // [rr][r], child coefficients
   const int64_t c = box0 + blockIdx.x;
   const int zc = blockIdx.y;
   const int64_t P = par[c];
@@ -264,24 +265,24 @@ static __global__ void k_l2l(int64_t box0, const int64_t* par, const int32_t* ix
     const C* Mz = M + (int64_t)(o * nwl + z) * sl * sc_;
     __syncthreads();
     for (int q = threadIdx.x; q < sl * rc; q += blockDim.x) {
-      int j = q / rc, rr = q - j * rc;
-      us[q] = cin[(slot[P] + (int64_t)z * sl + j) * nrhs + r0 + rr];
+      int rr = q / sl, j = q - rr * sl;
+      us[q] = cin[(int64_t)(r0 + rr) * ldc + slot[P] + (int64_t)z * sl + j];
     }
     __syncthreads();
     for (int r = w; r < sc_; r += nwarp) {
       const C* col = Mz + (int64_t)r * sl;  // column r of M~ = row r of M~^T
       for (int rr = 0; rr < rc; ++rr) {
         C a = mk((decltype(acc[0].x))0, (decltype(acc[0].x))0);
-        for (int j = lane; j < sl; j += 32) cfma(a, col[j], us[j * rc + rr]);
+        for (int j = lane; j < sl; j += 32) cfma(a, col[j], us[rr * sl + j]);
         a = warp_csum(a);
-        if (lane == 0) acc[r * rc + rr] = cadd(acc[r * rc + rr], a);
+        if (lane == 0) acc[rr * sc_ + r] = cadd(acc[rr * sc_ + r], a);
       }
     }
   }
   __syncthreads();
   for (int q = threadIdx.x; q < nout; q += blockDim.x) {
-    int r = q / rc, rr = q - r * rc;
-    C* d = cin + (slot[c] + (int64_t)zc * sc_ + r) * nrhs + r0 + rr;
+    int rr = q / sc_, r = q - rr * sc_;
+    C* d = cin + (int64_t)(r0 + rr) * ldc + slot[c] + (int64_t)zc * sc_ + r;
     *d = cadd(*d, acc[q]);
   }
 }
@@ -290,9 +291,9 @@ static __global__ void k_l2l(int64_t box0, const int64_t* par, const int32_t* ix
 template <typename C>
 static __global__ void k_l2t(const int64_t* leaves, const int64_t* toff, const int64_t* pb, const int64_t* pe,
                              const int32_t* lev, const int64_t* slot, const int* ls, const int* lnw, const C* Tm,
-                             const C* cin, C* yt, int nrhs, int r0, int rc) {
+                             const C* cin, C* yt, int nrhs, int64_t ldc, int r0, int rc) {
   extern __shared__ unsigned char smem_raw[];
-  C* us = (C*)smem_raw;
+  C* us = (C*)smem_raw;  // [rr][r]
   const int64_t b = leaves[blockIdx.x];
   const int l = lev[b];
   const int s = ls[l], nw = lnw[l];
@@ -301,15 +302,15 @@ static __global__ void k_l2t(const int64_t* leaves, const int64_t* toff, const i
   for (int z = 0; z < nw; ++z) {
     __syncthreads();
     for (int q = threadIdx.x; q < s * rc; q += blockDim.x) {
-      int r = q / rc, rr = q - r * rc;
-      us[q] = cin[(slot[b] + (int64_t)z * s + r) * nrhs + r0 + rr];
+      int rr = q / s, r = q - rr * s;
+      us[q] = cin[(int64_t)(r0 + rr) * ldc + slot[b] + (int64_t)z * s + r];
     }
     __syncthreads();
     const C* Tz = Tm + toff[blockIdx.x] + (int64_t)z * s * nC;
     for (int q = threadIdx.x; q < nC * rc; q += blockDim.x) {
       int i = q / rc, rr = q - i * rc;
       C acc = mk((decltype(us[0].x))0, (decltype(us[0].x))0);
-      for (int r = 0; r < s; ++r) cfma(acc, Tz[(int64_t)r * nC + i], us[r * rc + rr]);
+      for (int r = 0; r < s; ++r) cfma(acc, Tz[(int64_t)r * nC + i], us[rr * s + r]);
       C* d = yt + (p0 + i) * nrhs + r0 + rr;
       *d = cadd(*d, acc);
     }
@@ -324,7 +325,7 @@ template <typename C>
 static __global__ void __launch_bounds__(256) k_m2l(const GemmUnit* units, const C* poolK, const C* poolLR,
                                                     const int64_t* psrc,
                                                     const int64_t* ptgt, const int64_t* pmid, const C* cout,
-                                                    C* cin, C* mid, int nrhs) {
+                                                    C* cin, C* mid, int nrhs, int64_t ldc, int64_t ldm) {
   __shared__ C As[M2L_TK][M2L_TM + 1];
   __shared__ C Xs[M2L_TK][M2L_TN + 1];
   __shared__ int64_t sbase[M2L_TN], dbase[M2L_TN];
@@ -333,6 +334,7 @@ static __global__ void __launch_bounds__(256) k_m2l(const GemmUnit* units, const
   const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
   const C* A = (U.mode == 0 ? poolK : poolLR) + U.a_off;
   const C* X = (U.mode == 2) ? mid : cout;
+  const int64_t lds = (U.mode == 2) ? ldm : ldc, ldd = (U.mode == 1) ? ldm : ldc;  // right-hand-side strides
   const int ncols = U.p_count * nrhs;
   for (int c0 = 0; c0 < ncols; c0 += M2L_TN) {
     __syncthreads();
@@ -362,9 +364,9 @@ static __global__ void __launch_bounds__(256) k_m2l(const GemmUnit* units, const
         As[kk][mm] = (gm < U.M && gk < U.K) ? A[gm + (int64_t)gk * U.M] : mk((decltype(acc[0].x))0, (decltype(acc[0].x))0);
       }
       for (int q = t; q < M2L_TK * M2L_TN; q += 256) {
-        int cc = q % M2L_TN, kk = q / M2L_TN;
+        int kk = q % M2L_TK, cc = q / M2L_TK;
         int gk = k0 + kk;
-        Xs[kk][cc] = (sbase[cc] >= 0 && gk < U.K) ? X[(sbase[cc] + gk) * nrhs + srr[cc]]
+        Xs[kk][cc] = (sbase[cc] >= 0 && gk < U.K) ? X[(int64_t)srr[cc] * lds + sbase[cc] + gk]
                                                   : mk((decltype(acc[0].x))0, (decltype(acc[0].x))0);
       }
       __syncthreads();
@@ -380,7 +382,7 @@ static __global__ void __launch_bounds__(256) k_m2l(const GemmUnit* units, const
       for (int q = 0; q < 8; ++q) {
         int gm = U.m0 + ty + 8 * q;
         if (gm >= U.M) continue;
-        int64_t d = (dbase[tx] + gm) * nrhs + srr[tx];
+        int64_t d = (int64_t)srr[tx] * ldd + dbase[tx] + gm;
         if (U.mode == 1)
           mid[d] = acc[q];
         else
@@ -407,8 +409,8 @@ int m2l_stage(fda_plan_s* P, RunOps<C>& op, DBuf<C>& cout, DBuf<C>& cin, DBuf<C>
   if (variant == 1 && f32 && !P->h_tc3_units[l][st].empty()) {
     const size_t n3 = P->h_tc3_units[l][st].size();
     FDA_TRY(m2l_tc3_launch(P->tc3_units[l][st].p, n3, P->tc_img.p, P->pair_src.p, P->pair_tgt.p, P->pair_mid.p,
-                           (const float2*)cout.p, (float2*)cin.p, (float2*)mid.p, nrhs, P->tc3_mt[l][st], P->tc_err.p,
-                           s));
+                           (const float2*)cout.p, (float2*)cin.p, (float2*)mid.p, nrhs, P->n_coef, P->n_mid,
+                           P->tc3_mt[l][st], P->tc_err.p, s));
     *nl += (int64_t)((n3 + 65534) / 65535);
     return FDA_OK;
   }
@@ -416,7 +418,8 @@ int m2l_stage(fda_plan_s* P, RunOps<C>& op, DBuf<C>& cout, DBuf<C>& cin, DBuf<C>
     const size_t ntu = P->h_tc_units[l][st].size();
     FDA_TRY(m2l_tc_launch(P->tc_units[l][st].p, ntu, (const float2*)op.K.p, (const float2*)op.lr.p, P->pair_src.p,
                           P->pair_tgt.p, P->pair_mid.p, (const float2*)cout.p, (float2*)cin.p, (float2*)mid.p, nrhs,
-                          P->cfg.m2l_tensor == 2 ? 1 : 0, P->tc_max_rows[l][st], P->tc_err.p, s));
+                          P->n_coef, P->n_mid, P->cfg.m2l_tensor == 2 ? 1 : 0, P->tc_max_rows[l][st], P->tc_err.p,
+                          s));
     *nl += (int64_t)((ntu + 65534) / 65535);
     return FDA_OK;
   }
@@ -424,7 +427,7 @@ int m2l_stage(fda_plan_s* P, RunOps<C>& op, DBuf<C>& cout, DBuf<C>& cin, DBuf<C>
   for (size_t u0 = 0; u0 < nu; u0 += 65535) {
     unsigned n = (unsigned)std::min<size_t>(65535, nu - u0);
     k_m2l<C><<<n, 256, 0, s>>>(P->units[l][st].p + u0, op.K.p, op.lr.p, P->pair_src.p, P->pair_tgt.p, P->pair_mid.p,
-                               cout.p, cin.p, mid.p, nrhs);
+                               cout.p, cin.p, mid.p, nrhs, P->n_coef, P->n_mid);
     FDA_LAUNCH_CHECK();
     ++*nl;
   }
@@ -491,7 +494,7 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
         int rcc = std::min(rc, nrhs - r0);
         k_s2m<C><<<dim3((unsigned)P->h_leaves.size(), maxnw), 128, sizeof(C) * maxleaf * rcc, s>>>(
             P->leaves.p, P->leaf_s_off.p, T->pb.p, T->pe.p, T->lev.p, P->slot.p, d_ls, d_lnw, op.S.p, xt.p,
-            cout.p, nrhs, r0, rcc);
+            cout.p, nrhs, P->n_coef, r0, rcc);
         FDA_LAUNCH_CHECK();
         ++nl;
       }
@@ -508,7 +511,7 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
         while (nt * 4 < L.s * rcc && nt < 512) nt *= 2;
         k_m2m<C><<<dim3((unsigned)P->h_parents[l].size(), L.nw), nt, sizeof(C) * Lc.s * rcc, s>>>(
             P->parents[l].p, T->cbeg.p, T->nch.p, T->ix.p, T->iy.p, T->iz.p, P->slot.p, L.s, Lc.s, L.nw, L.n, Lc.n,
-            Lc.hf ? 1 : 0, op.M.p + P->m_off[l], cout.p, nrhs, r0, rcc);
+            Lc.hf ? 1 : 0, op.M.p + P->m_off[l], cout.p, nrhs, P->n_coef, r0, rcc);
         FDA_LAUNCH_CHECK();
         ++nl;
       }
@@ -530,7 +533,8 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
         size_t sm = sizeof(C) * ((size_t)L.s * rcc + (size_t)Lc.s * rcc);
         k_l2l<C><<<dim3((unsigned)nchild, Lc.nw), 256, sm, s>>>(Lc.box_begin, T->par.p, T->ix.p, T->iy.p, T->iz.p,
                                                                P->slot.p, L.s, Lc.s, L.nw, L.n, Lc.n, Lc.hf ? 1 : 0,
-                                                               op.M.p + P->m_off[l], cin.p, nrhs, r0, rcc);
+                                                               op.M.p + P->m_off[l], cin.p, nrhs, P->n_coef, r0,
+                                                               rcc);
         FDA_LAUNCH_CHECK();
         ++nl;
       }
@@ -543,7 +547,7 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
         int rcc = std::min(rc, nrhs - r0);
         k_l2t<C><<<(unsigned)P->h_leaves.size(), 128, sizeof(C) * maxs * rcc, s>>>(
             P->leaves.p, P->leaf_t_off.p, T->pb.p, T->pe.p, T->lev.p, P->slot.p, d_ls, d_lnw, op.T.p, cin.p, yt.p,
-            nrhs, r0, rcc);
+            nrhs, P->n_coef, r0, rcc);
         FDA_LAUNCH_CHECK();
         ++nl;
       }
