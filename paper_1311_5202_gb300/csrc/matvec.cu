@@ -318,27 +318,31 @@ static __global__ void k_l2t(const int64_t* leaves, const int64_t* toff, const i
 }
 
 // ------------------------------------------------------------------ M2L (a9): grouped gather-GEMM-scatter
-#define M2L_TM 64
-#define M2L_TN 32
+// One CTA per unit: a TM x TN output tile (TM operator rows, TN gathered columns = pairs x right-hand sides),
+// K in chunks of 16 through shared memory; each of the 256 threads accumulates 8 outputs of one column.
+// The row tile TM (16, 32 or 64; TN = 2048 / TM) is chosen per (level, stage) at plan time to fit the
+// operator's row count (low-rank ranks are often below 20).
 #define M2L_TK 16
-template <typename C>
+template <typename C, int TM>
 static __global__ void __launch_bounds__(256) k_m2l(const GemmUnit* units, const C* poolK, const C* poolLR,
-                                                    const int64_t* psrc,
-                                                    const int64_t* ptgt, const int64_t* pmid, const C* cout,
-                                                    C* cin, C* mid, int nrhs, int64_t ldc, int64_t ldm) {
-  __shared__ C As[M2L_TK][M2L_TM + 1];
-  __shared__ C Xs[M2L_TK][M2L_TN + 1];
-  __shared__ int64_t sbase[M2L_TN], dbase[M2L_TN];
-  __shared__ int srr[M2L_TN];
+                                                    const int64_t* psrc, const int64_t* ptgt, const int64_t* pmid,
+                                                    const C* cout, C* cin, C* mid, int nrhs, int64_t ldc,
+                                                    int64_t ldm) {
+  constexpr int TN = 2048 / TM, RT = 256 / TN;
+  typedef decltype(cout[0].x) R;
+  __shared__ C As[M2L_TK][TM + 1];
+  __shared__ C Xs[M2L_TK][TN + 1];
+  __shared__ int64_t sbase[TN], dbase[TN];
+  __shared__ int srr[TN];
   const GemmUnit U = units[blockIdx.x];
-  const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
+  const int t = threadIdx.x, tx = t % TN, ty = t / TN;
   const C* A = (U.mode == 0 ? poolK : poolLR) + U.a_off;
   const C* X = (U.mode == 2) ? mid : cout;
   const int64_t lds = (U.mode == 2) ? ldm : ldc, ldd = (U.mode == 1) ? ldm : ldc;  // right-hand-side strides
   const int ncols = U.p_count * nrhs;
-  for (int c0 = 0; c0 < ncols; c0 += M2L_TN) {
+  for (int c0 = 0; c0 < ncols; c0 += TN) {
     __syncthreads();
-    if (t < M2L_TN) {
+    if (t < TN) {
       int c = c0 + t;
       if (c < ncols) {
         int p = c / nrhs;
@@ -355,32 +359,32 @@ static __global__ void __launch_bounds__(256) k_m2l(const GemmUnit* units, const
     }
     C acc[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = mk((decltype(acc[0].x))0, (decltype(acc[0].x))0);
+    for (int q = 0; q < 8; ++q) acc[q] = mk((R)0, (R)0);
     for (int k0 = 0; k0 < U.K; k0 += M2L_TK) {
       __syncthreads();
-      for (int q = t; q < M2L_TK * M2L_TM; q += 256) {
-        int mm = q % M2L_TM, kk = q / M2L_TM;
+      for (int q = t; q < M2L_TK * TM; q += 256) {
+        int mm = q % TM, kk = q / TM;
         int gm = U.m0 + mm, gk = k0 + kk;
-        As[kk][mm] = (gm < U.M && gk < U.K) ? A[gm + (int64_t)gk * U.M] : mk((decltype(acc[0].x))0, (decltype(acc[0].x))0);
+        As[kk][mm] = (gm < U.M && gk < U.K) ? A[gm + (int64_t)gk * U.M] : mk((R)0, (R)0);
       }
-      for (int q = t; q < M2L_TK * M2L_TN; q += 256) {
+      for (int q = t; q < M2L_TK * TN; q += 256) {
         int kk = q % M2L_TK, cc = q / M2L_TK;
         int gk = k0 + kk;
-        Xs[kk][cc] = (sbase[cc] >= 0 && gk < U.K) ? X[(int64_t)srr[cc] * lds + sbase[cc] + gk]
-                                                  : mk((decltype(acc[0].x))0, (decltype(acc[0].x))0);
+        Xs[kk][cc] = (sbase[cc] >= 0 && gk < U.K) ? X[(int64_t)srr[cc] * lds + sbase[cc] + gk] : mk((R)0, (R)0);
       }
       __syncthreads();
+      const int kn = min(M2L_TK, U.K - k0);
 #pragma unroll 4
-      for (int kk = 0; kk < M2L_TK; ++kk) {
+      for (int kk = 0; kk < kn; ++kk) {
         C xv = Xs[kk][tx];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) cfma(acc[q], As[kk][ty + 8 * q], xv);
+        for (int q = 0; q < 8; ++q) cfma(acc[q], As[kk][ty + RT * q], xv);
       }
     }
     if (dbase[tx] >= 0) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        int gm = U.m0 + ty + 8 * q;
+        int gm = U.m0 + ty + RT * q;
         if (gm >= U.M) continue;
         int64_t d = (int64_t)srr[tx] * ldd + dbase[tx] + gm;
         if (U.mode == 1)
@@ -424,10 +428,19 @@ int m2l_stage(fda_plan_s* P, RunOps<C>& op, DBuf<C>& cout, DBuf<C>& cin, DBuf<C>
     return FDA_OK;
   }
   const size_t nu = P->h_units[l][st].size();
+  const int tm = P->fma_tm[l][st];
   for (size_t u0 = 0; u0 < nu; u0 += 65535) {
     unsigned n = (unsigned)std::min<size_t>(65535, nu - u0);
-    k_m2l<C><<<n, 256, 0, s>>>(P->units[l][st].p + u0, op.K.p, op.lr.p, P->pair_src.p, P->pair_tgt.p, P->pair_mid.p,
-                               cout.p, cin.p, mid.p, nrhs, P->n_coef, P->n_mid);
+    const GemmUnit* U = P->units[l][st].p + u0;
+    if (tm == 16)
+      k_m2l<C, 16><<<n, 256, 0, s>>>(U, op.K.p, op.lr.p, P->pair_src.p, P->pair_tgt.p, P->pair_mid.p, cout.p, cin.p,
+                                     mid.p, nrhs, P->n_coef, P->n_mid);
+    else if (tm == 32)
+      k_m2l<C, 32><<<n, 256, 0, s>>>(U, op.K.p, op.lr.p, P->pair_src.p, P->pair_tgt.p, P->pair_mid.p, cout.p, cin.p,
+                                     mid.p, nrhs, P->n_coef, P->n_mid);
+    else
+      k_m2l<C, 64><<<n, 256, 0, s>>>(U, op.K.p, op.lr.p, P->pair_src.p, P->pair_tgt.p, P->pair_mid.p, cout.p, cin.p,
+                                     mid.p, nrhs, P->n_coef, P->n_mid);
     FDA_LAUNCH_CHECK();
     ++*nl;
   }

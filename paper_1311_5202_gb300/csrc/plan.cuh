@@ -97,6 +97,7 @@ struct fda_plan_s {
   std::vector<fda::GemmUnit> h_tc3_units[FDA_MAXLEV][2];
   fda::DBuf<fda::GemmUnit> tc3_units[FDA_MAXLEV][2];
   int tc3_mt[FDA_MAXLEV][2] = {{0}};  // largest number of 128-row tiles of a unit
+  int fma_tm[FDA_MAXLEV][2] = {{0}};  // row tile of the FMA M2L units (16, 32 or 64)
   int m2l_choice[FDA_MAXLEV][2];      // autotuned M2L kernel per (level, stage), -1: from the plan options
   int near_wide = -1;                 // autotuned right-hand sides per near-field pass for wide batches
   fda::DBuf<int64_t> pair_src, pair_tgt;  // coefficient indices (slot + wedge * s)

@@ -1094,8 +1094,22 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
     FDA_TRY(P->pair_src.upload(ps));
     FDA_TRY(P->pair_tgt.upload(pt));
     FDA_TRY(P->pair_mid.upload(pm));
+    // FMA units: row tile per (level, stage) minimising the padded rows (plus a per-tile gather cost); the
+    // low-rank V^ stage has as many rows as the rank, often below 20
+    for (int l = 0; l < FDA_MAXLEV; ++l) {
+      P->fma_tm[l][0] = P->fma_tm[l][1] = 64;
+      if (offs[l].empty() || !P->lev[l].used) continue;
+      double best = 1e300;
+      for (int tm : {16, 32, 64}) {
+        double c = 0;
+        for (const OffInfo& o : offs[l]) {
+          const int M = o.rank > 0 ? o.rank : P->lev[l].s;
+          c += (double)o.count * ((M + tm - 1) / tm) * (tm + 16);
+        }
+        if (c < best) best = c, P->fma_tm[l][0] = tm;
+      }
+    }
     int64_t u = 0;
-    const int CP = 64, TM = 64;
     while (u < T->nm2l) {
       int64_t q = order[u];
       int l = T->h_m2l_info[6 * q];
@@ -1104,6 +1118,8 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
       while (v < T->nm2l && T->h_m2l_info[6 * order[v]] == l && pair_off[order[v]] == id) ++v;
       const OffInfo& o = offs[l][id];
       const LevelOps& L = P->lev[l];
+      const int TM0 = P->fma_tm[l][0], TM1 = P->fma_tm[l][1];
+      const int CP = std::max(64, 2048 / TM0);  // pairs per unit: fills the stage-0 column tile at nrhs = 1
       for (int64_t p0 = u; p0 < v; p0 += CP) {
         int pc = (int)std::min<int64_t>(CP, v - p0);
         // tensor-core units: up to 256 output rows each
@@ -1123,12 +1139,12 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
           }
         }
         if (o.rank > 0) {
-          for (int m0 = 0; m0 < o.rank; m0 += TM)
+          for (int m0 = 0; m0 < o.rank; m0 += TM0)
             P->h_units[l][0].push_back({o.v_off, o.rank, L.s, p0, pc, m0, 1, 0});
-          for (int m0 = 0; m0 < L.s; m0 += TM)
+          for (int m0 = 0; m0 < L.s; m0 += TM1)
             P->h_units[l][1].push_back({o.u_off, L.s, o.rank, p0, pc, m0, 2, 0});
         } else {
-          for (int m0 = 0; m0 < L.s; m0 += TM) P->h_units[l][0].push_back({o.k_off, L.s, L.s, p0, pc, m0, 0, 0});
+          for (int m0 = 0; m0 < L.s; m0 += TM0) P->h_units[l][0].push_back({o.k_off, L.s, L.s, p0, pc, m0, 0, 0});
         }
       }
       u = v;
