@@ -17,9 +17,11 @@
 namespace fda {
 
 struct TcImgJob {
-  const double2* src;  // M x K complex, column-major (lda = M)
+  const double2* src;  // the M x K operator: src[i + k ld], or src[k + i ld] when trans
   int M, K;
   int64_t img_off;     // first float of the image
+  int64_t ld;
+  int trans;
 };
 
 #define TC_M 128       // real rows per tile (64 complex rows)
@@ -393,7 +395,7 @@ static __global__ void k_tc3_image(const TcImgJob* jobs, float* img) {
     const int i = j >> 1, kx = kr >> 1;
     float val = 0.f;
     if (i < J.M && kx < J.K) {
-      const double2 a = J.src[i + (int64_t)kx * J.M];
+      const double2 a = J.trans ? J.src[kx + (int64_t)i * J.ld] : J.src[i + (int64_t)kx * J.ld];
       const double v = (j & 1) == 0 ? ((kr & 1) == 0 ? a.x : -a.y) : ((kr & 1) == 0 ? a.y : a.x);
       val = tf32_round((float)v);
     }
@@ -705,7 +707,7 @@ extern "C" int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_
     DBuf<float> img;
     FDA_TRY(dA64.upload(hA64));
     FDA_TRY(img.alloc((size_t)tc3_image_floats(M, K)));
-    FDA_TRY(tc3_build_images({TcImgJob{dA64.p, M, K, 0}}, img.p));
+    FDA_TRY(tc3_build_images({TcImgJob{dA64.p, M, K, 0, M, 0}}, img.p));
     GemmUnit u{0, M, K, 0, P, 0, 0, 0};
     FDA_TRY(du.upload(&u, 1));
     FDA_TRY(m2l_tc3_launch(du.p, 1, img.p, src.p, tgt.p, pm.p, dX.p, dY.p, dmid.p, 1, 0, 0, (2 * M + 127) / 128, err.p,

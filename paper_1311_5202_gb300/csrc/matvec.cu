@@ -447,6 +447,13 @@ int m2l_stage(fda_plan_s* P, RunOps<C>& op, DBuf<C>& cout, DBuf<C>& cin, DBuf<C>
   return FDA_OK;
 }
 
+// zero the outgoing coefficients before S2M (leaves are then written by S2M, parents accumulated by M2M)
+template <typename C>
+static int zero_parent_coefs(fda_plan_s* P, DBuf<C>& cout, int nrhs, cudaStream_t s) {
+  FDA_CUDA(cudaMemsetAsync(cout.p, 0, sizeof(C) * P->n_coef * nrhs, s));
+  return FDA_OK;
+}
+
 template <typename C>
 static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf<C>& cout, DBuf<C>& cin,
                     DBuf<C>& mid, const void* x, void* y, int nrhs, int io, cudaStream_t s) {
@@ -500,6 +507,9 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
     const int maxleaf = std::max(1, P->max_leaf);
     const size_t SMEM = 40960;
     auto chunk = [&](size_t rows) { return (int)std::max<size_t>(1, std::min<size_t>(nrhs, SMEM / (rows * sizeof(C)))); };
+    // the grouped tensor-core M2M accumulates into the parents: clear the outgoing coefficients first
+    const bool tc_mm = std::is_same<C, float2>::value && P->cfg.m2l_tensor == 1;
+    if (tc_mm) FDA_TRY(zero_parent_coefs<C>(P, cout, nrhs, s));
     // S2M
     if (!P->h_leaves.empty()) {
       int rc = chunk(maxleaf);
@@ -516,6 +526,13 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
     // M2M bottom-up
     for (int l = P->lmax - 1; l >= P->lmin; --l) {
       if (P->h_parents[l].empty()) continue;
+      if (tc_mm && !P->h_mm_units[l].empty()) {
+        FDA_TRY(m2l_tc3_launch(P->mm_units[l].p, P->h_mm_units[l].size(), P->tc_img.p, P->mm_src.p, P->mm_tgt.p,
+                               P->mm_src.p, (const float2*)cout.p, (float2*)cout.p, (float2*)cout.p, nrhs, P->n_coef,
+                               P->n_coef, P->mm_mt[l], P->tc_err.p, s));
+        ++nl;
+        continue;
+      }
       const LevelOps &L = P->lev[l], &Lc = P->lev[l + 1];
       int rc = chunk(Lc.s);
       for (int r0 = 0; r0 < nrhs; r0 += rc) {
@@ -540,6 +557,13 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
       const LevelOps &L = P->lev[l], &Lc = P->lev[l + 1];
       int64_t nchild = Lc.box_end - Lc.box_begin;
       if (nchild <= 0 || P->h_parents[l].empty()) continue;
+      if (tc_mm && !P->h_ll_units[l].empty()) {
+        FDA_TRY(m2l_tc3_launch(P->ll_units[l].p, P->h_ll_units[l].size(), P->tc_img.p, P->ll_src.p, P->ll_tgt.p,
+                               P->ll_src.p, (const float2*)cin.p, (float2*)cin.p, (float2*)cin.p, nrhs, P->n_coef,
+                               P->n_coef, P->ll_mt[l], P->tc_err.p, s));
+        ++nl;
+        continue;
+      }
       int rc = chunk(L.s + Lc.s);
       for (int r0 = 0; r0 < nrhs; r0 += rc) {
         int rcc = std::min(rc, nrhs - r0);

@@ -97,6 +97,11 @@ struct fda_plan_s {
   std::vector<fda::GemmUnit> h_tc3_units[FDA_MAXLEV][2];
   fda::DBuf<fda::GemmUnit> tc3_units[FDA_MAXLEV][2];
   int tc3_mt[FDA_MAXLEV][2] = {{0}};  // largest number of 128-row tiles of a unit
+  // M2M / L2L on the same tensor-core kernel: per level (parent level l), units and pair arrays
+  std::vector<fda::GemmUnit> h_mm_units[FDA_MAXLEV], h_ll_units[FDA_MAXLEV];
+  fda::DBuf<fda::GemmUnit> mm_units[FDA_MAXLEV], ll_units[FDA_MAXLEV];
+  fda::DBuf<int64_t> mm_src, mm_tgt, ll_src, ll_tgt;
+  int mm_mt[FDA_MAXLEV] = {0}, ll_mt[FDA_MAXLEV] = {0};
   int fma_tm[FDA_MAXLEV][2] = {{0}};  // row tile of the FMA M2L units (16, 32 or 64)
   int m2l_choice[FDA_MAXLEV][2];      // autotuned M2L kernel per (level, stage), -1: from the plan options
   int near_wide = -1;                 // autotuned right-hand sides per near-field pass for wide batches

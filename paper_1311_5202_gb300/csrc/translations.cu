@@ -50,9 +50,11 @@ struct SVDJob {
 };
 int pivoted_qr_batched(const std::vector<QRJob>& jobs, cudaStream_t s);
 struct TcImgJob {
-  const double2* src;  // M x K complex, column-major (lda = M)
+  const double2* src;  // the M x K operator: src[i + k ld], or src[k + i ld] when trans
   int M, K;
   int64_t img_off;     // first float of the image
+  int64_t ld;
+  int trans;
 };
 int64_t tc3_image_floats(int M, int K);
 int tc3_build_images(const std::vector<TcImgJob>& jobs, float* img);
@@ -1159,24 +1161,75 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
     if (P->cfg.m2l_tensor == 1 && P->cfg.precision == FDA_PREC_FP32) {
       std::vector<TcImgJob> jobs;
       int64_t img_tot = 0;
+      auto add_img = [&](const double2* src, int M, int K, int64_t ld, int trans) {
+        int64_t off = img_tot;
+        jobs.push_back({src, M, K, off, ld, trans});
+        img_tot += tc3_image_floats(M, K);
+        return off;
+      };
       std::vector<std::vector<std::array<int64_t, 3>>> img_of(FDA_MAXLEV);  // (k, v, u) image offsets
       for (int l = lmin; l <= lmax && far; ++l) {
         img_of[l].resize(offs[l].size());
         const int sl = P->lev[l].s;
         for (size_t i = 0; i < offs[l].size(); ++i) {
           const OffInfo& o = offs[l][i];
-          auto add = [&](const double2* src, int M, int K) {
-            int64_t off = img_tot;
-            jobs.push_back({src, M, K, off});
-            img_tot += tc3_image_floats(M, K);
-            return off;
-          };
+          auto add = [&](const double2* src, int M, int K) { return add_img(src, M, K, M, 0); };
           if (o.rank > 0) {
             img_of[l][i] = {-1, add(P->op64.lr.p + o.v_off, o.rank, sl), add(P->op64.lr.p + o.u_off, sl, o.rank)};
           } else {
             img_of[l][i] = {add(P->op64.K.p + o.k_off, sl, sl), -1, -1};
           }
         }
+      }
+      // M2M and L2L as grouped products on the same kernel: one group per (level, octant, parent wedge) with
+      // operator M~(o, z) (child wedge -> parent wedge, Eq. cmpm) and its plain transpose (parent wedge ->
+      // child wedge, Eq. cmpl), and one "pair" per parent that has a child in octant o
+      std::vector<int64_t> mms, mmt, lls, llt;
+      for (int l = lmin; l < lmax && far; ++l) {
+        const LevelOps& L = P->lev[l];
+        const LevelOps& Lc = P->lev[l + 1];
+        if (P->h_parents[l].empty() || (2 * L.s + 127) / 128 > 4 || (2 * Lc.s + 127) / 128 > 4) continue;
+        std::vector<std::vector<std::pair<int64_t, int64_t>>> byo(8);  // (parent, child)
+        for (int64_t pb : P->h_parents[l])
+          for (int c = 0; c < T->h_nch[pb]; ++c) {
+            const int64_t cb = T->h_cbeg[pb] + c;
+            const int o = ((T->h_ix[cb] & 1) << 2) | ((T->h_iy[cb] & 1) << 1) | (T->h_iz[cb] & 1);
+            byo[o].push_back({pb, cb});
+          }
+        for (int o = 0; o < 8; ++o) {
+          if (byo[o].empty()) continue;
+          for (int z = 0; z < L.nw; ++z) {
+            const double2* Mz = P->op64.M.p + P->m_off[l] + (int64_t)(o * L.nw + z) * L.s * Lc.s;
+            const int zc = child_wedge(L, Lc, z);
+            const int64_t im = add_img(Mz, L.s, Lc.s, L.s, 0);
+            const int64_t il = add_img(Mz, Lc.s, L.s, L.s, 1);
+            const int64_t p0 = (int64_t)mms.size();
+            for (const auto& pc : byo[o]) {
+              const int64_t child = P->h_slot[pc.second] + (int64_t)zc * Lc.s;
+              const int64_t parent = P->h_slot[pc.first] + (int64_t)z * L.s;
+              mms.push_back(child);
+              mmt.push_back(parent);
+              lls.push_back(parent);
+              llt.push_back(child);
+            }
+            const int64_t np = (int64_t)byo[o].size();
+            for (int64_t c0 = 0; c0 < np; c0 += 128) {
+              const int pc = (int)std::min<int64_t>(128, np - c0);
+              P->h_mm_units[l].push_back({im, L.s, Lc.s, p0 + c0, pc, 0, 0, 0});
+              P->h_ll_units[l].push_back({il, Lc.s, L.s, p0 + c0, pc, 0, 0, 0});
+            }
+          }
+        }
+        P->mm_mt[l] = (2 * L.s + 127) / 128;
+        P->ll_mt[l] = (2 * Lc.s + 127) / 128;
+      }
+      FDA_TRY(P->mm_src.upload(mms));
+      FDA_TRY(P->mm_tgt.upload(mmt));
+      FDA_TRY(P->ll_src.upload(lls));
+      FDA_TRY(P->ll_tgt.upload(llt));
+      for (int l = 0; l < FDA_MAXLEV; ++l) {
+        FDA_TRY(P->mm_units[l].upload(P->h_mm_units[l]));
+        FDA_TRY(P->ll_units[l].upload(P->h_ll_units[l]));
       }
       FDA_TRY(P->tc_img.alloc(std::max<int64_t>(img_tot, 1)));
       FDA_TRY(tc3_build_images(jobs, P->tc_img.p));

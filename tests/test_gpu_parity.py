@@ -183,23 +183,31 @@ def test_refinement_solve_fp32_inner(c1):
 
 
 # ------------------------------------------------------------------ high-frequency levels (directional wedges)
-def test_fda_matvec_with_directional_levels_sampled_rows():
+@pytest.mark.parametrize("form", ["fp64", "tensor"])
+def test_fda_matvec_with_directional_levels_sampled_rows(form):
+    """kD = 100 sphere with directional (wedge) levels: the FP64 form (<= 1e-4) and the mixed form with M2L,
+    M2M and L2L on the TF32 tensor cores (<= 3e-4), two right-hand sides, against the oracle's rows."""
     _need_gpu()
     mesh = inputs.icosphere(14, 0.5)
     k = 100.0
-    S = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=1e-5, leaf_max=64)
+    if form == "fp64":
+        S = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=1e-5, leaf_max=64, nrhs_max=2)
+    else:
+        S = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=1e-5, leaf_max=64, precision=fdbem.FDA_PREC_FP32,
+                         m2l_tensor=1, nrhs_max=2)
     try:
         info = S.info()
         assert any(info["n_wedges"][l] > 1 and info["m2l_pairs"][l] > 0 for l in range(32))
-        x = inputs.complex_gaussian(S.N, 20131120)
-        xd = torch.from_numpy(x).to(DEV)
+        x = inputs.complex_gaussian(S.N, 20131120, nrhs=2)
+        xd = torch.from_numpy(x).to(DEV).contiguous()
         yd = torch.empty_like(xd)
         S.matvec(xd, yd)
         torch.cuda.synchronize()
         rows = inputs.sample_rows(S.N, 256, 7)
-        yo = _oracle_rows(mesh, k, x, rows)
-        err = np.linalg.norm(yd.cpu().numpy()[rows] - yo) / np.linalg.norm(yo)
-        assert err < 1e-4, err
+        for r in range(2):
+            yo = _oracle_rows(mesh, k, x[r], rows)
+            err = np.linalg.norm(yd[r].cpu().numpy()[rows] - yo) / np.linalg.norm(yo)
+            assert err < (1e-4 if form == "fp64" else 3e-4), (form, r, err)
     finally:
         S.close()
 
