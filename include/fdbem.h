@@ -179,7 +179,7 @@ int fda_matvec_ex(fda_plan_t* plan, int precision, const void* x, void* y, int n
 
 /* Autotuner (no paper counterpart). For an FP32 plan and a batch width nrhs (1..nrhs_max), times on the
  * plan's own operators every M2L (level, stage) with the FP32 FMA kernel and with the plan's tensor-core
- * kernel (m2l_tensor 1 or 2), and for nrhs >= 12 the near field at 4 and 16 right-hand sides per pass over
+ * kernel (m2l_tensor 1: four tile shapes; m2l_tensor 2: one), and for nrhs >= 12 the near field at 4 and 16 right-hand sides per pass over
  * the near-field matrices; the plan keeps the faster variant of each for all later products. Synchronous;
  * overwrites the plan's internal workspaces only. report (HOST) receives the timings and choices.
  * Errors: FDA_E_INVALID_ARG, FDA_E_STATE (FP64-only plan), FDA_E_OOM, FDA_E_CUDA. */
@@ -188,8 +188,9 @@ typedef struct {
   int32_t level[64];
   int32_t stage[64];      /* 0: dense K~ or V^ stage, 1: U^ stage */
   double ms_fma[64];      /* FP32 FMA kernel, best of 3 */
-  double ms_tensor[64];   /* tensor-core kernel, best of 3 (-1 when the plan holds none) */
-  int32_t chosen[64];     /* 0: FMA kernel, 1: tensor-core kernel */
+  double ms_tensor[64];   /* tensor-core kernel, best of 3 over its tile shapes (-1 when the plan holds none) */
+  int32_t chosen[64];     /* 0: FMA kernel, 1: tensor-core kernel (default shape), 2 to 4: tensor-core kernel
+                             (alternative shapes: other column width or stage count) */
   double near_ms[2];      /* near field at 4 and 16 right-hand sides per pass (nrhs >= 12; else 0) */
   int32_t near_rhs_per_pass;
   int32_t reserved[7];
@@ -336,7 +337,8 @@ int bm_fgmres_solve(fda_plan_t* plan, bm_precond_t* precond, bm_net_t* net, cons
 /* Self-test of the tensor-core M2L kernels (diagnostic; no paper counterpart): one complex M x K operator
  * (K <= 1024) applied to P gathered columns, against an FP64 host product of the same FP32 data.
  * split = 0: TF32 with operands expanded in the kernel (M = 64, P = 64); 1: 3xTF32 split (M = 64, P = 64);
- * 2: TF32 with the pre-expanded operator image of the m2l_tensor = 1 form (M = min(256, K), P = 100).
+ * 2..5: TF32 with the pre-expanded operator image of the m2l_tensor = 1 form (M = min(256, K), P = 100),
+ * in its default tile shape (2) or the autotuner's alternatives (3, 4, 5).
  * *max_rel_err is the largest entrywise error relative to the sum of |a||x| over the row, *wait_failed is 1
  * when a bounded device wait gave up. Synchronous. */
 int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_failed);

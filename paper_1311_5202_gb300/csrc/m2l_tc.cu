@@ -592,16 +592,18 @@ static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units
     }
     for (int c = max(0, nk - NST); c < nk; ++c) ok = wait_mdone(c % NST) && ok;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
-      const int q4 = w & 3, half = w >> 2;
+    // columns per warp: half of the tile for N >= 64; the whole tile (warps 0-3 only) for N = 32
+    constexpr int CPW = N >= 64 ? N / 2 : N;
+    if (ok && (N >= 64 || w < 4)) {
+      const int q4 = w & 3, half = N >= 64 ? (w >> 2) : 0;
       const int row = 32 * q4 + lane;  // real row within a tile
       const int part = row & 1;
 #pragma unroll 1
       for (int mt = 0; mt < MT; ++mt) {
         const int ci = 64 * mt + (row >> 1);
 #pragma unroll 1
-        for (int h = 0; h < N / 64; ++h) {
-          const int col0 = half * (N / 2) + 32 * h;
+        for (int h = 0; h < CPW / 32; ++h) {
+          const int col0 = half * CPW + 32 * h;
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(N * mt + col0), v);
 #pragma unroll
@@ -649,18 +651,54 @@ static int tc3_launch_t(const GemmUnit* units, size_t nunits, const float* img, 
   return FDA_OK;
 }
 
-// max_mt: the largest number of 128-row tiles of any unit of this launch (1..4)
+// max_mt: the largest number of 128-row tiles of any unit of this launch (1..4); max_k: the largest complex
+// K. Launches whose K fits two 32-wide real chunks (the U^ stage of low-rank pairs) gain little from double
+// buffering and run single-stage, smaller CTAs, several per SM. shape 0 is the default tile shape of each
+// class, shapes 1 to 3 alternatives (other column width or stage count) that the autotuner may pick.
 int m2l_tc3_launch(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc, const int64_t* ptgt,
                    const int64_t* pmid, const float2* cout, float2* cin, float2* mid, int nrhs, int64_t ldc,
-                   int64_t ldm, int max_mt, int* err, cudaStream_t s) {
+                   int64_t ldm, int max_mt, int max_k, int* err, cudaStream_t s, int shape) {
   if (max_mt < 1 || max_mt > 4) {
     set_error("tensor-core M2L supports at most 256 complex output rows (got %d tiles)", max_mt);
     return FDA_E_INVALID_ARG;
   }
   if (nunits == 0) return FDA_OK;
-  if (max_mt == 1) return tc3_launch_t<1, 128, 3>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, ldc, ldm, err, s);
-  if (max_mt == 2) return tc3_launch_t<2, 128, 2>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, ldc, ldm, err, s);
-  return tc3_launch_t<4, 64, 2>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, ldc, ldm, err, s);
+#define TC3L(M_, N_, S_) \
+  return tc3_launch_t<M_, N_, S_>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, ldc, ldm, err, s)
+  const bool alt = shape == 1;
+  if (shape == 2) {  // single-stage
+    if (max_mt == 1) TC3L(1, 128, 1);
+    if (max_mt == 2) TC3L(2, 64, 1);
+    TC3L(4, 64, 1);
+  }
+  if (shape == 3) {  // single-stage, narrow: the most CTAs per SM (TMEM and shared memory)
+    if (max_mt == 1) TC3L(1, 64, 1);
+    if (max_mt == 2) TC3L(2, 32, 1);
+    TC3L(4, 32, 1);
+  }
+  if (max_k > 0 && 2 * max_k <= 2 * TC3_KC) {
+    if (max_mt == 1) {
+      if (alt) TC3L(1, 64, 1);
+      TC3L(1, 128, 1);
+    }
+    if (max_mt == 2) {
+      if (alt) TC3L(2, 128, 1);
+      TC3L(2, 64, 1);
+    }
+    if (alt) TC3L(4, 64, 2);
+    TC3L(4, 64, 1);
+  }
+  if (max_mt == 1) {
+    if (alt) TC3L(1, 128, 2);
+    TC3L(1, 128, 3);
+  }
+  if (max_mt == 2) {
+    if (alt) TC3L(2, 64, 2);
+    TC3L(2, 128, 2);
+  }
+  if (alt) TC3L(4, 64, 1);
+  TC3L(4, 64, 2);
+#undef TC3L
 }
 
 }  // namespace fda
@@ -669,13 +707,13 @@ using namespace fda;
 
 // Self-test of the tensor-core path: one complex M x K product applied to P gathered columns, against an FP64
 // host product of the same FP32 data. split 0: TF32 (M = 64, P = 64); 1: 3xTF32 split (M = 64, P = 64);
-// 2: TF32 with the pre-expanded operator image (M = min(256, K), P = 100).
+// 2..5: TF32 with the pre-expanded operator image (M = min(256, K), P = 100), tile shape split - 2.
 extern "C" int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_failed) {
-  if (K < 1 || K > 1024 || split < 0 || split > 2 || !max_rel_err || !wait_failed) {
+  if (K < 1 || K > 1024 || split < 0 || split > 5 || !max_rel_err || !wait_failed) {
     set_error("bad arguments");
     return FDA_E_INVALID_ARG;
   }
-  const int M = split == 2 ? std::min(256, K) : 64, P = split == 2 ? 100 : 64;
+  const int M = split >= 2 ? std::min(256, K) : 64, P = split >= 2 ? 100 : 64;
   std::vector<float2> hA((size_t)M * K), hX((size_t)K * P);
   uint64_t st = 12345;
   auto rnd = [&]() {
@@ -700,7 +738,7 @@ extern "C" int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_
   FDA_TRY(pm.upload(hm));
   FDA_TRY(err.alloc(1));
   FDA_TRY(err.zero());
-  if (split == 2) {
+  if (split >= 2) {
     std::vector<double2> hA64(hA.size());
     for (size_t q = 0; q < hA.size(); ++q) hA64[q] = make_double2(hA[q].x, hA[q].y);
     DBuf<double2> dA64;
@@ -710,8 +748,8 @@ extern "C" int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_
     FDA_TRY(tc3_build_images({TcImgJob{dA64.p, M, K, 0, M, 0}}, img.p));
     GemmUnit u{0, M, K, 0, P, 0, 0, 0};
     FDA_TRY(du.upload(&u, 1));
-    FDA_TRY(m2l_tc3_launch(du.p, 1, img.p, src.p, tgt.p, pm.p, dX.p, dY.p, dmid.p, 1, 0, 0, (2 * M + 127) / 128, err.p,
-                           0));
+    FDA_TRY(m2l_tc3_launch(du.p, 1, img.p, src.p, tgt.p, pm.p, dX.p, dY.p, dmid.p, 1, 0, 0, (2 * M + 127) / 128, K,
+                           err.p, 0, split - 2));
     FDA_CUDA(cudaDeviceSynchronize());
   } else {
     GemmUnit u{0, M, K, 0, P, 0, 0, 0};

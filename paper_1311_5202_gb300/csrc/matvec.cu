@@ -18,7 +18,7 @@ namespace fda {
 
 int m2l_tc3_launch(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc, const int64_t* ptgt,
                    const int64_t* pmid, const float2* cout, float2* cin, float2* mid, int nrhs, int64_t ldc,
-                   int64_t ldm, int max_mt, int* err, cudaStream_t s);
+                   int64_t ldm, int max_mt, int max_k, int* err, cudaStream_t s, int shape);
 int m2l_tc_launch(const GemmUnit* units, size_t nunits, const float2* poolK, const float2* poolLR,
                   const int64_t* psrc, const int64_t* ptgt, const int64_t* pmid, const float2* cout, float2* cin,
                   float2* mid, int nrhs, int64_t ldc, int64_t ldm, int split, int max_rows, int* err, cudaStream_t s);
@@ -398,7 +398,8 @@ static __global__ void __launch_bounds__(256) k_m2l(const GemmUnit* units, const
 
 // ------------------------------------------------------------------ driver
 // M2L kernel variants of one (level, stage): 0 = FP32/FP64 FMA, 1 = TF32 from pre-expanded operator images,
-// 2 = TF32 or 3xTF32 with operands expanded in the kernel (plan option m2l_tensor = 2)
+// 2 = TF32 or 3xTF32 with operands expanded in the kernel (plan option m2l_tensor = 2), 3 to 5 = variant 1
+// with its alternative tile shapes 1 to 3 (picked by the autotuner only)
 int m2l_variant(const fda_plan_s* P, int l, int st) {
   if (P->m2l_choice[l][st] >= 0) return P->m2l_choice[l][st];
   if (P->cfg.m2l_tensor == 1 && !P->h_tc3_units[l][st].empty() && P->tc3_mt[l][st] <= 4) return 1;
@@ -410,12 +411,22 @@ template <typename C>
 int m2l_stage(fda_plan_s* P, RunOps<C>& op, DBuf<C>& cout, DBuf<C>& cin, DBuf<C>& mid, int l, int st, int variant,
               int nrhs, cudaStream_t s, int64_t* nl) {
   const bool f32 = std::is_same<C, float2>::value;
-  if (variant == 1 && f32 && !P->h_tc3_units[l][st].empty()) {
-    const size_t n3 = P->h_tc3_units[l][st].size();
-    FDA_TRY(m2l_tc3_launch(P->tc3_units[l][st].p, n3, P->tc_img.p, P->pair_src.p, P->pair_tgt.p, P->pair_mid.p,
-                           (const float2*)cout.p, (float2*)cin.p, (float2*)mid.p, nrhs, P->n_coef, P->n_mid,
-                           P->tc3_mt[l][st], P->tc_err.p, s));
-    *nl += (int64_t)((n3 + 65534) / 65535);
+  if ((variant == 1 || variant >= 3) && f32 && !P->h_tc3_units[l][st].empty()) {
+    const int shape = variant >= 3 ? variant - 2 : 0;
+    const size_t n3 = P->h_tc3_units[l][st].size(), ns = (size_t)P->tc3_split[l][st];
+    // short-K units (single-stage launch), then the rest
+    if (ns) {
+      FDA_TRY(m2l_tc3_launch(P->tc3_units[l][st].p, ns, P->tc_img.p, P->pair_src.p, P->pair_tgt.p, P->pair_mid.p,
+                             (const float2*)cout.p, (float2*)cin.p, (float2*)mid.p, nrhs, P->n_coef, P->n_mid,
+                             P->tc3_mt[l][st], 32, P->tc_err.p, s, shape));
+      *nl += (int64_t)((ns + 65534) / 65535);
+    }
+    if (n3 > ns) {
+      FDA_TRY(m2l_tc3_launch(P->tc3_units[l][st].p + ns, n3 - ns, P->tc_img.p, P->pair_src.p, P->pair_tgt.p,
+                             P->pair_mid.p, (const float2*)cout.p, (float2*)cin.p, (float2*)mid.p, nrhs, P->n_coef,
+                             P->n_mid, P->tc3_mt[l][st], P->tc3_maxk[l][st], P->tc_err.p, s, shape));
+      *nl += (int64_t)((n3 - ns + 65534) / 65535);
+    }
     return FDA_OK;
   }
   if (variant == 2 && f32 && !P->h_tc_units[l][st].empty()) {
@@ -529,7 +540,7 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
       if (tc_mm && !P->h_mm_units[l].empty()) {
         FDA_TRY(m2l_tc3_launch(P->mm_units[l].p, P->h_mm_units[l].size(), P->tc_img.p, P->mm_src.p, P->mm_tgt.p,
                                P->mm_src.p, (const float2*)cout.p, (float2*)cout.p, (float2*)cout.p, nrhs, P->n_coef,
-                               P->n_coef, P->mm_mt[l], P->tc_err.p, s));
+                               P->n_coef, P->mm_mt[l], P->lev[l + 1].s, P->tc_err.p, s, 0));
         ++nl;
         continue;
       }
@@ -560,7 +571,7 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
       if (tc_mm && !P->h_ll_units[l].empty()) {
         FDA_TRY(m2l_tc3_launch(P->ll_units[l].p, P->h_ll_units[l].size(), P->tc_img.p, P->ll_src.p, P->ll_tgt.p,
                                P->ll_src.p, (const float2*)cin.p, (float2*)cin.p, (float2*)cin.p, nrhs, P->n_coef,
-                               P->n_coef, P->ll_mt[l], P->tc_err.p, s));
+                               P->n_coef, P->ll_mt[l], P->lev[l].s, P->tc_err.p, s, 0));
         ++nl;
         continue;
       }
@@ -670,12 +681,21 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
         FDA_TRY(time_ms(s, [&]() { return m2l_stage<float2>(P, P->op32, P->cout32, P->cin32, P->mid32, l, st, tv, nrhs,
                                                             s, &nl); },
                         3, &t1));
+      int tvb = tv;  // the tensor-core shape kept
+      if (tv == 1)
+        for (int alt = 3; alt <= 5; ++alt) {
+          double ta = 0;
+          FDA_TRY(time_ms(s, [&]() { return m2l_stage<float2>(P, P->op32, P->cout32, P->cin32, P->mid32, l, st, alt,
+                                                              nrhs, s, &nl); },
+                          3, &ta));
+          if (ta < t1) t1 = ta, tvb = alt;
+        }
       R->level[e] = l;
       R->stage[e] = st;
       R->ms_fma[e] = t0;
       R->ms_tensor[e] = t1;
-      const int pick = (tv != 0 && t1 < t0) ? tv : 0;
-      R->chosen[e] = pick ? 1 : 0;
+      const int pick = (tv != 0 && t1 < t0) ? tvb : 0;
+      R->chosen[e] = pick == 0 ? 0 : (pick >= 3 ? pick - 1 : 1);
       P->m2l_choice[l][st] = pick;
       ++e;
     }

@@ -97,6 +97,8 @@ struct fda_plan_s {
   std::vector<fda::GemmUnit> h_tc3_units[FDA_MAXLEV][2];
   fda::DBuf<fda::GemmUnit> tc3_units[FDA_MAXLEV][2];
   int tc3_mt[FDA_MAXLEV][2] = {{0}};  // largest number of 128-row tiles of a unit
+  int tc3_maxk[FDA_MAXLEV][2] = {{0}};  // largest complex K of a unit
+  int64_t tc3_split[FDA_MAXLEV][2] = {{0}};  // units [0, split) have 2K <= 64
   // M2M / L2L on the same tensor-core kernel: per level (parent level l), units and pair arrays
   std::vector<fda::GemmUnit> h_mm_units[FDA_MAXLEV], h_ll_units[FDA_MAXLEV];
   fda::DBuf<fda::GemmUnit> mm_units[FDA_MAXLEV], ll_units[FDA_MAXLEV];

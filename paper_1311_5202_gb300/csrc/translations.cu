@@ -1250,15 +1250,24 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
             P->h_tc3_units[l][1].push_back({img_of[l][id][2], sl, o.rank, p0, pc, 0, 2, 0});
             P->tc3_mt[l][0] = std::max(P->tc3_mt[l][0], (2 * o.rank + 127) / 128);
             P->tc3_mt[l][1] = std::max(P->tc3_mt[l][1], (2 * sl + 127) / 128);
+            P->tc3_maxk[l][0] = std::max(P->tc3_maxk[l][0], sl);
+            P->tc3_maxk[l][1] = std::max(P->tc3_maxk[l][1], o.rank);
           } else {
             P->h_tc3_units[l][0].push_back({img_of[l][id][0], sl, sl, p0, pc, 0, 0, 0});
             P->tc3_mt[l][0] = std::max(P->tc3_mt[l][0], (2 * sl + 127) / 128);
+            P->tc3_maxk[l][0] = std::max(P->tc3_maxk[l][0], sl);
           }
         }
         u3 = v;
       }
+      // short-K units (K fits two 32-wide real chunks) first: they run as a separate single-stage launch
       for (int l = 0; l < FDA_MAXLEV; ++l)
-        for (int st = 0; st < 2; ++st) FDA_TRY(P->tc3_units[l][st].upload(P->h_tc3_units[l][st]));
+        for (int st = 0; st < 2; ++st) {
+          auto& v = P->h_tc3_units[l][st];
+          auto mid_it = std::stable_partition(v.begin(), v.end(), [](const GemmUnit& u) { return 2 * u.K <= 64; });
+          P->tc3_split[l][st] = (int64_t)(mid_it - v.begin());
+          FDA_TRY(P->tc3_units[l][st].upload(v));
+        }
     }
   }
 

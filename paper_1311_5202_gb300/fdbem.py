@@ -302,7 +302,7 @@ def fda_autotune(plan, nrhs=1, stream=None) -> dict:
     R = fda_tune_report_t()
     _check(lib().fda_autotune(plan, int(nrhs), _stream(stream), C.byref(R)))
     rows = [dict(level=R.level[e], stage=R.stage[e], ms_fma=R.ms_fma[e], ms_tensor=R.ms_tensor[e],
-                 chosen="tensor" if R.chosen[e] else "fma") for e in range(R.entries)]
+                 chosen=("fma", "tensor", "tensor-alt1", "tensor-alt2", "tensor-alt3")[R.chosen[e]]) for e in range(R.entries)]
     return dict(m2l=rows, near_ms=list(R.near_ms), near_rhs_per_pass=R.near_rhs_per_pass)
 
 

@@ -230,11 +230,12 @@ def test_tiny_mesh_without_far_field():
 
 
 # ------------------------------------------------------------------ tensor-core M2L (tcgen05)
-@pytest.mark.parametrize("split", [0, 1, 2])
+@pytest.mark.parametrize("split", [0, 1, 2, 3, 4, 5])
 def test_tensor_core_selftest(split):
     """A complex operator applied to gathered columns on the tensor cores against an FP64 host product (TF32:
-    ~1e-4 of the row scale; 3xTF32 split: FP32 level). split 2 is the pre-expanded-image kernel with
-    M = min(256, K) rows: K = 8, 37 (one 128-row tile, ragged K), 111 (two tiles), 222 (four tiles)."""
+    ~1e-4 of the row scale; 3xTF32 split: FP32 level). split 2..5 is the pre-expanded-image kernel in its four
+    tile shapes with M = min(256, K) rows: K = 8, 37 (one 128-row tile, ragged K), 111 (two tiles), 222 (four
+    tiles)."""
     _need_gpu()
     for K in ((16, 111, 222) if split < 2 else (8, 37, 111, 222)):
         err, wait_failed = fdbem.fda_tc_selftest(K, split)
