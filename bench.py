@@ -209,6 +209,61 @@ def run_batched(S2, args, N, dev, stream, single_mixed, fdbem, torch):
     return out
 
 
+def table1_case(N, k, eps, fdbem, torch, dev, stream, tune=True, reps=3):
+    """One particle summation of the paper's Table 1 (Sec. 5.1, Eq. sum): unit sphere, ~20 points per
+    wavelength, zero-mean random densities; the FDA product in FP64 and in the mixed form, its phases, and
+    eps_a over 200 random targets against the oracle's direct sum (the paper's error measure)."""
+    from oracle import oracle as O
+    x, n = inputs.sphere_points(N, 1.0)
+    q = inputs.complex_gaussian(N, 20131120)
+    t0 = time.perf_counter()
+    P = fdbem.ParticleSum(x, n, k, eps=eps, leaf_max=64, precision=fdbem.FDA_PREC_FP32, m2l_tensor=1)
+    setup = time.perf_counter() - t0
+    try:
+        if tune:
+            fdbem.fda_autotune(P.plan, 1)
+        info = P.info()
+        qd = torch.from_numpy(q).to(dev)
+        pd = torch.empty_like(qd)
+        rows = inputs.sample_rows(N, 200, 5)
+        t1 = time.perf_counter()
+        po = O.particle_rows(x, n, k, q, rows)
+        oracle_s = time.perf_counter() - t1
+        out = {"N": N, "k": k, "eps": eps, "setup_s": setup, "device_gb": info["device_bytes"] / 1e9,
+               "oracle_200_rows_s": oracle_s}
+        for prec, name in ((fdbem.FDA_PREC_FP64, "fp64"), (fdbem.FDA_PREC_FP32, "mixed")):
+            fdbem.fda_matvec_ex(P.plan, prec, qd, pd, stream)
+            torch.cuda.synchronize()
+            pa = pd.cpu().numpy()[rows]
+            err = float(np.sqrt(np.sum(np.abs(pa - po) ** 2) / np.sum(np.abs(po) ** 2)))
+            phs = [fdbem.fda_matvec_phases(P.plan, prec, qd, pd, stream) for _ in range(reps)]
+            ph = {key: float(np.median([p_[key] for p_ in phs])) for key in phs[0]}
+            out[name] = {"eps_a": err, "ms": sum(ph.values()), "m2l_ms": ph["m2l"], "up_ms": ph["s2m"] + ph["m2m"],
+                         "down_ms": ph["l2l"] + ph["l2t"], "near_ms": ph["near"]}
+        return out
+    finally:
+        P.close()
+
+
+def run_table1(args):
+    import torch
+    from paper_1311_5202_gb300 import fdbem
+    ws, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for N, k in inputs.TABLE1[: args.table1_max]:
+        for eps in args.table1_eps:
+            rows.append(table1_case(N, k, eps, fdbem, torch, dev, stream, tune=not args.no_tune))
+            print(json.dumps({"table1_row": rows[-1]}), file=sys.stderr, flush=True)
+    print(json.dumps({"table1": rows, "unit_ms": "per product on one GB300",
+                      "paper": "Table 1, one Xeon 5450 core, T_M2L and T_up in seconds"}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -231,9 +286,16 @@ def main():
                     help="directions of the batched section (autotuned, graph-captured matvec and block solve); "
                          "0 skips it")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner")
+    ap.add_argument("--table1", action="store_true",
+                    help="run only the particle summations of the paper's Table 1 and print their JSON line")
+    ap.add_argument("--table1-max", type=int, default=3, help="number of Table 1 sizes (4 adds N = 4.7M)")
+    ap.add_argument("--table1-eps", type=float, nargs="+", default=[1e-4, 1e-6])
+    ap.add_argument("--no-table1-sample", action="store_true", help="skip the Table 1 case in the default run")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.table1:
+        return run_table1(args)
 
     import torch
     from paper_1311_5202_gb300 import fdbem
@@ -372,6 +434,10 @@ def main():
         if args.batch > 1:
             batched = run_batched(S2, args, N, dev, stream, solve_alt.get("mixed"), fdbem, torch)
         S2.close()
+    table1 = None
+    if rank == 0 and not args.no_table1_sample:
+        # the paper's own FDA benchmark (Table 1), one size: N = 294,912 points, k = 16 pi, eps = 1e-4
+        table1 = table1_case(294912, 16 * math.pi, 1e-4, fdbem, torch, dev, stream, tune=not args.no_tune)
     peaks, peak_src = _peaks()
     p64, p32 = fdbem.fda_device_peaks()
     # roofline of the dominant phase of the mixed-precision matvec
@@ -430,6 +496,7 @@ def main():
         "m2l_tensor": args.m2l_tensor,
         "autotune": tune_main,
         "batched": batched,
+        "table1_sample": table1,
         "solve_alpha_i_over_k": solve,
         "solve_alpha_minus_i_over_k": solve_alt,
         "speedup_solve_mixed_vs_fp64": (solve_alt["fp64"]["wall_s"] / solve_alt["mixed"]["wall_s"])

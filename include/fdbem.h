@@ -64,6 +64,15 @@ typedef struct fda_plan_s fda_plan_t;
 /* Problem: mesh, wavenumber, Burton-Miller coupling (Sec. 2.1-2.2).                          */
 /* ------------------------------------------------------------------------------------------ */
 
+/* Create a particle-summation problem (Sec. 5.1, Eq. sum): N points x (host, N x 3) with unit normals n
+ * (host, N x 3), on which fda_matvec evaluates p_i = sum_{j != i} [G(x_i, y_j) + alpha dG/dn_y(x_i, y_j)] q_j
+ * with the same octree, translations and near field as the boundary-element operator, but plain kernel
+ * values (no quadrature weights, no local corrections) and no 1/2 q_i term. Inputs are copied.
+ * fda_corrections_export and bm_precond_create refuse such problems (FDA_E_STATE).
+ * Errors: FDA_E_INVALID_ARG for N < 2, k <= 0 or a non-finite coordinate. */
+int bm_particles_create(const double* x, const double* n, int64_t N, double k, double alpha_re, double alpha_im,
+                        bm_problem_t** out);
+
 /* Create a problem from a host mesh. Computes on the GPU the Nystrom points, the paper's
  * normals (into the body) and the quadrature weights w_j = Gauss weight * area Jacobian
  * (6-point rule, Sec. 2.2). alpha is the Burton-Miller coupling constant (the paper uses

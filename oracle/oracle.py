@@ -52,6 +52,10 @@ def lib():
                                       C.c_double, C.c_double, C.c_double, dp, i64p, C.c_int64, dp]
         L.orc_dense_matrix.argtypes = [dp, C.c_int64, i32p, C.c_int64, C.c_double, C.c_double, C.c_double,
                                        C.c_double, C.c_double, C.c_double, dp]
+        L.orc_particle_rows.argtypes = [dp, dp, C.c_int64, C.c_double, C.c_double, C.c_double, dp, i64p, C.c_int64,
+                                        dp]
+        L.orc_particle_field.argtypes = [dp, dp, C.c_int64, C.c_double, C.c_double, C.c_double, dp, dp, C.c_int64,
+                                         dp]
         L.orc_wedge_of.argtypes = [C.c_int, C.c_int32, C.c_int32, C.c_int32]
         L.orc_wedge_of.restype = C.c_int32
         L.orc_tree_build.argtypes = [dp, C.c_int64, C.c_int, C.c_double]
@@ -172,6 +176,32 @@ def correction_weights(nodes, elems, k, rows, cap=512):
         a = wD[r, :n].copy().view(np.complex128)[..., 0]
         b = wH[r, :n].copy().view(np.complex128)[..., 0]
         out.append((lst[r, :n].copy(), a, b))
+    return out
+
+
+def particle_rows(x, n, k, q, rows, alpha=None):
+    """Direct sum p_i = sum_{j != i} [G + alpha dG/dn_y](x_i, x_j; n_j) q_j at the given rows (Eq. sum)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.complex128)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    a = complex(1j / k) if alpha is None else complex(alpha)
+    out = np.zeros(len(rows), dtype=np.complex128)
+    lib().orc_particle_rows(_p(x), _p(n), x.shape[0], float(k), a.real, a.imag, _p(q.view(np.float64)),
+                            _p(rows, C.c_int64), len(rows), _p(out.view(np.float64)))
+    return out
+
+
+def particle_field(x, n, k, q, targets, alpha=None):
+    """p(t) = sum_j [G + alpha dG/dn_y](t, x_j; n_j) q_j at target points t (not sources)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.complex128)
+    t = np.ascontiguousarray(np.atleast_2d(targets), dtype=np.float64)
+    a = complex(1j / k) if alpha is None else complex(alpha)
+    out = np.zeros(t.shape[0], dtype=np.complex128)
+    lib().orc_particle_field(_p(x), _p(n), x.shape[0], float(k), a.real, a.imag, _p(q.view(np.float64)), _p(t),
+                             t.shape[0], _p(out.view(np.float64)))
     return out
 
 

@@ -5,6 +5,8 @@
 
 #include "plan.cuh"
 
+#include <vector>
+
 namespace fda {
 static thread_local char g_err[1024] = "";
 void set_error(const char* fmt, ...) {
@@ -79,6 +81,37 @@ int bm_problem_create(const double* nodes, int64_t n_nodes, const int32_t* elems
     }
   }
   if (rc == FDA_OK) rc = nystrom_points(P);
+  if (rc != FDA_OK) {
+    delete P;
+    return rc;
+  }
+  *out = P;
+  return FDA_OK;
+}
+
+int bm_particles_create(const double* x, const double* n, int64_t N, double k, double alpha_re, double alpha_im,
+                        bm_problem_t** out) {
+  ARG_CHECK(out, "out is NULL");
+  *out = nullptr;
+  ARG_CHECK(x && n, "x/n is NULL");
+  ARG_CHECK(N >= 2 && N <= ((int64_t)1 << 31), "N outside [2, 2^31]");
+  ARG_CHECK(k > 0 && std::isfinite(k), "k must be positive and finite");
+  for (int64_t i = 0; i < 3 * N; ++i) ARG_CHECK(std::isfinite(x[i]) && std::isfinite(n[i]), "non-finite coordinate");
+  bm_problem_s* P = new (std::nothrow) bm_problem_s();
+  if (!P) {
+    set_error("host allocation failed");
+    return FDA_E_OOM;
+  }
+  P->particles = 1;
+  P->ne = 0;
+  P->nn = 0;
+  P->N = N;
+  P->k = k;
+  P->alpha = make_double2(alpha_re, alpha_im);
+  std::vector<double> w((size_t)N, 1.0);
+  int rc = P->x.upload(x, 3 * N);
+  if (rc == FDA_OK) rc = P->n.upload(n, 3 * N);
+  if (rc == FDA_OK) rc = P->w.upload(w);
   if (rc != FDA_OK) {
     delete P;
     return rc;
@@ -383,6 +416,10 @@ int fda_plan_info(const fda_plan_t* P, fda_plan_info_t* I) {
 int fda_corrections_export(const fda_plan_t* P, const int64_t* rows, int64_t nrows, int64_t cap, int64_t* cnt,
                            int64_t* cols, double* vals) {
   ARG_CHECK(P && rows && cnt && cols && vals, "NULL argument");
+  if (P->prob->particles) {
+    set_error("a particle-summation problem has no locally corrected weights");
+    return FDA_E_STATE;
+  }
   const int64_t N = P->tree->N;
   for (int64_t r = 0; r < nrows; ++r) ARG_CHECK(rows[r] >= 0 && rows[r] < N, "row out of range");
   // the plan folds most corrections into its direct blocks, so recompute them (same kernels) for export

@@ -11,6 +11,7 @@ struct bm_problem_s {
   int64_t ne = 0, N = 0, nn = 0;
   double k = 0;
   double2 alpha = {0, 0};
+  int particles = 0;         // 1: points with normals (no elements): the particle summation of Sec. 5.1
   fda::DBuf<double> nodes;   // nn x 3
   fda::DBuf<int32_t> elems;  // ne x 6
   fda::DBuf<double> x, n, w; // N x 3, N x 3 (paper normal, into the body), N

@@ -41,7 +41,7 @@ static __global__ void k_perm_in(const void* x, int io, const int64_t* perm, int
 
 template <typename C>
 static __global__ void k_assemble(const void* x, void* y, int io, const int64_t* perm, int64_t N, int nrhs,
-                                  const C* yt) {
+                                  const C* yt, double c) {
   int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= N * nrhs) return;
   int64_t t = q / nrhs;
@@ -50,10 +50,11 @@ static __global__ void k_assemble(const void* x, void* y, int io, const int64_t*
   double2 a = to_d(yt[q]);
   if (io == FDA_CPLX128) {
     double2 xv = ((const double2*)x)[d];
-    ((double2*)y)[d] = make_double2(0.5 * xv.x + a.x, 0.5 * xv.y + a.y);
+    ((double2*)y)[d] = make_double2(c * xv.x + a.x, c * xv.y + a.y);
   } else {
     float2 xv = ((const float2*)x)[d];
-    ((float2*)y)[d] = make_float2(0.5f * xv.x + (float)a.x, 0.5f * xv.y + (float)a.y);
+    const float cf = (float)c;
+    ((float2*)y)[d] = make_float2(cf * xv.x + (float)a.x, cf * xv.y + (float)a.y);
   }
 }
 
@@ -608,7 +609,7 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
   }
   ev(7);
   ++nl;
-  k_assemble<C><<<cdiv(N * nrhs, 256), 256, 0, s>>>(x, y, io, T->perm.p, N, nrhs, yt.p);
+  k_assemble<C><<<cdiv(N * nrhs, 256), 256, 0, s>>>(x, y, io, T->perm.p, N, nrhs, yt.p, P->diag_c);
   FDA_LAUNCH_CHECK();
   ev(8);
   P->launches = nl;

@@ -120,6 +120,7 @@ struct fda_plan_s {
   fda::DBuf<int64_t> iperm;
   fda::DBuf<int> lev_s, lev_nw;  // per level: compressed dimension and wedge count
   int max_leaf = 1;
+  double diag_c = 0.5;           // y = diag_c x + ... (1/2 for the Burton-Miller operator, 0 for particle sums)
   int64_t launches = 0;          // kernels launched by the last matvec
   fda::DBuf<int> tc_err;         // set by a tensor-core kernel whose bounded wait gave up
   cudaEvent_t* phase_ev = nullptr;  // when set, 9 events recorded between the matvec phases

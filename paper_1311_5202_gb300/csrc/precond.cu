@@ -387,6 +387,10 @@ int bm_precond_create(fda_plan_t* plan, bm_precond_t** out) {
     return FDA_E_INVALID_ARG;
   }
   *out = nullptr;
+  if (plan->prob->particles) {
+    set_error("the leaf-block preconditioner needs a boundary-element problem");
+    return FDA_E_STATE;
+  }
   fda_tree_s* T = plan->tree;
   bm_precond_s* Pc = new (std::nothrow) bm_precond_s();
   if (!Pc) return FDA_E_OOM;

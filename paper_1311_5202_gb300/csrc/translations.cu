@@ -236,7 +236,7 @@ struct LeafJob {
   double2* out;
 };
 static __global__ void k_gen_leaf(const LeafJob* jobs, const double* xt, const double* nt, const double* wt,
-                                  double k, double2 alpha, int ncol, int mode) {
+                                  double k, double2 alpha, int ncol, int mode, int particles) {
   const LeafJob J = jobs[blockIdx.y];
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < J.sc * ncol; q += gridDim.x * blockDim.x) {
     int i = q % J.sc, j = q / J.sc;
@@ -248,16 +248,16 @@ static __global__ void k_gen_leaf(const LeafJob* jobs, const double* xt, const d
       const double* y = xt + 3 * p;
       const double* ny = nt + 3 * p;
       if (mode == 0) {
-        // dG/dn_y(a, y) with r = a - y
+        // dG/dn_y(a, y) with r = a - y; particle sums: (G + alpha dG/dn_y)(a, y) (Eq. sum)
         double dummy[3] = {0, 0, 0};
         KernVals K = helmholtz4(a, dummy, y, ny, k);
-        v = cscale(K.Dy, J.W[i] * wt[p]);
+        v = particles ? cscale(cadd(K.G, cmul(alpha, K.Dy)), J.W[i] * wt[p]) : cscale(K.Dy, J.W[i] * wt[p]);
         J.out[i + (int64_t)j * J.sc] = v;
       } else {
-        // (G + alpha dG/dn_x)(x, a) with r = x - a
+        // (G + alpha dG/dn_x)(x, a) with r = x - a; particle sums: G(x, a)
         double dummy[3] = {0, 0, 0};
         KernVals K = helmholtz4(y, ny, a, dummy, k);
-        v = cscale(cadd(K.G, cmul(alpha, K.Dx)), J.W[i]);
+        v = particles ? cscale(K.G, J.W[i]) : cscale(cadd(K.G, cmul(alpha, K.Dx)), J.W[i]);
         J.out[j + (int64_t)i * ncol] = v;
       }
     } else {
@@ -308,7 +308,7 @@ struct NearJob {
   int64_t off;
 };
 static __global__ void k_gen_near(const NearJob* jobs, const double* xt, const double* nt, const double* wt, double k,
-                                  double2 alpha, double2* out) {
+                                  double2 alpha, double2* out, int particles) {
   const NearJob J = jobs[blockIdx.x];
   int64_t nr = J.te - J.tb, nc = J.se - J.sb;
   for (int64_t q = threadIdx.x; q < nr * nc; q += blockDim.x) {
@@ -316,7 +316,7 @@ static __global__ void k_gen_near(const NearJob* jobs, const double* xt, const d
     double2 v = make_double2(0, 0);
     if (i != j) {
       KernVals K = helmholtz4(xt + 3 * i, nt + 3 * i, xt + 3 * j, nt + 3 * j, k);
-      v = cscale(cadd(K.Dy, cmul(alpha, K.H)), wt[j]);
+      v = particles ? cscale(cadd(K.G, cmul(alpha, K.Dy)), wt[j]) : cscale(cadd(K.Dy, cmul(alpha, K.H)), wt[j]);
     }
     out[J.off + q] = v;
   }
@@ -795,7 +795,8 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
           }
           DBuf<LeafJob> dlj;
           FDA_TRY(dlj.upload(lj));
-          k_gen_leaf<<<dim3(16, (unsigned)nb), 256>>>(dlj.p, xt.p, nt.p, wt.p, k, alpha, ncol, mode);
+          k_gen_leaf<<<dim3(16, (unsigned)nb), 256>>>(dlj.p, xt.p, nt.p, wt.p, k, alpha, ncol, mode,
+                                                      pr->particles);
           FDA_LAUNCH_CHECK();
           DBuf<const double2*> dA, dB;
           DBuf<double2*> dC;
@@ -1277,7 +1278,16 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
     DBuf<int32_t> di_cols;
     DBuf<double2> corr;
     double ms = 0;
-    FDA_TRY(near_corrections(pr, di_ptr, di_cols, corr, &ms));
+    if (pr->particles) {
+      // particle sums: plain kernel values everywhere, no locally corrected weights
+      FDA_TRY(di_ptr.alloc(N + 1));
+      FDA_TRY(di_ptr.zero());
+      FDA_TRY(di_cols.alloc(1));
+      FDA_TRY(corr.alloc(6));
+      P->diag_c = 0.0;
+    } else {
+      FDA_TRY(near_corrections(pr, di_ptr, di_cols, corr, &ms));
+    }
     P->setup_ms[6] = ms;
     DBuf<int64_t> cnt;
     FDA_TRY(cnt.alloc(N));
@@ -1391,7 +1401,7 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
     FDA_TRY(dj.upload(jobs));
     for (size_t b0 = 0; b0 < jobs.size(); b0 += 65535) {
       unsigned nb = (unsigned)std::min<size_t>(65535, jobs.size() - b0);
-      k_gen_near<<<nb, 256>>>(dj.p + b0, xt.p, nt.p, wt.p, k, alpha, P->op64.near.p);
+      k_gen_near<<<nb, 256>>>(dj.p + b0, xt.p, nt.p, wt.p, k, alpha, P->op64.near.p, pr->particles);
       FDA_LAUNCH_CHECK();
     }
     FDA_CUDA(cudaDeviceSynchronize());

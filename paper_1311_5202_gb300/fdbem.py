@@ -95,6 +95,8 @@ _SIGS = [
     ("bm_problem_create", C.c_int, [_dp, C.c_int64, _i32p, C.c_int64, C.c_double, C.c_double, C.c_double,
                                     C.POINTER(C.c_void_p)]),
     ("bm_problem_geometry", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("bm_particles_create", C.c_int, [_dp, _dp, C.c_int64, C.c_double, C.c_double, C.c_double,
+                                      C.POINTER(C.c_void_p)]),
     ("bm_rhs_plane_wave", C.c_int, [C.c_void_p, _dp, C.c_int, C.c_void_p, C.c_void_p]),
     ("bm_rhs_plane_wave_noalloc", C.c_int, [C.c_void_p, _dp, C.c_int, C.c_void_p, C.c_void_p]),
     ("bm_problem_destroy", None, [C.c_void_p]),
@@ -181,6 +183,16 @@ def bm_problem_create(nodes, elems, k, alpha=None):
 
 def bm_problem_geometry(prob, x_dev, n_dev, w_dev):
     _check(lib().bm_problem_geometry(prob, x_dev.data_ptr(), n_dev.data_ptr(), w_dev.data_ptr()))
+
+
+def bm_particles_create(x, n, k, alpha=None):
+    """Particle-summation problem: points x (N x 3) with unit normals n (N x 3); alpha defaults to i/k."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    a = complex(1j / k) if alpha is None else complex(alpha)
+    h = C.c_void_p()
+    _check(lib().bm_particles_create(_ptr(x), _ptr(n), x.shape[0], float(k), a.real, a.imag, C.byref(h)))
+    return h
 
 
 def bm_rhs_plane_wave(prob, dirs, b_dev, stream=None):
@@ -462,6 +474,35 @@ def fda_last_error() -> str:
 
 
 # ----------------------------------------------------------------------------- owning wrappers
+class ParticleSum:
+    """Particle summation (Eq. sum) on points with normals: problem + tree + plan with ordered destruction."""
+
+    def __init__(self, x, n, k, eps=1e-4, leaf_max=64, precision=FDA_PREC_FP64, lowrank=1, nrhs_max=1,
+                 alpha=None, m2l_tensor=0):
+        self.k = float(k)
+        self.prob = bm_particles_create(x, n, k, alpha)
+        self.tree = fda_build_tree(self.prob, leaf_max)
+        self.plan = fda_precompute_translations(self.tree, eps, precision, lowrank, nrhs_max, m2l_tensor)
+        self.N = int(np.asarray(x).shape[0])
+
+    def matvec(self, x, y, stream=None):
+        fda_matvec(self.plan, x, y, stream)
+
+    def info(self):
+        return fda_plan_info(self.plan)
+
+    def close(self):
+        if getattr(self, "plan", None):
+            fda_plan_destroy(self.plan)
+            self.plan = None
+        if getattr(self, "tree", None):
+            fda_tree_destroy(self.tree)
+            self.tree = None
+        if getattr(self, "prob", None):
+            bm_problem_destroy(self.prob)
+            self.prob = None
+
+
 class Solver:
     """Problem + tree + plan with ordered destruction."""
 

@@ -178,6 +178,22 @@ def random_ellipsoid_params(count: int, seed: int = 1, kd_range=(20.0, 80.0), ax
 
 
 # Named workloads (the sizes and wavenumbers of the paper-shaped configurations)
+def sphere_points(n: int, radius: float = 1.0):
+    """n points on a sphere (Fibonacci lattice, nearly uniform) and their outward unit normals."""
+    d = fibonacci_directions(n)
+    return radius * d, d.copy()
+
+
+def table1_k(n: int, points_per_wavelength: float = 20.0, radius: float = 1.0) -> float:
+    """Wavenumber at which n uniform points on the sphere have about ppw points per wavelength."""
+    h = math.sqrt(4.0 * math.pi * radius * radius / n)
+    return 2.0 * math.pi / (points_per_wavelength * h)
+
+
+# particle summations of Sec. 5.1 (Table 1): unit sphere, ~20 points per wavelength, k = 8 pi ... 64 pi
+TABLE1 = [(73728, 8 * math.pi), (294912, 16 * math.pi), (1179648, 32 * math.pi), (4718592, 64 * math.pi)]
+
+
 WORKLOADS = {
     # sphere a=0.5 (D=1), kD=10, 320 elements, 1920 DOF
     "sphere_kd10": dict(kind="sphere", m=4, radius=0.5, k=10.0, eps=1e-6, leaf=64),
