@@ -160,7 +160,12 @@ typedef struct {
                         0 = FP32 FMA; 1 = TF32 with operators pre-expanded at plan time into their
                         shared-memory images (extra device memory about twice the FP32 M2L operators;
                         levels with s > 256 keep the FMA kernel); 2 = 3xTF32 split (FP32-level accuracy) */
-  int reserved[4];
+  int op;            /* operator of fda_matvec (boundary-element problems; particle problems ignore it):
+                        0 = A = 1/2 I + Dbar + alpha Hbar (Eq. bm, the unknown u); 1 = B = Sbar + alpha Mbar
+                        - alpha/2 I, which maps Neumann data q to the radiation right-hand side of Eq. bm
+                        (same tree and translations; S2M from monopole sources, near field and local
+                        corrections of G + alpha dG/dn_x) */
+  int reserved[3];
 } fda_config_t;
 
 /* Build every translation operator and the near-field matrices on the GPU (FP64 masters):

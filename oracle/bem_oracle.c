@@ -17,6 +17,8 @@
  *     finite-part formula for a spherical exclusion neighbourhood (Guiggiani's
  *     direct method). Nearly singular moments use recursive subdivision (Sec. 2.2).
  *   - Particle summation of Sec. 5.1 (Eq. sum) by direct summation.
+ *   - Rows of any combination of the four layer operators with their own corrected weights, such as the
+ *     radiation right-hand side (S + alpha M - alpha/2 I) q of Eq. bm.
  *   - Corrected sum K_bar (Eq. kcorrection) and the rigid-scatter operator
  *     A = c I + beta_D Dbar + beta_H Hbar (Eq. bm with q = 0, Eq. hmat),
  *     row by row, O(N) per row.
@@ -322,7 +324,7 @@ void orc_phi_matrix(double* phi /*6x6, [n][j]*/, double* phiinv /*6x6*/) {
  *   F_{-2} = phi0 J0 / (4 pi |A|^3),
  *   F_{-1} = (J1 phi0 + J0 phi1 - 3 J0 phi0 (A.B)/|A|^2) / (4 pi |A|^3),
  * J1, phi1 the directional derivatives of J and phi along e at xi0. */
-static void moments_self(const elem_t* E, int g, double k, cplx ID[6], cplx IH[6]) {
+static void moments_self4(const elem_t* E, int g, double k, cplx IG[6], cplx ID[6], cplx IM[6], cplx IH[6]) {
   double gx[GL_MAX], gw[GL_MAX], rx[GL_MAX], rw[GL_MAX];
   gauss_legendre01(q_ntheta, gx, gw);
   gauss_legendre01(q_nrho, rx, rw);
@@ -344,7 +346,7 @@ static void moments_self(const elem_t* E, int g, double k, cplx ID[6], cplx IH[6
   double gJ1 = dot3(N0, dN1) / J0, gJ2 = dot3(N0, dN2) / J0;
   double phi0[6];
   basis(s0, t0, phi0);
-  for (int n = 0; n < 6; ++n) ID[n] = IH[n] = 0.0;
+  for (int n = 0; n < 6; ++n) IG[n] = ID[n] = IM[n] = IH[n] = 0.0;
   const double V[3][2] = {{0, 0}, {1, 0}, {0, 1}};
   for (int ed = 0; ed < 3; ++ed) {
     const double* Pv = V[ed];
@@ -413,7 +415,10 @@ static void moments_self(const elem_t* E, int g, double k, cplx ID[6], cplx IH[6
           double phi[6];
           basis(s0 + rho * e1, t0 + rho * e2, phi);
           for (int n = 0; n < 6; ++n) {
+            /* G ~ 1/rho and dG/dn_x ~ (r.n_x)/rho^3 ~ 1/rho: bounded once multiplied by rho */
+            IG[n] += wth * wr * kk[0] * phi[n] * J * rho;
             ID[n] += wth * wr * kk[1] * phi[n] * J * rho;
+            IM[n] += wth * wr * kk[2] * phi[n] * J * rho;
             IH[n] += wth * wr * (kk[3] * phi[n] * J * rho - Fm2[n] / (rho * rho) - Fm1[n] / rho);
           }
         }
@@ -424,9 +429,14 @@ static void moments_self(const elem_t* E, int g, double k, cplx ID[6], cplx IH[6
   }
 }
 
+static void moments_self(const elem_t* E, int g, double k, cplx ID[6], cplx IH[6]) {
+  cplx IG[6], IM[6];
+  moments_self4(E, g, k, IG, ID, IM, IH);
+}
+
 /* ---------------- moments over a nearby element (nearly singular): recursive subdivision ---------------- */
 static void moments_sub_rec(const elem_t* E, const double x[3], const double nx[3], double k, const double T[3][2],
-                            int depth, const double* qx, const double* qw, cplx ID[6], cplx IH[6]) {
+                            int depth, const double* qx, const double* qw, cplx I4[4][6]) {
   double pts[7][2] = {
       {T[0][0], T[0][1]},
       {T[1][0], T[1][1]},
@@ -455,10 +465,8 @@ static void moments_sub_rec(const elem_t* E, const double x[3], const double nx[
         kern4(x, nx, y, ny, k, kk);
         double phi[6];
         basis(s, t, phi);
-        for (int n = 0; n < 6; ++n) {
-          ID[n] += w * kk[1] * phi[n] * J;
-          IH[n] += w * kk[3] * phi[n] * J;
-        }
+        for (int n = 0; n < 6; ++n)
+          for (int q = 0; q < 4; ++q) I4[q][n] += w * kk[q] * phi[n] * J;
       }
     return;
   }
@@ -468,15 +476,26 @@ static void moments_sub_rec(const elem_t* E, const double x[3], const double nx[
       {{m01[0], m01[1]}, {T[1][0], T[1][1]}, {m12[0], m12[1]}},
       {{m20[0], m20[1]}, {m12[0], m12[1]}, {T[2][0], T[2][1]}},
       {{m01[0], m01[1]}, {m12[0], m12[1]}, {m20[0], m20[1]}}};
-  for (int c = 0; c < 4; ++c) moments_sub_rec(E, x, nx, k, (const double(*)[2])C[c], depth + 1, qx, qw, ID, IH);
+  for (int c = 0; c < 4; ++c) moments_sub_rec(E, x, nx, k, (const double(*)[2])C[c], depth + 1, qx, qw, I4);
+}
+
+/* moments of G, dG/dn_y, dG/dn_x, d2G/dn_x dn_y (I4[0..3]) over a nearby element */
+static void moments_near4(const elem_t* E, const double x[3], const double nx[3], double k, cplx I4[4][6]) {
+  double qx[GL_MAX], qw[GL_MAX];
+  gauss_legendre01(q_nsub, qx, qw);
+  for (int q = 0; q < 4; ++q)
+    for (int n = 0; n < 6; ++n) I4[q][n] = 0.0;
+  const double T[3][2] = {{0, 0}, {1, 0}, {0, 1}};
+  moments_sub_rec(E, x, nx, k, T, 0, qx, qw, I4);
 }
 
 static void moments_near(const elem_t* E, const double x[3], const double nx[3], double k, cplx ID[6], cplx IH[6]) {
-  double qx[GL_MAX], qw[GL_MAX];
-  gauss_legendre01(q_nsub, qx, qw);
-  for (int n = 0; n < 6; ++n) ID[n] = IH[n] = 0.0;
-  const double T[3][2] = {{0, 0}, {1, 0}, {0, 1}};
-  moments_sub_rec(E, x, nx, k, T, 0, qx, qw, ID, IH);
+  cplx I4[4][6];
+  moments_near4(E, x, nx, k, I4);
+  for (int n = 0; n < 6; ++n) {
+    ID[n] = I4[1][n];
+    IH[n] = I4[3][n];
+  }
 }
 
 /* Moments of element e for target x (x = Nystrom point g of e when self_g >= 0). */
@@ -683,6 +702,83 @@ static int row_apply(const mesh_t* M, int64_t i, double k, double c, cplx bD, cp
   free(wH);
   if (out) *out = acc;
   return 0;
+}
+
+/* ---------------- rows of c I + bS Sbar + bD Dbar + bM Mbar + bH Hbar (all four layer operators) ----------------
+ * The corrected weights of every kernel come from its own moments (Eq. local correction); the radiation
+ * right-hand side of Eq. bm is (Sbar + alpha Mbar - alpha/2 I) q. */
+static int row_apply4(const mesh_t* M, int64_t i, double k, cplx c, const cplx b[4], const cplx* xv, cplx* out) {
+  phi_init();
+  int32_t* list = (int32_t*)malloc(sizeof(int32_t) * DI_CAP);
+  cplx* wb = (cplx*)malloc(sizeof(cplx) * 6 * DI_CAP);
+  if (!list || !wb) {
+    free(list);
+    free(wb);
+    return -2;
+  }
+  int64_t nl = local_region(M, i, list, DI_CAP);
+  if (nl < 0) {
+    free(list);
+    free(wb);
+    return -1;
+  }
+  const int64_t ei = i / 6;
+  const int gi = (int)(i % 6);
+  const double* x = M->xs + 3 * i;
+  const double* nx = M->ns + 3 * i;
+  for (int64_t q = 0; q < nl; ++q) {
+    elem_t E;
+    elem_load(&E, M->nodes, M->elems + 6 * (int64_t)list[q]);
+    cplx I4[4][6];
+    if (list[q] == ei)
+      moments_self4(&E, gi, k, I4[0], I4[1], I4[2], I4[3]);
+    else
+      moments_near4(&E, x, nx, k, I4);
+    for (int j = 0; j < 6; ++j) {
+      cplx a = 0;
+      for (int n = 0; n < 6; ++n) a += PhiInv[j][n] * (b[0] * I4[0][n] + b[1] * I4[1][n] + b[2] * I4[2][n] + b[3] * I4[3][n]);
+      wb[6 * q + j] = a;
+    }
+  }
+  char* inD = (char*)calloc((size_t)M->ne, 1);
+  for (int64_t q = 0; q < nl; ++q) inD[list[q]] = 1;
+  cplx acc = c * xv[i];
+  for (int64_t e = 0; e < M->ne; ++e) {
+    if (inD[e]) continue;
+    for (int a = 0; a < 6; ++a) {
+      int64_t j = 6 * e + a;
+      cplx kk[4];
+      kern4(x, nx, M->xs + 3 * j, M->ns + 3 * j, k, kk);
+      acc += (b[0] * kk[0] + b[1] * kk[1] + b[2] * kk[2] + b[3] * kk[3]) * M->ws[j] * xv[j];
+    }
+  }
+  for (int64_t q = 0; q < nl; ++q)
+    for (int a = 0; a < 6; ++a) acc += wb[6 * q + a] * xv[6 * (int64_t)list[q] + a];
+  free(inD);
+  free(list);
+  free(wb);
+  *out = acc;
+  return 0;
+}
+
+int orc_rows4(const double* nodes, int64_t nn, const int32_t* elems, int64_t ne, double k, double c_re, double c_im,
+              const double* b /* 4 complex: S, D, M, H */, const double* xv, const int64_t* rows, int64_t nrows,
+              double* y) {
+  mesh_t M;
+  if (mesh_init(&M, nodes, nn, elems, ne)) return -2;
+  const cplx c = c_re + I * c_im;
+  cplx bb[4];
+  for (int q = 0; q < 4; ++q) bb[q] = b[2 * q] + I * b[2 * q + 1];
+  int err = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t r = 0; r < nrows; ++r) {
+    cplx o = 0;
+    if (row_apply4(&M, rows[r], k, c, bb, (const cplx*)xv, &o)) err = -1;
+    y[2 * r] = creal(o);
+    y[2 * r + 1] = cimag(o);
+  }
+  mesh_free(&M);
+  return err;
 }
 
 int orc_matvec_rows(const double* nodes, int64_t nn, const int32_t* elems, int64_t ne, double k, double c,

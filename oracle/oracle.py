@@ -56,6 +56,8 @@ def lib():
                                         dp]
         L.orc_particle_field.argtypes = [dp, dp, C.c_int64, C.c_double, C.c_double, C.c_double, dp, dp, C.c_int64,
                                          dp]
+        L.orc_rows4.argtypes = [dp, C.c_int64, i32p, C.c_int64, C.c_double, C.c_double, C.c_double, dp, dp, i64p,
+                                C.c_int64, dp]
         L.orc_wedge_of.argtypes = [C.c_int, C.c_int32, C.c_int32, C.c_int32]
         L.orc_wedge_of.restype = C.c_int32
         L.orc_tree_build.argtypes = [dp, C.c_int64, C.c_int, C.c_double]
@@ -221,6 +223,35 @@ def matvec_rows(nodes, elems, k, x, rows, c=0.5, beta_d=1.0, beta_h=None):
     if rc:
         raise RuntimeError(f"orc_matvec_rows failed ({rc})")
     return y
+
+
+def rows4(nodes, elems, k, x, rows, c=0.0, b_s=0.0, b_d=0.0, b_m=0.0, b_h=0.0):
+    """Rows of (c I + b_s Sbar + b_d Dbar + b_m Mbar + b_h Hbar) x, every operator with its own locally
+    corrected weights (Eq. local correction)."""
+    nodes, elems = _mesh_args(nodes, elems)
+    x = np.ascontiguousarray(x, dtype=np.complex128)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    b = np.array([b_s, b_d, b_m, b_h], dtype=np.complex128)
+    y = np.zeros(len(rows), dtype=np.complex128)
+    cc = complex(c)
+    rc = lib().orc_rows4(_p(nodes), nodes.shape[0], _p(elems, C.c_int32), elems.shape[0], float(k), cc.real, cc.imag,
+                         _p(b.view(np.float64)), _p(x.view(np.float64)), _p(rows, C.c_int64), len(rows),
+                         _p(y.view(np.float64)))
+    if rc:
+        raise RuntimeError(f"orc_rows4 failed ({rc})")
+    return y
+
+
+def radiation_rhs_rows(nodes, elems, k, q, rows, alpha=None):
+    """Rows of the radiation right-hand side of Eq. bm (no incident wave): (Sbar + alpha Mbar - alpha/2 I) q."""
+    a = 1j / k if alpha is None else complex(alpha)
+    return rows4(nodes, elems, k, q, rows, c=-0.5 * a, b_s=1.0, b_m=a)
+
+
+def pulsating_sphere(k, a):
+    """Surface potential of a sphere of radius a pulsating with q = du/dn = 1, n into the body (Sec. 5.2: the
+    paper prints u = 1/(1 - ik) for the unit sphere): u = a / (1 - i k a)."""
+    return a / (1.0 - 1j * k * a)
 
 
 def dense_matrix(nodes, elems, k, c=0.5, beta_d=1.0, beta_h=None):

@@ -4,7 +4,8 @@
 //  local regions   : D_i = elements whose distance to x_i is <= 2x their longest vertex chord
 //                    (distance = min over the element's 6 nodes and 6 Nystrom points), found by
 //                    hashing element centroids into a uniform grid of cell size >= every element's reach.
-//  k_corrections   : one warp per (x_i, element in D_i): moments of dG/dn_y and d2G/dn_x dn_y against
+//  k_corrections   : one warp per (x_i, element in D_i): moments of dG/dn_y and d2G/dn_x dn_y (or, for the
+//                    radiation right-hand side, of G and dG/dn_x) against
 //                    the basis xi1^p xi2^q (p+q <= 2) (Eq. local correction), the 6x6 solve, and the
 //                    correction C_ij = wbar_ij - [j != i] K_H(x_i, y_j) w_j of Eq. kcorrection.
 //                    Element carrying x_i: polar coordinates about x_i; the hypersingular moment is the
@@ -414,7 +415,9 @@ __device__ __forceinline__ void mom_zero(Mom& m) {
 }
 
 // Self element: x = y(xi0). One lane per angular node; the radial integral runs in the lane.
-__device__ void moments_self_warp(const Tri6& E, int g, double k, Mom& acc) {
+// op 0: moments of dG/dn_y and d2G/dn_x dn_y (finite part); op 1: moments of G and dG/dn_x (both bounded in
+// polar coordinates, no finite-part terms), the kernels of the radiation right-hand side (S + alpha M) q.
+__device__ void moments_self_warp(const Tri6& E, int g, double k, Mom& acc, int op) {
   const int lane = threadIdx.x & 31;
   const double s0 = c_gxi[g][0], t0 = c_gxi[g][1];
   double x[3], xs[3], xt[3];
@@ -510,8 +513,8 @@ __device__ void moments_self_warp(const Tri6& E, int g, double k, Mom& acc) {
     double c3 = 0.25 / FDA_PI / (A2 * An);
     double Fm2[6], Fm1[6];
     for (int q = 0; q < 6; ++q) {
-      Fm2[q] = phi0[q] * J0 * c3;
-      Fm1[q] = (J1 * phi0[q] + J0 * dphi[q] - 3.0 * J0 * phi0[q] * AB / A2) * c3;
+      Fm2[q] = op ? 0.0 : phi0[q] * J0 * c3;
+      Fm1[q] = op ? 0.0 : (J1 * phi0[q] + J0 * dphi[q] - 3.0 * J0 * phi0[q] * AB / A2) * c3;
     }
     // radial integral of the regular part
     double2 rD[6], rH[6];
@@ -526,9 +529,10 @@ __device__ void moments_self_warp(const Tri6& E, int g, double k, Mom& acc) {
       basis6(ss, tt, ph6);
       double f = wr * J * rho;
       double ir = 1.0 / rho;
+      const double2 k1 = op ? K.G : K.Dy, k2 = op ? K.Dx : K.H;
       for (int q = 0; q < 6; ++q) {
-        rD[q] = cadd(rD[q], cscale(K.Dy, f * ph6[q]));
-        double2 h = cscale(K.H, f * ph6[q]);
+        rD[q] = cadd(rD[q], cscale(k1, f * ph6[q]));
+        double2 h = cscale(k2, f * ph6[q]);
         h.x -= wr * (Fm2[q] * ir * ir + Fm1[q] * ir);
         rH[q] = cadd(rH[q], h);
       }
@@ -548,7 +552,7 @@ __device__ void moments_self_warp(const Tri6& E, int g, double k, Mom& acc) {
 // Nearby element: depth-first subdivision, the warp walks one shared stack.
 #define SUB_STACK 64
 __device__ void moments_near_warp(const Tri6& E, const double* x, const double* nx, double k, Mom& acc,
-                                  double (*stk)[6]) {
+                                  double (*stk)[6], int op) {
   const int lane = threadIdx.x & 31;
   int sp = 0;
   if (lane == 0) {
@@ -617,9 +621,10 @@ __device__ void moments_near_warp(const Tri6& E, const double* x, const double* 
         double ph6[6];
         basis6(ss, tt, ph6);
         double f = wq * J;
+        const double2 k1 = op ? K.G : K.Dy, k2 = op ? K.Dx : K.H;
         for (int r = 0; r < 6; ++r) {
-          acc.D[r] = cadd(acc.D[r], cscale(K.Dy, f * ph6[r]));
-          acc.H[r] = cadd(acc.H[r], cscale(K.H, f * ph6[r]));
+          acc.D[r] = cadd(acc.D[r], cscale(k1, f * ph6[r]));
+          acc.H[r] = cadd(acc.H[r], cscale(k2, f * ph6[r]));
         }
       }
     } else {
@@ -644,7 +649,7 @@ __device__ void moments_near_warp(const Tri6& E, const double* x, const double* 
 static __global__ void k_corrections(const double* nodes, const int32_t* elems, const double* xs, const double* ns,
                                      const double* ws, double k, double2 alpha, const int64_t* rowptr,
                                      const int32_t* dcols, int64_t N, int64_t nitems, const int64_t* item_row,
-                                     double2* corr /* nitems x 6 */) {
+                                     double2* corr /* nitems x 6 */, int op) {
   __shared__ double stk_all[4][SUB_STACK][6];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t it = (int64_t)blockIdx.x * 4 + wib;
@@ -658,9 +663,9 @@ static __global__ void k_corrections(const double* nodes, const int32_t* elems, 
   Mom m;
   mom_zero(m);
   if (i / 6 == e)
-    moments_self_warp(E, (int)(i - 6 * e), k, m);
+    moments_self_warp(E, (int)(i - 6 * e), k, m, op);
   else
-    moments_near_warp(E, x, nx, k, m, stk_all[wib]);
+    moments_near_warp(E, x, nx, k, m, stk_all[wib], op);
   for (int q = 0; q < 6; ++q) {
     m.D[q] = warp_csum(m.D[q]);
     m.H[q] = warp_csum(m.H[q]);
@@ -676,7 +681,7 @@ static __global__ void k_corrections(const double* nodes, const int32_t* elems, 
     int64_t col = 6 * e + j;
     if (col != i) {
       KernVals K = helmholtz4(x, nx, xs + 3 * col, ns + 3 * col, k);
-      double2 kh = cadd(K.Dy, cmul(alpha, K.H));
+      double2 kh = op ? cadd(K.G, cmul(alpha, K.Dx)) : cadd(K.Dy, cmul(alpha, K.H));
       wbar = csub(wbar, cscale(kh, ws[col]));
     }
     corr[6 * it + j] = wbar;
@@ -691,7 +696,7 @@ static __global__ void k_item_rows(const int64_t* rowptr, int64_t N, int64_t* it
 
 // Corrections in user DOF order: CSR with one entry per (row, element in D_i, local point j).
 int near_corrections(bm_problem_s* P, DBuf<int64_t>& di_ptr, DBuf<int32_t>& di_cols, DBuf<double2>& corr,
-                     double* ms) {
+                     double* ms, int op) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -709,7 +714,7 @@ int near_corrections(bm_problem_s* P, DBuf<int64_t>& di_ptr, DBuf<int32_t>& di_c
   for (int64_t s0 = 0; s0 < nitems; s0 += chunk) {
     int64_t n = std::min(chunk, nitems - s0);
     k_corrections<<<cdiv(n, 4), 128>>>(P->nodes.p, P->elems.p, P->x.p, P->n.p, P->w.p, P->k, P->alpha,
-                                       di_ptr.p, di_cols.p + s0, P->N, n, item_row.p + s0, corr.p + 6 * s0);
+                                       di_ptr.p, di_cols.p + s0, P->N, n, item_row.p + s0, corr.p + 6 * s0, op);
     FDA_LAUNCH_CHECK();
   }
   FDA_CUDA(cudaDeviceSynchronize());

@@ -41,7 +41,7 @@ static __global__ void k_perm_in(const void* x, int io, const int64_t* perm, int
 
 template <typename C>
 static __global__ void k_assemble(const void* x, void* y, int io, const int64_t* perm, int64_t N, int nrhs,
-                                  const C* yt, double c) {
+                                  const C* yt, double2 c) {
   int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= N * nrhs) return;
   int64_t t = q / nrhs;
@@ -50,11 +50,11 @@ static __global__ void k_assemble(const void* x, void* y, int io, const int64_t*
   double2 a = to_d(yt[q]);
   if (io == FDA_CPLX128) {
     double2 xv = ((const double2*)x)[d];
-    ((double2*)y)[d] = make_double2(c * xv.x + a.x, c * xv.y + a.y);
+    ((double2*)y)[d] = make_double2(c.x * xv.x - c.y * xv.y + a.x, c.x * xv.y + c.y * xv.x + a.y);
   } else {
     float2 xv = ((const float2*)x)[d];
-    const float cf = (float)c;
-    ((float2*)y)[d] = make_float2(cf * xv.x + (float)a.x, cf * xv.y + (float)a.y);
+    const float cr = (float)c.x, ci = (float)c.y;
+    ((float2*)y)[d] = make_float2(cr * xv.x - ci * xv.y + (float)a.x, cr * xv.y + ci * xv.x + (float)a.y);
   }
 }
 

@@ -11,7 +11,7 @@ int zgemm_batched(char opa, char opb, int M, int N, int K, double2 alpha, const 
                   const double2* const* B, int ldb, double2 beta, double2* const* C, int ldc, int64_t batch,
                   cudaStream_t s);
 int near_corrections(bm_problem_s* P, DBuf<int64_t>& di_ptr, DBuf<int32_t>& di_cols, DBuf<double2>& corr,
-                     double* ms);
+                     double* ms, int op);
 int upload_geometry_constants();
 
 // One level of the tree that carries outgoing/incoming representations.
@@ -120,7 +120,7 @@ struct fda_plan_s {
   fda::DBuf<int64_t> iperm;
   fda::DBuf<int> lev_s, lev_nw;  // per level: compressed dimension and wedge count
   int max_leaf = 1;
-  double diag_c = 0.5;           // y = diag_c x + ... (1/2 for the Burton-Miller operator, 0 for particle sums)
+  double2 diag_c = {0.5, 0.0};   // y = diag_c x + ...: 1/2 (operator A), -alpha/2 (operator B), 0 (particle sums)
   int64_t launches = 0;          // kernels launched by the last matvec
   fda::DBuf<int> tc_err;         // set by a tensor-core kernel whose bounded wait gave up
   cudaEvent_t* phase_ev = nullptr;  // when set, 9 events recorded between the matvec phases

@@ -387,8 +387,8 @@ int bm_precond_create(fda_plan_t* plan, bm_precond_t** out) {
     return FDA_E_INVALID_ARG;
   }
   *out = nullptr;
-  if (plan->prob->particles) {
-    set_error("the leaf-block preconditioner needs a boundary-element problem");
+  if (plan->prob->particles || plan->cfg.op != 0) {
+    set_error("the leaf-block preconditioner needs the boundary-element operator A (op = 0)");
     return FDA_E_STATE;
   }
   fda_tree_s* T = plan->tree;

@@ -236,7 +236,7 @@ struct LeafJob {
   double2* out;
 };
 static __global__ void k_gen_leaf(const LeafJob* jobs, const double* xt, const double* nt, const double* wt,
-                                  double k, double2 alpha, int ncol, int mode, int particles) {
+                                  double k, double2 alpha, int ncol, int mode, int particles, int op) {
   const LeafJob J = jobs[blockIdx.y];
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < J.sc * ncol; q += gridDim.x * blockDim.x) {
     int i = q % J.sc, j = q / J.sc;
@@ -251,7 +251,8 @@ static __global__ void k_gen_leaf(const LeafJob* jobs, const double* xt, const d
         // dG/dn_y(a, y) with r = a - y; particle sums: (G + alpha dG/dn_y)(a, y) (Eq. sum)
         double dummy[3] = {0, 0, 0};
         KernVals K = helmholtz4(a, dummy, y, ny, k);
-        v = particles ? cscale(cadd(K.G, cmul(alpha, K.Dy)), J.W[i] * wt[p]) : cscale(K.Dy, J.W[i] * wt[p]);
+        v = particles ? cscale(cadd(K.G, cmul(alpha, K.Dy)), J.W[i] * wt[p])
+                      : cscale(op ? K.G : K.Dy, J.W[i] * wt[p]);  // operator B: monopole sources (S + alpha M)
         J.out[i + (int64_t)j * J.sc] = v;
       } else {
         // (G + alpha dG/dn_x)(x, a) with r = x - a; particle sums: G(x, a)
@@ -308,7 +309,7 @@ struct NearJob {
   int64_t off;
 };
 static __global__ void k_gen_near(const NearJob* jobs, const double* xt, const double* nt, const double* wt, double k,
-                                  double2 alpha, double2* out, int particles) {
+                                  double2 alpha, double2* out, int particles, int op) {
   const NearJob J = jobs[blockIdx.x];
   int64_t nr = J.te - J.tb, nc = J.se - J.sb;
   for (int64_t q = threadIdx.x; q < nr * nc; q += blockDim.x) {
@@ -316,7 +317,8 @@ static __global__ void k_gen_near(const NearJob* jobs, const double* xt, const d
     double2 v = make_double2(0, 0);
     if (i != j) {
       KernVals K = helmholtz4(xt + 3 * i, nt + 3 * i, xt + 3 * j, nt + 3 * j, k);
-      v = particles ? cscale(cadd(K.G, cmul(alpha, K.Dy)), wt[j]) : cscale(cadd(K.Dy, cmul(alpha, K.H)), wt[j]);
+      v = particles ? cscale(cadd(K.G, cmul(alpha, K.Dy)), wt[j])
+                    : cscale(op ? cadd(K.G, cmul(alpha, K.Dx)) : cadd(K.Dy, cmul(alpha, K.H)), wt[j]);
     }
     out[J.off + q] = v;
   }
@@ -796,7 +798,7 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
           DBuf<LeafJob> dlj;
           FDA_TRY(dlj.upload(lj));
           k_gen_leaf<<<dim3(16, (unsigned)nb), 256>>>(dlj.p, xt.p, nt.p, wt.p, k, alpha, ncol, mode,
-                                                      pr->particles);
+                                                      pr->particles, P->cfg.op);
           FDA_LAUNCH_CHECK();
           DBuf<const double2*> dA, dB;
           DBuf<double2*> dC;
@@ -1284,9 +1286,11 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
       FDA_TRY(di_ptr.zero());
       FDA_TRY(di_cols.alloc(1));
       FDA_TRY(corr.alloc(6));
-      P->diag_c = 0.0;
+      P->diag_c = make_double2(0.0, 0.0);
     } else {
-      FDA_TRY(near_corrections(pr, di_ptr, di_cols, corr, &ms));
+      FDA_TRY(near_corrections(pr, di_ptr, di_cols, corr, &ms, P->cfg.op));
+      // operator A: 1/2 I + Dbar + alpha Hbar; operator B (radiation data): Sbar + alpha Mbar - alpha/2 I
+      P->diag_c = P->cfg.op ? make_double2(-0.5 * pr->alpha.x, -0.5 * pr->alpha.y) : make_double2(0.5, 0.0);
     }
     P->setup_ms[6] = ms;
     DBuf<int64_t> cnt;
@@ -1401,7 +1405,8 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
     FDA_TRY(dj.upload(jobs));
     for (size_t b0 = 0; b0 < jobs.size(); b0 += 65535) {
       unsigned nb = (unsigned)std::min<size_t>(65535, jobs.size() - b0);
-      k_gen_near<<<nb, 256>>>(dj.p + b0, xt.p, nt.p, wt.p, k, alpha, P->op64.near.p, pr->particles);
+      k_gen_near<<<nb, 256>>>(dj.p + b0, xt.p, nt.p, wt.p, k, alpha, P->op64.near.p, pr->particles,
+                              P->cfg.op);
       FDA_LAUNCH_CHECK();
     }
     FDA_CUDA(cudaDeviceSynchronize());

@@ -39,7 +39,7 @@ class FdaError(RuntimeError):
 
 class fda_config_t(C.Structure):
     _fields_ = [("eps", C.c_double), ("precision", C.c_int), ("lowrank", C.c_int), ("nrhs_max", C.c_int),
-                ("m2l_tensor", C.c_int), ("reserved", C.c_int * 4)]
+                ("m2l_tensor", C.c_int), ("op", C.c_int), ("reserved", C.c_int * 3)]
 
 
 class bm_gmres_opts_t(C.Structure):
@@ -248,13 +248,14 @@ def fda_tree_destroy(tree):
     lib().fda_tree_destroy(tree)
 
 
-def fda_precompute_translations(tree, eps, precision=FDA_PREC_FP64, lowrank=1, nrhs_max=1, m2l_tensor=0):
+def fda_precompute_translations(tree, eps, precision=FDA_PREC_FP64, lowrank=1, nrhs_max=1, m2l_tensor=0, op=0):
     cfg = fda_config_t()
     cfg.eps = float(eps)
     cfg.precision = int(precision)
     cfg.lowrank = int(lowrank)
     cfg.nrhs_max = int(nrhs_max)
     cfg.m2l_tensor = int(m2l_tensor)
+    cfg.op = int(op)
     h = C.c_void_p()
     _check(lib().fda_precompute_translations(tree, C.byref(cfg), C.byref(h)))
     return h
@@ -507,11 +508,11 @@ class Solver:
     """Problem + tree + plan with ordered destruction."""
 
     def __init__(self, nodes, elems, k, eps=1e-4, leaf_max=64, precision=FDA_PREC_FP64, lowrank=1, nrhs_max=1,
-                 alpha=None, m2l_tensor=0):
+                 alpha=None, m2l_tensor=0, op=0):
         self.k = float(k)
         self.prob = bm_problem_create(nodes, elems, k, alpha)
         self.tree = fda_build_tree(self.prob, leaf_max)
-        self.plan = fda_precompute_translations(self.tree, eps, precision, lowrank, nrhs_max, m2l_tensor)
+        self.plan = fda_precompute_translations(self.tree, eps, precision, lowrank, nrhs_max, m2l_tensor, op)
         self.N = 6 * int(np.asarray(elems).shape[0])
 
     def matvec(self, x, y, stream=None):

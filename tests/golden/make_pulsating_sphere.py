@@ -1,0 +1,20 @@
+"""Writes tests/golden/pulsating_sphere.txt: the surface potential of the unit sphere pulsating with
+q = du/dn = 1 that the paper prints for its radiation benchmark (Sec. 5.2: u = 1/(1 - ik)), at the paper's
+wavenumbers k = 2 pi, 4 pi, 8 pi, 16 pi, 32 pi. Calls only oracle/."""
+import math
+import os
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+from oracle import oracle as O  # noqa: E402
+
+if __name__ == "__main__":
+    with open(os.path.join(HERE, "pulsating_sphere.txt"), "w") as f:
+        f.write("# Sec. 5.2: unit sphere, q = du/dn = 1 (n into the body), u = 1/(1 - i k) on the surface\n")
+        f.write("# k  Re(u)  Im(u)\n")
+        for m in (1, 2, 4, 8, 16):
+            k = 2.0 * math.pi * m
+            u = O.pulsating_sphere(k, 1.0)
+            f.write(f"{k:.17g} {u.real:.17g} {u.imag:.17g}\n")

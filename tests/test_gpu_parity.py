@@ -347,3 +347,34 @@ def test_autotuner_choices_keep_parity():
             assert err < 3e-4, (r, err)
     finally:
         S.close()
+
+
+# ------------------------------------------------------------------ radiation data operator B = S + alpha M - alpha/2
+def test_radiation_operator_and_pulsating_sphere():
+    """Operator B (op = 1) against the oracle's rows on all 1920 rows (FP64: 1e-4), then the pulsating sphere:
+    b = B 1 and A u = b solved through the library give the paper's u = a/(1 - ika) within the
+    discretisation error of the oracle's own solve (max 5e-3)."""
+    _need_gpu()
+    mesh = inputs.icosphere(4, 0.5)
+    k = 10.0
+    N = mesh.n_dof
+    SB = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=1e-6, leaf_max=64, op=1)
+    SA = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=1e-6, leaf_max=64)
+    try:
+        q = inputs.complex_gaussian(N, 13)
+        qd = torch.from_numpy(q).to(DEV)
+        bd = torch.empty_like(qd)
+        SB.matvec(qd, bd)
+        torch.cuda.synchronize()
+        bo = O.radiation_rhs_rows(mesh.nodes, mesh.elems, k, q, np.arange(N))
+        assert np.linalg.norm(bd.cpu().numpy() - bo) / np.linalg.norm(bo) < 1e-4
+        one = torch.ones(N, dtype=torch.complex128, device=DEV)
+        SB.matvec(one, bd)
+        u = torch.zeros_like(bd)
+        st = SA.solve(bd, u, tol=1e-8, restart=60, max_iter=400)
+        assert st["rel_residual"] <= 1e-8
+        ue = O.pulsating_sphere(k, 0.5)
+        assert np.max(np.abs(u.cpu().numpy() - ue)) < 5e-3 * abs(ue)
+    finally:
+        SB.close()
+        SA.close()

@@ -364,3 +364,35 @@ def test_network_identity_start_and_scaling():
     l1, _ = O.net_loss_grad(w2, H, r, y, e, segs)
     l2, _ = O.net_loss_grad(w2, H, c * r, c * y, c * e, segs)
     assert abs(l1 - l2) < 1e-12 * l1
+
+
+# ---------------------------------------------------------------- radiation problem (Eq. bm with q given)
+def _pulsating_solve(m, a, k):
+    mesh = inputs.icosphere(m, a)
+    N = mesh.n_dof
+    b = O.radiation_rhs_rows(mesh.nodes, mesh.elems, k, np.ones(N, dtype=complex), np.arange(N))
+    A = O.dense_matrix(mesh.nodes, mesh.elems, k)
+    return np.linalg.solve(A, b)
+
+
+def test_pulsating_sphere_matches_paper_value():
+    """Sec. 5.2: the unit sphere pulsating with q = 1 has u = 1/(1 - ik); tests/golden/pulsating_sphere.txt holds
+    the paper's values. The oracle's Burton-Miller radiation solve (S, M, D, H with their own corrected weights)
+    at k = 2 pi on 320 curved elements lands within its discretisation error."""
+    import os
+    rows = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "pulsating_sphere.txt"))
+    k, ure, uim = rows[0]
+    ue = ure + 1j * uim
+    assert abs(O.pulsating_sphere(k, 1.0) - ue) < 1e-15
+    u = _pulsating_solve(4, 1.0, k)
+    assert np.max(np.abs(u - ue)) < 1e-2 * abs(ue)
+    assert abs(np.mean(u) - ue) < 1e-3 * abs(ue)
+
+
+def test_radiation_solve_converges_under_refinement():
+    """The same solve at kD = 10 converges to a/(1 - ika) as the mesh is refined (320 -> 720 elements)."""
+    k, a = 10.0, 0.5
+    ue = O.pulsating_sphere(k, a)
+    e4 = np.max(np.abs(_pulsating_solve(4, a, k) - ue)) / abs(ue)
+    e6 = np.max(np.abs(_pulsating_solve(6, a, k) - ue)) / abs(ue)
+    assert e4 < 5e-3 and e6 < 2e-3 and e4 / e6 > 2.0, (e4, e6)
