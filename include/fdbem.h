@@ -348,6 +348,17 @@ int bm_residual_pair(fda_plan_t* plan, const void* b, const void* xstar, const v
 int bm_fgmres_solve(fda_plan_t* plan, bm_precond_t* precond, bm_net_t* net, const void* b, void* x, int nrhs,
                     const bm_gmres_opts_t* opts, bm_gmres_stats_t* stats, void* stream);
 
+/* Failure detection (no paper counterpart). Every wait inside the library's kernels (bulk-copy and MMA
+ * completion on mbarriers) has a wall-clock bound of 1 s; a wait that gives up records it in the plan's
+ * device error flag and the kernel finishes without touching other memory. fda_plan_check synchronizes
+ * the device, reads and clears that flag: FDA_OK, or FDA_E_TIMEOUT when some earlier product on this plan
+ * had a wait give up (its results are invalid). bm_gmres_solve and bm_fgmres_solve check it before they
+ * return. fda_wait_selftest launches one kernel that waits on an mbarrier nothing completes, bounded by
+ * limit_ms (0 < limit_ms <= 1000), and reports *timed_out = 1 when the bound ran out (the expected
+ * outcome); the context stays usable. */
+int fda_plan_check(fda_plan_t* plan);
+int fda_wait_selftest(double limit_ms, int* timed_out);
+
 /* Self-test of the tensor-core M2L kernels (diagnostic; no paper counterpart): one complex M x K operator
  * (K <= 1024) applied to P gathered columns, against an FP64 host product of the same FP32 data.
  * split = 0: TF32 with operands expanded in the kernel (M = 64, P = 64); 1: 3xTF32 split (M = 64, P = 64);

@@ -264,6 +264,22 @@ int fda_autotune(fda_plan_t* plan, int nrhs, void* stream, fda_tune_report_t* re
   return autotune(plan, nrhs, (cudaStream_t)stream, report);
 }
 
+int fda_plan_check(fda_plan_t* plan) {
+  ARG_CHECK(plan, "NULL plan");
+  FDA_CUDA(cudaDeviceSynchronize());
+  int flag = 0;
+  if (plan->tc_err.p) {
+    FDA_CUDA(cudaMemcpy(&flag, plan->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    FDA_TRY(plan->tc_err.zero());
+    FDA_CUDA(cudaDeviceSynchronize());
+  }
+  if (flag) {
+    set_error("a bounded device wait gave up in an earlier product (results of that product are invalid)");
+    return FDA_E_TIMEOUT;
+  }
+  return FDA_OK;
+}
+
 struct fda_graph_s {
   fda_plan_s* plan = nullptr;
   cudaGraph_t graph = nullptr;

@@ -754,6 +754,14 @@ int gmres_solve(fda_plan_s* P, const double2* b, double2* x, int nrhs, const bm_
     if (rc != FDA_OK) break;
   }
   FDA_CUDA(cudaStreamSynchronize(s));
+  if (rc == FDA_OK && P->tc_err.p) {  // a bounded device wait that gave up invalidates the solve
+    int flag = 0;
+    FDA_CUDA(cudaMemcpy(&flag, P->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+      set_error("a bounded device wait gave up during the solve");
+      rc = FDA_E_TIMEOUT;
+    }
+  }
   if (st) {
     st->iterations = total_it;
     st->outer_iterations = outer;

@@ -705,6 +705,33 @@ int m2l_tc3_launch(const GemmUnit* units, size_t nunits, const float* img, const
 
 using namespace fda;
 
+// Failure-detection self-test: one thread waits on an mbarrier phase that nothing completes, with the given
+// wall-clock bound; when the bound runs out it records the timeout and returns (no trap, no fault).
+static __global__ void k_wait_probe(uint64_t limit_ns, int* timed_out) {
+  __shared__ alignas(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t a = smem_u32(&bar);
+    const uint64_t t0 = tc_clock_ns();
+    int done = 0;
+    while (!done) {
+      uint32_t ok;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(ok)
+          : "r"(a), "r"(0u)
+          : "memory");
+      if (ok) done = 1;
+      else if (tc_clock_ns() - t0 > limit_ns) done = 2;
+    }
+    *timed_out = done == 2 ? 1 : 0;
+  }
+}
+
 // Self-test of the tensor-core path: one complex M x K product applied to P gathered columns, against an FP64
 // host product of the same FP32 data. split 0: TF32 (M = 64, P = 64); 1: 3xTF32 split (M = 64, P = 64);
 // 2..5: TF32 with the pre-expanded operator image (M = min(256, K), P = 100), tile shape split - 2.
@@ -777,5 +804,20 @@ extern "C" int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_
     }
   *max_rel_err = worst;
   *wait_failed = he;
+  return FDA_OK;
+}
+
+extern "C" int fda_wait_selftest(double limit_ms, int* timed_out) {
+  if (!(limit_ms > 0 && limit_ms <= 1000.0) || !timed_out) {
+    set_error("limit_ms must lie in (0, 1000]");
+    return FDA_E_INVALID_ARG;
+  }
+  DBuf<int> d;
+  FDA_TRY(d.alloc(1));
+  FDA_TRY(d.zero());
+  k_wait_probe<<<1, 32>>>((uint64_t)(limit_ms * 1e6), d.p);
+  FDA_LAUNCH_CHECK();
+  FDA_CUDA(cudaDeviceSynchronize());
+  FDA_CUDA(cudaMemcpy(timed_out, d.p, sizeof(int), cudaMemcpyDeviceToHost));
   return FDA_OK;
 }

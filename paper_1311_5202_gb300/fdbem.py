@@ -109,6 +109,8 @@ _SIGS = [
     ("fda_matvec_graph_create", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                           C.POINTER(C.c_void_p)]),
     ("fda_graph_launch", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("fda_plan_check", C.c_int, [C.c_void_p]),
+    ("fda_wait_selftest", C.c_int, [C.c_double, C.POINTER(C.c_int)]),
     ("fda_autotune", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(fda_tune_report_t)]),
     ("fda_graph_nodes", C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     ("fda_graph_destroy", None, [C.c_void_p]),
@@ -317,6 +319,18 @@ def fda_autotune(plan, nrhs=1, stream=None) -> dict:
     rows = [dict(level=R.level[e], stage=R.stage[e], ms_fma=R.ms_fma[e], ms_tensor=R.ms_tensor[e],
                  chosen=("fma", "tensor", "tensor-alt1", "tensor-alt2", "tensor-alt3")[R.chosen[e]]) for e in range(R.entries)]
     return dict(m2l=rows, near_ms=list(R.near_ms), near_rhs_per_pass=R.near_rhs_per_pass)
+
+
+def fda_plan_check(plan):
+    """FDA_OK, or FDA_E_TIMEOUT if a bounded device wait gave up in an earlier product (flag cleared)."""
+    return lib().fda_plan_check(plan)
+
+
+def fda_wait_selftest(limit_ms=50.0) -> int:
+    """Run one kernel whose wait can never complete, bounded by limit_ms; returns 1 when it timed out."""
+    t = C.c_int(0)
+    _check(lib().fda_wait_selftest(float(limit_ms), C.byref(t)))
+    return int(t.value)
 
 
 def fda_graph_launch(g, stream=None):

@@ -378,3 +378,52 @@ def test_radiation_operator_and_pulsating_sphere():
     finally:
         SB.close()
         SA.close()
+
+
+def test_dirichlet_data_recovers_pulsating_velocity():
+    """Dirichlet data (f4): with u given, the same Burton-Miller equation is B q = A u (both operators of the
+    library). Given the pulsating sphere's u = a/(1 - ika), GMRES on the op = 1 plan returns q = 1."""
+    _need_gpu()
+    mesh = inputs.icosphere(4, 0.5)
+    k = 10.0
+    N = mesh.n_dof
+    SA = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=1e-6, leaf_max=64)
+    SB = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=1e-6, leaf_max=64, op=1)
+    try:
+        ud = torch.full((N,), complex(O.pulsating_sphere(k, 0.5)), dtype=torch.complex128, device=DEV)
+        b = torch.empty_like(ud)
+        SA.matvec(ud, b)
+        q = torch.zeros_like(b)
+        st = SB.solve(b, q, tol=1e-8, restart=60, max_iter=400)
+        assert st["rel_residual"] <= 1e-8
+        qh = q.cpu().numpy()
+        # the library's q satisfies the oracle's own discrete equation B q = A u_D (FDA accuracy) ...
+        rows = np.arange(N)
+        lhs = O.radiation_rhs_rows(mesh.nodes, mesh.elems, k, qh, rows)
+        rhs = O.matvec_rows(mesh.nodes, mesh.elems, k, ud.cpu().numpy(), rows)
+        assert np.linalg.norm(lhs - rhs) / np.linalg.norm(rhs) < 1e-4
+        # ... and q = 1 up to the discretisation error of a normal-derivative unknown on 320 elements
+        assert np.max(np.abs(qh - 1.0)) < 1.5e-2 and abs(np.mean(qh) - 1.0) < 3e-3
+    finally:
+        SA.close()
+        SB.close()
+
+
+# ------------------------------------------------------------------ failure detection (bounded device waits)
+def test_bounded_wait_times_out_and_context_survives():
+    """A kernel waits on an mbarrier that nothing completes: its 50 ms bound runs out, it reports the timeout
+    and returns; the context keeps working (a product and the plan's error check afterwards)."""
+    _need_gpu()
+    assert fdbem.fda_wait_selftest(50.0) == 1
+    mesh = inputs.icosphere(3, 0.5)
+    S = fdbem.Solver(mesh.nodes, mesh.elems, 5.0, eps=1e-4, leaf_max=64, precision=fdbem.FDA_PREC_FP32,
+                     m2l_tensor=1)
+    try:
+        x = torch.ones(S.N, dtype=torch.complex128, device=DEV)
+        y = torch.empty_like(x)
+        S.matvec(x, y)
+        torch.cuda.synchronize()
+        assert torch.isfinite(torch.view_as_real(y)).all()
+        assert fdbem.fda_plan_check(S.plan) == fdbem.FDA_OK
+    finally:
+        S.close()
