@@ -427,3 +427,32 @@ def test_bounded_wait_times_out_and_context_survives():
         assert fdbem.fda_plan_check(S.plan) == fdbem.FDA_OK
     finally:
         S.close()
+
+
+# ------------------------------------------------------------------ full sizes, as the bench runs them
+@pytest.mark.parametrize("workload", ["sphere_kd100", "sphere_kd200"])
+def test_full_size_sampled_rows(workload):
+    """The configurations the bench times (kD = 100: 100,920 DOF; kD = 200: 1,129,080 DOF; eps = 1e-4, 64 points
+    per leaf): the autotuned mixed plan (FP32 near field, TF32 tensor-core M2L/M2M/L2L) and its FP64 form
+    against the oracle on 64 sampled rows computed one by one (bars 3e-4 and 1e-4)."""
+    _need_gpu()
+    spec = inputs.WORKLOADS[workload]
+    mesh = inputs.make_mesh(spec)
+    k = spec["k"]
+    S = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=spec["eps"], leaf_max=spec["leaf"],
+                     precision=fdbem.FDA_PREC_FP32, m2l_tensor=1)
+    try:
+        fdbem.fda_autotune(S.plan, 1)
+        x = inputs.complex_gaussian(S.N, 20131120)
+        xd = torch.from_numpy(x).to(DEV)
+        yd = torch.empty_like(xd)
+        rows = inputs.sample_rows(S.N, 64, 7)
+        yo = _oracle_rows(mesh, k, x, rows)
+        for prec, bar in ((fdbem.FDA_PREC_FP32, 3e-4), (fdbem.FDA_PREC_FP64, 1e-4)):
+            fdbem.fda_matvec_ex(S.plan, prec, xd, yd)
+            torch.cuda.synchronize()
+            err = np.linalg.norm(yd.cpu().numpy()[rows] - yo) / np.linalg.norm(yo)
+            assert err < bar, (workload, prec, err)
+        assert fdbem.fda_plan_check(S.plan) == fdbem.FDA_OK
+    finally:
+        S.close()
