@@ -165,7 +165,10 @@ typedef struct {
                         - alpha/2 I, which maps Neumann data q to the radiation right-hand side of Eq. bm
                         (same tree and translations; S2M from monopole sources, near field and local
                         corrections of G + alpha dG/dn_x) */
-  int reserved[3];
+  int near_split;    /* near-field schedule until fda_autotune chooses: 0 = the correction entries outside the
+                        direct blocks are applied inside the near-field stream, per target leaf; 1 = by their
+                        own CSR kernel (one warp per row) before the stream. Same sums, other order. */
+  int reserved[2];
 } fda_config_t;
 
 /* Build every translation operator and the near-field matrices on the GPU (FP64 masters):
@@ -193,8 +196,9 @@ int fda_matvec_ex(fda_plan_t* plan, int precision, const void* x, void* y, int n
 
 /* Autotuner (no paper counterpart). For an FP32 plan and a batch width nrhs (1..nrhs_max), times on the
  * plan's own operators every M2L (level, stage) with the FP32 FMA kernel and with the plan's tensor-core
- * kernel (m2l_tensor 1: four tile shapes; m2l_tensor 2: one), and for nrhs >= 12 the near field at 4 and 16 right-hand sides per pass over
- * the near-field matrices; the plan keeps the faster variant of each for all later products. Synchronous;
+ * kernel (m2l_tensor 1: four tile shapes; m2l_tensor 2: one), for nrhs >= 12 the near field at 4 and 16 right-hand sides per pass over
+ * the near-field matrices, and the near field with its off-block correction entries inside the stream or as a
+ * separate CSR kernel; the plan keeps the faster variant of each for all later products. Synchronous;
  * overwrites the plan's internal workspaces only. report (HOST) receives the timings and choices.
  * Errors: FDA_E_INVALID_ARG, FDA_E_STATE (FP64-only plan), FDA_E_OOM, FDA_E_CUDA. */
 typedef struct {
@@ -207,7 +211,10 @@ typedef struct {
                              (alternative shapes: other column width or stage count) */
   double near_ms[2];      /* near field at 4 and 16 right-hand sides per pass (nrhs >= 12; else 0) */
   int32_t near_rhs_per_pass;
-  int32_t reserved[7];
+  int32_t near_split;     /* 1: the correction entries outside the direct blocks run as their own CSR kernel
+                             before the near-field stream; 0: inside the stream, per target leaf */
+  double near_split_ms[2];  /* near field (at the chosen width) with the corrections per leaf (0) and split (1) */
+  int32_t reserved[2];
 } fda_tune_report_t;
 int fda_autotune(fda_plan_t* plan, int nrhs, void* stream, fda_tune_report_t* report);
 

@@ -430,6 +430,9 @@ __device__ __forceinline__ void tc3_bulk(void* dst, const void* src, uint32_t by
 __device__ __forceinline__ void tc3_cp8(uint32_t dst, const void* src, uint32_t src_bytes) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
+__device__ __forceinline__ void tc3_cp16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
 __device__ __forceinline__ void tc3_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void tc3_wait_group() {
@@ -513,7 +516,6 @@ static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units
     ph_m[s] ^= 1;
     return all;
   };
-  const int n_lo = (lane >> 1) & 7, j_lo = (lane & 1) | (((lane >> 4) & 1) << 1);
   auto issue = [&](int kc) {
     const int s = kc % NST;
     if (t == 0) {
@@ -527,13 +529,21 @@ static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units
       }
     }
     const uint32_t bbase = smem_u32(S.b[s]);
-    for (int r = w; r < (N / 8) * 4; r += TC3_NT / 32) {
-      const int n = (r >> 2) * 8 + n_lo, j = (r & 3) * 4 + j_lo;
+    // two complex values (16 bytes, one K-major core row segment) per copy: lane = (column n mod 8, pair
+    // of K indices); four lanes read 64 contiguous bytes of a column
+    for (int r = w; r < (N / 8) * 2; r += TC3_NT / 32) {
+      const int n = (r >> 1) * 8 + (lane >> 2), j = (r & 1) * 8 + 2 * (lane & 3);
       if (S.sbase[n] < 0) continue;  // unused column: its results are never read
       const int gj = kc * (TC3_KC / 2) + j;
-      const bool in = gj < U.K;
-      const float2* src = in ? X + (int64_t)S.srr[n] * lds + S.sbase[n] + gj : X;
-      tc3_cp8(bbase + kmaj_off(n, 2 * j, TC3_KC), src, in ? 8u : 0u);
+      const uint32_t dst = bbase + kmaj_off(n, 2 * j, TC3_KC);
+      const float2* src = gj < U.K ? X + (int64_t)S.srr[n] * lds + S.sbase[n] + gj : X;
+      const uint32_t nb = gj + 1 < U.K ? 16u : (gj < U.K ? 8u : 0u);  // the rest is zero-filled
+      if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        tc3_cp16(dst, src, nb);
+      } else {  // odd coefficient offset: two 8-byte copies
+        tc3_cp8(dst, src, nb >= 8 ? 8u : 0u);
+        tc3_cp8(dst + 8, nb == 16 ? src + 1 : X, nb == 16 ? 8u : 0u);
+      }
     }
     tc3_commit_group();
   };

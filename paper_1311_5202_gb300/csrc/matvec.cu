@@ -666,6 +666,7 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
   FDA_TRY(x.zero(s));
   for (int l = 0; l < FDA_MAXLEV; ++l) P->m2l_choice[l][0] = P->m2l_choice[l][1] = -1;
   P->near_wide = -1;
+  P->near_csep = -1;
   FDA_TRY(plan_matvec(P, FDA_PREC_FP32, x.p, y.p, nrhs, FDA_CPLX64, s, false));  // workspaces hold valid data
   FDA_CUDA(cudaStreamSynchronize(s));
   int64_t nl = 0;
@@ -716,6 +717,19 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
   } else {
     R->near_rhs_per_pass = nrhs == 1 ? 1 : 4;
   }
+  if (P->n_near_tleaf > 0 && P->near_max_nr <= 256) {
+    double tc[2];
+    for (int cs = 0; cs < 2; ++cs) {
+      P->near_csep = cs;
+      FDA_TRY(time_ms(s, [&]() { return near_stream<float2>(P, P->op32.near.p, P->op32.corr.p, P->xt32.p, P->yt32.p,
+                                                            nrhs, s, &nl); },
+                      3, &tc[cs]));
+    }
+    R->near_split_ms[0] = tc[0];
+    R->near_split_ms[1] = tc[1];
+    P->near_csep = tc[1] < tc[0] ? 1 : 0;
+  }
+  R->near_split = P->near_csep == 1 ? 1 : 0;
   FDA_TRY(plan_matvec(P, FDA_PREC_FP32, x.p, y.p, nrhs, FDA_CPLX64, s, false));
   FDA_CUDA(cudaStreamSynchronize(s));
   return FDA_OK;

@@ -60,22 +60,35 @@ __device__ __forceinline__ void ns_bulk(void* dst, const void* src, uint32_t byt
                : "memory");
 }
 
+// global -> shared asynchronous copies of densities (zero-filled beyond src_bytes)
+__device__ __forceinline__ void ns_cp8(void* dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(ns_smem(dst)), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void ns_cp16(void* dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(ns_smem(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+
 // barrier among the consumer warps only (the producer warp never joins it)
 __device__ __forceinline__ void ns_cons_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NS_CONS) : "memory"); }
 
 // single right-hand side: three CTAs per SM (3-stage ring, 16 KB density window); batches: fewer, larger CTAs
+// 16 right-hand sides per pass: two density windows of at most 256 columns (32 KB each), the next one copied
+// with cp.async while the current one is used; corrections always by the separate CSR kernel (no buffer)
 template <typename C, int NR>
 struct NsLayout {
   static constexpr int E = sizeof(C);
+  static constexpr bool DB = NR == 16;
   static constexpr int STAGES = NR == 1 ? 3 : 4;
   static constexpr int MINB = NR == 1 ? 3 : (NR <= 4 ? 2 : 1);
-  static constexpr int XBYTES = (NR == 1 || E * NR >= 64) ? 16384 : 32768;
-  static constexpr int XW = (XBYTES / (NR * E)) & ~1;  // columns per density window (even)
+  static constexpr int XBYTES = DB ? 32768 : ((NR == 1 || E * NR >= 64) ? 16384 : 32768);
+  static constexpr int XW0 = (XBYTES / (NR * E)) & ~1;
+  static constexpr int XW = DB && XW0 > NS_CONS ? NS_CONS : XW0;  // columns per density window (even)
   static constexpr size_t ring = (size_t)STAGES * NS_STAGE_BYTES;
   static constexpr size_t xs = ring;
-  static constexpr size_t red = xs + (size_t)XW * NR * E;
+  static constexpr size_t red = xs + (size_t)(DB ? 2 : 1) * XW * NR * E;
   static constexpr size_t cor = red + (size_t)NS_CONS * NR * E;
-  static constexpr size_t crow = cor + (size_t)NS_CONS * NR * E;
+  static constexpr size_t crow = cor + (DB ? (size_t)0 : (size_t)NS_CONS * NR * E);
   static constexpr size_t bars = crow + (NS_CONS + 8) * sizeof(int);
   static constexpr size_t total = bars + 2 * STAGES * sizeof(uint64_t) + 128;  // + alignment slack
 };
@@ -87,7 +100,7 @@ template <typename C, int NR>
 static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR>::MINB) k_near_stream(
     const int32_t* part, const int64_t* tleaf, const int64_t* pb, const int64_t* pe, const int64_t* nbase,
     const int32_t* ncolv, const int64_t* xbase, const int32_t* xcol, const C* B, const int64_t* cptr,
-    const int32_t* ccol, const C* cval, const C* xt, C* yt, int nrhs, int r0, int rc, int* err) {
+    const int32_t* ccol, const C* cval, const C* xt, C* yt, int nrhs, int r0, int rc, int csep, int* err) {
   typedef NsLayout<C, NR> Ly;
   typedef decltype(xt[0].x) R;
   constexpr int E = Ly::E, XW = Ly::XW, NS_STAGES = Ly::STAGES;
@@ -149,6 +162,49 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR>::MINB) k_near_st
   const int lane = t & 31;
   int it = 0;
   bool failed = false;
+  // double-buffered windows (16 right-hand sides): window A is the next one to copy; colA is this thread's
+  // column of it (one column per thread), loaded one window ahead so that its latency hides behind compute
+  int ua = u0, wa = 0, buf = 0;
+  auto col_of = [&](int uu, int ww) -> int {
+    const int c = ww + t;
+    return (uu < u1 && t < XW && c < ncolv[uu]) ? xcol[xbase[uu] + c] : -1;
+  };
+  // next window in the consumers' order (leaves without columns have no window)
+  auto normalize = [&]() {
+    while (ua < u1 && wa >= ncolv[ua]) {
+      ++ua;
+      wa = 0;
+    }
+  };
+  auto advance = [&]() {
+    wa += XW;
+    normalize();
+  };
+  auto copy_window = [&](int col, int b) {
+    if (col >= 0) {
+      C* dst = xs + ((size_t)b * XW + t) * NR;
+      const C* src = xt + (int64_t)col * nrhs + r0;
+      if (E == 16 || (nrhs & 1) == 0) {  // 16-byte aligned runs of 16 / E right-hand sides
+        constexpr int V = 16 / E;
+#pragma unroll
+        for (int q = 0; q < NR; q += V) {
+          const int nb = min(16, max(0, (rc - q) * E));
+          ns_cp16(dst + q, nb > 0 ? (const void*)(src + q) : (const void*)xt, (uint32_t)nb);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < NR; ++q) ns_cp8(dst + q, q < rc ? (const void*)(src + q) : (const void*)xt, q < rc ? 8u : 0u);
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  int colA = -1;
+  if constexpr (Ly::DB) {
+    normalize();
+    copy_window(col_of(ua, wa), 0);  // window 0
+    advance();
+    colA = col_of(ua, wa);
+  }
   for (int u = u0; u < u1; ++u) {
     const int64_t L = tleaf[u];
     const int64_t tb = pb[L];
@@ -162,11 +218,13 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR>::MINB) k_near_st
     // correction entries outside the direct blocks. A leaf's rows are consecutive, so its entries are one
     // CSR range: every thread takes entries, finds the row by binary search over the leaf's row pointers
     // and adds into shared memory (one parallel pass instead of a chain per row).
-    const int64_t cb = cptr[tb];
-    for (int q = t; q <= nr; q += NS_CONS) crow[q] = (int)(cptr[tb + q] - cb);
-    for (int q = t; q < nr * NR; q += NS_CONS) cor[q] = mk((R)0, (R)0);
-    ns_cons_sync();
-    const int ncor = crow[nr];
+    const int64_t cb = csep ? 0 : cptr[tb];
+    if (!csep) {
+      for (int q = t; q <= nr; q += NS_CONS) crow[q] = (int)(cptr[tb + q] - cb);
+      for (int q = t; q < nr * NR; q += NS_CONS) cor[q] = mk((R)0, (R)0);
+      ns_cons_sync();
+    }
+    const int ncor = csep ? 0 : crow[nr];
     constexpr int CE = NR <= 4 ? 4 : 1;  // correction entries per thread and pass (register budget)
     for (int e0 = 0; e0 < ncor; e0 += CE * NS_CONS) {
       // all loads first (CE entries per thread), then the density gathers, then per-entry products
@@ -232,13 +290,25 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR>::MINB) k_near_st
     for (int q = 0; q < NR; ++q) acc[q] = mk((R)0, (R)0);
     for (int wb = 0; wb < ncol; wb += XW) {
       const int we = min(ncol, wb + XW);
-      ns_cons_sync();  // readers of the previous window are done
-      for (int c = wb + t; c < we; c += NS_CONS) {
-        const C* xp = xt + (int64_t)xcol[xb + c] * nrhs + r0;
+      const C* xcur = xs;
+      if constexpr (Ly::DB) {
+        // this window's copies have landed (own, then everyone's); the other buffer's readers are done
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        ns_cons_sync();
+        copy_window(colA, buf ^ 1);
+        advance();
+        colA = col_of(ua, wa);
+        xcur = xs + (size_t)buf * XW * NR;
+        buf ^= 1;
+      } else {
+        ns_cons_sync();  // readers of the previous window are done
+        for (int c = wb + t; c < we; c += NS_CONS) {
+          const C* xp = xt + (int64_t)xcol[xb + c] * nrhs + r0;
 #pragma unroll
-        for (int q = 0; q < NR; ++q) xs[(c - wb) * NR + q] = (q < rc) ? xp[q] : mk((R)0, (R)0);
+          for (int q = 0; q < NR; ++q) xs[(c - wb) * NR + q] = (q < rc) ? xp[q] : mk((R)0, (R)0);
+        }
+        ns_cons_sync();
       }
-      ns_cons_sync();
       for (int c = wb; c < we;) {
         const int cc = min(cpc, we - c);
         const int st = it % NS_STAGES;
@@ -248,7 +318,7 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR>::MINB) k_near_st
         }
         if (!failed && act) {
           const C* Bs = (const C*)(ring + (size_t)st * NS_STAGE_BYTES) + i;
-          const C* xw = xs + (c - wb) * NR;
+          const C* xw = xcur + (c - wb) * NR;
           int cl = g;
           for (; cl + 3 * G < cc; cl += 4 * G) {
             const C b0 = Bs[cl * nr], b1 = Bs[(cl + G) * nr], b2 = Bs[(cl + 2 * G) * nr], b3 = Bs[(cl + 3 * G) * nr];
@@ -277,12 +347,62 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR>::MINB) k_near_st
     ns_cons_sync();
     for (int q = t; q < nr * rc; q += NS_CONS) {
       const int r = q / rc, rr = q - r * rc;
-      C s = cor[r * NR + rr];
+      C* yp = yt + (tb + r) * nrhs + r0 + rr;
+      C s = csep ? *yp : cor[r * NR + rr];
       for (int gg = 0; gg < G; ++gg) s = cadd(s, red[(gg * nr + r) * NR + rr]);
-      yt[(tb + r) * nrhs + r0 + rr] = s;
+      *yp = s;
     }
     ns_cons_sync();  // red and cor are rewritten by the next leaf
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");  // no copy in flight when the CTA exits
+}
+
+// Correction entries outside the direct blocks as their own CSR product (tree order), run before the stream
+// when the plan chooses it: one warp per row, lanes over the row's entries, NR right-hand sides per pass. The
+// lane sums are reduced by recursive halving (each exchange step keeps half of the right-hand sides on each
+// side of the butterfly), so NR = 16 needs 32 shuffles per row instead of 16 full reductions. The row sums
+// are stored into y; the stream then adds its direct-block sums to them.
+template <typename C, int NR>
+static __global__ void __launch_bounds__(256) k_near_corr(const int64_t* cptr, const int32_t* ccol, const C* cval,
+                                                          const C* xt, C* yt, int64_t N, int nrhs, int r0, int rc) {
+  typedef decltype(xt[0].x) R;
+  const int64_t row = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= N) return;
+  const int64_t e0 = cptr[row], e1 = cptr[row + 1];
+  C a[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) a[q] = mk((R)0, (R)0);
+  for (int64_t e = e0 + lane; e < e1; e += 32) {
+    const C v = cval[e];
+    const C* xp = xt + (int64_t)ccol[e] * nrhs + r0;
+#pragma unroll
+    for (int q = 0; q < NR; ++q)
+      if (q < rc) cfma(a[q], v, xp[q]);
+  }
+  // recursive halving: after the step at lane distance off, a lane keeps the upper or lower half of its
+  // right-hand sides (by its lane bit) and adds the partner's copy of that half
+  int qi = 0;
+  int off = 16;
+#pragma unroll
+  for (int w = NR; w > 1; w >>= 1, off >>= 1) {
+    const int h = w >> 1;
+    const bool hi = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const C send = hi ? a[i] : a[i + h];
+      const C keep = hi ? a[i + h] : a[i];
+      a[i] = mk(keep.x + __shfl_xor_sync(0xffffffffu, send.x, off), keep.y + __shfl_xor_sync(0xffffffffu, send.y, off));
+    }
+    if (hi) qi += h;
+  }
+  for (; off >= 1; off >>= 1) {
+    a[0].x += __shfl_xor_sync(0xffffffffu, a[0].x, off);
+    a[0].y += __shfl_xor_sync(0xffffffffu, a[0].y, off);
+  }
+  // lanes whose remaining (fully reduced) bits are zero hold right-hand side qi
+  constexpr int LOGNR = NR == 1 ? 0 : (NR == 4 ? 2 : 4);
+  if ((lane & ((1 << (5 - LOGNR)) - 1)) == 0 && qi < rc) yt[row * nrhs + r0 + qi] = a[0];
 }
 
 template <typename C, int NR>
@@ -295,11 +415,18 @@ static int near_stream_t(fda_plan_s* P, const C* B, const C* cval, const C* xt, 
     attr = true;
   }
   fda_tree_s* T = P->tree;
+  const int csep = (Ly::DB || P->near_csep == 1) ? 1 : 0;  // the 16-wide pass has no correction buffer
   for (int r0 = 0; r0 < nrhs; r0 += NR) {
     const int rc = std::min(NR, nrhs - r0);
+    if (csep) {
+      k_near_corr<C, NR><<<(unsigned)((T->N + 7) / 8), 256, 0, s>>>(P->corr_ptr.p, P->corr_col.p, cval, xt, yt, T->N,
+                                                                    nrhs, r0, rc);
+      FDA_LAUNCH_CHECK();
+      ++*launches;
+    }
     k_near_stream<C, NR><<<(unsigned)P->near_grid, NS_NT, Ly::total, s>>>(
         P->near_part.p, P->near_tleaf.p, T->pb.p, T->pe.p, P->near_nbase.p, P->near_ncol.p, P->near_xbase.p,
-        P->near_xcol.p, B, P->corr_ptr.p, P->corr_col.p, cval, xt, yt, nrhs, r0, rc, P->tc_err.p);
+        P->near_xcol.p, B, P->corr_ptr.p, P->corr_col.p, cval, xt, yt, nrhs, r0, rc, csep, P->tc_err.p);
     FDA_LAUNCH_CHECK();
     ++*launches;
   }

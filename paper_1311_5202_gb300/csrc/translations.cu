@@ -434,6 +434,7 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
   P->tree = T;
   P->prob = pr;
   P->cfg = *cfg;
+  P->near_csep = cfg->near_split == 1 ? 1 : 0;
   if (P->cfg.nrhs_max < 1) P->cfg.nrhs_max = 1;
   FDA_TRY(upload_geometry_constants());
   const int64_t N = T->N, nbox = T->nbox;
@@ -687,6 +688,9 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
       double s1 = sg[ord[0]];
       int s = 0;
       while (s < L.se && s < L.sc && sg[ord[s]] >= eps * s1) ++s;
+      // an even rank keeps every coefficient vector 16-byte aligned (two complex FP32 values per vector
+      // atomic in the tensor-core epilogue); the extra singular vector only adds accuracy
+      if ((s & 1) && s < L.se && s < L.sc) ++s;
       L.s = s;
       L.sigma.resize(s);
       std::vector<double2> Ph((size_t)L.sc * s), Pch((size_t)L.sc * s), Vh((size_t)L.se * s);
@@ -1085,7 +1089,7 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
       const OffInfo& o = offs[l][pair_off[q]];
       if (o.rank > 0) {
         pm[u] = mid;
-        mid += o.rank;
+        mid += (o.rank + 1) & ~1;  // even stride: every intermediate vector starts 16-byte aligned
       }
       double fl = o.rank > 0 ? 16.0 * o.rank * L.s : 8.0 * L.s * L.s;
       P->flops_m2l += fl;

@@ -39,7 +39,8 @@ class FdaError(RuntimeError):
 
 class fda_config_t(C.Structure):
     _fields_ = [("eps", C.c_double), ("precision", C.c_int), ("lowrank", C.c_int), ("nrhs_max", C.c_int),
-                ("m2l_tensor", C.c_int), ("op", C.c_int), ("reserved", C.c_int * 3)]
+                ("m2l_tensor", C.c_int), ("op", C.c_int), ("near_split", C.c_int),
+                ("reserved", C.c_int * 2)]
 
 
 class bm_gmres_opts_t(C.Structure):
@@ -73,7 +74,8 @@ class fda_tree_view_t(C.Structure):
 class fda_tune_report_t(C.Structure):
     _fields_ = [("entries", C.c_int32), ("level", C.c_int32 * 64), ("stage", C.c_int32 * 64),
                 ("ms_fma", C.c_double * 64), ("ms_tensor", C.c_double * 64), ("chosen", C.c_int32 * 64),
-                ("near_ms", C.c_double * 2), ("near_rhs_per_pass", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("near_ms", C.c_double * 2), ("near_rhs_per_pass", C.c_int32), ("near_split", C.c_int32),
+                ("near_split_ms", C.c_double * 2), ("reserved", C.c_int32 * 2)]
 
 
 class fda_plan_info_t(C.Structure):
@@ -250,7 +252,8 @@ def fda_tree_destroy(tree):
     lib().fda_tree_destroy(tree)
 
 
-def fda_precompute_translations(tree, eps, precision=FDA_PREC_FP64, lowrank=1, nrhs_max=1, m2l_tensor=0, op=0):
+def fda_precompute_translations(tree, eps, precision=FDA_PREC_FP64, lowrank=1, nrhs_max=1, m2l_tensor=0, op=0,
+                                near_split=0):
     cfg = fda_config_t()
     cfg.eps = float(eps)
     cfg.precision = int(precision)
@@ -258,6 +261,7 @@ def fda_precompute_translations(tree, eps, precision=FDA_PREC_FP64, lowrank=1, n
     cfg.nrhs_max = int(nrhs_max)
     cfg.m2l_tensor = int(m2l_tensor)
     cfg.op = int(op)
+    cfg.near_split = int(near_split)
     h = C.c_void_p()
     _check(lib().fda_precompute_translations(tree, C.byref(cfg), C.byref(h)))
     return h
@@ -313,12 +317,14 @@ def fda_matvec_graph_create(plan, precision, x, y, stream=None):
 
 
 def fda_autotune(plan, nrhs=1, stream=None) -> dict:
-    """Pick the faster M2L kernel per (level, stage), and the near-field batch width, for this nrhs."""
+    """Pick the faster M2L kernel per (level, stage), the near-field batch width and the correction split,
+    for this nrhs."""
     R = fda_tune_report_t()
     _check(lib().fda_autotune(plan, int(nrhs), _stream(stream), C.byref(R)))
     rows = [dict(level=R.level[e], stage=R.stage[e], ms_fma=R.ms_fma[e], ms_tensor=R.ms_tensor[e],
                  chosen=("fma", "tensor", "tensor-alt1", "tensor-alt2", "tensor-alt3")[R.chosen[e]]) for e in range(R.entries)]
-    return dict(m2l=rows, near_ms=list(R.near_ms), near_rhs_per_pass=R.near_rhs_per_pass)
+    return dict(m2l=rows, near_ms=list(R.near_ms), near_rhs_per_pass=R.near_rhs_per_pass,
+                near_split=R.near_split, near_split_ms=list(R.near_split_ms))
 
 
 def fda_plan_check(plan):
@@ -522,11 +528,12 @@ class Solver:
     """Problem + tree + plan with ordered destruction."""
 
     def __init__(self, nodes, elems, k, eps=1e-4, leaf_max=64, precision=FDA_PREC_FP64, lowrank=1, nrhs_max=1,
-                 alpha=None, m2l_tensor=0, op=0):
+                 alpha=None, m2l_tensor=0, op=0, near_split=0):
         self.k = float(k)
         self.prob = bm_problem_create(nodes, elems, k, alpha)
         self.tree = fda_build_tree(self.prob, leaf_max)
-        self.plan = fda_precompute_translations(self.tree, eps, precision, lowrank, nrhs_max, m2l_tensor, op)
+        self.plan = fda_precompute_translations(self.tree, eps, precision, lowrank, nrhs_max, m2l_tensor, op,
+                                                near_split)
         self.N = 6 * int(np.asarray(elems).shape[0])
 
     def matvec(self, x, y, stream=None):
