@@ -23,6 +23,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -291,6 +292,10 @@ def main():
     ap.add_argument("--table1-max", type=int, default=3, help="number of Table 1 sizes (4 adds N = 4.7M)")
     ap.add_argument("--table1-eps", type=float, nargs="+", default=[1e-4, 1e-6])
     ap.add_argument("--no-table1-sample", action="store_true", help="skip the Table 1 case in the default run")
+    ap.add_argument("--near-split", type=int, default=0, choices=[0, 1],
+                    help="near-field correction schedule of the plan before the autotuner (with --no-tune: kept)")
+    ap.add_argument("--clocks-dir", default=None,
+                    help="where the nvidia-smi clock samples of the timed region are kept (default: temp dir)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -316,7 +321,7 @@ def main():
     nrhs = args.nrhs
     t0 = time.perf_counter()
     S = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=eps, leaf_max=spec["leaf"], precision=fdbem.FDA_PREC_FP32,
-                     lowrank=1, nrhs_max=nrhs, m2l_tensor=args.m2l_tensor)
+                     lowrank=1, nrhs_max=nrhs, m2l_tensor=args.m2l_tensor, near_split=args.near_split)
     setup_s = time.perf_counter() - t0
     tune_main = None if args.no_tune else fdbem.fda_autotune(S.plan, nrhs)
     info = S.info()
@@ -343,8 +348,7 @@ def main():
             ms = max_over_ranks(ms, pg, dev)
         return ms
 
-    clocks = Clocks(os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                                 f"bench_clocks_r{rank}.csv"))
+    clocks = Clocks(os.path.join(args.clocks_dir or tempfile.gettempdir(), f"bench_clocks_r{rank}.csv"))
     with clocks:
         ms32 = timed(fdbem.FDA_PREC_FP32, args.steps, args.warmup)
         launches = int(S.info()["launches_per_matvec"])
@@ -473,7 +477,7 @@ def main():
     # the near-field matrices stream once per pass of rpp right-hand sides
     rpp = tune_main["near_rhs_per_pass"] if tune_main else (1 if nrhs == 1 else (16 if nrhs >= 12 else 4))
     near_passes = -(-nrhs // rpp)
-    near_split = bool(tune_main and tune_main.get("near_split"))
+    near_split = bool(tune_main["near_split"]) if tune_main else (args.near_split == 1 or rpp == 16)
     near_kernel = f"k_near_stream<float2, {rpp}>" + (" after k_near_corr" if near_split else "")
     near_gbs = bytes_near * near_passes / (ph32["near"] * 1e-3) / 1e9
     dom = max((p for p in ph32 if p not in ("perm", "assemble")), key=lambda p: ph32[p])

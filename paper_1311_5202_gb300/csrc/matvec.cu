@@ -288,6 +288,43 @@ static __global__ void k_l2l(int64_t box0, const int64_t* par, const int32_t* ix
   }
 }
 
+// ------------------------------------------------------------------ L2T (a11), one right-hand side
+// One CTA per leaf; thread (i, g) takes target point i and local coefficients r = g, g + G, ... (G = blockDim /
+// nC), so consecutive threads read consecutive words of T~ and every thread works; the G partial sums of a
+// point are added in shared memory and the total once into y (all wedges of the leaf's level).
+template <typename C>
+static __global__ void k_l2t1(const int64_t* leaves, const int64_t* toff, const int64_t* pb, const int64_t* pe,
+                              const int32_t* lev, const int64_t* slot, const int* ls, const int* lnw, const C* Tm,
+                              const C* cin, C* yt) {
+  extern __shared__ unsigned char smem_raw[];
+  C* part = (C*)smem_raw;     // [blockDim]
+  C* us = part + blockDim.x;  // [s]
+  const int64_t b = leaves[blockIdx.x];
+  const int l = lev[b];
+  const int s = ls[l], nw = lnw[l];
+  const int64_t p0 = pb[b];
+  const int nC = (int)(pe[b] - p0);
+  const int t = threadIdx.x;
+  const int G = (int)blockDim.x / nC;
+  const int i = t % nC, g = t / nC;
+  C acc = mk((decltype(us[0].x))0, (decltype(us[0].x))0);
+  for (int z = 0; z < nw; ++z) {
+    __syncthreads();
+    for (int q = t; q < s; q += blockDim.x) us[q] = cin[slot[b] + (int64_t)z * s + q];
+    __syncthreads();
+    const C* Tz = Tm + toff[blockIdx.x] + (int64_t)z * s * nC;
+    if (g < G)
+      for (int r = g; r < s; r += G) cfma(acc, Tz[(int64_t)r * nC + i], us[r]);
+  }
+  part[t] = acc;
+  __syncthreads();
+  if (t < nC) {
+    C sum = part[t];
+    for (int gg = 1; gg < G; ++gg) sum = cadd(sum, part[gg * nC + t]);
+    yt[p0 + t] = cadd(yt[p0 + t], sum);
+  }
+}
+
 // ------------------------------------------------------------------ L2T (a11): one CTA per leaf
 template <typename C>
 static __global__ void k_l2t(const int64_t* leaves, const int64_t* toff, const int64_t* pb, const int64_t* pe,
@@ -594,9 +631,13 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
       int rc = chunk(maxs);
       for (int r0 = 0; r0 < nrhs; r0 += rc) {
         int rcc = std::min(rc, nrhs - r0);
-        k_l2t<C><<<(unsigned)P->h_leaves.size(), 128, sizeof(C) * maxs * rcc, s>>>(
-            P->leaves.p, P->leaf_t_off.p, T->pb.p, T->pe.p, T->lev.p, P->slot.p, d_ls, d_lnw, op.T.p, cin.p, yt.p,
-            nrhs, P->n_coef, r0, rcc);
+        if (nrhs == 1 && maxleaf <= 128)  // every leaf has at most 128 points: one column group or more
+          k_l2t1<C><<<(unsigned)P->h_leaves.size(), 128, sizeof(C) * (128 + maxs), s>>>(
+              P->leaves.p, P->leaf_t_off.p, T->pb.p, T->pe.p, T->lev.p, P->slot.p, d_ls, d_lnw, op.T.p, cin.p, yt.p);
+        else
+          k_l2t<C><<<(unsigned)P->h_leaves.size(), 128, sizeof(C) * maxs * rcc, s>>>(
+              P->leaves.p, P->leaf_t_off.p, T->pb.p, T->pe.p, T->lev.p, P->slot.p, d_ls, d_lnw, op.T.p, cin.p, yt.p,
+              nrhs, P->n_coef, r0, rcc);
         FDA_LAUNCH_CHECK();
         ++nl;
       }
