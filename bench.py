@@ -292,7 +292,7 @@ def main():
     ap.add_argument("--table1-max", type=int, default=3, help="number of Table 1 sizes (4 adds N = 4.7M)")
     ap.add_argument("--table1-eps", type=float, nargs="+", default=[1e-4, 1e-6])
     ap.add_argument("--no-table1-sample", action="store_true", help="skip the Table 1 case in the default run")
-    ap.add_argument("--near-split", type=int, default=0, choices=[0, 1],
+    ap.add_argument("--near-split", type=int, default=0, choices=[0, 1, 2],
                     help="near-field correction schedule of the plan before the autotuner (with --no-tune: kept)")
     ap.add_argument("--clocks-dir", default=None,
                     help="where the nvidia-smi clock samples of the timed region are kept (default: temp dir)")
@@ -477,8 +477,10 @@ def main():
     # the near-field matrices stream once per pass of rpp right-hand sides
     rpp = tune_main["near_rhs_per_pass"] if tune_main else (1 if nrhs == 1 else (16 if nrhs >= 12 else 4))
     near_passes = -(-nrhs // rpp)
-    near_split = bool(tune_main["near_split"]) if tune_main else (args.near_split == 1 or rpp == 16)
-    near_kernel = f"k_near_stream<float2, {rpp}>" + (" after k_near_corr" if near_split else "")
+    near_sched = tune_main["near_split"] if tune_main else (1 if rpp == 16 else args.near_split)
+    near_split = near_sched >= 1
+    near_kernel = (f"k_near_stream<float2, {rpp}>" + (" after k_near_corr" if near_split else "")
+                   + (" (double-buffered windows)" if near_sched == 2 or rpp == 16 else ""))
     near_gbs = bytes_near * near_passes / (ph32["near"] * 1e-3) / 1e9
     dom = max((p for p in ph32 if p not in ("perm", "assemble")), key=lambda p: ph32[p])
     dom_ms = ph32[dom]

@@ -167,7 +167,9 @@ typedef struct {
                         corrections of G + alpha dG/dn_x) */
   int near_split;    /* near-field schedule until fda_autotune chooses: 0 = the correction entries outside the
                         direct blocks are applied inside the near-field stream, per target leaf; 1 = by their
-                        own CSR kernel (one warp per row) before the stream. Same sums, other order. */
+                        own CSR kernel (one warp per row) before the stream; 2 = as 1, with the stream's
+                        density windows double-buffered for one right-hand side (the next window's densities
+                        copied while the current one is used). Same sums, other order. */
   int reserved[2];
 } fda_config_t;
 
@@ -211,10 +213,11 @@ typedef struct {
                              (alternative shapes: other column width or stage count) */
   double near_ms[2];      /* near field at 4 and 16 right-hand sides per pass (nrhs >= 12; else 0) */
   int32_t near_rhs_per_pass;
-  int32_t near_split;     /* 1: the correction entries outside the direct blocks run as their own CSR kernel
-                             before the near-field stream; 0: inside the stream, per target leaf */
-  double near_split_ms[2];  /* near field (at the chosen width) with the corrections per leaf (0) and split (1) */
-  int32_t reserved[2];
+  int32_t near_split;     /* near-field schedule kept: 0 = the correction entries outside the direct blocks inside
+                             the stream, per target leaf; 1 = by their own CSR kernel before the stream; 2 = as 1,
+                             and the stream's density windows double-buffered (one right-hand side) */
+  double near_split_ms[2];  /* near field (at the chosen width) with schedules 0 and 1 */
+  double near_window_ms;    /* schedule 2 (nrhs = 1; else -1) */
 } fda_tune_report_t;
 int fda_autotune(fda_plan_t* plan, int nrhs, void* stream, fda_tune_report_t* report);
 

@@ -758,19 +758,25 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
   } else {
     R->near_rhs_per_pass = nrhs == 1 ? 1 : 4;
   }
+  R->near_window_ms = -1;
   if (P->n_near_tleaf > 0 && P->near_max_nr <= 256) {
-    double tc[2];
-    for (int cs = 0; cs < 2; ++cs) {
+    // schedules: 0 corrections per leaf; 1 split; 2 split with double-buffered windows (one right-hand side)
+    double tc[3] = {0, 0, -1};
+    const int ncs = nrhs == 1 ? 3 : 2;
+    int best = 0;
+    for (int cs = 0; cs < ncs; ++cs) {
       P->near_csep = cs;
       FDA_TRY(time_ms(s, [&]() { return near_stream<float2>(P, P->op32.near.p, P->op32.corr.p, P->xt32.p, P->yt32.p,
                                                             nrhs, s, &nl); },
                       3, &tc[cs]));
+      if (tc[cs] < tc[best]) best = cs;
     }
     R->near_split_ms[0] = tc[0];
     R->near_split_ms[1] = tc[1];
-    P->near_csep = tc[1] < tc[0] ? 1 : 0;
+    R->near_window_ms = tc[2];
+    P->near_csep = best;
   }
-  R->near_split = P->near_csep == 1 ? 1 : 0;
+  R->near_split = P->near_csep < 0 ? 0 : P->near_csep;
   FDA_TRY(plan_matvec(P, FDA_PREC_FP32, x.p, y.p, nrhs, FDA_CPLX64, s, false));
   FDA_CUDA(cudaStreamSynchronize(s));
   return FDA_OK;

@@ -73,17 +73,21 @@ __device__ __forceinline__ void ns_cp16(void* dst, const void* src, uint32_t src
 __device__ __forceinline__ void ns_cons_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NS_CONS) : "memory"); }
 
 // single right-hand side: three CTAs per SM (3-stage ring, 16 KB density window); batches: fewer, larger CTAs
-// 16 right-hand sides per pass: two density windows of at most 256 columns (32 KB each), the next one copied
-// with cp.async while the current one is used; corrections always by the separate CSR kernel (no buffer)
-template <typename C, int NR>
+// Double-buffered density windows (DB): two windows, the next one copied with cp.async while the current one
+// is used; corrections always by the separate CSR kernel (no correction buffer). 16 right-hand sides per pass
+// always run this way (two windows of at most 256 columns, 32 KB each); one right-hand side does when W is set
+// (two windows of 8 KB: 1024 FP32 or 512 FP64 columns, several per thread).
+template <typename C, int NR, bool W = false>
 struct NsLayout {
   static constexpr int E = sizeof(C);
-  static constexpr bool DB = NR == 16;
+  static constexpr bool DB = NR == 16 || W;
   static constexpr int STAGES = NR == 1 ? 3 : 4;
   static constexpr int MINB = NR == 1 ? 3 : (NR <= 4 ? 2 : 1);
-  static constexpr int XBYTES = DB ? 32768 : ((NR == 1 || E * NR >= 64) ? 16384 : 32768);
+  static constexpr int XBYTES = NR == 16 ? 32768 : (W ? 8192 : ((NR == 1 || E * NR >= 64) ? 16384 : 32768));
   static constexpr int XW0 = (XBYTES / (NR * E)) & ~1;
-  static constexpr int XW = DB && XW0 > NS_CONS ? NS_CONS : XW0;  // columns per density window (even)
+  static constexpr int XW = NR == 16 && XW0 > NS_CONS ? NS_CONS : XW0;  // columns per density window (even)
+  static constexpr int CPT = DB && XW > NS_CONS ? XW / NS_CONS : 1;     // window columns per consumer thread
+  static_assert(!DB || XW <= NS_CONS || XW % NS_CONS == 0, "double-buffered window: whole columns per thread");
   static constexpr size_t ring = (size_t)STAGES * NS_STAGE_BYTES;
   static constexpr size_t xs = ring;
   static constexpr size_t red = xs + (size_t)(DB ? 2 : 1) * XW * NR * E;
@@ -96,12 +100,12 @@ struct NsLayout {
 // columns per chunk: whole columns, an even count, at most one stage
 __device__ __forceinline__ int ns_cpc(int nr, int E) { return max(2, (NS_STAGE_BYTES / (nr * E)) & ~1); }
 
-template <typename C, int NR>
-static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR>::MINB) k_near_stream(
+template <typename C, int NR, bool W>
+static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR, W>::MINB) k_near_stream(
     const int32_t* part, const int64_t* tleaf, const int64_t* pb, const int64_t* pe, const int64_t* nbase,
     const int32_t* ncolv, const int64_t* xbase, const int32_t* xcol, const C* B, const int64_t* cptr,
     const int32_t* ccol, const C* cval, const C* xt, C* yt, int nrhs, int r0, int rc, int csep, int* err) {
-  typedef NsLayout<C, NR> Ly;
+  typedef NsLayout<C, NR, W> Ly;
   typedef decltype(xt[0].x) R;
   constexpr int E = Ly::E, XW = Ly::XW, NS_STAGES = Ly::STAGES;
   extern __shared__ unsigned char smem_raw[];
@@ -162,12 +166,17 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR>::MINB) k_near_st
   const int lane = t & 31;
   int it = 0;
   bool failed = false;
-  // double-buffered windows (16 right-hand sides): window A is the next one to copy; colA is this thread's
-  // column of it (one column per thread), loaded one window ahead so that its latency hides behind compute
+  // double-buffered windows: window A is the next one to copy; colA[] are this thread's columns of it (column
+  // t + j * 256), loaded one window ahead so that their latency hides behind the current window's work
+  constexpr int CPT = Ly::CPT;
   int ua = u0, wa = 0, buf = 0;
-  auto col_of = [&](int uu, int ww) -> int {
-    const int c = ww + t;
-    return (uu < u1 && t < XW && c < ncolv[uu]) ? xcol[xbase[uu] + c] : -1;
+  int colA[CPT];
+  auto load_cols = [&]() {
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+      const int k = t + j * NS_CONS, c = wa + k;
+      colA[j] = (ua < u1 && k < XW && c < ncolv[ua]) ? xcol[xbase[ua] + c] : -1;
+    }
   };
   // next window in the consumers' order (leaves without columns have no window)
   auto normalize = [&]() {
@@ -180,12 +189,15 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR>::MINB) k_near_st
     wa += XW;
     normalize();
   };
-  auto copy_window = [&](int col, int b) {
-    if (col >= 0) {
-      C* dst = xs + ((size_t)b * XW + t) * NR;
+  auto copy_window = [&](int b) {
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+      const int col = colA[j];
+      if (col < 0) continue;
+      C* dst = xs + ((size_t)b * XW + t + j * NS_CONS) * NR;
       const C* src = xt + (int64_t)col * nrhs + r0;
-      if (E == 16 || (nrhs & 1) == 0) {  // 16-byte aligned runs of 16 / E right-hand sides
-        constexpr int V = 16 / E;
+      if (E == 16 || (NR > 1 && (nrhs & 1) == 0)) {  // 16-byte aligned runs of 16 / E right-hand sides
+        constexpr int V = E == 16 ? 1 : 2;
 #pragma unroll
         for (int q = 0; q < NR; q += V) {
           const int nb = min(16, max(0, (rc - q) * E));
@@ -198,12 +210,12 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR>::MINB) k_near_st
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
-  int colA = -1;
   if constexpr (Ly::DB) {
     normalize();
-    copy_window(col_of(ua, wa), 0);  // window 0
+    load_cols();
+    copy_window(0);  // window 0
     advance();
-    colA = col_of(ua, wa);
+    load_cols();
   }
   for (int u = u0; u < u1; ++u) {
     const int64_t L = tleaf[u];
@@ -295,9 +307,9 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR>::MINB) k_near_st
         // this window's copies have landed (own, then everyone's); the other buffer's readers are done
         asm volatile("cp.async.wait_all;" ::: "memory");
         ns_cons_sync();
-        copy_window(colA, buf ^ 1);
+        copy_window(buf ^ 1);
         advance();
-        colA = col_of(ua, wa);
+        load_cols();
         xcur = xs + (size_t)buf * XW * NR;
         buf ^= 1;
       } else {
@@ -405,17 +417,18 @@ static __global__ void __launch_bounds__(256) k_near_corr(const int64_t* cptr, c
   if ((lane & ((1 << (5 - LOGNR)) - 1)) == 0 && qi < rc) yt[row * nrhs + r0 + qi] = a[0];
 }
 
-template <typename C, int NR>
+template <typename C, int NR, bool W>
 static int near_stream_t(fda_plan_s* P, const C* B, const C* cval, const C* xt, C* yt, int nrhs, cudaStream_t s,
                          int64_t* launches) {
-  typedef NsLayout<C, NR> Ly;
+  typedef NsLayout<C, NR, W> Ly;
   static bool attr = false;
   if (!attr) {
-    FDA_CUDA(cudaFuncSetAttribute(k_near_stream<C, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Ly::total));
+    FDA_CUDA(cudaFuncSetAttribute(k_near_stream<C, NR, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)Ly::total));
     attr = true;
   }
   fda_tree_s* T = P->tree;
-  const int csep = (Ly::DB || P->near_csep == 1) ? 1 : 0;  // the 16-wide pass has no correction buffer
+  const int csep = (Ly::DB || P->near_csep >= 1) ? 1 : 0;  // double-buffered passes have no correction buffer
   for (int r0 = 0; r0 < nrhs; r0 += NR) {
     const int rc = std::min(NR, nrhs - r0);
     if (csep) {
@@ -424,7 +437,7 @@ static int near_stream_t(fda_plan_s* P, const C* B, const C* cval, const C* xt, 
       FDA_LAUNCH_CHECK();
       ++*launches;
     }
-    k_near_stream<C, NR><<<(unsigned)P->near_grid, NS_NT, Ly::total, s>>>(
+    k_near_stream<C, NR, W><<<(unsigned)P->near_grid, NS_NT, Ly::total, s>>>(
         P->near_part.p, P->near_tleaf.p, T->pb.p, T->pe.p, P->near_nbase.p, P->near_ncol.p, P->near_xbase.p,
         P->near_xcol.p, B, P->corr_ptr.p, P->corr_col.p, cval, xt, yt, nrhs, r0, rc, csep, P->tc_err.p);
     FDA_LAUNCH_CHECK();
@@ -441,9 +454,11 @@ int near_stream(fda_plan_s* P, const C* B, const C* cval, const C* xt, C* yt, in
     return FDA_E_INVALID_ARG;
   }
   // right-hand sides per pass over the matrix: 1, 4, or 16 for wide batches (each pass streams it once)
-  if (nrhs == 1) return near_stream_t<C, 1>(P, B, cval, xt, yt, nrhs, s, launches);
-  if (nrhs < 12 || P->near_wide == 0) return near_stream_t<C, 4>(P, B, cval, xt, yt, nrhs, s, launches);
-  return near_stream_t<C, 16>(P, B, cval, xt, yt, nrhs, s, launches);
+  if (nrhs == 1)
+    return P->near_csep == 2 ? near_stream_t<C, 1, true>(P, B, cval, xt, yt, nrhs, s, launches)
+                             : near_stream_t<C, 1, false>(P, B, cval, xt, yt, nrhs, s, launches);
+  if (nrhs < 12 || P->near_wide == 0) return near_stream_t<C, 4, false>(P, B, cval, xt, yt, nrhs, s, launches);
+  return near_stream_t<C, 16, false>(P, B, cval, xt, yt, nrhs, s, launches);
 }
 
 template int near_stream<float2>(fda_plan_s*, const float2*, const float2*, const float2*, float2*, int,

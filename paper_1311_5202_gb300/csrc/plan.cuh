@@ -106,7 +106,7 @@ struct fda_plan_s {
   int mm_mt[FDA_MAXLEV] = {0}, ll_mt[FDA_MAXLEV] = {0};
   int fma_tm[FDA_MAXLEV][2] = {{0}};  // row tile of the FMA M2L units (16, 32 or 64)
   int m2l_choice[FDA_MAXLEV][2];      // autotuned M2L kernel per (level, stage), -1: from the plan options
-  int near_csep = -1;                 // autotuned: off-block corrections as their own CSR kernel (1) or per leaf
+  int near_csep = -1;                 // near-field schedule: 0 per-leaf corrections, 1 split, 2 split + DB windows
   int near_wide = -1;                 // autotuned right-hand sides per near-field pass for wide batches
   fda::DBuf<int64_t> pair_src, pair_tgt;  // coefficient indices (slot + wedge * s)
   fda::DBuf<int64_t> pair_mid;            // low-rank intermediate index per pair (-1 if dense)

@@ -75,7 +75,7 @@ class fda_tune_report_t(C.Structure):
     _fields_ = [("entries", C.c_int32), ("level", C.c_int32 * 64), ("stage", C.c_int32 * 64),
                 ("ms_fma", C.c_double * 64), ("ms_tensor", C.c_double * 64), ("chosen", C.c_int32 * 64),
                 ("near_ms", C.c_double * 2), ("near_rhs_per_pass", C.c_int32), ("near_split", C.c_int32),
-                ("near_split_ms", C.c_double * 2), ("reserved", C.c_int32 * 2)]
+                ("near_split_ms", C.c_double * 2), ("near_window_ms", C.c_double)]
 
 
 class fda_plan_info_t(C.Structure):
@@ -324,7 +324,7 @@ def fda_autotune(plan, nrhs=1, stream=None) -> dict:
     rows = [dict(level=R.level[e], stage=R.stage[e], ms_fma=R.ms_fma[e], ms_tensor=R.ms_tensor[e],
                  chosen=("fma", "tensor", "tensor-alt1", "tensor-alt2", "tensor-alt3")[R.chosen[e]]) for e in range(R.entries)]
     return dict(m2l=rows, near_ms=list(R.near_ms), near_rhs_per_pass=R.near_rhs_per_pass,
-                near_split=R.near_split, near_split_ms=list(R.near_split_ms))
+                near_split=R.near_split, near_split_ms=list(R.near_split_ms), near_window_ms=R.near_window_ms)
 
 
 def fda_plan_check(plan):

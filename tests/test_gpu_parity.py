@@ -152,14 +152,16 @@ def test_matvec_batched_rhs_equals_single(c1):
         assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-6
 
 
-def test_near_correction_split_schedule(c1):
+@pytest.mark.parametrize("split", [1, 2])
+def test_near_correction_split_schedule(c1, split):
     """The off-block correction entries of Eq. kcorrection as their own CSR kernel before the near-field stream
-    (near_split = 1): the FP64 product on all rows against the oracle (1e-4), and against the per-leaf schedule
-    of the same plan (same sums in another order: 1e-12 in FP64, 1e-5 in FP32), for 1 and 16 right-hand sides
-    (the 16-wide pass reduces lane sums by recursive halving)."""
+    (near_split = 1), and with the stream's density windows double-buffered (near_split = 2): the FP64 product on
+    all rows against the oracle (1e-4), and against the per-leaf schedule of the same plan (same sums in another
+    order: 1e-12 in FP64, 1e-5 in FP32); for split = 1 also 16 right-hand sides (the 16-wide pass reduces lane
+    sums by recursive halving and always double-buffers its windows)."""
     mesh, S0 = c1
     S1 = fdbem.Solver(mesh.nodes, mesh.elems, 10.0, eps=1e-6, leaf_max=64, precision=fdbem.FDA_PREC_FP32,
-                      nrhs_max=16, near_split=1)
+                      nrhs_max=16, near_split=split)
     try:
         x = inputs.complex_gaussian(S1.N, 77)
         xd = torch.from_numpy(x).to(DEV)
@@ -171,20 +173,28 @@ def test_near_correction_split_schedule(c1):
         yo = _oracle_rows(mesh, 10.0, x, np.arange(S1.N))
         assert np.linalg.norm(a - yo) / np.linalg.norm(yo) < 1e-4
         assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-12
-        X = inputs.complex_gaussian(S1.N, 78, nrhs=16)
-        Xd = torch.from_numpy(X.astype(np.complex64)).to(DEV).contiguous()
-        Y1 = torch.empty_like(Xd)
-        S1.matvec(Xd, Y1)
+        x32 = torch.from_numpy(x.astype(np.complex64)).to(DEV)
+        z1, z0 = torch.empty_like(x32), torch.empty_like(x32)
+        S1.matvec(x32, z1)
+        S0.matvec(x32, z0)
         torch.cuda.synchronize()
-        rows = inputs.sample_rows(S1.N, 64, 79)
-        for r in (0, 7, 15):
-            y0r = torch.empty_like(Xd[r])
-            S0.matvec(Xd[r].contiguous(), y0r)
+        g, h = z1.cpu().numpy(), z0.cpu().numpy()
+        assert np.linalg.norm(g - h) / np.linalg.norm(h) < 1e-5
+        if split == 1:
+            X = inputs.complex_gaussian(S1.N, 78, nrhs=16)
+            Xd = torch.from_numpy(X.astype(np.complex64)).to(DEV).contiguous()
+            Y1 = torch.empty_like(Xd)
+            S1.matvec(Xd, Y1)
             torch.cuda.synchronize()
-            g, h = Y1[r].cpu().numpy(), y0r.cpu().numpy()
-            assert np.linalg.norm(g - h) / np.linalg.norm(h) < 1e-5, r
-            yo = _oracle_rows(mesh, 10.0, X[r].astype(np.complex128), rows)
-            assert np.linalg.norm(g[rows] - yo) / np.linalg.norm(yo) < 3e-4, r
+            rows = inputs.sample_rows(S1.N, 64, 79)
+            for r in (0, 7, 15):
+                y0r = torch.empty_like(Xd[r])
+                S0.matvec(Xd[r].contiguous(), y0r)
+                torch.cuda.synchronize()
+                g, h = Y1[r].cpu().numpy(), y0r.cpu().numpy()
+                assert np.linalg.norm(g - h) / np.linalg.norm(h) < 1e-5, r
+                yo = _oracle_rows(mesh, 10.0, X[r].astype(np.complex128), rows)
+                assert np.linalg.norm(g[rows] - yo) / np.linalg.norm(yo) < 3e-4, r
         assert fdbem.fda_plan_check(S1.plan) == fdbem.FDA_OK
     finally:
         S1.close()
