@@ -69,3 +69,33 @@ def test_invalid_arguments_fail_cleanly_without_gpu(built):
     cfg.eps = 2.0
     rc = fdbem.lib().fda_precompute_translations(None, C.byref(cfg), C.byref(h))
     assert rc == fdbem.FDA_E_INVALID_ARG
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    """Every struct the header declares has the same size and field offsets in the ctypes binding (gcc compiles
+    a probe against include/fdbem.h; no GPU)."""
+    import ctypes as C
+
+    from paper_1311_5202_gb300 import fdbem
+    structs = [fdbem.fda_config_t, fdbem.bm_gmres_opts_t, fdbem.bm_gmres_stats_t, fdbem.fda_tree_view_t,
+               fdbem.fda_tune_report_t, fdbem.fda_plan_info_t]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "fdbem.h"', "int main(void) {"]
+    for S in structs:
+        n = S.__name__
+        lines.append(f'  printf("{n} size %zu\\n", sizeof({n}));')
+        for f, _ in S._fields_:
+            lines.append(f'  printf("{n} {f} %zu\\n", offsetof({n}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "probe.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        n, f, v = line.split()
+        got[(n, f)] = int(v)
+    for S in structs:
+        n = S.__name__
+        assert got[(n, "size")] == C.sizeof(S), n
+        for f, _ in S._fields_:
+            assert got[(n, f)] == getattr(S, f).offset, (n, f)
