@@ -128,6 +128,14 @@ def cpu_baseline(mesh, k, x, rows_n, seed=7):
                       f"{dt:.2f} s wall, extrapolated x N/rows"}
 
 
+def workload_config(args, spec, mesh, ws):
+    """The `config` object of both arms: the workload by name and size."""
+    k = spec["k"]
+    return {"workload": args.workload, "N": mesh.n_dof, "k": k, "kD": k * float(np.ptp(mesh.nodes, axis=0).max()),
+            "eps": args.eps or spec["eps"], "leaf_max": spec["leaf"], "nrhs": args.nrhs,
+            "parallelism": f"replicas{ws}", "l2": "operators and vectors (GBs) larger than L2; no flush"}
+
+
 def run_reference(args):
     """Reference arm: the oracle as it stands, on this machine's host cores, same workload, metric and unit."""
     ws, rank, _ = dist_setup()
@@ -152,7 +160,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "matvec/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_matvec * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": {"workload": args.workload, "N": mesh.n_dof, "k": k, "nrhs": 1},
+            "config": workload_config(args, spec, mesh, ws),
             "cpu_baseline": {"value": value, "unit": "matvec/s", "cores": O.num_threads(), "kind": "oracle",
                              "sample": f"{rows_per_step} sampled rows per step of the dense FP64 oracle matvec, "
                                        f"extrapolated x N/rows"},
@@ -515,9 +523,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "matvec/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-        "config": {"workload": args.workload, "N": N, "k": k, "kD": k * float(np.ptp(mesh.nodes, axis=0).max()),
-                   "eps": eps, "leaf_max": spec["leaf"], "nrhs": nrhs, "parallelism": f"replicas{ws}",
-                   "l2": "operators and vectors (GBs) larger than L2; no flush"},
+        "config": workload_config(args, spec, mesh, ws),
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": job_throughput(ws, nrhs, e2e_ms), "unit": "matvec/s",
