@@ -184,7 +184,9 @@ typedef struct {
  *  - the local regions D_i, the locally corrected weights (Eq. local correction; singular and
  *    hypersingular self-element moments in FP64), the direct near-field blocks and the
  *    correction matrix of Eq. kcorrection.
- * Synchronous (returns when the plan is complete). The tree and problem must outlive the plan. */
+ * Synchronous (returns when the plan is complete). The tree and problem must outlive the plan.
+ * Errors: FDA_E_INVALID_ARG (NULL cfg or out; a configuration field out of range, checked before the tree;
+ * NULL tree), FDA_E_OOM, FDA_E_CUDA. On error *out is NULL. */
 int fda_precompute_translations(fda_tree_t* tree, const fda_config_t* cfg, fda_plan_t** out);
 
 /* y = A x with A = (1/2) I + Dbar + alpha Hbar (Eq. bm, q = 0; Eq. kcorrection), evaluated

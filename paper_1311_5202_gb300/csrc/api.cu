@@ -219,12 +219,14 @@ void fda_tree_destroy(fda_tree_t* T) { delete T; }
 int fda_precompute_translations(fda_tree_t* tree, const fda_config_t* cfg, fda_plan_t** out) {
   ARG_CHECK(out, "out is NULL");
   *out = nullptr;
-  ARG_CHECK(tree && cfg, "NULL argument");
+  ARG_CHECK(cfg, "cfg is NULL");
   ARG_CHECK(cfg->eps > 0 && cfg->eps < 1, "eps must lie in (0, 1)");
   ARG_CHECK(cfg->precision == FDA_PREC_FP64 || cfg->precision == FDA_PREC_FP32, "unknown precision");
   ARG_CHECK(cfg->nrhs_max >= 1 && cfg->nrhs_max <= 4096, "nrhs_max must lie in [1, 4096]");
   ARG_CHECK(cfg->m2l_tensor >= 0 && cfg->m2l_tensor <= 2, "m2l_tensor must be 0, 1 or 2");
   ARG_CHECK(cfg->op == 0 || cfg->op == 1, "op must be 0 or 1");
+  ARG_CHECK(cfg->near_split >= 0 && cfg->near_split <= 2, "near_split must be 0, 1 or 2");
+  ARG_CHECK(tree, "tree is NULL");
   fda_plan_s* P = new (std::nothrow) fda_plan_s();
   if (!P) {
     set_error("host allocation failed");

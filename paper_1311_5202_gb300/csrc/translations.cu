@@ -434,7 +434,7 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
   P->tree = T;
   P->prob = pr;
   P->cfg = *cfg;
-  P->near_csep = (cfg->near_split >= 0 && cfg->near_split <= 2) ? cfg->near_split : 0;
+  P->near_csep = cfg->near_split;  // 0, 1 or 2 (checked at the entry point)
   if (P->cfg.nrhs_max < 1) P->cfg.nrhs_max = 1;
   FDA_TRY(upload_geometry_constants());
   const int64_t N = T->N, nbox = T->nbox;

@@ -68,7 +68,18 @@ def test_invalid_arguments_fail_cleanly_without_gpu(built):
     cfg = fdbem.fda_config_t()
     cfg.eps = 2.0
     rc = fdbem.lib().fda_precompute_translations(None, C.byref(cfg), C.byref(h))
-    assert rc == fdbem.FDA_E_INVALID_ARG
+    assert rc == fdbem.FDA_E_INVALID_ARG and "eps" in fdbem.fda_last_error()
+    # configuration fields are checked before the tree
+    cfg.eps, cfg.precision, cfg.nrhs_max = 1e-4, fdbem.FDA_PREC_FP32, 1
+    for field, bad, word in (("m2l_tensor", 3, "m2l_tensor"), ("op", 2, "op"), ("near_split", 3, "near_split"),
+                             ("nrhs_max", 0, "nrhs_max")):
+        good = getattr(cfg, field)
+        setattr(cfg, field, bad)
+        rc = fdbem.lib().fda_precompute_translations(None, C.byref(cfg), C.byref(h))
+        assert rc == fdbem.FDA_E_INVALID_ARG and word in fdbem.fda_last_error(), field
+        setattr(cfg, field, good)
+    rc = fdbem.lib().fda_precompute_translations(None, C.byref(cfg), C.byref(h))
+    assert rc == fdbem.FDA_E_INVALID_ARG and "tree" in fdbem.fda_last_error()
 
 
 def test_struct_layouts_match_the_binding(tmp_path):
