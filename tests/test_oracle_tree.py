@@ -119,11 +119,37 @@ def test_lists_match_paper_definitions(case):
     assert got_m == {(c, b) for (b, c) in got_m}
 
 
+def _coverage_by_leaf_tiling(T, N):
+    """Every point of a leaf L meets the same (target, source) pairs: those whose target is L or an ancestor of
+    L. So every pair (i, j) is covered exactly once iff, for every leaf, the source point ranges of those pairs
+    tile [0, N) with no gap and no overlap."""
+    pairs = {}
+    for P, Q in T["direct"]:
+        pairs.setdefault(int(P), []).append(int(Q))
+    for b, c in zip(T["m2l_tgt"], T["m2l_src"]):
+        pairs.setdefault(int(b), []).append(int(c))
+    for L in np.nonzero(T["leaf"])[0]:
+        if T["pend"][L] <= T["pbeg"][L]:
+            continue
+        ranges = []
+        A = int(L)
+        while A >= 0:
+            ranges += [(int(T["pbeg"][Q]), int(T["pend"][Q])) for Q in pairs.get(A, [])]
+            A = int(T["parent"][A])
+        ranges.sort()
+        pos = 0
+        for a, b in ranges:
+            assert a == pos, (int(L), a, pos)  # a gap (a > pos) or an overlap (a < pos)
+            pos = b
+        assert pos == N, (int(L), pos)
+
+
 def test_every_point_pair_covered_once(case):
     x, leaf, k, T = case
     N = x.shape[0]
+    _coverage_by_leaf_tiling(T, N)
     if N > 4000:
-        pytest.skip("coverage matrix sized for small cases")
+        return  # the dense cross-check below is sized for small cases
     cov = np.zeros((N, N), dtype=np.int16)
     for P, Q in T["direct"]:
         cov[T["pbeg"][P]:T["pend"][P], T["pbeg"][Q]:T["pend"][Q]] += 1
