@@ -4,14 +4,22 @@
 // columns: the points of its direct source boxes), 4-entry aligned in HBM. A persistent grid of CTAs
 // (three per SM) owns balanced, contiguous ranges of target leaves. In each CTA one producer thread walks
 // the leaves' matrices chunk by chunk (whole columns, <= 16 KB) and issues cp.async.bulk copies into a
-// ring of shared-memory stages (three, or four for batches), each guarded by a "full" mbarrier (transaction bytes) and an
-// "empty" mbarrier (one arrival per consumer warp). Eight consumer warps gather the leaf's source
-// densities into shared memory once per column window (one index per column, a single parallel pass),
-// then read each landed stage: thread (i, g) takes row i and columns g, g + G, ... (G = 256 / rows), so
-// consecutive threads read consecutive shared-memory words. Group partial sums are reduced per row; the
-// correction entries that fall outside the leaf's direct blocks (a CSR per row, one contiguous range per
-// leaf) are spread over all consumer threads and summed per row in shared memory. Every wait is bounded: a wait that gives up sets the error flag, the kernel runs to its end
-// without touching other memory, and the producer still waits (bounded) for its own copies in flight.
+// ring of shared-memory stages (three, or four for batches), each guarded by a "full" mbarrier (transaction
+// bytes) and an "empty" mbarrier (one arrival per consumer warp). Eight consumer warps bring the leaf's source
+// densities into shared memory per column window (one index per column), then read each landed stage: thread
+// (i, g) takes row i and columns g, g + G, ... (G = 256 / rows), so consecutive threads read consecutive
+// shared-memory words. Group partial sums are reduced per row.
+//
+// The correction entries that fall outside the leaf's direct blocks (a CSR per row, one contiguous range per
+// leaf) are applied in one of three schedules, chosen per plan by timing:
+//  0: inside the stream: spread over all consumer threads, summed per row by a segmented warp scan;
+//  1: by k_near_corr before the stream (one warp per row); the stream adds its sums to y;
+//  2: as 1, with the density windows double-buffered: the next window's densities are copied with cp.async
+//     while the current one is used, and its column indices are loaded a window ahead.
+// 16 right-hand sides per pass always run as 2.
+//
+// Every wait is bounded: a wait that gives up sets the error flag, the kernel runs to its end without
+// touching other memory, and the producer still waits (bounded) for its own copies in flight.
 #include "plan.cuh"
 
 namespace fda {
