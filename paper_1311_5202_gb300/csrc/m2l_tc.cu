@@ -464,7 +464,8 @@ struct Tc3Smem {
 
 // One CTA per unit (operator, up to 128 pairs); all its output rows (up to MTC tiles) in TMEM. Per K chunk,
 // thread 0 copies the operator tiles with cp.async.bulk while all threads gather the pairs' coefficients
-// with 8-byte cp.async; NST chunks in flight.
+// with 16-byte cp.async (two complex values; 8-byte copies for a source off a 16-byte boundary); NST chunks
+// in flight.
 template <int MTC, int N, int NST>
 static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units, const float* img,
                                                           const int64_t* psrc, const int64_t* ptgt,
