@@ -361,8 +361,9 @@ int m2l_tc_launch(const GemmUnit* units, size_t nunits, const float2* poolK, con
 // (8-row groups of 1 KB), rounded to TF32, with only the 8-row groups that hold rows stored. A unit is
 // one operator with up to 128 pairs and covers all its output rows (up to MTC tiles, accumulators in
 // TMEM). Per K chunk, one thread copies the operator tiles with cp.async.bulk (completion on an
-// mbarrier with transaction bytes) while all threads gather the pairs' source coefficients with 8-byte
-// cp.async (zero fill past K); NST chunks are in flight. The MMA issuer commits each chunk to a
+// mbarrier with transaction bytes) while all threads gather the pairs' source coefficients with 16-byte
+// cp.async, two complex values per copy (zero fill past K; every coefficient vector starts 16-byte aligned
+// because ranks are even and intermediates padded to even length); NST chunks are in flight. The MMA issuer commits each chunk to a
 // per-stage mbarrier that frees its buffers. Epilogue: warp w reads TMEM lane quadrant w % 4 and half of
 // the columns; lanes hold consecutive real rows, and after a lane-pair exchange every lane owns one complex
 // value, so a warp updates 16 consecutive complex coefficients of each of two columns per instruction
