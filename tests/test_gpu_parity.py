@@ -200,6 +200,32 @@ def test_near_correction_split_schedule(c1, split):
         S1.close()
 
 
+@pytest.mark.parametrize("nrhs", [13, 17])
+def test_ragged_wide_batches_equal_single_products(c1, nrhs):
+    """Ragged passes of the 16-wide near field: 13 right-hand sides (one pass with 3 zero-filled lanes) and 17
+    (a full pass, then a pass of one), odd counts that take the 8-byte density copies. Every right-hand side
+    equals its own single product to FP32 rounding (1e-5; the two use different near-field kernels and
+    summation orders)."""
+    mesh, S0 = c1
+    S = fdbem.Solver(mesh.nodes, mesh.elems, 10.0, eps=1e-6, leaf_max=64, precision=fdbem.FDA_PREC_FP32,
+                     nrhs_max=nrhs)
+    try:
+        X = inputs.complex_gaussian(S.N, 300 + nrhs, nrhs=nrhs).astype(np.complex64)
+        Xd = torch.from_numpy(X).to(DEV).contiguous()
+        Yd = torch.empty_like(Xd)
+        S.matvec(Xd, Yd)
+        torch.cuda.synchronize()
+        for r in sorted({0, 11, 12, nrhs - 1}):
+            y1 = torch.empty_like(Xd[r])
+            S0.matvec(Xd[r].contiguous(), y1)
+            torch.cuda.synchronize()
+            a, b = Yd[r].cpu().numpy(), y1.cpu().numpy()
+            assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-5, r
+        assert fdbem.fda_plan_check(S.plan) == fdbem.FDA_OK
+    finally:
+        S.close()
+
+
 # ------------------------------------------------------------------ a13 solve
 def test_gmres_solve_matches_oracle_and_mie(c1):
     mesh, S = c1
