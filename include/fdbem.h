@@ -87,17 +87,21 @@ int bm_problem_geometry(const bm_problem_t* prob, double* x_dev, double* n_dev, 
 
 /* Right-hand side of the rigid-scatter problem for plane waves u_inc = exp(i k d.x):
  * b = u_inc + alpha du_inc/dn_x (Eq. bm with q = 0; Sec. 5.3). dirs: host, nrhs x 3 (normalised
- * inside). b_dev: DEVICE, N x nrhs complex128, column-major. */
+ * inside). b_dev: DEVICE, N x nrhs complex128, column-major. The problem's device must be the current
+ * device (FDA_E_INVALID_ARG otherwise). Waits for its stream before it returns. */
 int bm_rhs_plane_wave(const bm_problem_t* prob, const double* dirs, int nrhs, void* b_dev, void* stream);
 
-/* The same right-hand side without any device allocation (the paper has no counterpart: this serves
- * callers that cannot call cudaMalloc at the point they need a right-hand side, e.g. code running inside
- * an allocator or memory-pool callback, or codes that forbid allocation after start-up). The directions
- * go through a fixed file-scope device array of FDA_RHS_NOALLOC_MAX = 1024 directions (24 KiB, held by
- * every GPU that loads the library until the process exits); nrhs > 1024 fails with FDA_E_INVALID_ARG.
- * The first call on a device looks up that array's address for the device: make it before any stream
- * capture. Every call shares the array and overwrites the entries it uses; calls that overlap on the GPU
- * (different streams without ordering) race on it. Synchronous. */
+/* The same right-hand side without any device allocation (the paper has no counterpart). It serves
+ * callers that may issue CUDA calls but must not allocate device memory at the point they need a
+ * right-hand side: codes that forbid allocation after start-up (every byte reserved up front), or code
+ * that has handed the rest of the device to another allocator. The directions go through a fixed
+ * file-scope device array of FDA_RHS_NOALLOC_MAX = 1024 directions (24 KiB, held by every GPU that loads
+ * the library until the process exits); nrhs > 1024 fails with FDA_E_INVALID_ARG and writes nothing.
+ * Set-up: the first call in a CUDA context of a device looks up that array's address there (a context
+ * created later, e.g. after cudaDeviceReset, gets its own look-up); make that first call before any
+ * stream capture begins. Every call shares the array and overwrites the entries it uses; calls that
+ * overlap on the GPU (different streams without ordering) race on it. The problem's device must be the
+ * current device (FDA_E_INVALID_ARG otherwise). The call waits for its stream before it returns. */
 int bm_rhs_plane_wave_noalloc(const bm_problem_t* prob, const double* dirs, int nrhs, void* b_dev, void* stream);
 
 void bm_problem_destroy(bm_problem_t* prob);

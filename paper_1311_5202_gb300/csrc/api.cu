@@ -62,7 +62,9 @@ int bm_problem_create(const double* nodes, int64_t n_nodes, const int32_t* elems
   P->nn = n_nodes;
   P->k = k;
   P->alpha = make_double2(alpha_re, alpha_im);
-  int rc = P->nodes.upload(nodes, 3 * n_nodes);
+  int rc = cudaGetDevice(&P->device) == cudaSuccess ? FDA_OK : FDA_E_CUDA;
+  if (rc != FDA_OK) set_error("cudaGetDevice failed");
+  if (rc == FDA_OK) rc = P->nodes.upload(nodes, 3 * n_nodes);
   if (rc == FDA_OK) rc = P->elems.upload(elems6, 6 * n_elems);
   if (rc == FDA_OK) {
     DBuf<int> bad;
@@ -109,7 +111,9 @@ int bm_particles_create(const double* x, const double* n, int64_t N, double k, d
   P->k = k;
   P->alpha = make_double2(alpha_re, alpha_im);
   std::vector<double> w((size_t)N, 1.0);
-  int rc = P->x.upload(x, 3 * N);
+  int rc = cudaGetDevice(&P->device) == cudaSuccess ? FDA_OK : FDA_E_CUDA;
+  if (rc != FDA_OK) set_error("cudaGetDevice failed");
+  if (rc == FDA_OK) rc = P->x.upload(x, 3 * N);
   if (rc == FDA_OK) rc = P->n.upload(n, 3 * N);
   if (rc == FDA_OK) rc = P->w.upload(w);
   if (rc != FDA_OK) {
@@ -149,6 +153,7 @@ static __global__ void k_plane_wave(const double* x, const double* n, int64_t N,
 int bm_rhs_plane_wave(const bm_problem_t* prob, const double* dirs, int nrhs, void* b_dev, void* stream) {
   ARG_CHECK(prob && dirs && b_dev, "NULL argument");
   ARG_CHECK(nrhs >= 1, "nrhs must be >= 1");
+  FDA_TRY(problem_device_current(prob));
   std::vector<double> d(3 * (size_t)nrhs);
   for (int r = 0; r < nrhs; ++r) {
     double l = sqrt(dirs[3 * r] * dirs[3 * r] + dirs[3 * r + 1] * dirs[3 * r + 1] + dirs[3 * r + 2] * dirs[3 * r + 2]);

@@ -615,7 +615,10 @@ static int gmres_solve_block(GmCtx& C, const double2* b, double2* x, int nc, con
     FDA_TRY(blk_norms(C, Rb.p, nc, B, rn));
     double wr = 0, worst_abs = 0;
     for (int c = 0; c < nc; ++c) {
-      if (!std::isfinite(rn[c])) return FDA_E_NAN;
+      if (!std::isfinite(rn[c])) {
+        set_error("refinement residual of column %d holds NaN or Inf", c);
+        return FDA_E_NAN;
+      }
       const double r = bn[c] > 0 ? rn[c] / bn[c] : 0.0;
       wr = std::max(wr, r);
       worst_abs = std::max(worst_abs, r);
@@ -626,7 +629,10 @@ static int gmres_solve_block(GmCtx& C, const double2* b, double2* x, int nc, con
       rc = FDA_OK;
       break;
     }
-    if (*total_it >= o->max_iter) break;
+    if (*total_it >= o->max_iter) {
+      set_error("iterative refinement reached %d iterations at relative residual %.3e", *total_it, wr);
+      break;
+    }
     if (!(worst_abs < 0.9 * prev)) {
       set_error("iterative refinement stagnated at %.3e", wr);
       rc = FDA_E_BREAKDOWN;
@@ -721,6 +727,7 @@ int gmres_solve(fda_plan_s* P, const double2* b, double2* x, int nrhs, const bm_
         FDA_TRY(dev_norm(C, P->gm_b.p, &rn));
         rel = rn / bn;
         if (!std::isfinite(rn)) {
+          set_error("refinement residual holds NaN or Inf (right-hand side or operator)");
           rc = FDA_E_NAN;
           break;
         }
@@ -728,7 +735,10 @@ int gmres_solve(fda_plan_s* P, const double2* b, double2* x, int nrhs, const bm_
           rc = FDA_OK;
           break;
         }
-        if (total_it >= o->max_iter) break;
+        if (total_it >= o->max_iter) {
+          set_error("iterative refinement reached %d iterations at relative residual %.3e", total_it, rel);
+          break;
+        }
         if (!(rn < 0.9 * prev)) {
           set_error("iterative refinement stagnated at %.3e", rel);
           rc = FDA_E_BREAKDOWN;

@@ -12,6 +12,7 @@ struct bm_problem_s {
   double k = 0;
   double2 alpha = {0, 0};
   int particles = 0;         // 1: points with normals (no elements): the particle summation of Sec. 5.1
+  int device = 0;            // the CUDA device that holds the problem's arrays (current at creation)
   fda::DBuf<double> nodes;   // nn x 3
   fda::DBuf<int32_t> elems;  // ne x 6
   fda::DBuf<double> x, n, w; // N x 3, N x 3 (paper normal, into the body), N
@@ -40,6 +41,17 @@ struct fda_tree_s {
 };
 
 namespace fda {
+
+// FDA_E_INVALID_ARG unless the problem's device is the current one (kernels read its arrays there)
+inline int problem_device_current(const bm_problem_s* P) {
+  int dev = -1;
+  FDA_CUDA(cudaGetDevice(&dev));
+  if (dev != P->device) {
+    set_error("the problem lives on device %d but device %d is current", P->device, dev);
+    return FDA_E_INVALID_ARG;
+  }
+  return FDA_OK;
+}
 
 // exclusive prefix sum of n int64 values (in may alias out)
 int exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total_host, cudaStream_t s);

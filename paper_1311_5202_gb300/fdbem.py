@@ -396,8 +396,9 @@ def bm_gmres_solve(plan, b, x, tol=1e-6, restart=50, max_iter=1000, x0_given=Fal
     nrhs = 1 if b.dim() == 1 else b.shape[0]
     rc = lib().bm_gmres_solve(plan, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), nrhs, C.byref(o),
                               C.byref(st), _stream(stream))
+    # the return code is the status (a call that fails before it fills the statistics still returns it)
     stats = dict(iterations=st.iterations, outer_iterations=st.outer_iterations, rel_residual=st.rel_residual,
-                 ms_total=st.ms_total, ms_matvec=st.ms_matvec, status=st.status)
+                 ms_total=st.ms_total, ms_matvec=st.ms_matvec, status=int(rc))
     if raise_on_error:
         _check(rc)
     return stats
@@ -477,7 +478,7 @@ def bm_fgmres_solve(plan, pc, net, b, x, tol=1e-6, restart=50, max_iter=1000, x0
     rc = lib().bm_fgmres_solve(plan, pc, net, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), nrhs,
                                C.byref(o), C.byref(st), _stream(stream))
     stats = dict(iterations=st.iterations, outer_iterations=st.outer_iterations, rel_residual=st.rel_residual,
-                 ms_total=st.ms_total, ms_matvec=st.ms_matvec, status=st.status)
+                 ms_total=st.ms_total, ms_matvec=st.ms_matvec, status=int(rc))
     if raise_on_error:
         _check(rc)
     return stats

@@ -244,7 +244,44 @@ def test_gmres_solve_matches_oracle_and_mie(c1):
     assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) < 1e-4
     th = np.arccos(np.clip(xs[:, 2] / np.linalg.norm(xs, axis=1), -1, 1))
     mie = O.mie_total_surface(th, k, 0.5)
+    # 320 elements (h ~ lambda/4.5): the discretisation error against the Mie series is 5.1e-3 here, the
+    # same as the oracle's own dense solve; the 1e-3 bar is met on the refined mesh below
     assert np.linalg.norm(xg - mie) / np.linalg.norm(mie) < 6e-3
+
+
+def _mie(xs, k, a, chunk=200000):
+    th = np.arccos(np.clip(xs[:, 2] / np.linalg.norm(xs, axis=1), -1, 1))
+    return np.concatenate([O.mie_total_surface(th[i:i + chunk], k, a) for i in range(0, len(th), chunk)])
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_mie_refined_sphere_within_1e3(form):
+    """Sec. 5.3, rigid-sphere scattering of u_inc = e^{ikz} at kD = 10 on 2000 curved elements (12,000 DOF,
+    h ~ lambda/7): the library's GMRES solution (plain FP64, and the mixed form: FP32 near field, TF32
+    tensor-core translations, FP64 refinement) is within 1e-3 of the Mie series in relative l2."""
+    _need_gpu()
+    mesh = inputs.icosphere(10, 0.5)
+    k = 10.0
+    if form == "fp64":
+        S = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=1e-6, leaf_max=64)
+    else:
+        S = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=1e-6, leaf_max=64, precision=fdbem.FDA_PREC_FP32,
+                         m2l_tensor=1)
+    try:
+        b = torch.empty(S.N, dtype=torch.complex128, device=DEV)
+        fdbem.bm_rhs_plane_wave(S.prob, [0.0, 0.0, 1.0], b)
+        x = torch.zeros_like(b)
+        if form == "fp64":
+            st = S.solve(b, x, tol=1e-7, restart=50, max_iter=400)
+        else:
+            st = S.solve(b, x, tol=1e-7, restart=50, max_iter=600, refine=True, inner_tol=1e-3)
+        assert st["rel_residual"] <= 1e-7
+        xs, _, _ = O.geometry(mesh.nodes, mesh.elems)
+        mie = _mie(xs, k, 0.5)
+        err = np.linalg.norm(x.cpu().numpy() - mie) / np.linalg.norm(mie)
+        assert err < 1e-3, (form, err)
+    finally:
+        S.close()
 
 
 def test_refinement_solve_fp32_inner(c1):
@@ -282,6 +319,41 @@ def test_fda_matvec_with_directional_levels_sampled_rows(form):
             yo = _oracle_rows(mesh, k, x[r], rows)
             err = np.linalg.norm(yd[r].cpu().numpy()[rows] - yo) / np.linalg.norm(yo)
             assert err < (1e-4 if form == "fp64" else 3e-4), (form, r, err)
+    finally:
+        S.close()
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_bm_operator_with_two_directional_levels(form):
+    """The Burton-Miller product with M2L pairs on two high-frequency levels, so that the nested-wedge
+    M2M and L2L (24 wedges at level 4, 6 at level 5) carry the far field: a coarse sphere at k = 300
+    (kD = 300, 48,000 DOF, 16 points per leaf). FP64 form (<= 1e-4) and the autotuned mixed form (FP32 near
+    field, TF32 tensor-core translations where the rank fits, <= 3e-4) on 256 oracle rows."""
+    _need_gpu()
+    mesh = inputs.icosphere(20, 0.5)
+    k = 300.0
+    if form == "fp64":
+        S = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=1e-4, leaf_max=16)
+    else:
+        S = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=1e-4, leaf_max=16, precision=fdbem.FDA_PREC_FP32,
+                         m2l_tensor=1)
+    try:
+        info = S.info()
+        hf_m2l = [l for l in range(32) if info["n_wedges"][l] > 1 and info["m2l_pairs"][l] > 0]
+        assert len(hf_m2l) >= 2, hf_m2l
+        assert max(info["n_wedges"][l] for l in hf_m2l) >= 24
+        if form == "mixed":
+            fdbem.fda_autotune(S.plan, 1)
+        x = inputs.complex_gaussian(S.N, 20131120)
+        xd = torch.from_numpy(x).to(DEV)
+        yd = torch.empty_like(xd)
+        S.matvec(xd, yd)
+        torch.cuda.synchronize()
+        rows = inputs.sample_rows(S.N, 256, 7)
+        yo = _oracle_rows(mesh, k, x, rows)
+        err = np.linalg.norm(yd.cpu().numpy()[rows] - yo) / np.linalg.norm(yo)
+        assert err < (1e-4 if form == "fp64" else 3e-4), (form, err)
+        assert fdbem.fda_plan_check(S.plan) == fdbem.FDA_OK
     finally:
         S.close()
 
@@ -508,7 +580,7 @@ def test_bounded_wait_times_out_and_context_survives():
 def test_full_size_sampled_rows(workload):
     """The configurations the bench times (kD = 100: 100,920 DOF; kD = 200: 1,129,080 DOF; eps = 1e-4, 64 points
     per leaf): the autotuned mixed plan (FP32 near field, TF32 tensor-core M2L/M2M/L2L) and its FP64 form
-    against the oracle on 64 sampled rows computed one by one (bars 3e-4 and 1e-4)."""
+    against the oracle on 256 sampled rows computed one by one (bars 3e-4 and 1e-4)."""
     _need_gpu()
     spec = inputs.WORKLOADS[workload]
     mesh = inputs.make_mesh(spec)
@@ -520,7 +592,7 @@ def test_full_size_sampled_rows(workload):
         x = inputs.complex_gaussian(S.N, 20131120)
         xd = torch.from_numpy(x).to(DEV)
         yd = torch.empty_like(xd)
-        rows = inputs.sample_rows(S.N, 64, 7)
+        rows = inputs.sample_rows(S.N, 256, 7)
         yo = _oracle_rows(mesh, k, x, rows)
         for prec, bar in ((fdbem.FDA_PREC_FP32, 3e-4), (fdbem.FDA_PREC_FP64, 1e-4)):
             fdbem.fda_matvec_ex(S.plan, prec, xd, yd)
@@ -528,5 +600,30 @@ def test_full_size_sampled_rows(workload):
             err = np.linalg.norm(yd.cpu().numpy()[rows] - yo) / np.linalg.norm(yo)
             assert err < bar, (workload, prec, err)
         assert fdbem.fda_plan_check(S.plan) == fdbem.FDA_OK
+    finally:
+        S.close()
+
+
+def test_mie_at_metric_sphere():
+    """Sec. 5.3 at the bench's sphere (kD = 200, 1,129,080 DOF, h ~ lambda/5.8, eps = 1e-4): the mixed
+    refinement solve to a 1e-5 residual is within 1e-3 of the Mie series in relative l2. The coupling is
+    alpha = -i/k in the library's normal convention (the reading under which the paper's iteration counts
+    hold); the continuous solution does not depend on alpha."""
+    _need_gpu()
+    spec = inputs.WORKLOADS["sphere_kd200"]
+    mesh = inputs.make_mesh(spec)
+    k = spec["k"]
+    S = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=spec["eps"], leaf_max=spec["leaf"],
+                     precision=fdbem.FDA_PREC_FP32, m2l_tensor=1, alpha=-1j / k)
+    try:
+        b = torch.empty(S.N, dtype=torch.complex128, device=DEV)
+        fdbem.bm_rhs_plane_wave(S.prob, [0.0, 0.0, 1.0], b)
+        x = torch.zeros_like(b)
+        st = S.solve(b, x, tol=1e-5, restart=50, max_iter=300, refine=True, inner_tol=1e-3)
+        assert st["rel_residual"] <= 1e-5
+        xs, _, _ = O.geometry(mesh.nodes, mesh.elems)
+        mie = _mie(xs, k, spec["radius"])
+        err = np.linalg.norm(x.cpu().numpy() - mie) / np.linalg.norm(mie)
+        assert err < 1e-3, err
     finally:
         S.close()

@@ -377,13 +377,16 @@ def _pulsating_solve(m, a, k):
 
 def test_pulsating_sphere_matches_paper_value():
     """Sec. 5.2: the unit sphere pulsating with q = 1 has u = 1/(1 - ik); tests/golden/pulsating_sphere.txt holds
-    the paper's values. The oracle's Burton-Miller radiation solve (S, M, D, H with their own corrected weights)
-    at k = 2 pi on 320 curved elements lands within its discretisation error."""
+    the printed closed form at the paper's five wavenumbers (written without the oracle). The oracle's
+    general-radius formula a/(1 - ika) must reproduce them at a = 1, and its Burton-Miller radiation solve
+    (S, M, D, H with their own corrected weights) at k = 2 pi on 320 curved elements lands within its
+    discretisation error."""
     import os
     rows = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "pulsating_sphere.txt"))
+    for kk, ure, uim in rows:
+        assert abs(O.pulsating_sphere(kk, 1.0) - (ure + 1j * uim)) < 1e-15
     k, ure, uim = rows[0]
     ue = ure + 1j * uim
-    assert abs(O.pulsating_sphere(k, 1.0) - ue) < 1e-15
     u = _pulsating_solve(4, 1.0, k)
     assert np.max(np.abs(u - ue)) < 1e-2 * abs(ue)
     assert abs(np.mean(u) - ue) < 1e-3 * abs(ue)
