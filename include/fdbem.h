@@ -204,7 +204,8 @@ int fda_matvec_ex(fda_plan_t* plan, int precision, const void* x, void* y, int n
 
 /* Autotuner (no paper counterpart). For an FP32 plan and a batch width nrhs (1..nrhs_max), times on the
  * plan's own operators every M2L (level, stage) with the FP32 FMA kernel and with the plan's tensor-core
- * kernel (m2l_tensor 1: four tile shapes; m2l_tensor 2: one), for nrhs >= 12 the near field at 4 and 16 right-hand sides per pass over
+ * kernels (m2l_tensor 1: four tile shapes, two with a bulk-reduction epilogue, and for the V^ stage the
+ * swapped-operand kernel; m2l_tensor 2: one), for nrhs >= 12 the near field at 4 and 16 right-hand sides per pass over
  * the near-field matrices, and the near field with its off-block correction entries inside the stream or as a
  * separate CSR kernel; the plan keeps the faster variant of each for all later products. Synchronous;
  * overwrites the plan's internal workspaces only. report (HOST) receives the timings and choices.
@@ -216,7 +217,9 @@ typedef struct {
   double ms_fma[64];      /* FP32 FMA kernel, best of 3 */
   double ms_tensor[64];   /* tensor-core kernel, best of 3 over its tile shapes (-1 when the plan holds none) */
   int32_t chosen[64];     /* 0: FMA kernel, 1: tensor-core kernel (default shape), 2 to 4: tensor-core kernel
-                             (alternative shapes: other column width or stage count) */
+                             (alternative shapes: other column width or stage count), 5 and 6: tensor-core
+                             kernel with the bulk-reduction epilogue (default and single-stage shape), 7 and 8:
+                             stage 0 with the swapped-operand V^ kernel (one and two pipeline stages) */
   double near_ms[2];      /* near field at 4 and 16 right-hand sides per pass (nrhs >= 12; else 0) */
   int32_t near_rhs_per_pass;
   int32_t near_split;     /* near-field schedule kept: 0 = the correction entries outside the direct blocks inside
@@ -226,6 +229,16 @@ typedef struct {
   double near_window_ms;    /* schedule 2 (nrhs = 1; else -1) */
 } fda_tune_report_t;
 int fda_autotune(fda_plan_t* plan, int nrhs, void* stream, fda_tune_report_t* report);
+
+/* Force one M2L kernel variant for every (level, stage) of an FP32 plan (diagnostic and testing; no paper
+ * counterpart), replacing the autotuner's choices: -1 = the plan's default, 0 = FP32 FMA kernel, 1 = TF32
+ * tensor cores from operator images (default shape), 2 = in-kernel expansion (plans with m2l_tensor = 2),
+ * 3 to 5 = variant 1 in the alternative tile shapes, 6 and 7 = variant 1 with the bulk-reduction epilogue
+ * (default and single-stage shape), 8 and 9 = the swapped-operand V^ kernel (one and two stages) for the V^
+ * stage, with variant 6 for the U^ stage. A variant that does not apply to a (level, stage) runs the FMA
+ * kernel there. Errors: FDA_E_INVALID_ARG (variant outside [-1, 9]), FDA_E_STATE (plan without the kernel's
+ * operators). */
+int fda_m2l_force(fda_plan_t* plan, int variant);
 
 /* CUDA-graph form of one product (the batched matvec of many incident directions replayed without
  * per-kernel launch cost; no paper counterpart). fda_matvec_graph_create runs the product once on `stream`
@@ -379,7 +392,9 @@ int fda_wait_selftest(double limit_ms, int* timed_out);
  * (K <= 1024) applied to P gathered columns, against an FP64 host product of the same FP32 data.
  * split = 0: TF32 with operands expanded in the kernel (M = 64, P = 64); 1: 3xTF32 split (M = 64, P = 64);
  * 2..5: TF32 with the pre-expanded operator image of the m2l_tensor = 1 form (M = min(256, K), P = 100),
- * in its default tile shape (2) or the autotuner's alternatives (3, 4, 5).
+ * in its default tile shape (2) or the autotuner's alternatives (3, 4, 5); 6, 7: the same kernel with the
+ * bulk-reduction epilogue (default and single-stage shape); 8, 9: the swapped-operand V^ kernel (one and
+ * two stages; M = min(100, K), P = 100, results stored as the low-rank intermediate).
  * *max_rel_err is the largest entrywise error relative to the sum of |a||x| over the row, *wait_failed is 1
  * when a bounded device wait gave up. Synchronous. */
 int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_failed);

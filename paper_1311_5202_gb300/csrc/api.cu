@@ -271,6 +271,27 @@ int fda_autotune(fda_plan_t* plan, int nrhs, void* stream, fda_tune_report_t* re
   return autotune(plan, nrhs, (cudaStream_t)stream, report);
 }
 
+int fda_m2l_force(fda_plan_t* plan, int variant) {
+  ARG_CHECK(plan, "NULL plan");
+  ARG_CHECK(variant >= -1 && variant <= 9, "variant outside [-1, 9]");
+  if (variant > 0 && plan->cfg.precision != FDA_PREC_FP32) {
+    set_error("tensor-core M2L variants need a plan built with FDA_PREC_FP32");
+    return FDA_E_STATE;
+  }
+  if (variant == 2 && plan->cfg.m2l_tensor != 2) {
+    set_error("variant 2 needs a plan built with m2l_tensor = 2");
+    return FDA_E_STATE;
+  }
+  if (variant != 2 && variant > 0 && plan->cfg.m2l_tensor != 1) {
+    set_error("variants 1 and 3 to 9 need a plan built with m2l_tensor = 1");
+    return FDA_E_STATE;
+  }
+  for (int l = 0; l < FDA_MAXLEV; ++l)
+    for (int st = 0; st < 2; ++st)
+      plan->m2l_choice[l][st] = (st == 1 && variant >= 8) ? 6 : variant;  // 8, 9 are V^-stage kernels
+  return FDA_OK;
+}
+
 int fda_plan_check(fda_plan_t* plan) {
   ARG_CHECK(plan, "NULL plan");
   FDA_CUDA(cudaDeviceSynchronize());

@@ -113,6 +113,32 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// bulk reduction global += shared (FP32 adds performed in L2 by the copy engine); both addresses 16-byte
+// aligned, bytes a multiple of 16; completion tracked per thread with bulk async-groups
+__device__ __forceinline__ void bulk_reduce_add(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_u32(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
 #define TC_MT 4      // row tiles per CTA (up to 256 complex rows)
 
 // Shared memory per pipeline buffer: A^ tiles (TC_MT x 128 x KC), B tile (64 x KC), hi and (split) lo parts
@@ -467,7 +493,7 @@ struct Tc3Smem {
 // thread 0 copies the operator tiles with cp.async.bulk while all threads gather the pairs' coefficients
 // with 16-byte cp.async (two complex values; 8-byte copies for a source off a 16-byte boundary); NST chunks
 // in flight.
-template <int MTC, int N, int NST>
+template <int MTC, int N, int NST, int BULK>
 static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units, const float* img,
                                                           const int64_t* psrc, const int64_t* ptgt,
                                                           const int64_t* pmid, const float2* cout, float2* cin,
@@ -594,6 +620,7 @@ static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units
         for (int mt = 0; mt < MT; ++mt) {
 #pragma unroll
           for (int s8 = 0; s8 < TC3_KC / 8; ++s8) {
+            if (kc * TC3_KC + s8 * 8 >= 2 * U.K) break;  // K steps past the operator hold only zeros
             const uint64_t ad = smem_desc(smem_u32(S.a[s][mt]) + s8 * 256, lbo, sbo);
             const uint64_t bd = smem_desc(smem_u32(S.b[s]) + s8 * 256, lbo, sbo);
             tc_mma(tmem + N * mt, ad, bd, IDESC, (kc > 0 || s8 > 0) ? 1 : 0);
@@ -604,6 +631,46 @@ static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units
     }
     for (int c = max(0, nk - NST); c < nk; ++c) ok = wait_mdone(c % NST) && ok;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (BULK && U.mode != 1 && (U.M & 1) == 0) {  // bulk reductions move whole 16-byte granules
+      // Bulk-reduction epilogue: the accumulators go through shared memory, 16 columns at a time in two
+      // alternating buffers aliased on the operator tiles (every MMA of this column block has completed and no
+      // copy writes them before the next block starts), and each column (a pair's complex output vector,
+      // U.M values) is added to its target with one cp.reduce.async.bulk; the copy engine performs the adds
+      // while the CTA moves on. Warps 0-3 read the even row tiles, warps 4-7 the odd ones (TMEM lane
+      // quadrant w % 4).
+      float* stg = &S.a[0][0][0];
+      const int RT = 128 * MT;  // staged real rows per column
+      const int q4 = w & 3;
+      for (int cg = 0; cg < N / 16; ++cg) {
+        float* sb = stg + (cg & 1) * 16 * RT;
+        if (t < 16) bulk_wait_read<1>();  // the reductions that read this buffer two groups ago are done
+        __syncthreads();
+        if (ok) {
+          for (int mt = w >> 2; mt < MT; mt += 2) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(N * mt + 16 * cg), v);
+            const int row = 128 * mt + 32 * q4 + lane;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) sb[c * RT + row] = v[c];
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (t < 16) {
+          const int n = 16 * cg + t;
+          const int64_t db = S.dbase[n];
+          if (ok && db >= 0) {
+            float2* dst = cin + (int64_t)S.srr[n] * ldd + db;
+            if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)
+              bulk_reduce_add(dst, sb + t * RT, 8u * (uint32_t)U.M);
+            else
+              atomicExch(err, 2);  // a target off a 16-byte boundary (the plan never makes one): reported, skipped
+          }
+          bulk_commit();
+        }
+      }
+      if (t < 16) bulk_wait_read<0>();
+    } else {
     // columns per warp: half of the tile for N >= 64; the whole tile (warps 0-3 only) for N = 32
     constexpr int CPW = N >= 64 ? N / 2 : N;
     if (ok && (N >= 64 || w < 4)) {
@@ -633,6 +700,7 @@ static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units
         }
       }
     }
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
   }
@@ -644,20 +712,21 @@ static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units
   }
 }
 
-template <int MTC, int N, int NST>
+template <int MTC, int N, int NST, int BULK>
 static int tc3_launch_t(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc,
                         const int64_t* ptgt, const int64_t* pmid, const float2* cout, float2* cin, float2* mid,
                         int nrhs, int64_t ldc, int64_t ldm, int* err, cudaStream_t s) {
   const size_t smem = sizeof(Tc3Smem<MTC, N, NST>) + 1024;
   static bool attr = false;
   if (!attr) {
-    FDA_CUDA(cudaFuncSetAttribute(k_m2l_tc3<MTC, N, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FDA_CUDA(cudaFuncSetAttribute(k_m2l_tc3<MTC, N, NST, BULK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
     attr = true;
   }
   for (size_t u0 = 0; u0 < nunits; u0 += 65535) {
     unsigned n = (unsigned)std::min<size_t>(65535, nunits - u0);
-    k_m2l_tc3<MTC, N, NST><<<n, TC3_NT, smem, s>>>(units + u0, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, ldc, ldm,
-                                                   err);
+    k_m2l_tc3<MTC, N, NST, BULK><<<n, TC3_NT, smem, s>>>(units + u0, img, psrc, ptgt, pmid, cout, cin, mid, nrhs,
+                                                         ldc, ldm, err);
     FDA_LAUNCH_CHECK();
   }
   return FDA_OK;
@@ -675,8 +744,22 @@ int m2l_tc3_launch(const GemmUnit* units, size_t nunits, const float* img, const
     return FDA_E_INVALID_ARG;
   }
   if (nunits == 0) return FDA_OK;
+  if (shape == 4 || shape == 5) {  // bulk-reduction epilogue: default shape (4) or single-stage (5)
+#define TC3B(M_, N_, S_) \
+  return tc3_launch_t<M_, N_, S_, 1>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, ldc, ldm, err, s)
+    const bool short_k = max_k > 0 && 2 * max_k <= 2 * TC3_KC;
+    if (shape == 5 || short_k) {
+      if (max_mt == 1) TC3B(1, 128, 1);
+      if (max_mt == 2) TC3B(2, 64, 1);
+      TC3B(4, 64, 1);
+    }
+    if (max_mt == 1) TC3B(1, 128, 3);
+    if (max_mt == 2) TC3B(2, 128, 2);
+    TC3B(4, 64, 2);
+#undef TC3B
+  }
 #define TC3L(M_, N_, S_) \
-  return tc3_launch_t<M_, N_, S_>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, ldc, ldm, err, s)
+  return tc3_launch_t<M_, N_, S_, 0>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, ldc, ldm, err, s)
   const bool alt = shape == 1;
   if (shape == 2) {  // single-stage
     if (max_mt == 1) TC3L(1, 128, 1);
@@ -713,6 +796,226 @@ int m2l_tc3_launch(const GemmUnit* units, size_t nunits, const float* img, const
 #undef TC3L
 }
 
+
+// ================================================================== V^ stage with swapped operand roles
+// The low-rank V^ stage, mid_p = V^ t_src(p), applied to up to 128 pairs: the gathered source coefficient
+// vectors are the A operand (M = 128 rows = pair x right-hand-side columns, K-major, the same 16-byte
+// cp.async gathers as above) and the rows of V^'s real expansion are the B operand (N = 2r rounded up to 16,
+// taken from the same pre-expanded operator image by cp.async.bulk). The accumulator is 128 TMEM lanes x
+// NB columns, so a rank of 16 needs 32 columns instead of 128 lanes x 128 columns in the other orientation:
+// up to 8 CTAs fit on an SM. Epilogue: lane = pair, so each thread writes its pair's 2r outputs as
+// consecutive 16-byte stores into the low-rank intermediate.
+template <int NB, int NST>
+struct VswSmem {
+  alignas(1024) float a[NST][128 * TC3_KC];  // gathered coefficient vectors (128 rows x 32 real K)
+  alignas(1024) float b[NST][NB * TC3_KC];   // operator rows (NB rows x 32 real K)
+  alignas(8) uint64_t bfull[NST];
+  uint64_t mdone[NST];
+  uint32_t tmem;
+  int64_t sbase[128], dbase[128];
+  int srr[128];
+};
+
+#define VSW_NT 128
+
+template <int NB, int NST>
+static __global__ void __launch_bounds__(VSW_NT, 8) k_m2l_vsw(const GemmUnit* units, const float* img,
+                                                          const int64_t* psrc, const int64_t* pmid,
+                                                          const float2* cout, float2* mid, int nrhs, int64_t ldc,
+                                                          int64_t ldm, int* err) {
+  typedef VswSmem<NB, NST> Sm;
+  extern __shared__ unsigned char smem_raw[];
+  Sm& S = *reinterpret_cast<Sm*>((((uintptr_t)smem_raw) + 1023) & ~(uintptr_t)1023);
+  constexpr int D = NST - 1;
+  const GemmUnit U = units[blockIdx.x];  // mode 1: M = r rows of V^, K = s
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const int MT = (2 * U.M + 127) / 128;  // operator image tiles (1 or 2)
+  const int nmma = ((2 * U.M + 15) / 16) * 16;
+  const int nk = (2 * U.K + TC3_KC - 1) / TC3_KC;
+  const float* A = img + U.a_off;
+  const uint32_t idesc = idesc_tf32(128, nmma);
+  if (w == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
+                 "r"(NB));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (t == 0) {
+    for (int q = 0; q < NST; ++q) {
+      mbar_init(&S.bfull[q], 1);
+      mbar_init(&S.mdone[q], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = S.tmem;
+  uint32_t ph_b[NST], ph_m[NST];
+#pragma unroll
+  for (int q = 0; q < NST; ++q) ph_b[q] = ph_m[q] = 0;
+  bool ok = true;
+  auto wait_mdone = [&](int q) {
+    bool mine = mbar_wait(&S.mdone[q], ph_m[q]);
+    bool all = __syncthreads_and(mine ? 1 : 0) != 0;
+    if (!all) {
+      if (t == 0) atomicExch(err, 1);
+      mbar_wait(&S.mdone[q], ph_m[q]);  // second bounded wait for MMAs still in flight
+    }
+    ph_m[q] ^= 1;
+    return all;
+  };
+  auto issue = [&](int kc) {
+    const int q = kc % NST;
+    if (t == 0) {
+      uint32_t bytes = 0;
+      for (int mt = 0; mt < MT; ++mt) bytes += (uint32_t)tc3_ng(U.M, mt) * 1024u;
+      tc3_expect_tx(&S.bfull[q], bytes);
+      for (int mt = 0; mt < MT; ++mt) {
+        const int ng = tc3_ng(U.M, mt);
+        tc3_bulk(S.b[q] + mt * 16 * 256, A + (int64_t)16 * mt * nk * 256 + (int64_t)kc * ng * 256,
+                 (uint32_t)ng * 1024u, &S.bfull[q]);
+      }
+    }
+    const uint32_t abase = smem_u32(S.a[q]);
+    for (int r = w; r < 32; r += VSW_NT / 32) {
+      const int n = (r >> 1) * 8 + (lane >> 2), j = (r & 1) * 8 + 2 * (lane & 3);
+      if (S.sbase[n] < 0) continue;  // unused row: its results are never read
+      const int gj = kc * (TC3_KC / 2) + j;
+      const uint32_t dst = abase + kmaj_off(n, 2 * j, TC3_KC);
+      const float2* src = gj < U.K ? cout + (int64_t)S.srr[n] * ldc + S.sbase[n] + gj : cout;
+      const uint32_t nbytes = gj + 1 < U.K ? 16u : (gj < U.K ? 8u : 0u);  // the rest is zero-filled
+      if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        tc3_cp16(dst, src, nbytes);
+      } else {
+        tc3_cp8(dst, src, nbytes >= 8 ? 8u : 0u);
+        tc3_cp8(dst + 8, nbytes == 16 ? src + 1 : cout, nbytes == 16 ? 8u : 0u);
+      }
+    }
+    tc3_commit_group();
+  };
+
+  const int ncols = U.p_count * nrhs;
+  for (int c0 = 0; c0 < ncols && ok; c0 += 128) {
+    {
+      const int c = c0 + t;
+      if (c < ncols) {
+        const int p = c / nrhs, rr = c - p * nrhs;
+        const int64_t pi = U.p_begin + p;
+        S.sbase[t] = psrc[pi];
+        S.dbase[t] = pmid[pi];
+        S.srr[t] = rr;
+      } else {
+        S.sbase[t] = -1;
+        S.dbase[t] = -1;
+        S.srr[t] = 0;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      if (j < nk)
+        issue(j);
+      else
+        tc3_commit_group();
+    }
+    for (int kc = 0; kc < nk; ++kc) {
+      const int j = kc + D;
+      if (j < nk) {
+        if (j >= NST) ok = wait_mdone(j % NST) && ok;
+        issue(j);
+      } else {
+        tc3_commit_group();
+      }
+      tc3_wait_group<D>();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (t == 0) {
+        const int q = kc % NST;
+        if (!mbar_wait(&S.bfull[q], ph_b[q])) atomicExch(err, 1);
+        ph_b[q] ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int s8 = 0; s8 < TC3_KC / 8; ++s8) {
+          if (kc * TC3_KC + s8 * 8 >= 2 * U.K) break;  // K steps past the operator hold only zeros
+          const uint64_t ad = smem_desc(smem_u32(S.a[q]) + s8 * 256, 128, (TC3_KC / 4) * 128);
+          const uint64_t bd = smem_desc(smem_u32(S.b[q]) + s8 * 256, 128, (TC3_KC / 4) * 128);
+          tc_mma(tmem, ad, bd, idesc, (kc > 0 || s8 > 0) ? 1 : 0);
+        }
+        tc_commit(&S.mdone[q]);
+      }
+    }
+    for (int c = max(0, nk - NST); c < nk; ++c) ok = wait_mdone(c % NST) && ok;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      const int n = 32 * w + lane;  // TMEM lane = pair column
+      const int64_t db = S.dbase[n];
+      float* dst = db >= 0 ? reinterpret_cast<float*>(mid + (int64_t)S.srr[n] * ldm + db) : nullptr;
+      const int nout = ((2 * U.M + 3) / 4) * 4;  // real outputs, rounded up to whole 16-byte stores (even-padded)
+#pragma unroll 1
+      for (int col0 = 0; col0 < nmma; col0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * w) << 16) + (uint32_t)col0, v);
+        if (dst) {
+#pragma unroll
+          for (int q = 0; q < 32; q += 4)
+            if (col0 + q < nout)
+              *reinterpret_cast<float4*>(dst + col0 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  if (w == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NB));
+  }
+}
+
+template <int NB, int NST>
+static int vsw_launch_t(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc,
+                        const int64_t* pmid, const float2* cout, float2* mid, int nrhs, int64_t ldc, int64_t ldm,
+                        int* err, cudaStream_t s) {
+  const size_t smem = sizeof(VswSmem<NB, NST>) + 1024;
+  static bool attr = false;
+  if (!attr) {
+    FDA_CUDA(cudaFuncSetAttribute(k_m2l_vsw<NB, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  for (size_t u0 = 0; u0 < nunits; u0 += 65535) {
+    unsigned n = (unsigned)std::min<size_t>(65535, nunits - u0);
+    k_m2l_vsw<NB, NST><<<n, VSW_NT, smem, s>>>(units + u0, img, psrc, pmid, cout, mid, nrhs, ldc, ldm, err);
+    FDA_LAUNCH_CHECK();
+  }
+  return FDA_OK;
+}
+
+// The swapped V^ kernel for units whose rank r satisfies round16(2 r) <= nb (nb = 32, 64, 128 or 256 TMEM
+// columns); nst = 1 or 2 pipeline stages.
+int m2l_vsw_launch(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc, const int64_t* pmid,
+                   const float2* cout, float2* mid, int nrhs, int64_t ldc, int64_t ldm, int nb, int nst, int* err,
+                   cudaStream_t s) {
+  if (nunits == 0) return FDA_OK;
+#define VSWL(B_, S_) return vsw_launch_t<B_, S_>(units, nunits, img, psrc, pmid, cout, mid, nrhs, ldc, ldm, err, s)
+  if (nst == 1) {
+    if (nb == 32) VSWL(32, 1);
+    if (nb == 64) VSWL(64, 1);
+    if (nb == 128) VSWL(128, 1);
+    if (nb == 256) VSWL(256, 1);
+  } else {
+    if (nb == 32) VSWL(32, 2);
+    if (nb == 64) VSWL(64, 2);
+    if (nb == 128) VSWL(128, 2);
+    if (nb == 256) VSWL(256, 2);
+  }
+#undef VSWL
+  set_error("swapped V^ kernel: no variant for %d TMEM columns and %d stages", nb, nst);
+  return FDA_E_INVALID_ARG;
+}
+
 }  // namespace fda
 
 using namespace fda;
@@ -746,13 +1049,19 @@ static __global__ void k_wait_probe(uint64_t limit_ns, int* timed_out) {
 
 // Self-test of the tensor-core path: one complex M x K product applied to P gathered columns, against an FP64
 // host product of the same FP32 data. split 0: TF32 (M = 64, P = 64); 1: 3xTF32 split (M = 64, P = 64);
-// 2..5: TF32 with the pre-expanded operator image (M = min(256, K), P = 100), tile shape split - 2.
+// 2..7: TF32 with the pre-expanded operator image (M = min(256, K), P = 100), tile shape split - 2 (6 and 7:
+// the bulk-reduction epilogue); 8, 9: the swapped-operand V^ kernel with one or two stages (M = min(100, K),
+// P = 100, results stored into an intermediate with even-padded vectors as the low-rank stage does).
 extern "C" int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_failed) {
-  if (K < 1 || K > 1024 || split < 0 || split > 5 || !max_rel_err || !wait_failed) {
+  if (K < 1 || K > 1024 || split < 0 || split > 9 || !max_rel_err || !wait_failed) {
     set_error("bad arguments");
     return FDA_E_INVALID_ARG;
   }
-  const int M = split >= 2 ? std::min(256, K) : 64, P = split >= 2 ? 100 : 64;
+  const bool vsw = split >= 8;
+  // the bulk-reduction epilogue adds whole 16-byte granules: even row counts (as every plan has)
+  const int Mb = split == 6 || split == 7 ? std::min(256, (K + 1) & ~1) : std::min(256, K);
+  const int M = vsw ? std::min(100, K) : (split >= 2 ? Mb : 64), P = split >= 2 ? 100 : 64;
+  const int Mp = vsw ? (M + 1) & ~1 : M;  // stride of the stored vectors
   std::vector<float2> hA((size_t)M * K), hX((size_t)K * P);
   uint64_t st = 12345;
   auto rnd = [&]() {
@@ -766,12 +1075,13 @@ extern "C" int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_
   DBuf<GemmUnit> du;
   DBuf<int> err;
   std::vector<int64_t> hs(P), ht(P), hm(P, -1);
-  for (int p = 0; p < P; ++p) hs[p] = (int64_t)p * K, ht[p] = (int64_t)p * M;
+  for (int p = 0; p < P; ++p) hs[p] = (int64_t)p * K, ht[p] = (int64_t)p * M, hm[p] = vsw ? (int64_t)p * Mp : -1;
   FDA_TRY(dA.upload(hA));
   FDA_TRY(dX.upload(hX));
-  FDA_TRY(dY.alloc((size_t)M * P));
+  FDA_TRY(dY.alloc((size_t)Mp * P));
   FDA_TRY(dY.zero());
-  FDA_TRY(dmid.alloc(1));
+  FDA_TRY(dmid.alloc(vsw ? (size_t)P * Mp : 1));
+  FDA_TRY(dmid.zero());
   FDA_TRY(src.upload(hs));
   FDA_TRY(tgt.upload(ht));
   FDA_TRY(pm.upload(hm));
@@ -785,10 +1095,18 @@ extern "C" int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_
     FDA_TRY(dA64.upload(hA64));
     FDA_TRY(img.alloc((size_t)tc3_image_floats(M, K)));
     FDA_TRY(tc3_build_images({TcImgJob{dA64.p, M, K, 0, M, 0}}, img.p));
-    GemmUnit u{0, M, K, 0, P, 0, 0, 0};
+    GemmUnit u{0, M, K, 0, P, 0, vsw ? 1 : 0, 0};
     FDA_TRY(du.upload(&u, 1));
-    FDA_TRY(m2l_tc3_launch(du.p, 1, img.p, src.p, tgt.p, pm.p, dX.p, dY.p, dmid.p, 1, 0, 0, (2 * M + 127) / 128, K,
-                           err.p, 0, split - 2));
+    if (vsw) {
+      const int nm = ((2 * M + 15) / 16) * 16;
+      const int nb = nm <= 32 ? 32 : nm <= 64 ? 64 : nm <= 128 ? 128 : 256;
+      FDA_TRY(m2l_vsw_launch(du.p, 1, img.p, src.p, pm.p, dX.p, dmid.p, 1, 0, 0, nb, split == 8 ? 1 : 2, err.p, 0));
+      FDA_CUDA(cudaDeviceSynchronize());
+      FDA_CUDA(cudaMemcpy(dY.p, dmid.p, sizeof(float2) * P * Mp, cudaMemcpyDeviceToDevice));
+    } else {
+      FDA_TRY(m2l_tc3_launch(du.p, 1, img.p, src.p, tgt.p, pm.p, dX.p, dY.p, dmid.p, 1, 0, 0, (2 * M + 127) / 128,
+                             K, err.p, 0, split - 2));
+    }
     FDA_CUDA(cudaDeviceSynchronize());
   } else {
     GemmUnit u{0, M, K, 0, P, 0, 0, 0};
@@ -810,7 +1128,7 @@ extern "C" int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_
         ri += (double)a.x * x.y + (double)a.y * x.x;
         nrm += sqrt(((double)a.x * a.x + (double)a.y * a.y) * ((double)x.x * x.x + (double)x.y * x.y));
       }
-      float2 y = hY[(size_t)p * M + i];
+      float2 y = hY[(size_t)p * Mp + i];
       double e = sqrt((y.x - rr) * (y.x - rr) + (y.y - ri) * (y.y - ri)) / nrm;
       worst = std::max(worst, e);
     }

@@ -19,6 +19,9 @@ namespace fda {
 int m2l_tc3_launch(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc, const int64_t* ptgt,
                    const int64_t* pmid, const float2* cout, float2* cin, float2* mid, int nrhs, int64_t ldc,
                    int64_t ldm, int max_mt, int max_k, int* err, cudaStream_t s, int shape);
+int m2l_vsw_launch(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc, const int64_t* pmid,
+                   const float2* cout, float2* mid, int nrhs, int64_t ldc, int64_t ldm, int nb, int nst, int* err,
+                   cudaStream_t s);
 int m2l_tc_launch(const GemmUnit* units, size_t nunits, const float2* poolK, const float2* poolLR,
                   const int64_t* psrc, const int64_t* ptgt, const int64_t* pmid, const float2* cout, float2* cin,
                   float2* mid, int nrhs, int64_t ldc, int64_t ldm, int split, int max_rows, int* err, cudaStream_t s);
@@ -437,7 +440,9 @@ static __global__ void __launch_bounds__(256) k_m2l(const GemmUnit* units, const
 // ------------------------------------------------------------------ driver
 // M2L kernel variants of one (level, stage): 0 = FP32/FP64 FMA, 1 = TF32 from pre-expanded operator images,
 // 2 = TF32 or 3xTF32 with operands expanded in the kernel (plan option m2l_tensor = 2), 3 to 5 = variant 1
-// with its alternative tile shapes 1 to 3 (picked by the autotuner only)
+// with its alternative tile shapes 1 to 3, 6 and 7 = variant 1 with the bulk-reduction epilogue (default and
+// single-stage shape), 8 and 9 = stage 0 only: the swapped-operand V^ kernel (one or two pipeline stages) for
+// the low-rank units and variant 6 for the dense ones (6 to 9 are picked by the autotuner only)
 int m2l_variant(const fda_plan_s* P, int l, int st) {
   if (P->m2l_choice[l][st] >= 0) return P->m2l_choice[l][st];
   if (P->cfg.m2l_tensor == 1 && !P->h_tc3_units[l][st].empty() && P->tc3_mt[l][st] <= 4) return 1;
@@ -449,8 +454,27 @@ template <typename C>
 int m2l_stage(fda_plan_s* P, RunOps<C>& op, DBuf<C>& cout, DBuf<C>& cin, DBuf<C>& mid, int l, int st, int variant,
               int nrhs, cudaStream_t s, int64_t* nl) {
   const bool f32 = std::is_same<C, float2>::value;
-  if ((variant == 1 || variant >= 3) && f32 && !P->h_tc3_units[l][st].empty()) {
-    const int shape = variant >= 3 ? variant - 2 : 0;
+  // the image kernels cover at most 4 row tiles (256 complex rows): a forced variant falls back to FMA beyond
+  const bool tc3_fits = P->tc3_mt[l][st] <= 4;
+  if ((variant == 8 || variant == 9) && f32 && st == 0 && !P->h_vsw_units[l].empty() && P->dn_mt[l] <= 4) {
+    for (int c = 0; c < 4; ++c) {
+      const int64_t u0 = P->vsw_cls[l][c], u1 = P->vsw_cls[l][c + 1];
+      if (u1 == u0) continue;
+      FDA_TRY(m2l_vsw_launch(P->vsw_units[l].p + u0, (size_t)(u1 - u0), P->tc_img.p, P->pair_src.p, P->pair_mid.p,
+                             (const float2*)cout.p, (float2*)mid.p, nrhs, P->n_coef, P->n_mid, 32 << c,
+                             variant == 8 ? 1 : 2, P->tc_err.p, s));
+      *nl += (int64_t)((u1 - u0 + 65534) / 65535);
+    }
+    if (!P->h_dn_units[l].empty()) {
+      FDA_TRY(m2l_tc3_launch(P->dn_units[l].p, P->h_dn_units[l].size(), P->tc_img.p, P->pair_src.p, P->pair_tgt.p,
+                             P->pair_mid.p, (const float2*)cout.p, (float2*)cin.p, (float2*)mid.p, nrhs, P->n_coef,
+                             P->n_mid, P->dn_mt[l], P->dn_maxk[l], P->tc_err.p, s, 4));
+      *nl += (int64_t)((P->h_dn_units[l].size() + 65534) / 65535);
+    }
+    return FDA_OK;
+  }
+  if ((variant == 1 || (variant >= 3 && variant <= 7)) && f32 && !P->h_tc3_units[l][st].empty() && tc3_fits) {
+    const int shape = variant >= 6 ? variant - 2 : (variant >= 3 ? variant - 2 : 0);
     const size_t n3 = P->h_tc3_units[l][st].size(), ns = (size_t)P->tc3_split[l][st];
     // short-K units (single-stage launch), then the rest
     if (ns) {
@@ -724,15 +748,18 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
         FDA_TRY(time_ms(s, [&]() { return m2l_stage<float2>(P, P->op32, P->cout32, P->cin32, P->mid32, l, st, tv, nrhs,
                                                             s, &nl); },
                         3, &t1));
-      int tvb = tv;  // the tensor-core shape kept
-      if (tv == 1)
-        for (int alt = 3; alt <= 5; ++alt) {
+      int tvb = tv;  // the tensor-core variant kept
+      if (tv == 1) {
+        std::vector<int> alts = {3, 4, 5, 6, 7};
+        if (st == 0 && !P->h_vsw_units[l].empty()) alts.push_back(8), alts.push_back(9);
+        for (int alt : alts) {
           double ta = 0;
           FDA_TRY(time_ms(s, [&]() { return m2l_stage<float2>(P, P->op32, P->cout32, P->cin32, P->mid32, l, st, alt,
                                                               nrhs, s, &nl); },
                           3, &ta));
           if (ta < t1) t1 = ta, tvb = alt;
         }
+      }
       R->level[e] = l;
       R->stage[e] = st;
       R->ms_fma[e] = t0;

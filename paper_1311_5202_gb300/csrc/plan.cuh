@@ -99,6 +99,15 @@ struct fda_plan_s {
   int tc3_mt[FDA_MAXLEV][2] = {{0}};  // largest number of 128-row tiles of a unit
   int tc3_maxk[FDA_MAXLEV][2] = {{0}};  // largest complex K of a unit
   int64_t tc3_split[FDA_MAXLEV][2] = {{0}};  // units [0, split) have 2K <= 64
+  // swapped-operand V^ kernel: the mode-1 units of stage 0 ordered by TMEM class (32, 64, 128, 256 columns);
+  // class c covers units [vsw_cls[l][c], vsw_cls[l][c + 1])
+  std::vector<fda::GemmUnit> h_vsw_units[FDA_MAXLEV];
+  fda::DBuf<fda::GemmUnit> vsw_units[FDA_MAXLEV];
+  int64_t vsw_cls[FDA_MAXLEV][5] = {{0}};
+  // the dense (mode 0) units of stage 0, run by the TF32 kernel beside the swapped V^ kernel
+  std::vector<fda::GemmUnit> h_dn_units[FDA_MAXLEV];
+  fda::DBuf<fda::GemmUnit> dn_units[FDA_MAXLEV];
+  int dn_mt[FDA_MAXLEV] = {0}, dn_maxk[FDA_MAXLEV] = {0};
   // M2M / L2L on the same tensor-core kernel: per level (parent level l), units and pair arrays
   std::vector<fda::GemmUnit> h_mm_units[FDA_MAXLEV], h_ll_units[FDA_MAXLEV];
   fda::DBuf<fda::GemmUnit> mm_units[FDA_MAXLEV], ll_units[FDA_MAXLEV];

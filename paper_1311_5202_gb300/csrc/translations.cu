@@ -1275,6 +1275,31 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
           P->tc3_split[l][st] = (int64_t)(mid_it - v.begin());
           FDA_TRY(P->tc3_units[l][st].upload(v));
         }
+      // the same stage-0 units for the swapped V^ kernel (mode 1, by TMEM class of round16(2 r)) and the dense
+      // ones beside it (mode 0)
+      for (int l = 0; l < FDA_MAXLEV; ++l) {
+        auto cls = [](const GemmUnit& u) {
+          const int nm = ((2 * u.M + 15) / 16) * 16;
+          return nm <= 32 ? 0 : nm <= 64 ? 1 : nm <= 128 ? 2 : 3;
+        };
+        std::vector<GemmUnit> byc[4];
+        for (const GemmUnit& u : P->h_tc3_units[l][0]) {
+          if (u.mode == 1 && 2 * u.M <= 256) {
+            byc[cls(u)].push_back(u);
+          } else {
+            P->h_dn_units[l].push_back(u);
+            P->dn_mt[l] = std::max(P->dn_mt[l], (2 * u.M + 127) / 128);
+            P->dn_maxk[l] = std::max(P->dn_maxk[l], u.K);
+          }
+        }
+        for (int c = 0; c < 4; ++c) {
+          P->vsw_cls[l][c] = (int64_t)P->h_vsw_units[l].size();
+          P->h_vsw_units[l].insert(P->h_vsw_units[l].end(), byc[c].begin(), byc[c].end());
+        }
+        P->vsw_cls[l][4] = (int64_t)P->h_vsw_units[l].size();
+        FDA_TRY(P->vsw_units[l].upload(P->h_vsw_units[l]));
+        FDA_TRY(P->dn_units[l].upload(P->h_dn_units[l]));
+      }
     }
   }
 

@@ -114,6 +114,7 @@ _SIGS = [
     ("fda_plan_check", C.c_int, [C.c_void_p]),
     ("fda_wait_selftest", C.c_int, [C.c_double, C.POINTER(C.c_int)]),
     ("fda_autotune", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(fda_tune_report_t)]),
+    ("fda_m2l_force", C.c_int, [C.c_void_p, C.c_int]),
     ("fda_graph_nodes", C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     ("fda_graph_destroy", None, [C.c_void_p]),
     ("fda_corrections_export", C.c_int, [C.c_void_p, _i64p, C.c_int64, C.c_int64, _i64p, _i64p, _dp]),
@@ -322,9 +323,16 @@ def fda_autotune(plan, nrhs=1, stream=None) -> dict:
     R = fda_tune_report_t()
     _check(lib().fda_autotune(plan, int(nrhs), _stream(stream), C.byref(R)))
     rows = [dict(level=R.level[e], stage=R.stage[e], ms_fma=R.ms_fma[e], ms_tensor=R.ms_tensor[e],
-                 chosen=("fma", "tensor", "tensor-alt1", "tensor-alt2", "tensor-alt3")[R.chosen[e]]) for e in range(R.entries)]
+                 chosen=("fma", "tensor", "tensor-alt1", "tensor-alt2", "tensor-alt3", "tensor-bulk",
+                         "tensor-bulk-1stage", "vhat-swapped", "vhat-swapped-2stage")[R.chosen[e]])
+            for e in range(R.entries)]
     return dict(m2l=rows, near_ms=list(R.near_ms), near_rhs_per_pass=R.near_rhs_per_pass,
                 near_split=R.near_split, near_split_ms=list(R.near_split_ms), near_window_ms=R.near_window_ms)
+
+
+def fda_m2l_force(plan, variant):
+    """Force one M2L kernel variant for every (level, stage) (-1: the plan's default; see include/fdbem.h)."""
+    _check(lib().fda_m2l_force(plan, int(variant)))
 
 
 def fda_plan_check(plan):
