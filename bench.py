@@ -264,37 +264,42 @@ def direct_particle_rows(x, n, k, q, rows, alpha, chunk=1 << 16):
 
 def table1_case(N, k, eps, fdbem, torch, dev, stream, tune=True, reps=3):
     """One particle summation of the paper's Table 1 (Sec. 5.1, Eq. sum): unit sphere, ~20 points per
-    wavelength, zero-mean random densities; the FDA product in FP64 and in the mixed form, its phases, and
-    eps_a over 200 random targets against the direct sum (the paper's error measure)."""
+    wavelength, zero-mean random densities; the FDA product in FP64, in the mixed form with TF32 translations
+    and in the mixed form with 3xTF32 translations (FP32 level), its phases, and eps_a over 200 random targets
+    against the direct sum (the paper's error measure)."""
     x, n = inputs.sphere_points(N, 1.0)
     q = inputs.complex_gaussian(N, 20131120)
-    t0 = time.perf_counter()
-    P = fdbem.ParticleSum(x, n, k, eps=eps, leaf_max=64, precision=fdbem.FDA_PREC_FP32, m2l_tensor=1)
-    setup = time.perf_counter() - t0
-    try:
-        if tune:
-            fdbem.fda_autotune(P.plan, 1)
-        info = P.info()
-        qd = torch.from_numpy(q).to(dev)
-        pd = torch.empty_like(qd)
-        rows = inputs.sample_rows(N, 200, 5)
-        t1 = time.perf_counter()
-        po = direct_particle_rows(x, n, k, q, rows, 1j / k)
-        direct_s = time.perf_counter() - t1
-        out = {"N": N, "k": k, "eps": eps, "setup_s": setup, "device_gb": info["device_bytes"] / 1e9,
-               "direct_200_rows_s": direct_s}
-        for prec, name in ((fdbem.FDA_PREC_FP64, "fp64"), (fdbem.FDA_PREC_FP32, "mixed")):
-            fdbem.fda_matvec_ex(P.plan, prec, qd, pd, stream)
-            torch.cuda.synchronize()
-            pa = pd.cpu().numpy()[rows]
-            err = float(np.sqrt(np.sum(np.abs(pa - po) ** 2) / np.sum(np.abs(po) ** 2)))
-            phs = [fdbem.fda_matvec_phases(P.plan, prec, qd, pd, stream) for _ in range(reps)]
-            ph = {key: float(np.median([p_[key] for p_ in phs])) for key in phs[0]}
-            out[name] = {"eps_a": err, "ms": sum(ph.values()), "m2l_ms": ph["m2l"], "up_ms": ph["s2m"] + ph["m2m"],
-                         "down_ms": ph["l2l"] + ph["l2t"], "near_ms": ph["near"]}
-        return out
-    finally:
-        P.close()
+    rows = inputs.sample_rows(N, 200, 5)
+    t1 = time.perf_counter()
+    po = direct_particle_rows(x, n, k, q, rows, 1j / k)
+    out = {"N": N, "k": k, "eps": eps, "direct_200_rows_s": time.perf_counter() - t1}
+    for m2lt, forms in ((1, ((fdbem.FDA_PREC_FP64, "fp64"), (fdbem.FDA_PREC_FP32, "mixed"))),
+                        (3, ((fdbem.FDA_PREC_FP32, "mixed_3xtf32"),))):
+        t0 = time.perf_counter()
+        P = fdbem.ParticleSum(x, n, k, eps=eps, leaf_max=64, precision=fdbem.FDA_PREC_FP32, m2l_tensor=m2lt)
+        setup = time.perf_counter() - t0
+        try:
+            if tune:
+                fdbem.fda_autotune(P.plan, 1)
+            info = P.info()
+            if m2lt == 1:
+                out.update({"setup_s": setup, "device_gb": info["device_bytes"] / 1e9})
+            else:
+                out["device_gb_3xtf32"] = info["device_bytes"] / 1e9
+            qd = torch.from_numpy(q).to(dev)
+            pd = torch.empty_like(qd)
+            for prec, name in forms:
+                fdbem.fda_matvec_ex(P.plan, prec, qd, pd, stream)
+                torch.cuda.synchronize()
+                pa = pd.cpu().numpy()[rows]
+                err = float(np.sqrt(np.sum(np.abs(pa - po) ** 2) / np.sum(np.abs(po) ** 2)))
+                phs = [fdbem.fda_matvec_phases(P.plan, prec, qd, pd, stream) for _ in range(reps)]
+                ph = {key: float(np.median([p_[key] for p_ in phs])) for key in phs[0]}
+                out[name] = {"eps_a": err, "ms": sum(ph.values()), "m2l_ms": ph["m2l"],
+                             "up_ms": ph["s2m"] + ph["m2m"], "down_ms": ph["l2l"] + ph["l2t"], "near_ms": ph["near"]}
+        finally:
+            P.close()
+    return out
 
 
 def run_table1(args):

@@ -163,7 +163,11 @@ typedef struct {
   int m2l_tensor;    /* FP32 plans: M2L (and its low-rank stages) on the tensor cores (tcgen05, TF32):
                         0 = FP32 FMA; 1 = TF32 with operators pre-expanded at plan time into their
                         shared-memory images (extra device memory about twice the FP32 M2L operators;
-                        levels with s > 256 keep the FMA kernel); 2 = 3xTF32 split (FP32-level accuracy) */
+                        levels with s > 256 keep the FMA kernel); 2 = 3xTF32 split with the operators
+                        expanded in the kernel (FP32-level accuracy); 3 = 3xTF32 from pre-expanded TF32 and
+                        remainder images (twice the images of 1; the gathered coefficients are split in
+                        shared memory; three products hi*hi + hi*lo + lo*hi; FP32-level accuracy for
+                        products whose far field dominates) */
   int op;            /* operator of fda_matvec (boundary-element problems; particle problems ignore it):
                         0 = A = 1/2 I + Dbar + alpha Hbar (Eq. bm, the unknown u); 1 = B = Sbar + alpha Mbar
                         - alpha/2 I, which maps Neumann data q to the radiation right-hand side of Eq. bm
@@ -394,7 +398,8 @@ int fda_wait_selftest(double limit_ms, int* timed_out);
  * 2..5: TF32 with the pre-expanded operator image of the m2l_tensor = 1 form (M = min(256, K), P = 100),
  * in its default tile shape (2) or the autotuner's alternatives (3, 4, 5); 6, 7: the same kernel with the
  * bulk-reduction epilogue (default and single-stage shape); 8, 9: the swapped-operand V^ kernel (one and
- * two stages; M = min(100, K), P = 100, results stored as the low-rank intermediate).
+ * two stages; M = min(100, K), P = 100, results stored as the low-rank intermediate); 10, 11: 3xTF32 from the
+ * TF32 and remainder images of the m2l_tensor = 3 form (atomic and bulk-reduction epilogue).
  * *max_rel_err is the largest entrywise error relative to the sum of |a||x| over the row, *wait_failed is 1
  * when a bounded device wait gave up. Synchronous. */
 int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_failed);

@@ -228,7 +228,7 @@ int fda_precompute_translations(fda_tree_t* tree, const fda_config_t* cfg, fda_p
   ARG_CHECK(cfg->eps > 0 && cfg->eps < 1, "eps must lie in (0, 1)");
   ARG_CHECK(cfg->precision == FDA_PREC_FP64 || cfg->precision == FDA_PREC_FP32, "unknown precision");
   ARG_CHECK(cfg->nrhs_max >= 1 && cfg->nrhs_max <= 4096, "nrhs_max must lie in [1, 4096]");
-  ARG_CHECK(cfg->m2l_tensor >= 0 && cfg->m2l_tensor <= 2, "m2l_tensor must be 0, 1 or 2");
+  ARG_CHECK(cfg->m2l_tensor >= 0 && cfg->m2l_tensor <= 3, "m2l_tensor must be 0, 1, 2 or 3");
   ARG_CHECK(cfg->op == 0 || cfg->op == 1, "op must be 0 or 1");
   ARG_CHECK(cfg->near_split >= 0 && cfg->near_split <= 2, "near_split must be 0, 1 or 2");
   ARG_CHECK(tree, "tree is NULL");
@@ -282,8 +282,12 @@ int fda_m2l_force(fda_plan_t* plan, int variant) {
     set_error("variant 2 needs a plan built with m2l_tensor = 2");
     return FDA_E_STATE;
   }
-  if (variant != 2 && variant > 0 && plan->cfg.m2l_tensor != 1) {
-    set_error("variants 1 and 3 to 9 need a plan built with m2l_tensor = 1");
+  if (variant != 2 && variant > 0 && plan->cfg.m2l_tensor != 1 && plan->cfg.m2l_tensor != 3) {
+    set_error("variants 1 and 3 to 9 need a plan built with m2l_tensor = 1 or 3");
+    return FDA_E_STATE;
+  }
+  if (variant >= 3 && plan->cfg.m2l_tensor == 3 && variant != 6 && variant != 7) {
+    set_error("a 3xTF32 plan (m2l_tensor = 3) runs variants 1, 6 and 7 only");
     return FDA_E_STATE;
   }
   for (int l = 0; l < FDA_MAXLEV; ++l)

@@ -16,14 +16,6 @@
 
 namespace fda {
 
-struct TcImgJob {
-  const double2* src;  // the M x K operator: src[i + k ld], or src[k + i ld] when trans
-  int M, K;
-  int64_t img_off;     // first float of the image
-  int64_t ld;
-  int trans;
-};
-
 #define TC_M 128       // real rows per tile (64 complex rows)
 #define TC_N 64        // real GEMM columns per tile (pairs x RHS)
 #define TC_KC 32       // real K per stage (16 complex)
@@ -397,12 +389,6 @@ int m2l_tc_launch(const GemmUnit* units, size_t nunits, const float2* poolK, con
 
 __device__ __forceinline__ int tc3_ng(int M, int mt) { return (min(128, 2 * M - 128 * mt) + 7) / 8; }
 
-int64_t tc3_image_floats(int M, int K) {
-  const int MT = (2 * M + 127) / 128, nk = (2 * K + 31) / 32;
-  const int last = (std::min(128, 2 * M - 128 * (MT - 1)) + 7) / 8;
-  return (int64_t)(MT - 1) * nk * 16 * 256 + (int64_t)nk * last * 256;
-}
-
 static __global__ void k_tc3_image(const TcImgJob* jobs, float* img) {
   const TcImgJob J = jobs[blockIdx.y];
   const int MT = (2 * J.M + 127) / 128, nk = (2 * J.K + 31) / 32;
@@ -420,13 +406,15 @@ static __global__ void k_tc3_image(const TcImgJob* jobs, float* img) {
     const int kk = (within >> 5) * 4 + (within & 3);
     const int j = 128 * mt + row, kr = 32 * kc + kk;
     const int i = j >> 1, kx = kr >> 1;
-    float val = 0.f;
+    float val = 0.f, vlo = 0.f;
     if (i < J.M && kx < J.K) {
       const double2 a = J.trans ? J.src[kx + (int64_t)i * J.ld] : J.src[i + (int64_t)kx * J.ld];
       const double v = (j & 1) == 0 ? ((kr & 1) == 0 ? a.x : -a.y) : ((kr & 1) == 0 ? a.y : a.x);
       val = tf32_round((float)v);
+      vlo = tf32_round((float)(v - (double)val));
     }
     img[J.img_off + q] = val;
+    if (J.split) img[J.img_off + total + q] = vlo;  // the remainder image follows the TF32 image
   }
 }
 
@@ -478,10 +466,13 @@ __device__ __forceinline__ float2 tc_pair(const float* v, int c, int part) {
   return part == 0 ? make_float2(v[c], recv) : make_float2(recv, v[c + 1]);
 }
 
-template <int MTC, int N, int NST>
+template <int MTC, int N, int NST, int SPLIT = 0>
 struct Tc3Smem {
   alignas(1024) float a[NST][MTC][128 * TC3_KC];
   alignas(1024) float b[NST][N * TC3_KC];
+  // 3xTF32: the operator remainders and the remainders of the gathered coefficients
+  alignas(1024) float alo[SPLIT ? NST : 1][SPLIT ? MTC : 1][SPLIT ? 128 * TC3_KC : 256];
+  alignas(1024) float blo[SPLIT ? NST : 1][SPLIT ? N * TC3_KC : 256];
   alignas(8) uint64_t afull[NST];
   uint64_t mdone[NST];
   uint32_t tmem;
@@ -493,12 +484,12 @@ struct Tc3Smem {
 // thread 0 copies the operator tiles with cp.async.bulk while all threads gather the pairs' coefficients
 // with 16-byte cp.async (two complex values; 8-byte copies for a source off a 16-byte boundary); NST chunks
 // in flight.
-template <int MTC, int N, int NST, int BULK>
+template <int MTC, int N, int NST, int BULK, int SPLIT>
 static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units, const float* img,
                                                           const int64_t* psrc, const int64_t* ptgt,
                                                           const int64_t* pmid, const float2* cout, float2* cin,
                                                           float2* mid, int nrhs, int64_t ldc, int64_t ldm, int* err) {
-  typedef Tc3Smem<MTC, N, NST> Sm;
+  typedef Tc3Smem<MTC, N, NST, SPLIT> Sm;
   extern __shared__ unsigned char smem_raw[];
   Sm& S = *reinterpret_cast<Sm*>((((uintptr_t)smem_raw) + 1023) & ~(uintptr_t)1023);
   constexpr int TCOLS = MTC * N < 32 ? 32 : MTC * N;
@@ -512,6 +503,7 @@ static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units
   const int MT = min(MTC, (2 * U.M + 127) / 128);
   const int nk = (2 * U.K + TC3_KC - 1) / TC3_KC;
   const float* A = img + U.a_off;
+  const float* Alo = A + (SPLIT ? tc3_image_floats(U.M, U.K) : 0);  // remainder image (3xTF32)
   if (w == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
                  "r"(TCOLS));
@@ -549,11 +541,12 @@ static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units
     if (t == 0) {
       uint32_t bytes = 0;
       for (int mt = 0; mt < MT; ++mt) bytes += (uint32_t)tc3_ng(U.M, mt) * 1024u;
-      tc3_expect_tx(&S.afull[s], bytes);
+      tc3_expect_tx(&S.afull[s], SPLIT ? 2 * bytes : bytes);
       for (int mt = 0; mt < MT; ++mt) {
         const int ng = tc3_ng(U.M, mt);
-        tc3_bulk(S.a[s][mt], A + (int64_t)16 * mt * nk * 256 + (int64_t)kc * ng * 256, (uint32_t)ng * 1024u,
-                 &S.afull[s]);
+        const int64_t o = (int64_t)16 * mt * nk * 256 + (int64_t)kc * ng * 256;
+        tc3_bulk(S.a[s][mt], A + o, (uint32_t)ng * 1024u, &S.afull[s]);
+        if (SPLIT) tc3_bulk(S.alo[s][mt], Alo + o, (uint32_t)ng * 1024u, &S.afull[s]);
       }
     }
     const uint32_t bbase = smem_u32(S.b[s]);
@@ -609,6 +602,19 @@ static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units
         tc3_commit_group();
       }
       tc3_wait_group<D>();  // this thread's copies of chunk kc have landed
+      if (SPLIT) {
+        // every thread splits the segments it gathered into a TF32 part (in place) and its remainder
+        const int s = kc % NST;
+        for (int r = w; r < (N / 8) * 2; r += TC3_NT / 32) {
+          const int n = (r >> 1) * 8 + (lane >> 2), j = (r & 1) * 8 + 2 * (lane & 3);
+          if (S.sbase[n] < 0) continue;
+          const uint32_t off = kmaj_off(n, 2 * j, TC3_KC) / 4;
+          float4 v = *reinterpret_cast<float4*>(&S.b[s][off]);
+          float4 h = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
+          *reinterpret_cast<float4*>(&S.b[s][off]) = h;
+          *reinterpret_cast<float4*>(&S.blo[s][off]) = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+        }
+      }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       if (t == 0) {
@@ -623,7 +629,16 @@ static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units
             if (kc * TC3_KC + s8 * 8 >= 2 * U.K) break;  // K steps past the operator hold only zeros
             const uint64_t ad = smem_desc(smem_u32(S.a[s][mt]) + s8 * 256, lbo, sbo);
             const uint64_t bd = smem_desc(smem_u32(S.b[s]) + s8 * 256, lbo, sbo);
-            tc_mma(tmem + N * mt, ad, bd, IDESC, (kc > 0 || s8 > 0) ? 1 : 0);
+            const int acc = (kc > 0 || s8 > 0) ? 1 : 0;
+            if (SPLIT) {  // the small products first, then hi * hi
+              const uint64_t adl = smem_desc(smem_u32(S.alo[s][mt]) + s8 * 256, lbo, sbo);
+              const uint64_t bdl = smem_desc(smem_u32(S.blo[s]) + s8 * 256, lbo, sbo);
+              tc_mma(tmem + N * mt, adl, bd, IDESC, acc);
+              tc_mma(tmem + N * mt, ad, bdl, IDESC, 1);
+              tc_mma(tmem + N * mt, ad, bd, IDESC, 1);
+            } else {
+              tc_mma(tmem + N * mt, ad, bd, IDESC, acc);
+            }
           }
         }
         tc_commit(&S.mdone[s]);
@@ -712,21 +727,21 @@ static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units
   }
 }
 
-template <int MTC, int N, int NST, int BULK>
+template <int MTC, int N, int NST, int BULK, int SPLIT = 0>
 static int tc3_launch_t(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc,
                         const int64_t* ptgt, const int64_t* pmid, const float2* cout, float2* cin, float2* mid,
                         int nrhs, int64_t ldc, int64_t ldm, int* err, cudaStream_t s) {
-  const size_t smem = sizeof(Tc3Smem<MTC, N, NST>) + 1024;
+  const size_t smem = sizeof(Tc3Smem<MTC, N, NST, SPLIT>) + 1024;
   static bool attr = false;
   if (!attr) {
-    FDA_CUDA(cudaFuncSetAttribute(k_m2l_tc3<MTC, N, NST, BULK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    FDA_CUDA(cudaFuncSetAttribute(k_m2l_tc3<MTC, N, NST, BULK, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
     attr = true;
   }
   for (size_t u0 = 0; u0 < nunits; u0 += 65535) {
     unsigned n = (unsigned)std::min<size_t>(65535, nunits - u0);
-    k_m2l_tc3<MTC, N, NST, BULK><<<n, TC3_NT, smem, s>>>(units + u0, img, psrc, ptgt, pmid, cout, cin, mid, nrhs,
-                                                         ldc, ldm, err);
+    k_m2l_tc3<MTC, N, NST, BULK, SPLIT><<<n, TC3_NT, smem, s>>>(units + u0, img, psrc, ptgt, pmid, cout, cin, mid,
+                                                                nrhs, ldc, ldm, err);
     FDA_LAUNCH_CHECK();
   }
   return FDA_OK;
@@ -744,6 +759,19 @@ int m2l_tc3_launch(const GemmUnit* units, size_t nunits, const float* img, const
     return FDA_E_INVALID_ARG;
   }
   if (nunits == 0) return FDA_OK;
+  if (shape >= 6) {  // 3xTF32 from the TF32 and remainder images, single stage: 6 atomics, 7 bulk reductions
+#define TC3S(M_, N_, B_) \
+  return tc3_launch_t<M_, N_, 1, B_, 1>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, ldc, ldm, err, s)
+    if (shape == 6) {
+      if (max_mt == 1) TC3S(1, 128, 0);
+      if (max_mt == 2) TC3S(2, 64, 0);
+      TC3S(4, 64, 0);
+    }
+    if (max_mt == 1) TC3S(1, 128, 1);
+    if (max_mt == 2) TC3S(2, 64, 1);
+    TC3S(4, 64, 1);
+#undef TC3S
+  }
   if (shape == 4 || shape == 5) {  // bulk-reduction epilogue: default shape (4) or single-stage (5)
 #define TC3B(M_, N_, S_) \
   return tc3_launch_t<M_, N_, S_, 1>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, ldc, ldm, err, s)
@@ -1051,15 +1079,18 @@ static __global__ void k_wait_probe(uint64_t limit_ns, int* timed_out) {
 // host product of the same FP32 data. split 0: TF32 (M = 64, P = 64); 1: 3xTF32 split (M = 64, P = 64);
 // 2..7: TF32 with the pre-expanded operator image (M = min(256, K), P = 100), tile shape split - 2 (6 and 7:
 // the bulk-reduction epilogue); 8, 9: the swapped-operand V^ kernel with one or two stages (M = min(100, K),
-// P = 100, results stored into an intermediate with even-padded vectors as the low-rank stage does).
+// P = 100, results stored into an intermediate with even-padded vectors as the low-rank stage does);
+// 10, 11: 3xTF32 from the TF32 and remainder images (atomics, bulk reductions).
 extern "C" int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_failed) {
-  if (K < 1 || K > 1024 || split < 0 || split > 9 || !max_rel_err || !wait_failed) {
+  if (K < 1 || K > 1024 || split < 0 || split > 11 || !max_rel_err || !wait_failed) {
     set_error("bad arguments");
     return FDA_E_INVALID_ARG;
   }
-  const bool vsw = split >= 8;
+  const bool vsw = split == 8 || split == 9;
+  const bool x3 = split >= 10;
   // the bulk-reduction epilogue adds whole 16-byte granules: even row counts (as every plan has)
-  const int Mb = split == 6 || split == 7 ? std::min(256, (K + 1) & ~1) : std::min(256, K);
+  const bool bulk = split == 6 || split == 7 || split == 11;
+  const int Mb = bulk ? std::min(256, (K + 1) & ~1) : std::min(256, K);
   const int M = vsw ? std::min(100, K) : (split >= 2 ? Mb : 64), P = split >= 2 ? 100 : 64;
   const int Mp = vsw ? (M + 1) & ~1 : M;  // stride of the stored vectors
   std::vector<float2> hA((size_t)M * K), hX((size_t)K * P);
@@ -1093,8 +1124,8 @@ extern "C" int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_
     DBuf<double2> dA64;
     DBuf<float> img;
     FDA_TRY(dA64.upload(hA64));
-    FDA_TRY(img.alloc((size_t)tc3_image_floats(M, K)));
-    FDA_TRY(tc3_build_images({TcImgJob{dA64.p, M, K, 0, M, 0}}, img.p));
+    FDA_TRY(img.alloc((size_t)tc3_image_floats(M, K) * (x3 ? 2 : 1)));
+    FDA_TRY(tc3_build_images({TcImgJob{dA64.p, M, K, 0, M, 0, x3 ? 1 : 0}}, img.p));
     GemmUnit u{0, M, K, 0, P, 0, vsw ? 1 : 0, 0};
     FDA_TRY(du.upload(&u, 1));
     if (vsw) {
@@ -1105,7 +1136,7 @@ extern "C" int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_
       FDA_CUDA(cudaMemcpy(dY.p, dmid.p, sizeof(float2) * P * Mp, cudaMemcpyDeviceToDevice));
     } else {
       FDA_TRY(m2l_tc3_launch(du.p, 1, img.p, src.p, tgt.p, pm.p, dX.p, dY.p, dmid.p, 1, 0, 0, (2 * M + 127) / 128,
-                             K, err.p, 0, split - 2));
+                             K, err.p, 0, x3 ? split - 4 : split - 2));
     }
     FDA_CUDA(cudaDeviceSynchronize());
   } else {

@@ -445,7 +445,9 @@ static __global__ void __launch_bounds__(256) k_m2l(const GemmUnit* units, const
 // the low-rank units and variant 6 for the dense ones (6 to 9 are picked by the autotuner only)
 int m2l_variant(const fda_plan_s* P, int l, int st) {
   if (P->m2l_choice[l][st] >= 0) return P->m2l_choice[l][st];
-  if (P->cfg.m2l_tensor == 1 && !P->h_tc3_units[l][st].empty() && P->tc3_mt[l][st] <= 4) return 1;
+  if ((P->cfg.m2l_tensor == 1 || P->cfg.m2l_tensor == 3) && !P->h_tc3_units[l][st].empty() &&
+      P->tc3_mt[l][st] <= 4)
+    return 1;
   if (P->cfg.m2l_tensor == 2 && !P->h_tc_units[l][st].empty()) return 2;
   return 0;
 }
@@ -456,7 +458,8 @@ int m2l_stage(fda_plan_s* P, RunOps<C>& op, DBuf<C>& cout, DBuf<C>& cin, DBuf<C>
   const bool f32 = std::is_same<C, float2>::value;
   // the image kernels cover at most 4 row tiles (256 complex rows): a forced variant falls back to FMA beyond
   const bool tc3_fits = P->tc3_mt[l][st] <= 4;
-  if ((variant == 8 || variant == 9) && f32 && st == 0 && !P->h_vsw_units[l].empty() && P->dn_mt[l] <= 4) {
+  const bool x3 = P->cfg.m2l_tensor == 3;  // 3xTF32 images: the split kernel for every tensor-core variant
+  if ((variant == 8 || variant == 9) && f32 && !x3 && st == 0 && !P->h_vsw_units[l].empty() && P->dn_mt[l] <= 4) {
     for (int c = 0; c < 4; ++c) {
       const int64_t u0 = P->vsw_cls[l][c], u1 = P->vsw_cls[l][c + 1];
       if (u1 == u0) continue;
@@ -474,7 +477,7 @@ int m2l_stage(fda_plan_s* P, RunOps<C>& op, DBuf<C>& cout, DBuf<C>& cin, DBuf<C>
     return FDA_OK;
   }
   if ((variant == 1 || (variant >= 3 && variant <= 7)) && f32 && !P->h_tc3_units[l][st].empty() && tc3_fits) {
-    const int shape = variant >= 6 ? variant - 2 : (variant >= 3 ? variant - 2 : 0);
+    const int shape = x3 ? (variant == 7 ? 7 : 6) : (variant >= 3 ? variant - 2 : 0);
     const size_t n3 = P->h_tc3_units[l][st].size(), ns = (size_t)P->tc3_split[l][st];
     // short-K units (single-stage launch), then the rest
     if (ns) {
@@ -581,7 +584,8 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
     const size_t SMEM = 40960;
     auto chunk = [&](size_t rows) { return (int)std::max<size_t>(1, std::min<size_t>(nrhs, SMEM / (rows * sizeof(C)))); };
     // the grouped tensor-core M2M accumulates into the parents: clear the outgoing coefficients first
-    const bool tc_mm = std::is_same<C, float2>::value && P->cfg.m2l_tensor == 1;
+    const bool tc_mm = std::is_same<C, float2>::value && (P->cfg.m2l_tensor == 1 || P->cfg.m2l_tensor == 3);
+    const int mm_shape = P->cfg.m2l_tensor == 3 ? 6 : 0;
     if (tc_mm) FDA_TRY(zero_parent_coefs<C>(P, cout, nrhs, s));
     // S2M
     if (!P->h_leaves.empty()) {
@@ -602,7 +606,7 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
       if (tc_mm && !P->h_mm_units[l].empty()) {
         FDA_TRY(m2l_tc3_launch(P->mm_units[l].p, P->h_mm_units[l].size(), P->tc_img.p, P->mm_src.p, P->mm_tgt.p,
                                P->mm_src.p, (const float2*)cout.p, (float2*)cout.p, (float2*)cout.p, nrhs, P->n_coef,
-                               P->n_coef, P->mm_mt[l], P->lev[l + 1].s, P->tc_err.p, s, 0));
+                               P->n_coef, P->mm_mt[l], P->lev[l + 1].s, P->tc_err.p, s, mm_shape));
         ++nl;
         continue;
       }
@@ -633,7 +637,7 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
       if (tc_mm && !P->h_ll_units[l].empty()) {
         FDA_TRY(m2l_tc3_launch(P->ll_units[l].p, P->h_ll_units[l].size(), P->tc_img.p, P->ll_src.p, P->ll_tgt.p,
                                P->ll_src.p, (const float2*)cin.p, (float2*)cin.p, (float2*)cin.p, nrhs, P->n_coef,
-                               P->n_coef, P->ll_mt[l], P->lev[l].s, P->tc_err.p, s, 0));
+                               P->n_coef, P->ll_mt[l], P->lev[l].s, P->tc_err.p, s, mm_shape));
         ++nl;
         continue;
       }
@@ -751,7 +755,8 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
       int tvb = tv;  // the tensor-core variant kept
       if (tv == 1) {
         std::vector<int> alts = {3, 4, 5, 6, 7};
-        if (st == 0 && !P->h_vsw_units[l].empty()) alts.push_back(8), alts.push_back(9);
+        if (P->cfg.m2l_tensor == 3) alts = {7};  // 3xTF32: atomics (1) or bulk reductions (7)
+        else if (st == 0 && !P->h_vsw_units[l].empty()) alts.push_back(8), alts.push_back(9);
         for (int alt : alts) {
           double ta = 0;
           FDA_TRY(time_ms(s, [&]() { return m2l_stage<float2>(P, P->op32, P->cout32, P->cin32, P->mid32, l, st, alt,

@@ -30,6 +30,25 @@ struct LevelOps {
   int64_t box_begin = 0, box_end = 0;  // boxes of this level
 };
 
+// One operator expanded into the tensor-core image (see m2l_tc.cu): the TF32 image, followed for split = 1
+// by the image of the TF32 remainders (value - TF32(value)), so that three products hi*hi + hi*lo + lo*hi
+// keep FP32 accuracy.
+struct TcImgJob {
+  const double2* src;  // the M x K operator: src[i + k ld], or src[k + i ld] when trans
+  int M, K;
+  int64_t img_off;     // first float of the image
+  int64_t ld;
+  int trans;
+  int split;
+};
+__host__ __device__ inline int64_t tc3_image_floats(int M, int K) {
+  const int MT = (2 * M + 127) / 128, nk = (2 * K + 31) / 32;
+  const int rows_last = 2 * M - 128 * (MT - 1);
+  const int last = ((rows_last < 128 ? rows_last : 128) + 7) / 8;
+  return (int64_t)(MT - 1) * nk * 16 * 256 + (int64_t)nk * last * 256;
+}
+int tc3_build_images(const std::vector<TcImgJob>& jobs, float* img);
+
 // A unit of grouped gather-GEMM-scatter work: Y[:, tgt(p)] (+)= A X[:, src(p)] for pairs p.
 struct GemmUnit {
   int64_t a_off;      // offset of A (M x K, column-major, lda = M) in the matrix pool

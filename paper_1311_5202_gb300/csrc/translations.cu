@@ -49,15 +49,6 @@ struct SVDJob {
   int* sweeps;
 };
 int pivoted_qr_batched(const std::vector<QRJob>& jobs, cudaStream_t s);
-struct TcImgJob {
-  const double2* src;  // the M x K operator: src[i + k ld], or src[k + i ld] when trans
-  int M, K;
-  int64_t img_off;     // first float of the image
-  int64_t ld;
-  int trans;
-};
-int64_t tc3_image_floats(int M, int K);
-int tc3_build_images(const std::vector<TcImgJob>& jobs, float* img);
 int form_q_batched(const std::vector<QFormJob>& jobs, cudaStream_t s);
 int jacobi_svd_batched(const std::vector<SVDJob>& jobs, cudaStream_t s);
 
@@ -1165,13 +1156,14 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
       }
     // tensor-core (TF32) form: every operator pre-expanded into its shared-memory image, units of up to
     // 128 pairs that cover all output rows
-    if (P->cfg.m2l_tensor == 1 && P->cfg.precision == FDA_PREC_FP32) {
+    if ((P->cfg.m2l_tensor == 1 || P->cfg.m2l_tensor == 3) && P->cfg.precision == FDA_PREC_FP32) {
       std::vector<TcImgJob> jobs;
       int64_t img_tot = 0;
+      const int split = P->cfg.m2l_tensor == 3 ? 1 : 0;  // 3xTF32: each image followed by its remainders
       auto add_img = [&](const double2* src, int M, int K, int64_t ld, int trans) {
         int64_t off = img_tot;
-        jobs.push_back({src, M, K, off, ld, trans});
-        img_tot += tc3_image_floats(M, K);
+        jobs.push_back({src, M, K, off, ld, trans, split});
+        img_tot += tc3_image_floats(M, K) * (split ? 2 : 1);
         return off;
       };
       std::vector<std::vector<std::array<int64_t, 3>>> img_of(FDA_MAXLEV);  // (k, v, u) image offsets

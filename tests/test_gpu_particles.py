@@ -67,6 +67,16 @@ def test_particle_sum_mixed_tensor_core():
     assert err < 2.0 * 2.0 ** -10, err
 
 
+def test_particle_sum_mixed_3xtf32_meets_paper_error():
+    """The mixed form with 3xTF32 translations (m2l_tensor = 3: TF32 and remainder operator images, gathered
+    coefficients split in shared memory, three products per K step): FP32-level translations, so eps_a meets
+    the paper's Table 1 bar at eps = 1e-4 (3.7e-4) as the FP64 form does."""
+    _need_gpu()
+    N, k = inputs.TABLE1[1]
+    err, _ = _eps_a(N, k, 1e-4, fdbem.FDA_PREC_FP32, m2l_tensor=3)
+    assert err < 3.7e-4, err
+
+
 def test_particle_problem_refuses_boundary_element_only_calls():
     _need_gpu()
     x, n = inputs.sphere_points(5000, 1.0)
