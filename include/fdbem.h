@@ -172,13 +172,17 @@ typedef struct {
                         0 = A = 1/2 I + Dbar + alpha Hbar (Eq. bm, the unknown u); 1 = B = Sbar + alpha Mbar
                         - alpha/2 I, which maps Neumann data q to the radiation right-hand side of Eq. bm
                         (same tree and translations; S2M from monopole sources, near field and local
-                        corrections of G + alpha dG/dn_x) */
+                        corrections of G + alpha dG/dn_x); 2 = A + gamma B, the operator of Eq. bm under
+                        Robin data a u + b q = g with gamma = a/b (q = (g - a u)/b eliminated; the right-hand
+                        side is u_inc + alpha q_inc + (1/b) B g): S2M from dipole + gamma monopole sources,
+                        near field and corrections of both kernel pairs, diagonal 1/2 - gamma alpha/2 */
   int near_split;    /* near-field schedule until fda_autotune chooses: 0 = the correction entries outside the
                         direct blocks are applied inside the near-field stream, per target leaf; 1 = by their
                         own CSR kernel (one warp per row) before the stream; 2 = as 1, with the stream's
                         density windows double-buffered for one right-hand side (the next window's densities
                         copied while the current one is used). Same sums, other order. */
   int reserved[2];
+  double gamma_re, gamma_im;  /* op = 2: the Robin coefficient gamma = a/b (ignored otherwise) */
 } fda_config_t;
 
 /* Build every translation operator and the near-field matrices on the GPU (FP64 masters):
@@ -283,7 +287,8 @@ typedef struct {
   double flops_m2m_l2l;     /* algorithmic flops of M2M + L2L per RHS */
   double flops_near;        /* 8 flops per stored complex entry per RHS */
   double device_bytes;      /* device memory held by the plan */
-  double setup_ms[8];       /* point selection + SVD, -, S~T~, M~, K~, low-rank, corrections, near blocks */
+  double setup_ms[8];       /* point selection, SVD of R (Eq. svdr), S~T~, M~, K~, low-rank, corrections,
+                               near blocks */
   int64_t launches_per_matvec; /* kernels launched by the last fda_matvec */
   double m2l_flops_lev[32];    /* algorithmic M2L flops per level per RHS */
   double m2l_op_bytes_lev[32]; /* FP64 bytes of the stored M2L operators per level (K~, or U^ and V^) */

@@ -254,6 +254,21 @@ def pulsating_sphere(k, a):
     return a / (1.0 - 1j * k * a)
 
 
+def robin_rows(nodes, elems, k, x, rows, gamma, alpha=None):
+    """Rows of the Burton-Miller operator under Robin data a u + b q = g (Eq. bm, Sec. 2.2, q = (g - a u)/b
+    eliminated): (A + gamma B) x with gamma = a/b, A = 1/2 I + Dbar + alpha Hbar, B = Sbar + alpha Mbar - alpha/2 I."""
+    a = 1j / k if alpha is None else complex(alpha)
+    g = complex(gamma)
+    return rows4(nodes, elems, k, x, rows, c=0.5 - 0.5 * a * g, b_s=g, b_d=1.0, b_m=g * a, b_h=a)
+
+
+def robin_sphere(k, a, ac, bc, g):
+    """Surface potential of the radiating monopole u = C e^{ikr}/r outside a sphere of radius a that meets the
+    Robin condition ac u + bc du/dn = g with constant g (n into the body, so du/dn = -du/dr = u (1/a - ik)):
+    u = g / (ac + bc (1/a - ik)). With ac = 0, bc = 1 (q = g = 1) it is the pulsating sphere of Sec. 5.2."""
+    return complex(g) / (complex(ac) + complex(bc) * (1.0 / a - 1j * k))
+
+
 def dense_matrix(nodes, elems, k, c=0.5, beta_d=1.0, beta_h=None):
     nodes, elems = _mesh_args(nodes, elems)
     if beta_h is None:

@@ -229,7 +229,9 @@ int fda_precompute_translations(fda_tree_t* tree, const fda_config_t* cfg, fda_p
   ARG_CHECK(cfg->precision == FDA_PREC_FP64 || cfg->precision == FDA_PREC_FP32, "unknown precision");
   ARG_CHECK(cfg->nrhs_max >= 1 && cfg->nrhs_max <= 4096, "nrhs_max must lie in [1, 4096]");
   ARG_CHECK(cfg->m2l_tensor >= 0 && cfg->m2l_tensor <= 3, "m2l_tensor must be 0, 1, 2 or 3");
-  ARG_CHECK(cfg->op == 0 || cfg->op == 1, "op must be 0 or 1");
+  ARG_CHECK(cfg->op >= 0 && cfg->op <= 2, "op must be 0, 1 or 2");
+  ARG_CHECK(cfg->op != 2 || (std::isfinite(cfg->gamma_re) && std::isfinite(cfg->gamma_im)),
+            "op = 2 needs a finite Robin coefficient gamma");
   ARG_CHECK(cfg->near_split >= 0 && cfg->near_split <= 2, "near_split must be 0, 1 or 2");
   ARG_CHECK(tree, "tree is NULL");
   fda_plan_s* P = new (std::nothrow) fda_plan_s();
@@ -475,7 +477,8 @@ int fda_corrections_export(const fda_plan_t* P, const int64_t* rows, int64_t nro
   DBuf<int64_t> di_ptr;
   DBuf<int32_t> di_cols;
   DBuf<double2> corr;
-  FDA_TRY(near_corrections(P->prob, di_ptr, di_cols, corr, nullptr, P->cfg.op));
+  FDA_TRY(near_corrections(P->prob, di_ptr, di_cols, corr, nullptr, P->cfg.op,
+                           make_double2(P->cfg.gamma_re, P->cfg.gamma_im)));
   for (int64_t r = 0; r < nrows; ++r) {
     int64_t rp[2];
     FDA_CUDA(cudaMemcpy(rp, di_ptr.p + rows[r], 2 * sizeof(int64_t), cudaMemcpyDeviceToHost));

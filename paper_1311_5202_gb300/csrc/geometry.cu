@@ -694,9 +694,28 @@ static __global__ void k_item_rows(const int64_t* rowptr, int64_t N, int64_t* it
   for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) item_row[p] = i;
 }
 
-// Corrections in user DOF order: CSR with one entry per (row, element in D_i, local point j).
+static __global__ void k_axpy_c(double2* y, const double2* x, double2 a, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = cadd(y[i], cmul(a, x[i]));
+}
+
+// Corrections in user DOF order: CSR with one entry per (row, element in D_i, local point j). op = 2 (Robin
+// data): the corrections of operator A plus gamma times those of operator B (same local regions).
 int near_corrections(bm_problem_s* P, DBuf<int64_t>& di_ptr, DBuf<int32_t>& di_cols, DBuf<double2>& corr,
-                     double* ms, int op) {
+                     double* ms, int op, double2 gamma) {
+  if (op == 2) {
+    DBuf<int64_t> p2;
+    DBuf<int32_t> c2;
+    DBuf<double2> corr_b;
+    double ms_a = 0, ms_b = 0;
+    FDA_TRY(near_corrections(P, di_ptr, di_cols, corr, &ms_a, 0, gamma));
+    FDA_TRY(near_corrections(P, p2, c2, corr_b, &ms_b, 1, gamma));
+    k_axpy_c<<<cdiv((int64_t)corr.n, 256), 256>>>(corr.p, corr_b.p, gamma, (int64_t)corr.n);
+    FDA_LAUNCH_CHECK();
+    FDA_CUDA(cudaDeviceSynchronize());
+    if (ms) *ms = ms_a + ms_b;
+    return FDA_OK;
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);

@@ -273,6 +273,31 @@ int form_q_batched(const std::vector<QFormJob>& jobs, cudaStream_t s) {
   return FDA_OK;
 }
 
+// ------------------------------------------------------------------ Gaussian sketch matrices
+// Entry q of a sketch is a standard normal variate (imaginary part 0) from a counter-based generator: two
+// SplitMix64 outputs (Steele, Lea and Flood, 2014) of the counter 2q and 2q + 1 offset by the seed, mapped
+// to (0, 1) and through the Box-Muller transform.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+static __global__ void k_gaussian(double2* out, int64_t n, uint64_t seed) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t a = splitmix64(seed + 0x9E3779B97F4A7C15ull * (uint64_t)(2 * q));
+    const uint64_t b = splitmix64(seed + 0x9E3779B97F4A7C15ull * (uint64_t)(2 * q + 1));
+    const double u1 = ((double)(a >> 11) + 0.5) * 0x1.0p-53, u2 = ((double)(b >> 11) + 0.5) * 0x1.0p-53;
+    out[q] = make_double2(sqrt(-2.0 * log(u1)) * cospi(2.0 * u2), 0.0);
+  }
+}
+int gaussian_fill(double2* out, int64_t n, uint64_t seed) {
+  if (n <= 0) return FDA_OK;
+  k_gaussian<<<(unsigned)std::min<int64_t>(4096, (n + 255) / 256), 256>>>(out, n, seed);
+  FDA_LAUNCH_CHECK();
+  return FDA_OK;
+}
+
 // ------------------------------------------------------------------ one-sided Jacobi SVD
 // A (m x n) -> columns become U_j sigma_j; V (n x n) accumulates the rotations. After the sweeps the
 // singular values are the column norms (sorted on the host).
@@ -284,78 +309,107 @@ struct SVDJob {
   int* sweeps;
 };
 
-#define SVD_NT 512
-static __global__ void __launch_bounds__(SVD_NT) k_jacobi_svd(const SVDJob* jobs) {
-  const SVDJob J = jobs[blockIdx.x];
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = SVD_NT / 32;
-  const int m = J.m, n = J.n;
-  __shared__ int s_rot;
-  for (int c = 0; c < n; ++c)
-    for (int i = t; i < n; i += SVD_NT) J.V[i + (int64_t)c * J.ldv] = make_double2(i == c ? 1.0 : 0.0, 0);
-  const int np = n + (n & 1);
-  int sweep = 0;
-  for (; sweep < 40; ++sweep) {
-    if (t == 0) s_rot = 0;
-    __syncthreads();
-    for (int r = 0; r < np - 1; ++r) {
-      for (int pr = w; pr < np / 2; pr += nw) {
-        int p = (pr == 0) ? 0 : 1 + (r + pr - 1) % (np - 1);
-        int q = 1 + (r + np - 2 - pr) % (np - 1);
-        if (p >= n || q >= n) continue;
-        if (p > q) {
-          int tmp = p;
-          p = q;
-          q = tmp;
-        }
-        double2* ap = J.A + (int64_t)p * J.lda;
-        double2* aq = J.A + (int64_t)q * J.lda;
-        double al = 0, be = 0;
-        double2 ga = make_double2(0, 0);
-        for (int i = lane; i < m; i += 32) {
-          double2 x = ap[i], y = aq[i];
-          al += cabs2(x);
-          be += cabs2(y);
-          cjfma(ga, x, y);
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_csum(ga);
-        double ag = sqrt(cabs2(ga));
-        if (ag <= 1e-15 * sqrt(al * be) || ag == 0.0) continue;
-        if (lane == 0) s_rot = 1;
-        double zeta = (be - al) / (2.0 * ag);
-        double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        double c = 1.0 / sqrt(1.0 + tt * tt), s = c * tt;
-        double2 ph = make_double2(ga.x / ag, -ga.y / ag);  // conj(gamma)/|gamma|
-        for (int i = lane; i < m; i += 32) {
-          double2 x = ap[i], y = cmul(aq[i], ph);
-          ap[i] = make_double2(c * x.x - s * y.x, c * x.y - s * y.y);
-          aq[i] = make_double2(s * x.x + c * y.x, s * x.y + c * y.y);
-        }
-        double2* vp = J.V + (int64_t)p * J.ldv;
-        double2* vq = J.V + (int64_t)q * J.ldv;
-        for (int i = lane; i < n; i += 32) {
-          double2 x = vp[i], y = cmul(vq[i], ph);
-          vp[i] = make_double2(c * x.x - s * y.x, c * x.y - s * y.y);
-          vq[i] = make_double2(s * x.x + c * y.x, s * x.y + c * y.y);
-        }
-      }
-      __syncthreads();
-    }
-    if (!s_rot) break;
-    __syncthreads();
+// Rounds of the round-robin pairing run as separate launches, one warp per column pair across many CTAs, all
+// matrices of the batch in one launch (blockIdx.y): the rounds of a sweep are ordered by the stream, and every
+// pair of a round is independent. A matrix whose last sweep rotated nothing is finished and skipped; the host
+// reads the per-matrix rotation flags once per sweep (at most 40 sweeps).
+static __global__ void k_jacobi_init(const SVDJob* jobs) {
+  const SVDJob J = jobs[blockIdx.y];
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)J.n * J.n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(q % J.n), c = (int)(q / J.n);
+    J.V[i + (int64_t)c * J.ldv] = make_double2(i == c ? 1.0 : 0.0, 0);
   }
-  if (t == 0) *J.sweeps = sweep;
+}
+
+#define JR_WARPS 8
+static __global__ void __launch_bounds__(32 * JR_WARPS) k_jacobi_round(const SVDJob* jobs, int r, const int* active,
+                                                                        int* rotated) {
+  const int j = blockIdx.y;
+  if (!active[j]) return;
+  const SVDJob J = jobs[j];
+  const int lane = threadIdx.x & 31, pr = blockIdx.x * JR_WARPS + (threadIdx.x >> 5);
+  const int m = J.m, n = J.n, np = n + (n & 1);
+  if (r >= np - 1 || pr >= np / 2) return;
+  int p = (pr == 0) ? 0 : 1 + (r + pr - 1) % (np - 1);
+  int q = 1 + (r + np - 2 - pr) % (np - 1);
+  if (p >= n || q >= n) return;
+  if (p > q) {
+    const int tmp = p;
+    p = q;
+    q = tmp;
+  }
+  double2* ap = J.A + (int64_t)p * J.lda;
+  double2* aq = J.A + (int64_t)q * J.lda;
+  double al = 0, be = 0;
+  double2 ga = make_double2(0, 0);
+  for (int i = lane; i < m; i += 32) {
+    double2 x = ap[i], y = aq[i];
+    al += cabs2(x);
+    be += cabs2(y);
+    cjfma(ga, x, y);
+  }
+  al = warp_sum(al);
+  be = warp_sum(be);
+  ga = warp_csum(ga);
+  const double ag = sqrt(cabs2(ga));
+  if (ag <= 1e-15 * sqrt(al * be) || ag == 0.0) return;
+  if (lane == 0) rotated[j] = 1;
+  const double zeta = (be - al) / (2.0 * ag);
+  const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  const double c = 1.0 / sqrt(1.0 + tt * tt), sn = c * tt;
+  const double2 ph = make_double2(ga.x / ag, -ga.y / ag);  // conj(gamma)/|gamma|
+  for (int i = lane; i < m; i += 32) {
+    double2 x = ap[i], y = cmul(aq[i], ph);
+    ap[i] = make_double2(c * x.x - sn * y.x, c * x.y - sn * y.y);
+    aq[i] = make_double2(sn * x.x + c * y.x, sn * x.y + c * y.y);
+  }
+  double2* vp = J.V + (int64_t)p * J.ldv;
+  double2* vq = J.V + (int64_t)q * J.ldv;
+  for (int i = lane; i < n; i += 32) {
+    double2 x = vp[i], y = cmul(vq[i], ph);
+    vp[i] = make_double2(c * x.x - sn * y.x, c * x.y - sn * y.y);
+    vq[i] = make_double2(sn * x.x + c * y.x, sn * x.y + c * y.y);
+  }
 }
 
 int jacobi_svd_batched(const std::vector<SVDJob>& jobs, cudaStream_t s) {
   if (jobs.empty()) return FDA_OK;
   DBuf<SVDJob> dj;
   FDA_TRY(dj.upload(jobs));
-  k_jacobi_svd<<<(unsigned)jobs.size(), SVD_NT, 0, s>>>(dj.p);
+  const int nj = (int)jobs.size();
+  int npmax = 2, nmax = 1;
+  for (const SVDJob& J : jobs) npmax = std::max(npmax, J.n + (J.n & 1)), nmax = std::max(nmax, J.n);
+  k_jacobi_init<<<dim3(std::max(1, std::min(1024, (nmax * nmax + 255) / 256)), nj), 256, 0, s>>>(dj.p);
   FDA_LAUNCH_CHECK();
+  std::vector<int> act(nj, 1), rot(nj, 0), sweeps(nj, 0);
+  DBuf<int> dact, drot;
+  FDA_TRY(dact.upload(act));
+  FDA_TRY(drot.alloc(nj));
+  const unsigned gx = (unsigned)((npmax / 2 + JR_WARPS - 1) / JR_WARPS);
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    FDA_CUDA(cudaMemsetAsync(drot.p, 0, sizeof(int) * nj, s));
+    for (int r = 0; r < npmax - 1; ++r) {
+      k_jacobi_round<<<dim3(gx, nj), 32 * JR_WARPS, 0, s>>>(dj.p, r, dact.p, drot.p);
+      FDA_LAUNCH_CHECK();
+    }
+    FDA_CUDA(cudaMemcpyAsync(rot.data(), drot.p, sizeof(int) * nj, cudaMemcpyDeviceToHost, s));
+    FDA_CUDA(cudaStreamSynchronize(s));
+    int live = 0;
+    for (int j = 0; j < nj; ++j) {
+      if (!act[j]) continue;
+      sweeps[j] = sweep + 1;
+      if (!rot[j]) act[j] = 0;
+      live += act[j];
+    }
+    if (!live) break;
+    FDA_CUDA(cudaMemcpyAsync(dact.p, act.data(), sizeof(int) * nj, cudaMemcpyHostToDevice, s));
+  }
+  for (int j = 0; j < nj; ++j)
+    if (jobs[j].sweeps) FDA_CUDA(cudaMemcpyAsync(jobs[j].sweeps, &sweeps[j], sizeof(int), cudaMemcpyHostToDevice, s));
   FDA_CUDA(cudaStreamSynchronize(s));
   return FDA_OK;
 }
+
 
 }  // namespace fda

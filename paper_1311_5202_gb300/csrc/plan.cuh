@@ -11,7 +11,7 @@ int zgemm_batched(char opa, char opb, int M, int N, int K, double2 alpha, const 
                   const double2* const* B, int ldb, double2 beta, double2* const* C, int ldc, int64_t batch,
                   cudaStream_t s);
 int near_corrections(bm_problem_s* P, DBuf<int64_t>& di_ptr, DBuf<int32_t>& di_cols, DBuf<double2>& corr,
-                     double* ms, int op);
+                     double* ms, int op, double2 gamma);
 int upload_geometry_constants();
 
 // One level of the tree that carries outgoing/incoming representations.

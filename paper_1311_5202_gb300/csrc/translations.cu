@@ -51,6 +51,7 @@ struct SVDJob {
 int pivoted_qr_batched(const std::vector<QRJob>& jobs, cudaStream_t s);
 int form_q_batched(const std::vector<QFormJob>& jobs, cudaStream_t s);
 int jacobi_svd_batched(const std::vector<SVDJob>& jobs, cudaStream_t s);
+int gaussian_fill(double2* out, int64_t n, uint64_t seed);
 
 // ------------------------------------------------------------------ candidate point sets (host)
 static void cube_surface(int p, double scale, std::vector<double>& out) {
@@ -227,7 +228,7 @@ struct LeafJob {
   double2* out;
 };
 static __global__ void k_gen_leaf(const LeafJob* jobs, const double* xt, const double* nt, const double* wt,
-                                  double k, double2 alpha, int ncol, int mode, int particles, int op) {
+                                  double k, double2 alpha, int ncol, int mode, int particles, int op, double2 gamma) {
   const LeafJob J = jobs[blockIdx.y];
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < J.sc * ncol; q += gridDim.x * blockDim.x) {
     int i = q % J.sc, j = q / J.sc;
@@ -242,8 +243,9 @@ static __global__ void k_gen_leaf(const LeafJob* jobs, const double* xt, const d
         // dG/dn_y(a, y) with r = a - y; particle sums: (G + alpha dG/dn_y)(a, y) (Eq. sum)
         double dummy[3] = {0, 0, 0};
         KernVals K = helmholtz4(a, dummy, y, ny, k);
-        v = particles ? cscale(cadd(K.G, cmul(alpha, K.Dy)), J.W[i] * wt[p])
-                      : cscale(op ? K.G : K.Dy, J.W[i] * wt[p]);  // operator B: monopole sources (S + alpha M)
+        // operator B: monopole sources (S + alpha M); A + gamma B (Robin data): dipole + gamma monopole
+        const double2 src = op == 2 ? cadd(K.Dy, cmul(gamma, K.G)) : (op ? K.G : K.Dy);
+        v = particles ? cscale(cadd(K.G, cmul(alpha, K.Dy)), J.W[i] * wt[p]) : cscale(src, J.W[i] * wt[p]);
         J.out[i + (int64_t)j * J.sc] = v;
       } else {
         // (G + alpha dG/dn_x)(x, a) with r = x - a; particle sums: G(x, a)
@@ -300,7 +302,7 @@ struct NearJob {
   int64_t off;
 };
 static __global__ void k_gen_near(const NearJob* jobs, const double* xt, const double* nt, const double* wt, double k,
-                                  double2 alpha, double2* out, int particles, int op) {
+                                  double2 alpha, double2* out, int particles, int op, double2 gamma) {
   const NearJob J = jobs[blockIdx.x];
   int64_t nr = J.te - J.tb, nc = J.se - J.sb;
   for (int64_t q = threadIdx.x; q < nr * nc; q += blockDim.x) {
@@ -308,8 +310,9 @@ static __global__ void k_gen_near(const NearJob* jobs, const double* xt, const d
     double2 v = make_double2(0, 0);
     if (i != j) {
       KernVals K = helmholtz4(xt + 3 * i, nt + 3 * i, xt + 3 * j, nt + 3 * j, k);
+      const double2 ka = cadd(K.Dy, cmul(alpha, K.H)), kb = cadd(K.G, cmul(alpha, K.Dx));
       v = particles ? cscale(cadd(K.G, cmul(alpha, K.Dy)), wt[j])
-                    : cscale(op ? cadd(K.G, cmul(alpha, K.Dx)) : cadd(K.Dy, cmul(alpha, K.H)), wt[j]);
+                    : cscale(op == 2 ? cadd(ka, cmul(gamma, kb)) : (op ? kb : ka), wt[j]);
     }
     out[J.off + q] = v;
   }
@@ -470,7 +473,6 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
     DBuf<int> sweeps;
   };
   std::vector<Cand> cand(FDA_MAXLEV);
-  std::vector<QRJob> qjobs;
   std::vector<int> qlev;
   const double lam = 2 * FDA_PI / k;
   if (far) {
@@ -540,22 +542,74 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
       g.out = C.A.p;
       g.ld = m;
       FDA_TRY(gen_G({g}, k));
-      QRJob q;
-      q.A = C.A.p;
-      q.m = m;
-      q.n = n;
-      q.lda = m;
-      q.kmax = std::min(m, n);
-      q.tol = 0.1 * eps;
-      q.perm = C.perm.p;
-      q.rank = C.rank.p;
-      q.rdiag = C.rd.p;
-      q.tau = C.tau.p;
-      q.cn = C.cn.p;
-      qjobs.push_back(q);
       qlev.push_back(l);
     }
-    FDA_TRY(pivoted_qr_batched(qjobs, 0));
+    // Equivalent points: a randomized interpolative decomposition of the candidate matrix A = W G(X, Y).
+    // A Gaussian sketch S = Omega A (ell x n, ell << m) keeps A's column space, and the column-pivoted QR of
+    // S to tolerance 0.1 eps selects the columns; a sketch whose rank comes within 8 of ell is redrawn with
+    // twice the rows (up to m), so that the selection never saturates the sketch.
+    std::vector<int> ell(qlev.size()), done(qlev.size(), 0);
+    for (size_t q = 0; q < qlev.size(); ++q) {
+      const Cand& C = cand[qlev[q]];
+      const int m = (int)(C.X.size() / 3), n = (int)(C.Y.size() / 3);
+      ell[q] = std::min(std::min(m, n), 256);
+    }
+    std::vector<DBuf<double2>> Om(qlev.size()), Sk(qlev.size());
+    for (int round = 0; round < 8; ++round) {
+      std::vector<QRJob> qj;
+      std::vector<size_t> which;
+      for (size_t q = 0; q < qlev.size(); ++q) {
+        if (done[q]) continue;
+        Cand& C = cand[qlev[q]];
+        const int m = (int)(C.X.size() / 3), n = (int)(C.Y.size() / 3), e = ell[q];
+        FDA_TRY(Om[q].alloc((size_t)e * m));
+        FDA_TRY(Sk[q].alloc((size_t)e * n));
+        FDA_TRY(gaussian_fill(Om[q].p, (int64_t)e * m, 0x5EEDull + 7919ull * (uint64_t)qlev[q] + 104729ull * round));
+        DBuf<const double2*> da, db;
+        DBuf<double2*> dc;
+        const double2* ha[1] = {Om[q].p};
+        const double2* hb[1] = {C.A.p};
+        double2* hc[1] = {Sk[q].p};
+        FDA_TRY(da.upload(ha, 1));
+        FDA_TRY(db.upload(hb, 1));
+        FDA_TRY(dc.upload(hc, 1));
+        FDA_TRY(zgemm_batched('N', 'N', e, n, m, make_double2(1, 0), da.p, e, db.p, m, make_double2(0, 0), dc.p, e, 1,
+                              0));
+        FDA_CUDA(cudaDeviceSynchronize());
+        QRJob qq;
+        qq.A = Sk[q].p;
+        qq.m = e;
+        qq.n = n;
+        qq.lda = e;
+        qq.kmax = std::min(e, n);
+        qq.tol = 0.1 * eps;
+        qq.perm = C.perm.p;
+        qq.rank = C.rank.p;
+        qq.rdiag = C.rd.p;
+        qq.tau = C.tau.p;
+        qq.cn = C.cn.p;
+        qj.push_back(qq);
+        which.push_back(q);
+      }
+      if (qj.empty()) break;
+      FDA_TRY(pivoted_qr_batched(qj, 0));
+      for (size_t u = 0; u < which.size(); ++u) {
+        const size_t q = which[u];
+        Cand& C = cand[qlev[q]];
+        const int m = (int)(C.X.size() / 3), n = (int)(C.Y.size() / 3);
+        int rk = 0;
+        FDA_CUDA(cudaMemcpy(&rk, C.rank.p, sizeof(int), cudaMemcpyDeviceToHost));
+        if (rk < ell[q] - 8 || ell[q] >= std::min(m, n)) {
+          done[q] = 1;
+        } else {
+          ell[q] = std::min(std::min(m, n), 2 * ell[q]);
+        }
+      }
+    }
+    for (size_t q = 0; q < qlev.size(); ++q) {
+      Om[q].release();
+      Sk[q].release();
+    }
     // selected equivalent points -> row selection on (W G(X, b))^H
     std::vector<QRJob> qjobs2;
     for (int l : qlev) {
@@ -659,7 +713,9 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
       sj.sweeps = C.sweeps.p;
       sjobs.push_back(sj);
     }
+    const double t_svd0 = now_ms();
     FDA_TRY(jacobi_svd_batched(sjobs, 0));
+    P->setup_ms[1] = now_ms() - t_svd0;
     for (size_t q = 0; q < qlev.size(); ++q) {
       int l = qlev[q];
       LevelOps& L = P->lev[l];
@@ -702,7 +758,7 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
     }
   }
   double t1 = now_ms();
-  P->setup_ms[0] = t1 - t0;
+  P->setup_ms[0] = t1 - t0 - P->setup_ms[1];
 
   // ---- 2. coefficient slots
   P->h_slot.assign(nbox, -1);
@@ -793,7 +849,8 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
           DBuf<LeafJob> dlj;
           FDA_TRY(dlj.upload(lj));
           k_gen_leaf<<<dim3(16, (unsigned)nb), 256>>>(dlj.p, xt.p, nt.p, wt.p, k, alpha, ncol, mode,
-                                                      pr->particles, P->cfg.op);
+                                                      pr->particles, P->cfg.op,
+                                                      make_double2(P->cfg.gamma_re, P->cfg.gamma_im));
           FDA_LAUNCH_CHECK();
           DBuf<const double2*> dA, dB;
           DBuf<double2*> dC;
@@ -1309,9 +1366,13 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
       FDA_TRY(corr.alloc(6));
       P->diag_c = make_double2(0.0, 0.0);
     } else {
-      FDA_TRY(near_corrections(pr, di_ptr, di_cols, corr, &ms, P->cfg.op));
-      // operator A: 1/2 I + Dbar + alpha Hbar; operator B (radiation data): Sbar + alpha Mbar - alpha/2 I
-      P->diag_c = P->cfg.op ? make_double2(-0.5 * pr->alpha.x, -0.5 * pr->alpha.y) : make_double2(0.5, 0.0);
+      const double2 gamma = make_double2(P->cfg.gamma_re, P->cfg.gamma_im);
+      FDA_TRY(near_corrections(pr, di_ptr, di_cols, corr, &ms, P->cfg.op, gamma));
+      // operator A: 1/2 I + Dbar + alpha Hbar; operator B (radiation data): Sbar + alpha Mbar - alpha/2 I;
+      // Robin data: A + gamma B, diagonal 1/2 - gamma alpha/2
+      const double2 half_alpha = make_double2(-0.5 * pr->alpha.x, -0.5 * pr->alpha.y);
+      P->diag_c = P->cfg.op == 2 ? cadd(make_double2(0.5, 0.0), cmul(gamma, half_alpha))
+                                 : (P->cfg.op ? half_alpha : make_double2(0.5, 0.0));
     }
     P->setup_ms[6] = ms;
     DBuf<int64_t> cnt;
@@ -1427,7 +1488,7 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
     for (size_t b0 = 0; b0 < jobs.size(); b0 += 65535) {
       unsigned nb = (unsigned)std::min<size_t>(65535, jobs.size() - b0);
       k_gen_near<<<nb, 256>>>(dj.p + b0, xt.p, nt.p, wt.p, k, alpha, P->op64.near.p, pr->particles,
-                              P->cfg.op);
+                              P->cfg.op, make_double2(P->cfg.gamma_re, P->cfg.gamma_im));
       FDA_LAUNCH_CHECK();
     }
     FDA_CUDA(cudaDeviceSynchronize());
@@ -1500,7 +1561,6 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
     for (int64_t b : P->h_leaves) P->max_leaf = std::max<int>(P->max_leaf, (int)(T->h_pe[b] - T->h_pb[b]));
   }
   FDA_CUDA(cudaDeviceSynchronize());
-  P->setup_ms[1] = 0;
   return FDA_OK;
 }
 

@@ -71,7 +71,7 @@ def test_invalid_arguments_fail_cleanly_without_gpu(built):
     assert rc == fdbem.FDA_E_INVALID_ARG and "eps" in fdbem.fda_last_error()
     # configuration fields are checked before the tree
     cfg.eps, cfg.precision, cfg.nrhs_max = 1e-4, fdbem.FDA_PREC_FP32, 1
-    for field, bad, word in (("m2l_tensor", 4, "m2l_tensor"), ("op", 2, "op"), ("near_split", 3, "near_split"),
+    for field, bad, word in (("m2l_tensor", 4, "m2l_tensor"), ("op", 3, "op"), ("near_split", 3, "near_split"),
                              ("nrhs_max", 0, "nrhs_max")):
         good = getattr(cfg, field)
         setattr(cfg, field, bad)
