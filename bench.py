@@ -343,6 +343,9 @@ def main():
                     help="directions of the batched section (autotuned, graph-captured matvec and block solve); "
                          "0 skips it")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner")
+    ap.add_argument("--m2l-variant", type=int, default=None,
+                    help="pin one M2L kernel variant for every level and stage instead of autotuning "
+                         "(fda_m2l_force; used to profile one kernel)")
     ap.add_argument("--table1", action="store_true",
                     help="run only the particle summations of the paper's Table 1 and print their JSON line")
     ap.add_argument("--table1-max", type=int, default=3, help="number of Table 1 sizes (4 adds N = 4.7M)")
@@ -379,7 +382,9 @@ def main():
     S = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=eps, leaf_max=spec["leaf"], precision=fdbem.FDA_PREC_FP32,
                      lowrank=1, nrhs_max=nrhs, m2l_tensor=args.m2l_tensor, near_split=args.near_split)
     setup_s = time.perf_counter() - t0
-    tune_main = None if args.no_tune else fdbem.fda_autotune(S.plan, nrhs)
+    tune_main = None if (args.no_tune or args.m2l_variant is not None) else fdbem.fda_autotune(S.plan, nrhs)
+    if args.m2l_variant is not None:
+        fdbem.fda_m2l_force(S.plan, args.m2l_variant)
     info = S.info()
     X = inputs.complex_gaussian(N, 20131120, nrhs=nrhs if nrhs > 1 else None)
     xd = torch.from_numpy(X).to(dev).contiguous()

@@ -227,7 +227,10 @@ typedef struct {
   int32_t chosen[64];     /* 0: FMA kernel, 1: tensor-core kernel (default shape), 2 to 4: tensor-core kernel
                              (alternative shapes: other column width or stage count), 5 and 6: tensor-core
                              kernel with the bulk-reduction epilogue (default and single-stage shape), 7 and 8:
-                             stage 0 with the swapped-operand V^ kernel (one and two pipeline stages) */
+                             stage 0 with the swapped-operand V^ kernel (one and two pipeline stages), 9: stage
+                             1 with the persistent warp-specialised scatter kernel, 10: bulk-reduction epilogue,
+                             32 columns, exact row tiles, 11 and 12: stage 0 with the V^ kernel fed by TMA row
+                             gathers (four and three stages) */
   double near_ms[2];      /* near field at 4 and 16 right-hand sides per pass (nrhs >= 12; else 0) */
   int32_t near_rhs_per_pass;
   int32_t near_split;     /* near-field schedule kept: 0 = the correction entries outside the direct blocks inside
@@ -243,9 +246,12 @@ int fda_autotune(fda_plan_t* plan, int nrhs, void* stream, fda_tune_report_t* re
  * tensor cores from operator images (default shape), 2 = in-kernel expansion (plans with m2l_tensor = 2),
  * 3 to 5 = variant 1 in the alternative tile shapes, 6 and 7 = variant 1 with the bulk-reduction epilogue
  * (default and single-stage shape), 8 and 9 = the swapped-operand V^ kernel (one and two stages) for the V^
- * stage, with variant 6 for the U^ stage. A variant that does not apply to a (level, stage) runs the FMA
- * kernel there. Errors: FDA_E_INVALID_ARG (variant outside [-1, 9]), FDA_E_STATE (plan without the kernel's
- * operators). */
+ * stage, with variant 6 for the U^ stage, 10 = the persistent warp-specialised scatter kernel for the U^ stage,
+ * with variant 8 for the V^ stage, 11 = variant 1 with the bulk-reduction epilogue, 32 columns and exactly the
+ * row tiles needed (the most CTAs per SM), 12 and 13 = the V^ kernel fed by TMA row gathers (four and three
+ * stages; one right-hand side, else variant 8), with variant 6 for the U^ stage. A variant that does not apply
+ * to a (level, stage) runs the FMA kernel there. Errors: FDA_E_INVALID_ARG (variant outside [-1, 13]),
+ * FDA_E_STATE (plan without the kernel's operators). */
 int fda_m2l_force(fda_plan_t* plan, int variant);
 
 /* CUDA-graph form of one product (the batched matvec of many incident directions replayed without

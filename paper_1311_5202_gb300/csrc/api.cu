@@ -275,7 +275,7 @@ int fda_autotune(fda_plan_t* plan, int nrhs, void* stream, fda_tune_report_t* re
 
 int fda_m2l_force(fda_plan_t* plan, int variant) {
   ARG_CHECK(plan, "NULL plan");
-  ARG_CHECK(variant >= -1 && variant <= 9, "variant outside [-1, 9]");
+  ARG_CHECK(variant >= -1 && variant <= 13, "variant outside [-1, 13]");
   if (variant > 0 && plan->cfg.precision != FDA_PREC_FP32) {
     set_error("tensor-core M2L variants need a plan built with FDA_PREC_FP32");
     return FDA_E_STATE;
@@ -288,13 +288,15 @@ int fda_m2l_force(fda_plan_t* plan, int variant) {
     set_error("variants 1 and 3 to 9 need a plan built with m2l_tensor = 1 or 3");
     return FDA_E_STATE;
   }
-  if (variant >= 3 && plan->cfg.m2l_tensor == 3 && variant != 6 && variant != 7) {
+  if (variant >= 3 && plan->cfg.m2l_tensor == 3 && variant != 6 && variant != 7) {  // 8 to 11: TF32 only
     set_error("a 3xTF32 plan (m2l_tensor = 3) runs variants 1, 6 and 7 only");
     return FDA_E_STATE;
   }
   for (int l = 0; l < FDA_MAXLEV; ++l)
     for (int st = 0; st < 2; ++st)
-      plan->m2l_choice[l][st] = (st == 1 && variant >= 8) ? 6 : variant;  // 8, 9 are V^-stage kernels
+      plan->m2l_choice[l][st] = (st == 1 && (variant == 8 || variant == 9 || variant >= 12)) ? 6  // V^ only
+                                : (st == 0 && variant == 10) ? 8                       // 10: U^ stage only
+                                                             : variant;
   return FDA_OK;
 }
 

@@ -10,6 +10,8 @@
 // with tcgen05.ld and scattered with atomics. With split = 1 every operand is split into TF32 hi + lo and
 // three products (hi hi + hi lo + lo hi) keep FP32 accuracy. Every wait is bounded: a wait that gives up
 // sets an error flag, and the kernel still releases its TMEM.
+#include <cuda.h>
+
 #include "plan.cuh"
 
 #include <vector>
@@ -492,7 +494,8 @@ static __global__ void __launch_bounds__(TC3_NT) k_m2l_tc3(const GemmUnit* units
   typedef Tc3Smem<MTC, N, NST, SPLIT> Sm;
   extern __shared__ unsigned char smem_raw[];
   Sm& S = *reinterpret_cast<Sm*>((((uintptr_t)smem_raw) + 1023) & ~(uintptr_t)1023);
-  constexpr int TCOLS = MTC * N < 32 ? 32 : MTC * N;
+  // TMEM allocations are powers of two of at least 32 columns
+  constexpr int TCOLS = MTC * N <= 32 ? 32 : MTC * N <= 64 ? 64 : MTC * N <= 128 ? 128 : MTC * N <= 256 ? 256 : 512;
   constexpr uint32_t IDESC = idesc_tf32(128, N);
   // refill distance: chunk kc + D is issued at step kc into the stage that served chunk kc + D - NST
   constexpr int D = NST - 1;
@@ -759,7 +762,7 @@ int m2l_tc3_launch(const GemmUnit* units, size_t nunits, const float* img, const
     return FDA_E_INVALID_ARG;
   }
   if (nunits == 0) return FDA_OK;
-  if (shape >= 6) {  // 3xTF32 from the TF32 and remainder images, single stage: 6 atomics, 7 bulk reductions
+  if (shape == 6 || shape == 7) {  // 3xTF32 from the TF32 and remainder images, single stage: 6 atomics, 7 bulk
 #define TC3S(M_, N_, B_) \
   return tc3_launch_t<M_, N_, 1, B_, 1>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, ldc, ldm, err, s)
     if (shape == 6) {
@@ -771,6 +774,15 @@ int m2l_tc3_launch(const GemmUnit* units, size_t nunits, const float* img, const
     if (max_mt == 2) TC3S(2, 64, 1);
     TC3S(4, 64, 1);
 #undef TC3S
+  }
+  if (shape == 8) {  // bulk reductions, single stage, 32 columns and exactly the rows needed: most CTAs per SM
+#define TC3N(M_) \
+  return tc3_launch_t<M_, 32, 1, 1>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, ldc, ldm, err, s)
+    if (max_mt == 1) TC3N(1);
+    if (max_mt == 2) TC3N(2);
+    if (max_mt == 3) TC3N(3);
+    TC3N(4);
+#undef TC3N
   }
   if (shape == 4 || shape == 5) {  // bulk-reduction epilogue: default shape (4) or single-stage (5)
 #define TC3B(M_, N_, S_) \
@@ -1041,6 +1053,502 @@ int m2l_vsw_launch(const GemmUnit* units, size_t nunits, const float* img, const
   }
 #undef VSWL
   set_error("swapped V^ kernel: no variant for %d TMEM columns and %d stages", nb, nst);
+  return FDA_E_INVALID_ARG;
+}
+
+
+// ================================================================== V^ stage fed by TMA row gathers
+// The swapped V^ kernel for one right-hand side with its gathered A operand loaded by the tensor memory
+// accelerator: the level's coefficient vectors are a 2-D tensor (rows of 2 s floats), and a K chunk of 128
+// rows x 32 floats is 32 cp.async.bulk.tensor tile::gather4 loads (four rows each, one per lane of warp 0)
+// into the 128-byte-swizzled K-major layout the MMA reads (8-row atoms of 1 KB). The operator rows come by
+// cp.async.bulk as before; both complete on the stage's mbarrier. Warp 0 runs the pipeline: lookahead
+// NST - 1 chunks, lane 0 issues the MMAs and commits each stage; the four warps share the epilogue.
+template <int NB, int NST>
+struct VtmSmem {
+  alignas(1024) float a[NST][128 * TC3_KC];  // gathered rows, 128-byte swizzle
+  alignas(1024) float b[NST][NB * TC3_KC];   // operator rows, canonical layout without swizzle
+  alignas(8) uint64_t full[NST];
+  uint64_t mdone[NST];
+  uint32_t tmem;
+  int rows[128];
+  int64_t dbase[128];
+};
+
+// shared-memory descriptor of a K-major operand in the 128-byte swizzle (8-row atoms of 1 KB)
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;               // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset: one 8-row atom
+  d |= (uint64_t)1 << 46;               // version
+  d |= (uint64_t)2 << 61;               // layout: 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap* map, int x, int y0, int y1, int y2,
+                                            int y3, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+      "%4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y0), "r"(y1), "r"(y2), "r"(y3), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <int NB, int NST>
+static __global__ void __launch_bounds__(VSW_NT) k_m2l_vtm(const GemmUnit* units, const float* img,
+                                                          const int64_t* psrc, const int64_t* pmid, float2* mid,
+                                                          int64_t base, int s_l, int* err,
+                                                          const __grid_constant__ CUtensorMap tmap) {
+  typedef VtmSmem<NB, NST> Sm;
+  extern __shared__ unsigned char smem_raw[];
+  Sm& S = *reinterpret_cast<Sm*>((((uintptr_t)smem_raw) + 1023) & ~(uintptr_t)1023);
+  constexpr int D = NST - 1;
+  const GemmUnit U = units[blockIdx.x];  // mode 1: M = r rows of V^, K = s
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const int MT = (2 * U.M + 127) / 128;
+  const int nmma = ((2 * U.M + 15) / 16) * 16;
+  const int nk = (2 * U.K + TC3_KC - 1) / TC3_KC;
+  const float* A = img + U.a_off;
+  const uint32_t idesc = idesc_tf32(128, nmma);
+  if (w == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
+                 "r"(NB));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (t == 0) {
+    for (int q = 0; q < NST; ++q) {
+      mbar_init(&S.full[q], 1);
+      mbar_init(&S.mdone[q], 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  {
+    // rows past the unit's pairs repeat its first source (their results are not stored)
+    const int p = t < U.p_count ? t : 0;
+    S.rows[t] = (int)((psrc[U.p_begin + p] - base) / s_l);
+    S.dbase[t] = t < U.p_count ? pmid[U.p_begin + t] : -1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = S.tmem;
+  int ok = 1;
+  if (w == 0) {
+    const int y0 = S.rows[4 * lane], y1 = S.rows[4 * lane + 1], y2 = S.rows[4 * lane + 2], y3 = S.rows[4 * lane + 3];
+    for (int step = 0; step < nk + D && ok; ++step) {
+      if (step < nk) {  // load chunk `step`
+        const int q = step % NST;
+        if (step >= NST) {
+          int mine = lane == 0 ? (mbar_wait(&S.mdone[q], (uint32_t)((step / NST - 1) & 1)) ? 1 : 0) : 1;
+          ok = __shfl_sync(0xffffffffu, mine, 0);
+          if (!ok) break;
+        }
+        if (lane == 0) {
+          uint32_t bytes = 128u * TC3_KC * 4u;
+          for (int mt = 0; mt < MT; ++mt) bytes += (uint32_t)tc3_ng(U.M, mt) * 1024u;
+          tc3_expect_tx(&S.full[q], bytes);
+          for (int mt = 0; mt < MT; ++mt) {
+            const int ng = tc3_ng(U.M, mt);
+            tc3_bulk(S.b[q] + mt * 16 * 256, A + (int64_t)16 * mt * nk * 256 + (int64_t)step * ng * 256,
+                     (uint32_t)ng * 1024u, &S.full[q]);
+          }
+        }
+        __syncwarp();
+        tma_gather4(smem_u32(S.a[q]) + 512u * (uint32_t)lane, &tmap, TC3_KC * step, y0, y1, y2, y3, &S.full[q]);
+      }
+      const int kc = step - D;
+      if (kc >= 0) {  // MMAs of chunk kc
+        const int q = kc % NST;
+        int mine = 1;
+        if (lane == 0) {
+          if (!mbar_wait(&S.full[q], (uint32_t)((kc / NST) & 1))) {
+            mine = 0;
+          } else {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int s8 = 0; s8 < TC3_KC / 8; ++s8) {
+              if (kc * TC3_KC + s8 * 8 >= 2 * U.K) break;
+              const uint64_t ad = smem_desc_sw128(smem_u32(S.a[q]) + 32u * (uint32_t)s8);
+              const uint64_t bd = smem_desc(smem_u32(S.b[q]) + s8 * 256, 128, (TC3_KC / 4) * 128);
+              tc_mma(tmem, ad, bd, idesc, (kc > 0 || s8 > 0) ? 1 : 0);
+            }
+            tc_commit(&S.mdone[q]);
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, mine, 0);
+      }
+    }
+  }
+  // the last chunk's commit covers every MMA of the unit
+  const int qlast = (nk - 1) % NST;
+  bool mine = mbar_wait(&S.mdone[qlast], (uint32_t)(((nk - 1) / NST) & 1));
+  const bool all = __syncthreads_and((mine && (w != 0 || ok)) ? 1 : 0) != 0;
+  if (!all && t == 0) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (all) {
+    const int n = 32 * w + lane;  // TMEM lane = pair
+    const int64_t db = S.dbase[n];
+    float* dst = db >= 0 ? reinterpret_cast<float*>(mid + db) : nullptr;
+    const int nout = ((2 * U.M + 3) / 4) * 4;
+#pragma unroll 1
+    for (int col0 = 0; col0 < nmma; col0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * w) << 16) + (uint32_t)col0, v);
+      if (dst) {
+#pragma unroll
+        for (int q = 0; q < 32; q += 4)
+          if (col0 + q < nout) *reinterpret_cast<float4*>(dst + col0 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+      }
+    }
+  } else {
+    // a wait gave up: let every copy issued into this CTA's buffers land (bounded) before it leaves
+    for (int q = 0; q < NST; ++q) mbar_wait(&S.full[q], 0u), mbar_wait(&S.full[q], 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (w == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NB));
+  }
+}
+
+template <int NB, int NST>
+static int vtm_launch_t(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc,
+                        const int64_t* pmid, float2* mid, int64_t base, int s_l, const CUtensorMap* map, int* err,
+                        cudaStream_t s) {
+  const size_t smem = sizeof(VtmSmem<NB, NST>) + 1024;
+  static bool attr = false;
+  if (!attr) {
+    FDA_CUDA(cudaFuncSetAttribute(k_m2l_vtm<NB, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  for (size_t u0 = 0; u0 < nunits; u0 += 65535) {
+    unsigned n = (unsigned)std::min<size_t>(65535, nunits - u0);
+    k_m2l_vtm<NB, NST><<<n, VSW_NT, smem, s>>>(units + u0, img, psrc, pmid, mid, base, s_l, err, *map);
+    FDA_LAUNCH_CHECK();
+  }
+  return FDA_OK;
+}
+
+// one right-hand side; nb = 32, 64, 128 or 256 TMEM columns (round16(2 r) <= nb), nst = 2, 3 or 4 stages
+int m2l_vtm_launch(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc, const int64_t* pmid,
+                   float2* mid, int64_t base, int s_l, const CUtensorMap* map, int nb, int nst, int* err,
+                   cudaStream_t s) {
+  if (nunits == 0) return FDA_OK;
+#define VTML(B_, S_) return vtm_launch_t<B_, S_>(units, nunits, img, psrc, pmid, mid, base, s_l, map, err, s)
+  if (nst == 2) {
+    if (nb == 32) VTML(32, 2);
+    if (nb == 64) VTML(64, 2);
+    if (nb == 128) VTML(128, 2);
+    if (nb == 256) VTML(256, 2);
+  } else if (nst == 3) {
+    if (nb == 32) VTML(32, 3);
+    if (nb == 64) VTML(64, 3);
+    if (nb == 128) VTML(128, 3);
+    if (nb == 256) VTML(256, 3);
+  } else {
+    if (nb == 32) VTML(32, 4);
+    if (nb == 64) VTML(64, 4);
+    if (nb == 128) VTML(128, 4);
+  }
+#undef VTML
+  set_error("TMA-fed V^ kernel: no variant for %d TMEM columns and %d stages", nb, nst);
+  return FDA_E_INVALID_ARG;
+}
+
+// ================================================================== persistent, warp-specialised scatter stage
+// For units whose K fits two 32-wide real chunks (the U^ stage of low-rank pairs, mode 2, and dense units
+// with K <= 32 complex, mode 0) the operator of a unit is loaded once and stays in shared memory while the
+// unit's columns stream through in blocks of WS_NB:
+//  - warps 0-2 (producers): 16-byte cp.async gathers of a block's source vectors into a ring of WS_NS
+//    stages, each thread signalling the stage's "full" mbarrier with cp.async.mbarrier.arrive.noinc; thread
+//    0 also loads each unit's operator tiles (cp.async.bulk, transaction bytes on an mbarrier);
+//  - warp 3, lane 0 (MMA): tcgen05.mma of all row tiles into one of two TMEM accumulators, committing the
+//    ring stage, the accumulator and, after a unit's last block, the operator buffer;
+//  - warps 4-7 (epilogue, TMEM lane quadrant w - 4): accumulators through shared memory, one
+//    cp.reduce.async.bulk per column into the target vectors, then the accumulator is handed back.
+// CTAs are persistent (one per SM) and take units round-robin. Every wait is bounded; a wait that gives up
+// sets the CTA's abort flag (and the error flag), every role leaves its loop at its next check, and the
+// epilogue warps decide together through a shared slot so that their named barrier never splits.
+#define WS_NB 32   // columns per block
+#define WS_NS 3    // ring stages
+#define WS_NT 256
+
+template <int MTC>
+struct WsSmem {
+  alignas(1024) float a[MTC][2][128 * TC3_KC];         // operator tiles, two K chunks
+  alignas(1024) float b[WS_NS][2][WS_NB * TC3_KC];     // gathered columns
+  alignas(1024) float stg[2][16 * 128 * MTC];          // epilogue staging: 16 columns x real rows
+  alignas(8) uint64_t a_full, a_empty;
+  uint64_t b_full[WS_NS], b_empty[WS_NS];
+  uint64_t acc_full[2], acc_empty[2];
+  uint32_t tmem;
+  int abort_flag, epi_fail, epi_abort;
+};
+
+__device__ __forceinline__ void ws_arrive(uint64_t* bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void ws_cp_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void ws_epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+template <int MTC>
+static __global__ void __launch_bounds__(WS_NT, 1) k_m2l_ws(const GemmUnit* units, int nunits, const float* img,
+                                                           const int64_t* psrc, const int64_t* ptgt,
+                                                           const int64_t* pmid, const float2* cout, float2* cin,
+                                                           const float2* mid, int nrhs, int64_t ldc, int64_t ldm,
+                                                           int* err) {
+  typedef WsSmem<MTC> Sm;
+  extern __shared__ unsigned char smem_raw[];
+  Sm& S = *reinterpret_cast<Sm*>((((uintptr_t)smem_raw) + 1023) & ~(uintptr_t)1023);
+  constexpr int TCOLS = 2 * MTC * WS_NB <= 256 ? 256 : 512;
+  constexpr uint32_t IDESC = idesc_tf32(128, WS_NB);
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  if (w == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem)),
+                 "r"(TCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (t == 0) {
+    mbar_init(&S.a_full, 1);
+    mbar_init(&S.a_empty, 1);
+    for (int q = 0; q < WS_NS; ++q) {
+      mbar_init(&S.b_full[q], 96);  // one cp.async arrival per producer thread
+      mbar_init(&S.b_empty[q], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&S.acc_full[q], 1);
+      mbar_init(&S.acc_empty[q], 4);  // lane 0 of each epilogue warp
+    }
+    S.abort_flag = 0;
+    S.epi_fail = 0;
+    S.epi_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = S.tmem;
+  volatile int* abort_flag = &S.abort_flag;
+  auto give_up = [&]() {
+    *abort_flag = 1;
+    atomicExch(err, 1);
+  };
+
+  if (w < 3) {
+    // ------------------------------------------------------------ producers
+    int64_t g = 0;  // block counter over this CTA's units
+    int ui = 0, a_loads = 0;
+    for (int u = blockIdx.x; u < nunits && !*abort_flag; u += gridDim.x, ++ui) {
+      const GemmUnit U = units[u];
+      const float2* X = U.mode == 2 ? mid : cout;
+      const int64_t lds = U.mode == 2 ? ldm : ldc;
+      const int MT = (2 * U.M + 127) / 128, nk = (2 * U.K + TC3_KC - 1) / TC3_KC;
+      if (t == 0) {
+        if (ui > 0 && !mbar_wait(&S.a_empty, (ui - 1) & 1)) give_up();
+        if (!*abort_flag) {
+          uint32_t bytes = 0;
+          for (int mt = 0; mt < MT; ++mt) bytes += (uint32_t)nk * tc3_ng(U.M, mt) * 1024u;
+          tc3_expect_tx(&S.a_full, bytes);
+          ++a_loads;
+          const float* A = img + U.a_off;
+          for (int mt = 0; mt < MT; ++mt) {
+            const int ng = tc3_ng(U.M, mt);
+            for (int kc = 0; kc < nk; ++kc)
+              tc3_bulk(S.a[mt][kc], A + (int64_t)16 * mt * nk * 256 + (int64_t)kc * ng * 256, (uint32_t)ng * 1024u,
+                       &S.a_full);
+          }
+        }
+      }
+      const int ncols = U.p_count * nrhs;
+      for (int c0 = 0; c0 < ncols && !*abort_flag; c0 += WS_NB, ++g) {
+        const int st = (int)(g % WS_NS);
+        if (g >= WS_NS && !mbar_wait(&S.b_empty[st], (uint32_t)((g / WS_NS - 1) & 1))) {
+          give_up();
+          break;
+        }
+        // WS_NB columns x nk chunks x 8 segments of 16 bytes; 8 consecutive threads read one column's chunk
+        for (int seg = t; seg < WS_NB * 16; seg += 96) {
+          const int j = seg & 7, kc = (seg >> 3) & 1, n = seg >> 4;
+          if (kc >= nk) continue;
+          const int c = c0 + n;
+          if (c >= ncols) continue;
+          const int p = c / nrhs, rr = c - p * nrhs;
+          const int64_t pi = U.p_begin + p;
+          const int64_t sb = U.mode == 2 ? pmid[pi] : psrc[pi];
+          const int gj = kc * (TC3_KC / 2) + 2 * j;
+          const uint32_t dst = smem_u32(S.b[st][kc]) + kmaj_off(n, 4 * j, TC3_KC);
+          const float2* src = gj < U.K ? X + (int64_t)rr * lds + sb + gj : X;
+          const uint32_t nbytes = gj + 1 < U.K ? 16u : (gj < U.K ? 8u : 0u);
+          if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+            tc3_cp16(dst, src, nbytes);
+          } else {
+            tc3_cp8(dst, src, nbytes >= 8 ? 8u : 0u);
+            tc3_cp8(dst + 8, nbytes == 16 ? src + 1 : X, nbytes == 16 ? 8u : 0u);
+          }
+        }
+        ws_cp_arrive(&S.b_full[st]);
+      }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    // the last operator load has landed before the CTA can leave (it already has unless the CTA aborted)
+    if (t == 0 && a_loads > 0) mbar_wait(&S.a_full, (uint32_t)((a_loads - 1) & 1));
+  } else if (w == 3) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int64_t g = 0;
+      int ui = 0;
+      bool pending = false;  // an accumulator commit whose MMAs may still run
+      uint32_t last_buf = 0, last_par = 0;
+      for (int u = blockIdx.x; u < nunits && !*abort_flag; u += gridDim.x, ++ui) {
+        const GemmUnit U = units[u];
+        const int MT = (2 * U.M + 127) / 128, nk = (2 * U.K + TC3_KC - 1) / TC3_KC;
+        if (!mbar_wait(&S.a_full, ui & 1)) {
+          give_up();
+          break;
+        }
+        const int ncols = U.p_count * nrhs;
+        for (int c0 = 0; c0 < ncols && !*abort_flag; c0 += WS_NB, ++g) {
+          const int st = (int)(g % WS_NS);
+          const uint32_t buf = (uint32_t)(g & 1);
+          if (g >= 2 && !mbar_wait(&S.acc_empty[buf], (uint32_t)(((g >> 1) - 1) & 1))) {
+            give_up();
+            break;
+          }
+          if (!mbar_wait(&S.b_full[st], (uint32_t)((g / WS_NS) & 1))) {
+            give_up();
+            break;
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // gathered data -> async proxy
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t d0 = tmem + buf * (uint32_t)(MTC * WS_NB);
+          for (int mt = 0; mt < MT; ++mt)
+            for (int kc = 0; kc < nk; ++kc)
+#pragma unroll
+              for (int s8 = 0; s8 < TC3_KC / 8; ++s8) {
+                if (kc * TC3_KC + s8 * 8 >= 2 * U.K) break;
+                const uint64_t ad = smem_desc(smem_u32(S.a[mt][kc]) + s8 * 256, 128, (TC3_KC / 4) * 128);
+                const uint64_t bd = smem_desc(smem_u32(S.b[st][kc]) + s8 * 256, 128, (TC3_KC / 4) * 128);
+                tc_mma(d0 + (uint32_t)(WS_NB * mt), ad, bd, IDESC, (kc > 0 || s8 > 0) ? 1 : 0);
+              }
+          tc_commit(&S.b_empty[st]);
+          tc_commit(&S.acc_full[buf]);
+          pending = true;
+          last_buf = buf;
+          last_par = (uint32_t)((g >> 1) & 1);
+          if (c0 + WS_NB >= ncols) tc_commit(&S.a_empty);
+        }
+      }
+      // on an abort, the MMAs already issued finish before the accumulators are released
+      if (*abort_flag && pending) mbar_wait(&S.acc_full[last_buf], last_par);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q4 = w - 4;
+    int64_t g = 0;
+    int grp = 0;  // staging group counter
+    for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+      const GemmUnit U = units[u];
+      const int MT = (2 * U.M + 127) / 128;
+      const int RT = 128 * MT;
+      const int ncols = U.p_count * nrhs;
+      bool stop = false;
+      for (int c0 = 0; c0 < ncols; c0 += WS_NB, ++g) {
+        const uint32_t buf = (uint32_t)(g & 1);
+        // one decision for the four epilogue warps: any abort, or any of their waits giving up
+        const bool mine = mbar_wait(&S.acc_full[buf], (uint32_t)((g >> 1) & 1));
+        if (!mine) atomicOr(&S.epi_fail, 1);
+        ws_epi_sync();
+        if (t == 128) S.epi_abort = (S.epi_fail || *abort_flag) ? 1 : 0;
+        ws_epi_sync();
+        if (S.epi_abort) {
+          if (t == 128) give_up();
+          stop = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d0 = tmem + buf * (uint32_t)(MTC * WS_NB);
+        for (int cg = 0; cg < WS_NB / 16; ++cg, ++grp) {
+          float* sb = S.stg[grp & 1];
+          if (t >= 128 && t < 144) bulk_wait_read<1>();
+          ws_epi_sync();
+          for (int mt = 0; mt < MT; ++mt) {
+            float v[16];
+            tmem_ld16(d0 + ((uint32_t)(32 * q4) << 16) + (uint32_t)(WS_NB * mt + 16 * cg), v);
+            const int row = 128 * mt + 32 * q4 + lane;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) sb[c * RT + row] = v[c];
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          ws_epi_sync();
+          if (t >= 128 && t < 144) {
+            const int c = c0 + 16 * cg + (t - 128);
+            if (c < ncols) {
+              const int p = c / nrhs, rr = c - p * nrhs;
+              float2* dst = cin + (int64_t)rr * ldc + ptgt[U.p_begin + p];
+              if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0 && (U.M & 1) == 0)
+                bulk_reduce_add(dst, sb + (t - 128) * RT, 8u * (uint32_t)U.M);
+              else
+                atomicExch(err, 2);  // never made by a plan: reported, skipped
+            }
+            bulk_commit();
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) ws_arrive(&S.acc_empty[buf]);
+      }
+      if (stop) break;
+    }
+    if (t >= 128 && t < 144) bulk_wait_read<0>();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (w == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
+  }
+}
+
+template <int MTC>
+static int ws_launch_t(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc,
+                       const int64_t* ptgt, const int64_t* pmid, const float2* cout, float2* cin, const float2* mid,
+                       int nrhs, int64_t ldc, int64_t ldm, int* err, cudaStream_t s) {
+  const size_t smem = sizeof(WsSmem<MTC>) + 1024;
+  static bool attr = false;
+  static int nsm = 0;
+  if (!attr) {
+    FDA_CUDA(cudaFuncSetAttribute(k_m2l_ws<MTC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0;
+    FDA_CUDA(cudaGetDevice(&dev));
+    FDA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    attr = true;
+  }
+  const unsigned grid = (unsigned)std::min<size_t>(nunits, (size_t)std::max(1, nsm));
+  k_m2l_ws<MTC><<<grid, WS_NT, smem, s>>>(units, (int)nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, ldc, ldm,
+                                          err);
+  FDA_LAUNCH_CHECK();
+  return FDA_OK;
+}
+
+// units: modes 0 or 2 with 2 K <= 64 real columns, even M; max_mt: largest row-tile count (<= 4)
+int m2l_ws_launch(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc, const int64_t* ptgt,
+                  const int64_t* pmid, const float2* cout, float2* cin, const float2* mid, int nrhs, int64_t ldc,
+                  int64_t ldm, int max_mt, int* err, cudaStream_t s) {
+  if (nunits == 0) return FDA_OK;
+  if (nunits > (size_t)INT32_MAX) {
+    set_error("too many units for the persistent scatter kernel");
+    return FDA_E_INVALID_ARG;
+  }
+  if (max_mt <= 2) return ws_launch_t<2>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, ldc, ldm, err, s);
+  if (max_mt == 3) return ws_launch_t<3>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, ldc, ldm, err, s);
+  if (max_mt == 4) return ws_launch_t<4>(units, nunits, img, psrc, ptgt, pmid, cout, cin, mid, nrhs, ldc, ldm, err, s);
+  set_error("persistent scatter kernel: at most 4 row tiles (got %d)", max_mt);
   return FDA_E_INVALID_ARG;
 }
 

@@ -22,6 +22,12 @@ int m2l_tc3_launch(const GemmUnit* units, size_t nunits, const float* img, const
 int m2l_vsw_launch(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc, const int64_t* pmid,
                    const float2* cout, float2* mid, int nrhs, int64_t ldc, int64_t ldm, int nb, int nst, int* err,
                    cudaStream_t s);
+int m2l_vtm_launch(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc, const int64_t* pmid,
+                   float2* mid, int64_t base, int s_l, const CUtensorMap* map, int nb, int nst, int* err,
+                   cudaStream_t s);
+int m2l_ws_launch(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc, const int64_t* ptgt,
+                  const int64_t* pmid, const float2* cout, float2* cin, const float2* mid, int nrhs, int64_t ldc,
+                  int64_t ldm, int max_mt, int* err, cudaStream_t s);
 int m2l_tc_launch(const GemmUnit* units, size_t nunits, const float2* poolK, const float2* poolLR,
                   const int64_t* psrc, const int64_t* ptgt, const int64_t* pmid, const float2* cout, float2* cin,
                   float2* mid, int nrhs, int64_t ldc, int64_t ldm, int split, int max_rows, int* err, cudaStream_t s);
@@ -442,7 +448,10 @@ static __global__ void __launch_bounds__(256) k_m2l(const GemmUnit* units, const
 // 2 = TF32 or 3xTF32 with operands expanded in the kernel (plan option m2l_tensor = 2), 3 to 5 = variant 1
 // with its alternative tile shapes 1 to 3, 6 and 7 = variant 1 with the bulk-reduction epilogue (default and
 // single-stage shape), 8 and 9 = stage 0 only: the swapped-operand V^ kernel (one or two pipeline stages) for
-// the low-rank units and variant 6 for the dense ones (6 to 9 are picked by the autotuner only)
+// the low-rank units and variant 6 for the dense ones, 10 = stage 1 only: the persistent warp-specialised
+// scatter kernel for the short-K U^ units and variant 6 for the rest, 11 = variant 1 with the bulk-reduction
+// epilogue, 32 columns and exactly the row tiles needed, 12 and 13 = stage 0 only: the V^ kernel fed by TMA row
+// gathers with four and three stages (one right-hand side; otherwise variant 8) (6 to 13: autotuner only)
 int m2l_variant(const fda_plan_s* P, int l, int st) {
   if (P->m2l_choice[l][st] >= 0) return P->m2l_choice[l][st];
   if ((P->cfg.m2l_tensor == 1 || P->cfg.m2l_tensor == 3) && !P->h_tc3_units[l][st].empty() &&
@@ -459,13 +468,21 @@ int m2l_stage(fda_plan_s* P, RunOps<C>& op, DBuf<C>& cout, DBuf<C>& cin, DBuf<C>
   // the image kernels cover at most 4 row tiles (256 complex rows): a forced variant falls back to FMA beyond
   const bool tc3_fits = P->tc3_mt[l][st] <= 4;
   const bool x3 = P->cfg.m2l_tensor == 3;  // 3xTF32 images: the split kernel for every tensor-core variant
-  if ((variant == 8 || variant == 9) && f32 && !x3 && st == 0 && !P->h_vsw_units[l].empty() && P->dn_mt[l] <= 4) {
+  // the TMA-fed V^ kernel serves one right-hand side; for more it is the swapped kernel
+  const bool vtm = (variant == 12 || variant == 13) && nrhs == 1 && P->vtm_ok[l];
+  if ((variant == 8 || variant == 9 || variant == 12 || variant == 13) && f32 && !x3 && st == 0 &&
+      !P->h_vsw_units[l].empty() && P->dn_mt[l] <= 4) {
     for (int c = 0; c < 4; ++c) {
       const int64_t u0 = P->vsw_cls[l][c], u1 = P->vsw_cls[l][c + 1];
       if (u1 == u0) continue;
-      FDA_TRY(m2l_vsw_launch(P->vsw_units[l].p + u0, (size_t)(u1 - u0), P->tc_img.p, P->pair_src.p, P->pair_mid.p,
-                             (const float2*)cout.p, (float2*)mid.p, nrhs, P->n_coef, P->n_mid, 32 << c,
-                             variant == 8 ? 1 : 2, P->tc_err.p, s));
+      if (vtm && !(c == 3 && variant == 12))
+        FDA_TRY(m2l_vtm_launch(P->vsw_units[l].p + u0, (size_t)(u1 - u0), P->tc_img.p, P->pair_src.p, P->pair_mid.p,
+                               (float2*)mid.p, P->vtm_base[l], P->lev[l].s, &P->vtm_map[l], 32 << c,
+                               variant == 12 ? 4 : 3, P->tc_err.p, s));
+      else
+        FDA_TRY(m2l_vsw_launch(P->vsw_units[l].p + u0, (size_t)(u1 - u0), P->tc_img.p, P->pair_src.p, P->pair_mid.p,
+                               (const float2*)cout.p, (float2*)mid.p, nrhs, P->n_coef, P->n_mid, 32 << c,
+                               variant == 9 ? 2 : 1, P->tc_err.p, s));
       *nl += (int64_t)((u1 - u0 + 65534) / 65535);
     }
     if (!P->h_dn_units[l].empty()) {
@@ -476,8 +493,24 @@ int m2l_stage(fda_plan_s* P, RunOps<C>& op, DBuf<C>& cout, DBuf<C>& cin, DBuf<C>
     }
     return FDA_OK;
   }
-  if ((variant == 1 || (variant >= 3 && variant <= 7)) && f32 && !P->h_tc3_units[l][st].empty() && tc3_fits) {
-    const int shape = x3 ? (variant == 7 ? 7 : 6) : (variant >= 3 ? variant - 2 : 0);
+  if (variant == 10 && f32 && !x3 && st == 1 && !P->h_ws_units[l].empty() && tc3_fits) {
+    // short-K U^ units on the persistent warp-specialised kernel, the rest with the bulk-reduction epilogue
+    FDA_TRY(m2l_ws_launch(P->ws_units[l].p, P->h_ws_units[l].size(), P->tc_img.p, P->pair_src.p, P->pair_tgt.p,
+                          P->pair_mid.p, (const float2*)cout.p, (float2*)cin.p, (const float2*)mid.p, nrhs, P->n_coef,
+                          P->n_mid, P->ws_mt[l], P->tc_err.p, s));
+    ++*nl;
+    const size_t n3 = P->h_tc3_units[l][st].size(), ns = (size_t)P->tc3_split[l][st];
+    if (n3 > ns) {
+      FDA_TRY(m2l_tc3_launch(P->tc3_units[l][st].p + ns, n3 - ns, P->tc_img.p, P->pair_src.p, P->pair_tgt.p,
+                             P->pair_mid.p, (const float2*)cout.p, (float2*)cin.p, (float2*)mid.p, nrhs, P->n_coef,
+                             P->n_mid, P->tc3_mt[l][st], P->tc3_maxk[l][st], P->tc_err.p, s, 4));
+      *nl += (int64_t)((n3 - ns + 65534) / 65535);
+    }
+    return FDA_OK;
+  }
+  if ((variant == 1 || (variant >= 3 && variant <= 7) || variant == 11) && f32 && !P->h_tc3_units[l][st].empty() &&
+      tc3_fits) {
+    const int shape = x3 ? (variant == 7 ? 7 : 6) : (variant == 11 ? 8 : (variant >= 3 ? variant - 2 : 0));
     const size_t n3 = P->h_tc3_units[l][st].size(), ns = (size_t)P->tc3_split[l][st];
     // short-K units (single-stage launch), then the rest
     if (ns) {
@@ -756,7 +789,12 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
       if (tv == 1) {
         std::vector<int> alts = {3, 4, 5, 6, 7};
         if (P->cfg.m2l_tensor == 3) alts = {7};  // 3xTF32: atomics (1) or bulk reductions (7)
-        else if (st == 0 && !P->h_vsw_units[l].empty()) alts.push_back(8), alts.push_back(9);
+        else if (st == 0 && !P->h_vsw_units[l].empty()) {
+          alts.push_back(8), alts.push_back(9);
+          if (nrhs == 1 && P->vtm_ok[l]) alts.push_back(12), alts.push_back(13);
+        }
+        else if (st == 1 && !P->h_ws_units[l].empty()) alts.push_back(10);
+        if (P->cfg.m2l_tensor != 3) alts.push_back(11);
         for (int alt : alts) {
           double ta = 0;
           FDA_TRY(time_ms(s, [&]() { return m2l_stage<float2>(P, P->op32, P->cout32, P->cin32, P->mid32, l, st, alt,

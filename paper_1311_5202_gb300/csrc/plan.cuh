@@ -1,5 +1,7 @@
 // Plan layout: translation operators, near-field matrices and execution schedules.
 #pragma once
+#include <cuda.h>
+
 #include "internal.cuh"
 
 namespace fda {
@@ -123,6 +125,15 @@ struct fda_plan_s {
   std::vector<fda::GemmUnit> h_vsw_units[FDA_MAXLEV];
   fda::DBuf<fda::GemmUnit> vsw_units[FDA_MAXLEV];
   int64_t vsw_cls[FDA_MAXLEV][5] = {{0}};
+  // TMA-fed V^ kernel (one right-hand side): per level, a 2-D tensor map over the level's FP32 outgoing
+  // coefficient vectors (rows of 2 s floats, 128-byte swizzle, boxes of 32 floats x 1 row for tile::gather4)
+  alignas(64) CUtensorMap vtm_map[FDA_MAXLEV];
+  bool vtm_ok[FDA_MAXLEV] = {false};
+  int64_t vtm_base[FDA_MAXLEV] = {0};
+  // persistent warp-specialised scatter kernel: the short-K U^-stage units (2 r <= 64), up to 512 pairs each
+  std::vector<fda::GemmUnit> h_ws_units[FDA_MAXLEV];
+  fda::DBuf<fda::GemmUnit> ws_units[FDA_MAXLEV];
+  int ws_mt[FDA_MAXLEV] = {0};
   // the dense (mode 0) units of stage 0, run by the TF32 kernel beside the swapped V^ kernel
   std::vector<fda::GemmUnit> h_dn_units[FDA_MAXLEV];
   fda::DBuf<fda::GemmUnit> dn_units[FDA_MAXLEV];

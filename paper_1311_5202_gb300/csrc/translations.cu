@@ -415,6 +415,48 @@ static int to_fp32(const DBuf<double2>& a, DBuf<C>& b) {
   return FDA_OK;
 }
 
+// Tensor maps of the TMA-fed V^ kernel: for every level whose V^ stage has swapped-kernel units, the level's
+// outgoing coefficient vectors of the first right-hand side (boxes consecutive in the tree, nw vectors of s
+// complex values each) as a 2-D FP32 tensor of 2 s columns. A level whose map cannot be encoded keeps the
+// other V^ kernels.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static int build_vtm_maps(fda_plan_s* P) {
+  static EncodeTiledFn encode = nullptr;
+  if (!encode) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !f)
+      return FDA_OK;  // no tensor maps: the TMA-fed kernel stays unused
+    encode = (EncodeTiledFn)f;
+  }
+  for (int l = 0; l < FDA_MAXLEV; ++l) {
+    P->vtm_ok[l] = false;
+    const LevelOps& L = P->lev[l];
+    if (P->h_vsw_units[l].empty() || !L.used || L.s <= 0 || (L.s & 1)) continue;
+    const int64_t b0 = L.box_begin, b1 = L.box_end;
+    if (b1 <= b0 || P->h_slot[b0] < 0) continue;
+    const int64_t base = P->h_slot[b0];
+    const int64_t nvec = (b1 - b0) * L.nw;
+    if (nvec >= ((int64_t)1 << 31)) continue;
+    void* addr = P->cout32.p + base;
+    if ((reinterpret_cast<uintptr_t>(addr) & 15) != 0) continue;
+    const cuuint64_t dims[2] = {(cuuint64_t)(2 * L.s), (cuuint64_t)nvec};
+    const cuuint64_t strides[1] = {(cuuint64_t)(8 * L.s)};
+    const cuuint32_t box[2] = {32, 1};
+    const cuuint32_t estr[2] = {1, 1};
+    if (encode(&P->vtm_map[l], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, addr, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
+      P->vtm_ok[l] = true;
+      P->vtm_base[l] = base;
+    }
+  }
+  return FDA_OK;
+}
+
 static double now_ms() {
   using namespace std::chrono;
   return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
@@ -1299,6 +1341,13 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
         while (v < T->nm2l && T->h_m2l_info[6 * order[v]] == l && pair_off[order[v]] == id) ++v;
         const OffInfo& o = offs[l][id];
         const int sl = P->lev[l].s;
+        if (o.rank > 0 && 2 * o.rank <= 64 && (sl & 1) == 0 && (2 * sl + 127) / 128 <= 4) {
+          for (int64_t p0 = u3; p0 < v; p0 += 512) {
+            const int pc = (int)std::min<int64_t>(512, v - p0);
+            P->h_ws_units[l].push_back({img_of[l][id][2], sl, o.rank, p0, pc, 0, 2, 0});
+            P->ws_mt[l] = std::max(P->ws_mt[l], (2 * sl + 127) / 128);
+          }
+        }
         for (int64_t p0 = u3; p0 < v; p0 += CP3) {
           int pc = (int)std::min<int64_t>(CP3, v - p0);
           if (o.rank > 0) {
@@ -1348,6 +1397,7 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
         P->vsw_cls[l][4] = (int64_t)P->h_vsw_units[l].size();
         FDA_TRY(P->vsw_units[l].upload(P->h_vsw_units[l]));
         FDA_TRY(P->dn_units[l].upload(P->h_dn_units[l]));
+        FDA_TRY(P->ws_units[l].upload(P->h_ws_units[l]));
       }
     }
   }
@@ -1552,6 +1602,7 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
     FDA_TRY(P->cout32.alloc((size_t)std::max<int64_t>(P->n_coef, 1) * nr));
     FDA_TRY(P->cin32.alloc((size_t)std::max<int64_t>(P->n_coef, 1) * nr));
     FDA_TRY(P->mid32.alloc((size_t)std::max<int64_t>(P->n_mid, 1) * nr));
+    FDA_TRY(build_vtm_maps(P));
   }
   {
     std::vector<int> ls(FDA_MAXLEV, 0), lnw(FDA_MAXLEV, 1);

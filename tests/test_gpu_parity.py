@@ -439,11 +439,14 @@ def kd100_variants():
     S.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 3, 4, 5, 6, 7, 8, 9])
+@pytest.mark.parametrize("variant", [0, 1, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13])
 def test_forced_m2l_variants_match_oracle(kd100_variants, variant):
     """Every M2L kernel variant the autotuner may choose, forced for all levels and stages of one plan: FMA (0),
     TF32 operator images in four tile shapes (1, 3-5), the bulk-reduction epilogue (6, 7), the swapped-operand
-    V^ kernel (8, 9). Each product meets the mixed bar on 256 oracle rows for three right-hand sides. The
+    V^ kernel (8, 9), the persistent warp-specialised U^ kernel (10, with 8 for the V^ stage), the narrow
+    bulk-reduction shape with exact row tiles (11), the V^ kernel fed by TMA row gathers (12, 13; with three
+    right-hand sides it falls back to 8, so a one-column product is checked too). Each product
+    meets the mixed bar on 256 oracle rows for three right-hand sides. The
     tensor-core variants share their TF32 arithmetic and differ from the default one only in the order of the
     additions (2e-5); the FP32 FMA variant differs from it by the TF32 rounding of the translations (5e-4)."""
     S, xd, y0, rows, yo = kd100_variants
@@ -458,6 +461,14 @@ def test_forced_m2l_variants_match_oracle(kd100_variants, variant):
             assert err < 3e-4, (variant, r, err)
             bar = 5e-4 if variant == 0 else 2e-5
             assert np.linalg.norm(y[r] - y0[r]) / np.linalg.norm(y0[r]) < bar, (variant, r)
+        if variant in (12, 13):  # the TMA-fed kernel runs for one right-hand side
+            x1 = xd[0].contiguous()
+            y1 = torch.empty_like(x1)
+            S.matvec(x1, y1)
+            torch.cuda.synchronize()
+            g = y1.cpu().numpy()
+            assert np.linalg.norm(g[rows] - yo[0]) / np.linalg.norm(yo[0]) < 3e-4
+            assert np.linalg.norm(g - y0[0]) / np.linalg.norm(y0[0]) < 2e-5
         assert fdbem.fda_plan_check(S.plan) == fdbem.FDA_OK
     finally:
         fdbem.fda_m2l_force(S.plan, -1)
