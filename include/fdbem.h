@@ -181,7 +181,13 @@ typedef struct {
                         own CSR kernel (one warp per row) before the stream; 2 = as 1, with the stream's
                         density windows double-buffered for one right-hand side (the next window's densities
                         copied while the current one is used). Same sums, other order. */
-  int reserved[2];
+  int drop_fp64;     /* FP32 plans: 1 = release every FP64 operator and near-field matrix once its FP32 copy
+                        exists (about 60% of the device memory of a plan that keeps both). Such a plan serves
+                        fda_matvec in FP32 only (FP64 requests fail with FDA_E_STATE), bm_gmres_solve with
+                        refine = 0 (FP64 Krylov basis around the FP32 operator; with TF32 translations the
+                        rounding stalls GMRES near a 1e-4 residual, with 3xTF32 ones, m2l_tensor = 3, it
+                        reaches 1e-5 and below) and no preconditioner. */
+  int reserved;
   double gamma_re, gamma_im;  /* op = 2: the Robin coefficient gamma = a/b (ignored otherwise) */
 } fda_config_t;
 

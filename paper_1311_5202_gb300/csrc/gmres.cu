@@ -584,7 +584,8 @@ static int gmres_solve_block(GmCtx& C, const double2* b, double2* x, int nc, con
   std::vector<double> rel;
   int it = 0;
   if (!o->refine) {
-    int rc = gmres_block(C, FDA_PREC_FP64, b, x, nc, o->tol, m, o->max_iter, &it, rel, !o->x0_given, B);
+    const int aprec = P->cfg.drop_fp64 ? FDA_PREC_FP32 : FDA_PREC_FP64;  // FP32-only plans: FP32 operator
+    int rc = gmres_block(C, aprec, b, x, nc, o->tol, m, o->max_iter, &it, rel, !o->x0_given, B);
     *total_it += it;
     for (double r : rel) *worst = std::max(*worst, r);
     return rc;
@@ -674,6 +675,10 @@ int gmres_solve(fda_plan_s* P, const double2* b, double2* x, int nrhs, const bm_
   C.nb = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (C.N + GM_NB - 1) / GM_NB));
   int m = std::max(1, std::min(512, o->restart));
   int mi = std::max(1, std::min(512, o->inner_restart > 0 ? o->inner_restart : o->restart));
+  if (P->cfg.drop_fp64 && o->refine) {
+    set_error("the plan released its FP64 operators (drop_fp64): solve with refine = 0");
+    return FDA_E_STATE;
+  }
   FDA_TRY(C.partial.alloc((size_t)C.nb * (std::max(m, mi) + 1)));
   FDA_TRY(C.h.alloc(std::max(m, mi) + 1));
   FDA_TRY(C.hacc.alloc(std::max(m, mi) + 1));
@@ -700,7 +705,8 @@ int gmres_solve(fda_plan_s* P, const double2* b, double2* x, int nrhs, const bm_
     double rel = 0;
     int it = 0;
     if (!o->refine) {
-      rc = gmres_core(C, FDA_PREC_FP64, bc, xc, o->tol, m, o->max_iter, &it, &rel, !o->x0_given);
+      rc = gmres_core(C, P->cfg.drop_fp64 ? FDA_PREC_FP32 : FDA_PREC_FP64, bc, xc, o->tol, m, o->max_iter, &it,
+                      &rel, !o->x0_given);
       total_it += it;
     } else {
       if (P->cfg.precision != FDA_PREC_FP32) {

@@ -732,6 +732,10 @@ int plan_matvec(fda_plan_s* P, int prec, const void* x, void* y, int nrhs, int i
     }
     return matvec_t<float2>(P, P->op32, P->xt32, P->yt32, P->cout32, P->cin32, P->mid32, x, y, nrhs, io_dtype, s);
   }
+  if (P->cfg.drop_fp64) {
+    set_error("the plan released its FP64 operators (drop_fp64): FP32 products only");
+    return FDA_E_STATE;
+  }
   return matvec_t<double2>(P, P->op64, P->xt64, P->yt64, P->cout64, P->cin64, P->mid64, x, y, nrhs, io_dtype, s);
 }
 

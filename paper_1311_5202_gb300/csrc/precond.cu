@@ -391,6 +391,10 @@ int bm_precond_create(fda_plan_t* plan, bm_precond_t** out) {
     set_error("the leaf-block preconditioner needs the boundary-element operator A (op = 0)");
     return FDA_E_STATE;
   }
+  if (plan->cfg.drop_fp64) {
+    set_error("the leaf-block preconditioner inverts the FP64 near-field blocks, which a drop_fp64 plan released");
+    return FDA_E_STATE;
+  }
   fda_tree_s* T = plan->tree;
   bm_precond_s* Pc = new (std::nothrow) bm_precond_s();
   if (!Pc) return FDA_E_OOM;

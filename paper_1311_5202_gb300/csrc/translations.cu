@@ -1154,6 +1154,50 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
       }
     }
   }
+  // the low-rank pool grew by doubling: trim it to the factors it holds
+  if (P->op64.lr.n > (size_t)std::max<int64_t>(lr_tot, 1)) {
+    DBuf<double2> lr;
+    FDA_TRY(lr.alloc(std::max<int64_t>(lr_tot, 1)));
+    if (lr_tot) FDA_CUDA(cudaMemcpy(lr.p, P->op64.lr.p, sizeof(double2) * lr_tot, cudaMemcpyDeviceToDevice));
+    std::swap(P->op64.lr.p, lr.p);
+    std::swap(P->op64.lr.n, lr.n);
+  }
+  // keep the dense K~ only for the offsets without a low-rank form: the products read U^ and V^ for the others
+  {
+    int64_t keep = 0;
+    std::vector<CopyJob> cj;
+    for (int l = lmin; l <= lmax && far; ++l)
+      for (auto& o : offs[l]) {
+        if (o.rank > 0) continue;
+        const int sl = P->lev[l].s;
+        cj.push_back({P->op64.K.p + o.k_off, sl, sl, sl, nullptr});
+        o.k_off = keep;
+        keep += (int64_t)sl * sl;
+      }
+    for (int l = lmin; l <= lmax && far; ++l)
+      for (auto& o : offs[l])
+        if (o.rank > 0) o.k_off = -1;
+    DBuf<double2> Kd;
+    FDA_TRY(Kd.alloc(std::max<int64_t>(keep, 1)));
+    {
+      int64_t o2 = 0;
+      for (auto& j : cj) {
+        j.dst = Kd.p + o2;
+        o2 += (int64_t)j.rows * j.cols;
+      }
+    }
+    if (!cj.empty()) {
+      DBuf<CopyJob> dcj;
+      FDA_TRY(dcj.upload(cj));
+      for (size_t b0 = 0; b0 < cj.size(); b0 += 65535) {
+        k_compact<<<dim3(16, (unsigned)std::min<size_t>(65535, cj.size() - b0)), 256>>>(dcj.p + b0);
+        FDA_LAUNCH_CHECK();
+      }
+      FDA_CUDA(cudaDeviceSynchronize());
+    }
+    std::swap(P->op64.K.p, Kd.p);
+    std::swap(P->op64.K.n, Kd.n);
+  }
   double t5 = now_ms();
   P->setup_ms[5] = t5 - t4;
 
@@ -1584,11 +1628,13 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
   const int nr = P->cfg.nrhs_max;
   FDA_TRY(P->tc_err.alloc(1));
   FDA_TRY(P->tc_err.zero());
-  FDA_TRY(P->xt64.alloc((size_t)N * nr));
-  FDA_TRY(P->yt64.alloc((size_t)N * nr));
-  FDA_TRY(P->cout64.alloc((size_t)std::max<int64_t>(P->n_coef, 1) * nr));
-  FDA_TRY(P->cin64.alloc((size_t)std::max<int64_t>(P->n_coef, 1) * nr));
-  FDA_TRY(P->mid64.alloc((size_t)std::max<int64_t>(P->n_mid, 1) * nr));
+  if (!P->cfg.drop_fp64) {
+    FDA_TRY(P->xt64.alloc((size_t)N * nr));
+    FDA_TRY(P->yt64.alloc((size_t)N * nr));
+    FDA_TRY(P->cout64.alloc((size_t)std::max<int64_t>(P->n_coef, 1) * nr));
+    FDA_TRY(P->cin64.alloc((size_t)std::max<int64_t>(P->n_coef, 1) * nr));
+    FDA_TRY(P->mid64.alloc((size_t)std::max<int64_t>(P->n_mid, 1) * nr));
+  }
   if (P->cfg.precision == FDA_PREC_FP32) {
     FDA_TRY(to_fp32(P->op64.S, P->op32.S));
     FDA_TRY(to_fp32(P->op64.T, P->op32.T));
@@ -1603,6 +1649,16 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
     FDA_TRY(P->cin32.alloc((size_t)std::max<int64_t>(P->n_coef, 1) * nr));
     FDA_TRY(P->mid32.alloc((size_t)std::max<int64_t>(P->n_mid, 1) * nr));
     FDA_TRY(build_vtm_maps(P));
+    if (P->cfg.drop_fp64) {  // FP32-only plan: the FP64 masters go once their copies exist
+      FDA_CUDA(cudaDeviceSynchronize());
+      P->op64.S.release();
+      P->op64.T.release();
+      P->op64.M.release();
+      P->op64.K.release();
+      P->op64.near.release();
+      P->op64.corr.release();
+      P->op64.lr.release();
+    }
   }
   {
     std::vector<int> ls(FDA_MAXLEV, 0), lnw(FDA_MAXLEV, 1);

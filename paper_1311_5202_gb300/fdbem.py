@@ -40,7 +40,7 @@ class FdaError(RuntimeError):
 class fda_config_t(C.Structure):
     _fields_ = [("eps", C.c_double), ("precision", C.c_int), ("lowrank", C.c_int), ("nrhs_max", C.c_int),
                 ("m2l_tensor", C.c_int), ("op", C.c_int), ("near_split", C.c_int),
-                ("reserved", C.c_int * 2), ("gamma_re", C.c_double), ("gamma_im", C.c_double)]
+                ("drop_fp64", C.c_int), ("reserved", C.c_int), ("gamma_re", C.c_double), ("gamma_im", C.c_double)]
 
 
 class bm_gmres_opts_t(C.Structure):
@@ -254,8 +254,9 @@ def fda_tree_destroy(tree):
 
 
 def fda_precompute_translations(tree, eps, precision=FDA_PREC_FP64, lowrank=1, nrhs_max=1, m2l_tensor=0, op=0,
-                                near_split=0, gamma=0.0):
+                                near_split=0, gamma=0.0, drop_fp64=False):
     cfg = fda_config_t()
+    cfg.drop_fp64 = int(bool(drop_fp64))
     cfg.gamma_re = complex(gamma).real
     cfg.gamma_im = complex(gamma).imag
     cfg.eps = float(eps)
@@ -540,12 +541,12 @@ class Solver:
     """Problem + tree + plan with ordered destruction."""
 
     def __init__(self, nodes, elems, k, eps=1e-4, leaf_max=64, precision=FDA_PREC_FP64, lowrank=1, nrhs_max=1,
-                 alpha=None, m2l_tensor=0, op=0, near_split=0, gamma=0.0):
+                 alpha=None, m2l_tensor=0, op=0, near_split=0, gamma=0.0, drop_fp64=False):
         self.k = float(k)
         self.prob = bm_problem_create(nodes, elems, k, alpha)
         self.tree = fda_build_tree(self.prob, leaf_max)
         self.plan = fda_precompute_translations(self.tree, eps, precision, lowrank, nrhs_max, m2l_tensor, op,
-                                                near_split, gamma)
+                                                near_split, gamma, drop_fp64)
         self.N = 6 * int(np.asarray(elems).shape[0])
 
     def matvec(self, x, y, stream=None):

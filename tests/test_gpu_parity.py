@@ -474,6 +474,50 @@ def test_forced_m2l_variants_match_oracle(kd100_variants, variant):
         fdbem.fda_m2l_force(S.plan, -1)
 
 
+def test_fp32_only_plan():
+    """A plan that drops its FP64 operators (drop_fp64 = 1) keeps the mixed product (3e-4 against the oracle,
+    and the same numbers as the plan that keeps both copies), refuses FP64 products and refinement with
+    FDA_E_STATE, solves with GMRES around its FP32 operator, and holds less device memory. The translations
+    are 3xTF32 here: GMRES on an operator whose translations round to TF32 stalls near a 1e-4 residual (the
+    rounding makes the product slightly nonlinear), while FP32-level translations reach 1e-5."""
+    _need_gpu()
+    mesh = inputs.icosphere(14, 0.5)
+    k = 100.0
+    kw = dict(eps=1e-4, leaf_max=64, precision=fdbem.FDA_PREC_FP32, m2l_tensor=3, alpha=-1j / k)
+    S1 = fdbem.Solver(mesh.nodes, mesh.elems, k, **kw)
+    S2 = fdbem.Solver(mesh.nodes, mesh.elems, k, drop_fp64=True, **kw)
+    try:
+        i1, i2 = S1.info(), S2.info()
+        assert i1["device_bytes"] - i2["device_bytes"] >= 16 * i1["near_entries"]  # at least the FP64 near field
+        x = inputs.complex_gaussian(S1.N, 23)
+        xd = torch.from_numpy(x.astype(np.complex64)).to(DEV)
+        y1, y2 = torch.empty_like(xd), torch.empty_like(xd)
+        S1.matvec(xd, y1)
+        S2.matvec(xd, y2)
+        torch.cuda.synchronize()
+        a, b = y2.cpu().numpy(), y1.cpu().numpy()
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-5
+        rows = inputs.sample_rows(S1.N, 128, 7)
+        yo = O.matvec_rows(mesh.nodes, mesh.elems, k, x, rows, beta_h=-1j / k)
+        assert np.linalg.norm(a[rows] - yo) / np.linalg.norm(yo) < 3e-4
+        x64 = torch.from_numpy(x).to(DEV)
+        rc = fdbem.lib().fda_matvec_ex(S2.plan, fdbem.FDA_PREC_FP64, fdbem.C.c_void_p(x64.data_ptr()),
+                                        fdbem.C.c_void_p(torch.empty_like(x64).data_ptr()), 1, fdbem.FDA_CPLX128,
+                                        None)
+        assert rc == fdbem.FDA_E_STATE and "drop_fp64" in fdbem.fda_last_error()
+        bb = torch.empty(S2.N, dtype=torch.complex128, device=DEV)
+        fdbem.bm_rhs_plane_wave(S2.prob, [0.0, 0.0, 1.0], bb)
+        u = torch.zeros_like(bb)
+        st = S2.solve(bb, u, tol=1e-5, restart=100, max_iter=3000, refine=True, raise_on_error=False)
+        assert st["status"] == fdbem.FDA_E_STATE
+        st = S2.solve(bb, u, tol=1e-5, restart=100, max_iter=3000)
+        assert st["status"] == fdbem.FDA_OK and st["rel_residual"] <= 1e-5
+        assert fdbem.fda_plan_check(S2.plan) == fdbem.FDA_OK
+    finally:
+        S2.close()
+        S1.close()
+
+
 # ------------------------------------------------------------------ lockstep block GMRES (several directions)
 @pytest.mark.parametrize("refine", [False, True])
 def test_block_gmres_several_directions_match_oracle(refine):
