@@ -236,7 +236,8 @@ typedef struct {
                              stage 0 with the swapped-operand V^ kernel (one and two pipeline stages), 9: stage
                              1 with the persistent warp-specialised scatter kernel, 10: bulk-reduction epilogue,
                              32 columns, exact row tiles, 11 and 12: stage 0 with the V^ kernel fed by TMA row
-                             gathers (four and three stages) */
+                             gathers (four and three stages), 13 and 14: stage 0 with the swapped V^ kernel in
+                             16-wide K chunks (two and three in flight) */
   double near_ms[2];      /* near field at 4 and 16 right-hand sides per pass (nrhs >= 12; else 0) */
   int32_t near_rhs_per_pass;
   int32_t near_split;     /* near-field schedule kept: 0 = the correction entries outside the direct blocks inside
@@ -255,9 +256,10 @@ int fda_autotune(fda_plan_t* plan, int nrhs, void* stream, fda_tune_report_t* re
  * stage, with variant 6 for the U^ stage, 10 = the persistent warp-specialised scatter kernel for the U^ stage,
  * with variant 8 for the V^ stage, 11 = variant 1 with the bulk-reduction epilogue, 32 columns and exactly the
  * row tiles needed (the most CTAs per SM), 12 and 13 = the V^ kernel fed by TMA row gathers (four and three
- * stages; one right-hand side, else variant 8), with variant 6 for the U^ stage. A variant that does not apply
- * to a (level, stage) runs the FMA kernel there. Errors: FDA_E_INVALID_ARG (variant outside [-1, 13]),
- * FDA_E_STATE (plan without the kernel's operators). */
+ * stages; one right-hand side, else variant 8), 14 and 15 = the swapped V^ kernel with 16-wide K chunks (two
+ * and three in flight), each with variant 6 for the U^ stage. A variant that does not apply to a (level, stage)
+ * runs the FMA kernel there. Errors: FDA_E_INVALID_ARG (variant outside [-1, 15]), FDA_E_STATE (plan without
+ * the kernel's operators). */
 int fda_m2l_force(fda_plan_t* plan, int variant);
 
 /* CUDA-graph form of one product (the batched matvec of many incident directions replayed without
@@ -416,7 +418,8 @@ int fda_wait_selftest(double limit_ms, int* timed_out);
  * in its default tile shape (2) or the autotuner's alternatives (3, 4, 5); 6, 7: the same kernel with the
  * bulk-reduction epilogue (default and single-stage shape); 8, 9: the swapped-operand V^ kernel (one and
  * two stages; M = min(100, K), P = 100, results stored as the low-rank intermediate); 10, 11: 3xTF32 from the
- * TF32 and remainder images of the m2l_tensor = 3 form (atomic and bulk-reduction epilogue).
+ * TF32 and remainder images of the m2l_tensor = 3 form (atomic and bulk-reduction epilogue); 12, 13: the
+ * swapped V^ kernel with 16-wide K chunks (two and three in flight).
  * *max_rel_err is the largest entrywise error relative to the sum of |a||x| over the row, *wait_failed is 1
  * when a bounded device wait gave up. Synchronous. */
 int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_failed);

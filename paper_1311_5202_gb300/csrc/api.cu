@@ -277,7 +277,7 @@ int fda_autotune(fda_plan_t* plan, int nrhs, void* stream, fda_tune_report_t* re
 
 int fda_m2l_force(fda_plan_t* plan, int variant) {
   ARG_CHECK(plan, "NULL plan");
-  ARG_CHECK(variant >= -1 && variant <= 13, "variant outside [-1, 13]");
+  ARG_CHECK(variant >= -1 && variant <= 15, "variant outside [-1, 15]");
   if (variant > 0 && plan->cfg.precision != FDA_PREC_FP32) {
     set_error("tensor-core M2L variants need a plan built with FDA_PREC_FP32");
     return FDA_E_STATE;
@@ -297,6 +297,7 @@ int fda_m2l_force(fda_plan_t* plan, int variant) {
   for (int l = 0; l < FDA_MAXLEV; ++l)
     for (int st = 0; st < 2; ++st)
       plan->m2l_choice[l][st] = (st == 1 && (variant == 8 || variant == 9 || variant >= 12)) ? 6  // V^ only
+                                                                                                 // (8, 9, 12-15)
                                 : (st == 0 && variant == 10) ? 8                       // 10: U^ stage only
                                                              : variant;
   return FDA_OK;

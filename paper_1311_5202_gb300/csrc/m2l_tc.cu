@@ -845,10 +845,10 @@ int m2l_tc3_launch(const GemmUnit* units, size_t nunits, const float* img, const
 // NB columns, so a rank of 16 needs 32 columns instead of 128 lanes x 128 columns in the other orientation:
 // up to 8 CTAs fit on an SM. Epilogue: lane = pair, so each thread writes its pair's 2r outputs as
 // consecutive 16-byte stores into the low-rank intermediate.
-template <int NB, int NST>
+template <int NB, int NST, int KCW = TC3_KC>
 struct VswSmem {
-  alignas(1024) float a[NST][128 * TC3_KC];  // gathered coefficient vectors (128 rows x 32 real K)
-  alignas(1024) float b[NST][NB * TC3_KC];   // operator rows (NB rows x 32 real K)
+  alignas(1024) float a[NST][128 * KCW];  // gathered coefficient vectors (128 rows x KCW real K)
+  alignas(1024) float b[NST][NB * KCW];   // operator rows (NB rows x KCW real K)
   alignas(8) uint64_t bfull[NST];
   uint64_t mdone[NST];
   uint32_t tmem;
@@ -858,12 +858,16 @@ struct VswSmem {
 
 #define VSW_NT 128
 
-template <int NB, int NST>
+// KCW: real K per pipeline chunk, 32 (one image chunk) or 16 (half of one: two chunks in flight in the shared
+// memory one 32-wide chunk takes, so a chunk's gathers overlap the previous chunk's MMAs at the same CTAs per SM)
+template <int NB, int NST, int KCW>
 static __global__ void __launch_bounds__(VSW_NT, 8) k_m2l_vsw(const GemmUnit* units, const float* img,
                                                           const int64_t* psrc, const int64_t* pmid,
                                                           const float2* cout, float2* mid, int nrhs, int64_t ldc,
                                                           int64_t ldm, int* err) {
-  typedef VswSmem<NB, NST> Sm;
+  typedef VswSmem<NB, NST, KCW> Sm;
+  constexpr int HALVES = TC3_KC / KCW;      // pipeline chunks per image chunk (1 or 2)
+  constexpr uint32_t SBO = (KCW / 4) * 128; // bytes between 8-row core-matrix groups
   extern __shared__ unsigned char smem_raw[];
   Sm& S = *reinterpret_cast<Sm*>((((uintptr_t)smem_raw) + 1023) & ~(uintptr_t)1023);
   constexpr int D = NST - 1;
@@ -871,7 +875,8 @@ static __global__ void __launch_bounds__(VSW_NT, 8) k_m2l_vsw(const GemmUnit* un
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   const int MT = (2 * U.M + 127) / 128;  // operator image tiles (1 or 2)
   const int nmma = ((2 * U.M + 15) / 16) * 16;
-  const int nk = (2 * U.K + TC3_KC - 1) / TC3_KC;
+  const int nki = (2 * U.K + TC3_KC - 1) / TC3_KC;  // image chunks
+  const int nk = (2 * U.K + KCW - 1) / KCW;          // pipeline chunks
   const float* A = img + U.a_off;
   const uint32_t idesc = idesc_tf32(128, nmma);
   if (w == 0) {
@@ -907,22 +912,39 @@ static __global__ void __launch_bounds__(VSW_NT, 8) k_m2l_vsw(const GemmUnit* un
   };
   auto issue = [&](int kc) {
     const int q = kc % NST;
-    if (t == 0) {
-      uint32_t bytes = 0;
-      for (int mt = 0; mt < MT; ++mt) bytes += (uint32_t)tc3_ng(U.M, mt) * 1024u;
-      tc3_expect_tx(&S.bfull[q], bytes);
-      for (int mt = 0; mt < MT; ++mt) {
-        const int ng = tc3_ng(U.M, mt);
-        tc3_bulk(S.b[q] + mt * 16 * 256, A + (int64_t)16 * mt * nk * 256 + (int64_t)kc * ng * 256,
-                 (uint32_t)ng * 1024u, &S.bfull[q]);
+    const int ic = kc / HALVES, h = kc % HALVES;  // image chunk and half
+    if (HALVES == 1) {
+      if (t == 0) {
+        uint32_t bytes = 0;
+        for (int mt = 0; mt < MT; ++mt) bytes += (uint32_t)tc3_ng(U.M, mt) * 1024u;
+        tc3_expect_tx(&S.bfull[q], bytes);
+        for (int mt = 0; mt < MT; ++mt) {
+          const int ng = tc3_ng(U.M, mt);
+          tc3_bulk(S.b[q] + mt * 16 * 256, A + (int64_t)16 * mt * nki * 256 + (int64_t)ic * ng * 256,
+                   (uint32_t)ng * 1024u, &S.bfull[q]);
+        }
+      }
+    } else {
+      // half of every 8-row group (the group's first or last four K core matrices, 512 contiguous bytes)
+      if (w == 0) {
+        const int ng0 = tc3_ng(U.M, 0), ngt = ng0 + (MT > 1 ? tc3_ng(U.M, 1) : 0);
+        if (lane == 0) tc3_expect_tx(&S.bfull[q], (uint32_t)ngt * 512u);
+        __syncwarp();
+        for (int gi = lane; gi < ngt; gi += 32) {
+          const int mt = gi < ng0 ? 0 : 1, g = gi < ng0 ? gi : gi - ng0, ng = tc3_ng(U.M, mt);
+          tc3_bulk(S.b[q] + (mt * 16 + g) * (8 * KCW),
+                   A + (int64_t)16 * mt * nki * 256 + (int64_t)ic * ng * 256 + (int64_t)g * 256 + h * (8 * KCW),
+                   512u, &S.bfull[q]);
+        }
       }
     }
     const uint32_t abase = smem_u32(S.a[q]);
-    for (int r = w; r < 32; r += VSW_NT / 32) {
-      const int n = (r >> 1) * 8 + (lane >> 2), j = (r & 1) * 8 + 2 * (lane & 3);
+    // 16-byte segments (two complex values): KCW / 4 per row, consecutive threads along a row
+    for (int seg = t; seg < 128 * (KCW / 4); seg += VSW_NT) {
+      const int n = seg / (KCW / 4), j = seg % (KCW / 4);
       if (S.sbase[n] < 0) continue;  // unused row: its results are never read
-      const int gj = kc * (TC3_KC / 2) + j;
-      const uint32_t dst = abase + kmaj_off(n, 2 * j, TC3_KC);
+      const int gj = kc * (KCW / 2) + 2 * j;
+      const uint32_t dst = abase + kmaj_off(n, 4 * j, KCW);
       const float2* src = gj < U.K ? cout + (int64_t)S.srr[n] * ldc + S.sbase[n] + gj : cout;
       const uint32_t nbytes = gj + 1 < U.K ? 16u : (gj < U.K ? 8u : 0u);  // the rest is zero-filled
       if ((reinterpret_cast<uintptr_t>(src) & 15) == 0) {
@@ -976,10 +998,10 @@ static __global__ void __launch_bounds__(VSW_NT, 8) k_m2l_vsw(const GemmUnit* un
         ph_b[q] ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int s8 = 0; s8 < TC3_KC / 8; ++s8) {
-          if (kc * TC3_KC + s8 * 8 >= 2 * U.K) break;  // K steps past the operator hold only zeros
-          const uint64_t ad = smem_desc(smem_u32(S.a[q]) + s8 * 256, 128, (TC3_KC / 4) * 128);
-          const uint64_t bd = smem_desc(smem_u32(S.b[q]) + s8 * 256, 128, (TC3_KC / 4) * 128);
+        for (int s8 = 0; s8 < KCW / 8; ++s8) {
+          if (kc * KCW + s8 * 8 >= 2 * U.K) break;  // K steps past the operator hold only zeros
+          const uint64_t ad = smem_desc(smem_u32(S.a[q]) + s8 * 256, 128, SBO);
+          const uint64_t bd = smem_desc(smem_u32(S.b[q]) + s8 * 256, 128, SBO);
           tc_mma(tmem, ad, bd, idesc, (kc > 0 || s8 > 0) ? 1 : 0);
         }
         tc_commit(&S.mdone[q]);
@@ -1015,41 +1037,52 @@ static __global__ void __launch_bounds__(VSW_NT, 8) k_m2l_vsw(const GemmUnit* un
   }
 }
 
-template <int NB, int NST>
+template <int NB, int NST, int KCW>
 static int vsw_launch_t(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc,
                         const int64_t* pmid, const float2* cout, float2* mid, int nrhs, int64_t ldc, int64_t ldm,
                         int* err, cudaStream_t s) {
-  const size_t smem = sizeof(VswSmem<NB, NST>) + 1024;
+  const size_t smem = sizeof(VswSmem<NB, NST, KCW>) + 1024;
   static bool attr = false;
   if (!attr) {
-    FDA_CUDA(cudaFuncSetAttribute(k_m2l_vsw<NB, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FDA_CUDA(cudaFuncSetAttribute(k_m2l_vsw<NB, NST, KCW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
   for (size_t u0 = 0; u0 < nunits; u0 += 65535) {
     unsigned n = (unsigned)std::min<size_t>(65535, nunits - u0);
-    k_m2l_vsw<NB, NST><<<n, VSW_NT, smem, s>>>(units + u0, img, psrc, pmid, cout, mid, nrhs, ldc, ldm, err);
+    k_m2l_vsw<NB, NST, KCW><<<n, VSW_NT, smem, s>>>(units + u0, img, psrc, pmid, cout, mid, nrhs, ldc, ldm, err);
     FDA_LAUNCH_CHECK();
   }
   return FDA_OK;
 }
 
 // The swapped V^ kernel for units whose rank r satisfies round16(2 r) <= nb (nb = 32, 64, 128 or 256 TMEM
-// columns); nst = 1 or 2 pipeline stages.
+// columns); nst = 1 or 2 pipeline stages of 32-wide chunks, or -2 / -3 for two / three stages of 16-wide ones.
 int m2l_vsw_launch(const GemmUnit* units, size_t nunits, const float* img, const int64_t* psrc, const int64_t* pmid,
                    const float2* cout, float2* mid, int nrhs, int64_t ldc, int64_t ldm, int nb, int nst, int* err,
                    cudaStream_t s) {
   if (nunits == 0) return FDA_OK;
-#define VSWL(B_, S_) return vsw_launch_t<B_, S_>(units, nunits, img, psrc, pmid, cout, mid, nrhs, ldc, ldm, err, s)
+#define VSWL(B_, S_, W_) \
+  return vsw_launch_t<B_, S_, W_>(units, nunits, img, psrc, pmid, cout, mid, nrhs, ldc, ldm, err, s)
   if (nst == 1) {
-    if (nb == 32) VSWL(32, 1);
-    if (nb == 64) VSWL(64, 1);
-    if (nb == 128) VSWL(128, 1);
-    if (nb == 256) VSWL(256, 1);
-  } else {
-    if (nb == 32) VSWL(32, 2);
-    if (nb == 64) VSWL(64, 2);
-    if (nb == 128) VSWL(128, 2);
-    if (nb == 256) VSWL(256, 2);
+    if (nb == 32) VSWL(32, 1, 32);
+    if (nb == 64) VSWL(64, 1, 32);
+    if (nb == 128) VSWL(128, 1, 32);
+    if (nb == 256) VSWL(256, 1, 32);
+  } else if (nst == 2) {
+    if (nb == 32) VSWL(32, 2, 32);
+    if (nb == 64) VSWL(64, 2, 32);
+    if (nb == 128) VSWL(128, 2, 32);
+    if (nb == 256) VSWL(256, 2, 32);
+  } else if (nst == -2) {  // 16-wide chunks, two in flight
+    if (nb == 32) VSWL(32, 2, 16);
+    if (nb == 64) VSWL(64, 2, 16);
+    if (nb == 128) VSWL(128, 2, 16);
+    if (nb == 256) VSWL(256, 2, 16);
+  } else if (nst == -3) {  // 16-wide chunks, three in flight
+    if (nb == 32) VSWL(32, 3, 16);
+    if (nb == 64) VSWL(64, 3, 16);
+    if (nb == 128) VSWL(128, 3, 16);
+    if (nb == 256) VSWL(256, 3, 16);
   }
 #undef VSWL
   set_error("swapped V^ kernel: no variant for %d TMEM columns and %d stages", nb, nst);
@@ -1588,14 +1621,15 @@ static __global__ void k_wait_probe(uint64_t limit_ns, int* timed_out) {
 // 2..7: TF32 with the pre-expanded operator image (M = min(256, K), P = 100), tile shape split - 2 (6 and 7:
 // the bulk-reduction epilogue); 8, 9: the swapped-operand V^ kernel with one or two stages (M = min(100, K),
 // P = 100, results stored into an intermediate with even-padded vectors as the low-rank stage does);
-// 10, 11: 3xTF32 from the TF32 and remainder images (atomics, bulk reductions).
+// 10, 11: 3xTF32 from the TF32 and remainder images (atomics, bulk reductions); 12, 13: the swapped V^ kernel
+// with 16-wide K chunks (two and three in flight).
 extern "C" int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_failed) {
-  if (K < 1 || K > 1024 || split < 0 || split > 11 || !max_rel_err || !wait_failed) {
+  if (K < 1 || K > 1024 || split < 0 || split > 13 || !max_rel_err || !wait_failed) {
     set_error("bad arguments");
     return FDA_E_INVALID_ARG;
   }
-  const bool vsw = split == 8 || split == 9;
-  const bool x3 = split >= 10;
+  const bool vsw = split == 8 || split == 9 || split == 12 || split == 13;
+  const bool x3 = split == 10 || split == 11;
   // the bulk-reduction epilogue adds whole 16-byte granules: even row counts (as every plan has)
   const bool bulk = split == 6 || split == 7 || split == 11;
   const int Mb = bulk ? std::min(256, (K + 1) & ~1) : std::min(256, K);
@@ -1639,7 +1673,8 @@ extern "C" int fda_tc_selftest(int K, int split, double* max_rel_err, int* wait_
     if (vsw) {
       const int nm = ((2 * M + 15) / 16) * 16;
       const int nb = nm <= 32 ? 32 : nm <= 64 ? 64 : nm <= 128 ? 128 : 256;
-      FDA_TRY(m2l_vsw_launch(du.p, 1, img.p, src.p, pm.p, dX.p, dmid.p, 1, 0, 0, nb, split == 8 ? 1 : 2, err.p, 0));
+      const int vst = split == 8 ? 1 : (split == 9 ? 2 : (split == 12 ? -2 : -3));
+      FDA_TRY(m2l_vsw_launch(du.p, 1, img.p, src.p, pm.p, dX.p, dmid.p, 1, 0, 0, nb, vst, err.p, 0));
       FDA_CUDA(cudaDeviceSynchronize());
       FDA_CUDA(cudaMemcpy(dY.p, dmid.p, sizeof(float2) * P * Mp, cudaMemcpyDeviceToDevice));
     } else {

@@ -451,7 +451,8 @@ static __global__ void __launch_bounds__(256) k_m2l(const GemmUnit* units, const
 // the low-rank units and variant 6 for the dense ones, 10 = stage 1 only: the persistent warp-specialised
 // scatter kernel for the short-K U^ units and variant 6 for the rest, 11 = variant 1 with the bulk-reduction
 // epilogue, 32 columns and exactly the row tiles needed, 12 and 13 = stage 0 only: the V^ kernel fed by TMA row
-// gathers with four and three stages (one right-hand side; otherwise variant 8) (6 to 13: autotuner only)
+// gathers with four and three stages (one right-hand side; otherwise variant 8), 14 and 15 = stage 0 only: the
+// swapped V^ kernel with 16-wide K chunks, two and three in flight (6 to 15: autotuner only)
 int m2l_variant(const fda_plan_s* P, int l, int st) {
   if (P->m2l_choice[l][st] >= 0) return P->m2l_choice[l][st];
   if ((P->cfg.m2l_tensor == 1 || P->cfg.m2l_tensor == 3) && !P->h_tc3_units[l][st].empty() &&
@@ -470,8 +471,9 @@ int m2l_stage(fda_plan_s* P, RunOps<C>& op, DBuf<C>& cout, DBuf<C>& cin, DBuf<C>
   const bool x3 = P->cfg.m2l_tensor == 3;  // 3xTF32 images: the split kernel for every tensor-core variant
   // the TMA-fed V^ kernel serves one right-hand side; for more it is the swapped kernel
   const bool vtm = (variant == 12 || variant == 13) && nrhs == 1 && P->vtm_ok[l];
-  if ((variant == 8 || variant == 9 || variant == 12 || variant == 13) && f32 && !x3 && st == 0 &&
-      !P->h_vsw_units[l].empty() && P->dn_mt[l] <= 4) {
+  if ((variant == 8 || variant == 9 || variant == 12 || variant == 13 || variant == 14 || variant == 15) && f32 &&
+      !x3 && st == 0 && !P->h_vsw_units[l].empty() && P->dn_mt[l] <= 4) {
+    const int vst = variant == 9 ? 2 : (variant == 14 ? -2 : (variant == 15 ? -3 : 1));  // swapped-kernel stages
     for (int c = 0; c < 4; ++c) {
       const int64_t u0 = P->vsw_cls[l][c], u1 = P->vsw_cls[l][c + 1];
       if (u1 == u0) continue;
@@ -481,8 +483,8 @@ int m2l_stage(fda_plan_s* P, RunOps<C>& op, DBuf<C>& cout, DBuf<C>& cin, DBuf<C>
                                variant == 12 ? 4 : 3, P->tc_err.p, s));
       else
         FDA_TRY(m2l_vsw_launch(P->vsw_units[l].p + u0, (size_t)(u1 - u0), P->tc_img.p, P->pair_src.p, P->pair_mid.p,
-                               (const float2*)cout.p, (float2*)mid.p, nrhs, P->n_coef, P->n_mid, 32 << c,
-                               variant == 9 ? 2 : 1, P->tc_err.p, s));
+                               (const float2*)cout.p, (float2*)mid.p, nrhs, P->n_coef, P->n_mid, 32 << c, vst,
+                               P->tc_err.p, s));
       *nl += (int64_t)((u1 - u0 + 65534) / 65535);
     }
     if (!P->h_dn_units[l].empty()) {
@@ -794,7 +796,7 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
         std::vector<int> alts = {3, 4, 5, 6, 7};
         if (P->cfg.m2l_tensor == 3) alts = {7};  // 3xTF32: atomics (1) or bulk reductions (7)
         else if (st == 0 && !P->h_vsw_units[l].empty()) {
-          alts.push_back(8), alts.push_back(9);
+          alts.push_back(8), alts.push_back(9), alts.push_back(14), alts.push_back(15);
           if (nrhs == 1 && P->vtm_ok[l]) alts.push_back(12), alts.push_back(13);
         }
         else if (st == 1 && !P->h_ws_units[l].empty()) alts.push_back(10);

@@ -328,7 +328,8 @@ def fda_autotune(plan, nrhs=1, stream=None) -> dict:
     rows = [dict(level=R.level[e], stage=R.stage[e], ms_fma=R.ms_fma[e], ms_tensor=R.ms_tensor[e],
                  chosen=("fma", "tensor", "tensor-alt1", "tensor-alt2", "tensor-alt3", "tensor-bulk",
                          "tensor-bulk-1stage", "vhat-swapped", "vhat-swapped-2stage", "uhat-persistent",
-                         "tensor-bulk-narrow", "vhat-tma-4stage", "vhat-tma-3stage")[R.chosen[e]])
+                         "tensor-bulk-narrow", "vhat-tma-4stage", "vhat-tma-3stage", "vhat-swapped-k16-2stage",
+                         "vhat-swapped-k16-3stage")[R.chosen[e]])
             for e in range(R.entries)]
     return dict(m2l=rows, near_ms=list(R.near_ms), near_rhs_per_pass=R.near_rhs_per_pass,
                 near_split=R.near_split, near_split_ms=list(R.near_split_ms), near_window_ms=R.near_window_ms)

@@ -380,14 +380,14 @@ def test_tiny_mesh_without_far_field():
 
 
 # ------------------------------------------------------------------ tensor-core M2L (tcgen05)
-@pytest.mark.parametrize("split", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11])
+@pytest.mark.parametrize("split", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13])
 def test_tensor_core_selftest(split):
     """A complex operator applied to gathered columns on the tensor cores against an FP64 host product (TF32:
     ~1e-4 of the row scale; 3xTF32 split: FP32 level). split 2..5 is the pre-expanded-image kernel in its four
     tile shapes with M = min(256, K) rows: K = 8, 37 (one 128-row tile, ragged K), 111 (two tiles), 222 (four
     tiles); 6, 7 the same kernel with the bulk-reduction epilogue; 8, 9 the swapped-operand V^ kernel
     (M = min(100, K): 32, 128 and 256 TMEM columns, one and two operator tiles); 10, 11 3xTF32 from the TF32
-    and remainder images (FP32 level)."""
+    and remainder images (FP32 level); 12, 13 the swapped kernel with 16-wide K chunks."""
     _need_gpu()
     for K in ((16, 111, 222) if split < 2 else (8, 37, 111, 222)):
         err, wait_failed = fdbem.fda_tc_selftest(K, split)
@@ -439,13 +439,14 @@ def kd100_variants():
     S.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13])
+@pytest.mark.parametrize("variant", [0, 1, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15])
 def test_forced_m2l_variants_match_oracle(kd100_variants, variant):
     """Every M2L kernel variant the autotuner may choose, forced for all levels and stages of one plan: FMA (0),
     TF32 operator images in four tile shapes (1, 3-5), the bulk-reduction epilogue (6, 7), the swapped-operand
     V^ kernel (8, 9), the persistent warp-specialised U^ kernel (10, with 8 for the V^ stage), the narrow
     bulk-reduction shape with exact row tiles (11), the V^ kernel fed by TMA row gathers (12, 13; with three
-    right-hand sides it falls back to 8, so a one-column product is checked too). Each product
+    right-hand sides it falls back to 8, so a one-column product is checked too), the swapped V^ kernel with
+    16-wide K chunks (14, 15). Each product
     meets the mixed bar on 256 oracle rows for three right-hand sides. The
     tensor-core variants share their TF32 arithmetic and differ from the default one only in the order of the
     additions (2e-5); the FP32 FMA variant differs from it by the TF32 rounding of the translations (5e-4)."""
