@@ -349,6 +349,12 @@ def main():
     ap.add_argument("--m2l-variant", type=int, default=None,
                     help="pin one M2L kernel variant for every level and stage instead of autotuning "
                          "(fda_m2l_force; used to profile one kernel)")
+    ap.add_argument("--overlap", type=int, default=None, choices=[0, 1, 2],
+                    help="force the FP32 product schedule instead of the autotuner's (0 serial; 1, 2 far field on "
+                         "a second stream beside the near field at two or one CTAs per SM; fda_overlap_force)")
+    ap.add_argument("--near-evict", type=int, default=None, choices=[0, 1],
+                    help="force the L2 policy of the near-field matrix copies (1 evict-first) instead of the "
+                         "autotuner's")
     ap.add_argument("--table1", action="store_true",
                     help="run only the particle summations of the paper's Table 1 and print their JSON line")
     ap.add_argument("--table1-max", type=int, default=3, help="number of Table 1 sizes (4 adds N = 4.7M)")
@@ -388,6 +394,10 @@ def main():
     tune_main = None if (args.no_tune or args.m2l_variant is not None) else fdbem.fda_autotune(S.plan, nrhs)
     if args.m2l_variant is not None:
         fdbem.fda_m2l_force(S.plan, args.m2l_variant)
+    overlap = args.overlap if args.overlap is not None else (tune_main["overlap"] if tune_main else 0)
+    evict = args.near_evict if args.near_evict is not None else (tune_main["near_evict_first"] if tune_main else 0)
+    if args.overlap is not None or args.near_evict is not None:
+        fdbem.fda_overlap_force(S.plan, overlap, evict)
     info = S.info()
     X = inputs.complex_gaussian(N, 20131120, nrhs=nrhs if nrhs > 1 else None)
     xd = torch.from_numpy(X).to(dev).contiguous()
@@ -622,7 +632,11 @@ def main():
         "gpu_launches": launches * args.steps,
         "clocks": clocks.summary(local),
         "fp64": {"matvec_per_s": 1000.0 / ms64, "ms_per_matvec": ms64, "phase_ms": ph64},
-        "mixed": {"matvec_per_s": 1000.0 / ms32, "ms_per_matvec": ms32, "phase_ms": ph32},
+        "mixed": {"matvec_per_s": 1000.0 / ms32, "ms_per_matvec": ms32, "phase_ms": ph32,
+                  "schedule": ["serial", "two streams, near field at 2 CTAs/SM",
+                               "two streams, near field at 1 CTA/SM"][overlap]
+                  + (", near-field matrices evict-first in L2" if evict else ""),
+                  "phase_note": "phase_ms come from one serial product with an event between phases"},
         "speedup_matvec_mixed_vs_fp64": ms64 / ms32,
         "near_field": {"kernel": near_kernel, "ms": ph32["near"], "achieved_gbs": near_gbs,
                        "peak_gbs": peaks["hbm_gbs"], "frac": near_gbs / peaks["hbm_gbs"],

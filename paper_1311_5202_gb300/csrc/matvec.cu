@@ -579,9 +579,25 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
   k_perm_in<C><<<cdiv(N * nrhs, 256), 256, 0, s>>>(x, io, T->perm.p, N, nrhs, xt.p);
   FDA_LAUNCH_CHECK();
   ev(1);
+  // FP32 products may run the far field on the plan's side stream while the near field streams on s. The
+  // two share only xt (read by both) and yt (written by the near field, then added to by L2T after the join).
+  const bool ovl = std::is_same<C, float2>::value && (P->overlap == 1 || P->overlap == 2) && !P->phase_ev &&
+                   P->side && P->n_coef > 0 && P->n_near_tleaf > 0 && P->near_max_nr <= 256;
+  const cudaStream_t sf = ovl ? P->side : s;
+  if (ovl) {
+    FDA_CUDA(cudaEventRecord(P->ev_fork, s));
+    FDA_CUDA(cudaStreamWaitEvent(P->side, P->ev_fork, 0));
+  }
   // near field
   if (P->n_near_tleaf > 0 && P->near_max_nr <= 256) {
-    FDA_TRY(near_stream<C>(P, op.near.p, op.corr.p, xt.p, yt.p, nrhs, s, &nl));
+    P->near_sel = ovl ? P->overlap : 0;
+    const int rc = near_stream<C>(P, op.near.p, op.corr.p, xt.p, yt.p, nrhs, s, &nl);
+    P->near_sel = 0;
+    if (rc != FDA_OK && ovl) {  // rejoin the side stream so that no capture or later work sees it forked
+      cudaEventRecord(P->ev_fork, P->side);
+      cudaStreamWaitEvent(s, P->ev_fork, 0);
+    }
+    FDA_TRY(rc);
   } else if (P->n_near_tleaf > 0) {
     static bool attr_set = false;
     if (!attr_set) {
@@ -621,13 +637,13 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
     // the grouped tensor-core M2M accumulates into the parents: clear the outgoing coefficients first
     const bool tc_mm = std::is_same<C, float2>::value && (P->cfg.m2l_tensor == 1 || P->cfg.m2l_tensor == 3);
     const int mm_shape = P->cfg.m2l_tensor == 3 ? 6 : 0;
-    if (tc_mm) FDA_TRY(zero_parent_coefs<C>(P, cout, nrhs, s));
+    if (tc_mm) FDA_TRY(zero_parent_coefs<C>(P, cout, nrhs, sf));
     // S2M
     if (!P->h_leaves.empty()) {
       int rc = chunk(maxleaf);
       for (int r0 = 0; r0 < nrhs; r0 += rc) {
         int rcc = std::min(rc, nrhs - r0);
-        k_s2m<C><<<dim3((unsigned)P->h_leaves.size(), maxnw), 128, sizeof(C) * maxleaf * rcc, s>>>(
+        k_s2m<C><<<dim3((unsigned)P->h_leaves.size(), maxnw), 128, sizeof(C) * maxleaf * rcc, sf>>>(
             P->leaves.p, P->leaf_s_off.p, T->pb.p, T->pe.p, T->lev.p, P->slot.p, d_ls, d_lnw, op.S.p, xt.p,
             cout.p, nrhs, P->n_coef, r0, rcc);
         FDA_LAUNCH_CHECK();
@@ -641,7 +657,7 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
       if (tc_mm && !P->h_mm_units[l].empty()) {
         FDA_TRY(m2l_tc3_launch(P->mm_units[l].p, P->h_mm_units[l].size(), P->tc_img.p, P->mm_src.p, P->mm_tgt.p,
                                P->mm_src.p, (const float2*)cout.p, (float2*)cout.p, (float2*)cout.p, nrhs, P->n_coef,
-                               P->n_coef, P->mm_mt[l], P->lev[l + 1].s, P->tc_err.p, s, mm_shape));
+                               P->n_coef, P->mm_mt[l], P->lev[l + 1].s, P->tc_err.p, sf, mm_shape));
         ++nl;
         continue;
       }
@@ -651,7 +667,7 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
         int rcc = std::min(rc, nrhs - r0);
         int nt = 128;
         while (nt * 4 < L.s * rcc && nt < 512) nt *= 2;
-        k_m2m<C><<<dim3((unsigned)P->h_parents[l].size(), L.nw), nt, sizeof(C) * Lc.s * rcc, s>>>(
+        k_m2m<C><<<dim3((unsigned)P->h_parents[l].size(), L.nw), nt, sizeof(C) * Lc.s * rcc, sf>>>(
             P->parents[l].p, T->cbeg.p, T->nch.p, T->ix.p, T->iy.p, T->iz.p, P->slot.p, L.s, Lc.s, L.nw, L.n, Lc.n,
             Lc.hf ? 1 : 0, op.M.p + P->m_off[l], cout.p, nrhs, P->n_coef, r0, rcc);
         FDA_LAUNCH_CHECK();
@@ -660,9 +676,9 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
     }
     ev(4);
     // M2L
-    FDA_CUDA(cudaMemsetAsync(cin.p, 0, sizeof(C) * P->n_coef * nrhs, s));
+    FDA_CUDA(cudaMemsetAsync(cin.p, 0, sizeof(C) * P->n_coef * nrhs, sf));
     for (int l = P->lmin; l <= P->lmax; ++l)
-      for (int st = 0; st < 2; ++st) FDA_TRY(m2l_stage<C>(P, op, cout, cin, mid, l, st, m2l_variant(P, l, st), nrhs, s, &nl));
+      for (int st = 0; st < 2; ++st) FDA_TRY(m2l_stage<C>(P, op, cout, cin, mid, l, st, m2l_variant(P, l, st), nrhs, sf, &nl));
     ev(5);
     // L2L top-down
     for (int l = P->lmin; l < P->lmax; ++l) {
@@ -672,7 +688,7 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
       if (tc_mm && !P->h_ll_units[l].empty()) {
         FDA_TRY(m2l_tc3_launch(P->ll_units[l].p, P->h_ll_units[l].size(), P->tc_img.p, P->ll_src.p, P->ll_tgt.p,
                                P->ll_src.p, (const float2*)cin.p, (float2*)cin.p, (float2*)cin.p, nrhs, P->n_coef,
-                               P->n_coef, P->ll_mt[l], P->lev[l].s, P->tc_err.p, s, mm_shape));
+                               P->n_coef, P->ll_mt[l], P->lev[l].s, P->tc_err.p, sf, mm_shape));
         ++nl;
         continue;
       }
@@ -680,7 +696,7 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
       for (int r0 = 0; r0 < nrhs; r0 += rc) {
         int rcc = std::min(rc, nrhs - r0);
         size_t sm = sizeof(C) * ((size_t)L.s * rcc + (size_t)Lc.s * rcc);
-        k_l2l<C><<<dim3((unsigned)nchild, Lc.nw), 256, sm, s>>>(Lc.box_begin, T->par.p, T->ix.p, T->iy.p, T->iz.p,
+        k_l2l<C><<<dim3((unsigned)nchild, Lc.nw), 256, sm, sf>>>(Lc.box_begin, T->par.p, T->ix.p, T->iy.p, T->iz.p,
                                                                P->slot.p, L.s, Lc.s, L.nw, L.n, Lc.n, Lc.hf ? 1 : 0,
                                                                op.M.p + P->m_off[l], cin.p, nrhs, P->n_coef, r0,
                                                                rcc);
@@ -689,6 +705,10 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
       }
     }
     ev(6);
+    if (ovl) {
+      FDA_CUDA(cudaEventRecord(P->ev_join, sf));
+      FDA_CUDA(cudaStreamWaitEvent(s, P->ev_join, 0));
+    }
     // L2T
     if (!P->h_leaves.empty()) {
       int rc = chunk(maxs);
@@ -775,6 +795,8 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
   for (int l = 0; l < FDA_MAXLEV; ++l) P->m2l_choice[l][0] = P->m2l_choice[l][1] = -1;
   P->near_wide = -1;
   P->near_csep = -1;
+  P->overlap = 0;
+  P->near_evict = 0;
   FDA_TRY(plan_matvec(P, FDA_PREC_FP32, x.p, y.p, nrhs, FDA_CPLX64, s, false));  // workspaces hold valid data
   FDA_CUDA(cudaStreamSynchronize(s));
   int64_t nl = 0;
@@ -853,6 +875,29 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
     P->near_csep = best;
   }
   R->near_split = P->near_csep < 0 ? 0 : P->near_csep;
+  // whole products: serial, or near and far field on two streams with two or one near-field CTAs per SM; each
+  // with and without the L2 evict-first policy on the near-field matrix copies
+  P->overlap = 0;
+  P->near_evict = 0;
+  R->overlap = 0;
+  R->near_evict_first = 0;
+  for (int q = 0; q < 6; ++q) R->overlap_ms[q] = -1;
+  if (P->n_near_tleaf > 0 && P->near_max_nr <= 256 && !P->phase_ev) {
+    const int nov = (P->n_coef > 0 && P->side) ? 3 : 1;
+    int best = 0;
+    for (int q = 0; q < 6; ++q) {
+      if (q % 3 >= nov) continue;
+      P->overlap = q % 3;
+      P->near_evict = q / 3;
+      FDA_TRY(time_ms(s, [&]() { return plan_matvec(P, FDA_PREC_FP32, x.p, y.p, nrhs, FDA_CPLX64, s, false); }, 5,
+                      &R->overlap_ms[q]));
+      if (R->overlap_ms[q] < R->overlap_ms[best]) best = q;
+    }
+    P->overlap = best % 3;
+    P->near_evict = best / 3;
+    R->overlap = best % 3;
+    R->near_evict_first = best / 3;
+  }
   FDA_TRY(plan_matvec(P, FDA_PREC_FP32, x.p, y.p, nrhs, FDA_CPLX64, s, false));
   FDA_CUDA(cudaStreamSynchronize(s));
   return FDA_OK;

@@ -68,6 +68,17 @@ __device__ __forceinline__ void ns_bulk(void* dst, const void* src, uint32_t byt
                : "memory");
 }
 
+// the same copy with an L2 policy (the near-field matrices are read once per pass: evict them first, so that
+// they do not push out what other kernels of the product keep in L2)
+__device__ __forceinline__ void ns_bulk_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                             uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+          "r"(ns_smem(dst)),
+      "l"(src), "r"(bytes), "r"(ns_smem(bar)), "l"(pol)
+      : "memory");
+}
+
 // global -> shared asynchronous copies of densities (zero-filled beyond src_bytes)
 __device__ __forceinline__ void ns_cp8(void* dst, const void* src, uint32_t src_bytes) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(ns_smem(dst)), "l"(src), "r"(src_bytes) : "memory");
@@ -112,7 +123,8 @@ template <typename C, int NR, bool W>
 static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR, W>::MINB) k_near_stream(
     const int32_t* part, const int64_t* tleaf, const int64_t* pb, const int64_t* pe, const int64_t* nbase,
     const int32_t* ncolv, const int64_t* xbase, const int32_t* xcol, const C* B, const int64_t* cptr,
-    const int32_t* ccol, const C* cval, const C* xt, C* yt, int nrhs, int r0, int rc, int csep, int* err) {
+    const int32_t* ccol, const C* cval, const C* xt, C* yt, int nrhs, int r0, int rc, int csep, int evict_first,
+    int* err) {
   typedef NsLayout<C, NR, W> Ly;
   typedef decltype(xt[0].x) R;
   constexpr int E = Ly::E, XW = Ly::XW, NS_STAGES = Ly::STAGES;
@@ -142,6 +154,8 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR, W>::MINB) k_near
     if (t == NS_CONS) {
       int it = 0;
       bool ok = true;
+      uint64_t pol = 0;
+      if (evict_first) asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
       for (int u = u0; u < u1 && ok; ++u) {
         const int64_t L = tleaf[u];
         const int nr = (int)(pe[L] - pb[L]);
@@ -159,7 +173,10 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR, W>::MINB) k_near
           }
           const uint32_t bytes = (uint32_t)(((int64_t)cc * nr * E + 15) & ~(int64_t)15);
           ns_expect_tx(&full[st], bytes);
-          ns_bulk(ring + (size_t)st * NS_STAGE_BYTES, src + (int64_t)c * nr * E, bytes, &full[st]);
+          if (evict_first)
+            ns_bulk_hint(ring + (size_t)st * NS_STAGE_BYTES, src + (int64_t)c * nr * E, bytes, &full[st], pol);
+          else
+            ns_bulk(ring + (size_t)st * NS_STAGE_BYTES, src + (int64_t)c * nr * E, bytes, &full[st]);
           c += cc;
           ++it;
         }
@@ -445,9 +462,12 @@ static int near_stream_t(fda_plan_s* P, const C* B, const C* cval, const C* xt, 
       FDA_LAUNCH_CHECK();
       ++*launches;
     }
-    k_near_stream<C, NR, W><<<(unsigned)P->near_grid, NS_NT, Ly::total, s>>>(
-        P->near_part.p, P->near_tleaf.p, T->pb.p, T->pe.p, P->near_nbase.p, P->near_ncol.p, P->near_xbase.p,
-        P->near_xcol.p, B, P->corr_ptr.p, P->corr_col.p, cval, xt, yt, nrhs, r0, rc, csep, P->tc_err.p);
+    const int ov = (P->near_sel == 1 || P->near_sel == 2) && P->near_grid_ov[P->near_sel - 1] > 0 ? P->near_sel : 0;
+    k_near_stream<C, NR, W><<<(unsigned)(ov ? P->near_grid_ov[ov - 1] : P->near_grid), NS_NT, Ly::total, s>>>(
+        ov ? P->near_part_ov[ov - 1].p : P->near_part.p, P->near_tleaf.p, T->pb.p, T->pe.p, P->near_nbase.p,
+        P->near_ncol.p, P->near_xbase.p,
+        P->near_xcol.p, B, P->corr_ptr.p, P->corr_col.p, cval, xt, yt, nrhs, r0, rc, csep, P->near_evict,
+        P->tc_err.p);
     FDA_LAUNCH_CHECK();
     ++*launches;
   }

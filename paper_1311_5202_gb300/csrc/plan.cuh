@@ -73,6 +73,23 @@ struct fda_plan_s {
   fda_plan_s() {
     for (int l = 0; l < FDA_MAXLEV; ++l) m2l_choice[l][0] = m2l_choice[l][1] = -1;
   }
+  ~fda_plan_s() {
+    if (side) cudaStreamDestroy(side);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+  }
+  // near field and far field of an FP32 product on two streams: the far field (S2M, M2M, M2L, L2L) on the
+  // plan's side stream, forked after the permutation and joined before L2T; the near field on the caller's
+  // stream with a smaller persistent grid, so that the far-field kernels find room on every SM.
+  // overlap: -1 or 0 serial (the default until the autotuner or fda_overlap_force sets it), 1 two streams
+  // with two near-field CTAs per SM, 2 two streams with one near-field CTA per SM.
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int overlap = -1;
+  int near_grid_ov[2] = {0, 0};
+  fda::DBuf<int32_t> near_part_ov[2];
+  int near_sel = 0;    // the overlap code of the near-field launch being issued (0: the full grid)
+  int near_evict = 0;  // 1: the near-field matrix copies carry an L2 evict-first policy
   fda_tree_s* tree = nullptr;
   bm_problem_s* prob = nullptr;
   fda_config_t cfg;

@@ -1549,22 +1549,28 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
       FDA_CUDA(cudaGetDevice(&dev));
       FDA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
       const int64_t nt = (int64_t)tleaf.size();
-      int grid = (int)std::max<int64_t>(1, std::min<int64_t>(3 * (int64_t)nsm, nt));
       std::vector<int64_t> cost(nt + 1, 0);
       for (int64_t u = 0; u < nt; ++u) {
         int64_t nr = T->h_pe[tleaf[u]] - T->h_pb[tleaf[u]];
         cost[u + 1] = cost[u] + nr * ncolv[u] + 64 * nr + 256;  // entries + per-row and per-leaf overheads
       }
-      std::vector<int32_t> part(grid + 1, 0);
-      int64_t u = 0;
-      for (int b = 1; b < grid; ++b) {
-        int64_t target = cost[nt] * b / grid;
-        while (u < nt && cost[u + 1] <= target) ++u;
-        part[b] = (int32_t)u;
-      }
-      part[grid] = (int32_t)nt;
-      P->near_grid = grid;
-      FDA_TRY(P->near_part.upload(part));
+      auto partition = [&](int per_sm, int* grid_out, DBuf<int32_t>& dpart) {
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(per_sm * (int64_t)nsm, nt));
+        std::vector<int32_t> part(grid + 1, 0);
+        int64_t u = 0;
+        for (int b = 1; b < grid; ++b) {
+          int64_t target = cost[nt] * b / grid;
+          while (u < nt && cost[u + 1] <= target) ++u;
+          part[b] = (int32_t)u;
+        }
+        part[grid] = (int32_t)nt;
+        *grid_out = grid;
+        return dpart.upload(part);
+      };
+      // three CTAs per SM alone; two or one when the far field runs beside it on the side stream
+      FDA_TRY(partition(3, &P->near_grid, P->near_part));
+      FDA_TRY(partition(2, &P->near_grid_ov[0], P->near_part_ov[0]));
+      FDA_TRY(partition(1, &P->near_grid_ov[1], P->near_part_ov[1]));
     }
     FDA_TRY(P->near_tleaf.upload(tleaf));
     FDA_TRY(P->near_tptr.upload(tptr));
@@ -1649,6 +1655,13 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
     FDA_TRY(P->cin32.alloc((size_t)std::max<int64_t>(P->n_coef, 1) * nr));
     FDA_TRY(P->mid32.alloc((size_t)std::max<int64_t>(P->n_mid, 1) * nr));
     FDA_TRY(build_vtm_maps(P));
+    {  // the far field is the longer branch of a two-stream product: its CTAs go first when slots free up
+      int lo = 0, hi = 0;
+      FDA_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+      FDA_CUDA(cudaStreamCreateWithPriority(&P->side, cudaStreamNonBlocking, hi));
+    }
+    FDA_CUDA(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+    FDA_CUDA(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
     if (P->cfg.drop_fp64) {  // FP32-only plan: the FP64 masters go once their copies exist
       FDA_CUDA(cudaDeviceSynchronize());
       P->op64.S.release();

@@ -546,6 +546,45 @@ def test_block_gmres_several_directions_match_oracle(refine):
         S.close()
 
 
+@pytest.mark.parametrize("mode,evict", [(0, 1), (1, 0), (2, 0), (1, 1)])
+def test_two_stream_schedule_matches_serial(kd100_variants, mode, evict):
+    """FP32 products with the far field (S2M, M2M, M2L, L2L) on the plan's own stream beside the near field on
+    the caller's stream (two or one near-field CTAs per SM), and with the L2 evict-first policy on the near-field
+    matrix copies, meet the mixed bar on 256 oracle rows and equal the serial product up to the order of the M2L
+    additions; one right-hand side, and a captured graph of the product replayed after x is refreshed in place,
+    as well."""
+    S, xd, y0, rows, yo = kd100_variants
+    fdbem.fda_overlap_force(S.plan, mode, evict)
+    try:
+        yd = torch.empty_like(xd)
+        S.matvec(xd, yd)
+        torch.cuda.synchronize()
+        y = yd.cpu().numpy()
+        for r in range(3):
+            assert np.linalg.norm(y[r][rows] - yo[r]) / np.linalg.norm(yo[r]) < 3e-4, (mode, r)
+            assert np.linalg.norm(y[r] - y0[r]) / np.linalg.norm(y0[r]) < 2e-5, (mode, r)
+        x1 = xd[0].contiguous()
+        y1 = torch.empty_like(x1)
+        S.matvec(x1, y1)
+        torch.cuda.synchronize()
+        assert np.linalg.norm(y1.cpu().numpy() - y0[0]) / np.linalg.norm(y0[0]) < 2e-5
+        xg = torch.zeros_like(xd)
+        yg = torch.empty_like(xd)
+        g = fdbem.fda_matvec_graph_create(S.plan, fdbem.FDA_PREC_FP32, xg, yg)
+        try:
+            xg.copy_(xd)
+            fdbem.fda_graph_launch(g)
+            torch.cuda.synchronize()
+            yr = yg.cpu().numpy()
+            for r in range(3):
+                assert np.linalg.norm(yr[r] - y0[r]) / np.linalg.norm(y0[r]) < 2e-5, (mode, r)
+        finally:
+            fdbem.fda_graph_destroy(g)
+        assert fdbem.fda_plan_check(S.plan) == fdbem.FDA_OK
+    finally:
+        fdbem.fda_overlap_force(S.plan, 0, 0)
+
+
 # ------------------------------------------------------------------ CUDA-graph replay and the autotuner
 def test_graph_replay_equals_direct_matvec():
     """A captured product replayed twice (x refreshed in place) equals the direct product of the same x."""
