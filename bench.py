@@ -355,6 +355,9 @@ def main():
     ap.add_argument("--near-evict", type=int, default=None, choices=[0, 1],
                     help="force the L2 policy of the near-field matrix copies (1 evict-first) instead of the "
                          "autotuner's")
+    ap.add_argument("--far-levels", type=int, default=None, choices=[0, 1],
+                    help="force the M2L levels onto concurrent streams (1) or in sequence (0) instead of the "
+                         "autotuner's choice")
     ap.add_argument("--table1", action="store_true",
                     help="run only the particle summations of the paper's Table 1 and print their JSON line")
     ap.add_argument("--table1-max", type=int, default=3, help="number of Table 1 sizes (4 adds N = 4.7M)")
@@ -396,8 +399,10 @@ def main():
         fdbem.fda_m2l_force(S.plan, args.m2l_variant)
     overlap = args.overlap if args.overlap is not None else (tune_main["overlap"] if tune_main else 0)
     evict = args.near_evict if args.near_evict is not None else (tune_main["near_evict_first"] if tune_main else 0)
-    if args.overlap is not None or args.near_evict is not None:
-        fdbem.fda_overlap_force(S.plan, overlap, evict)
+    farp = args.far_levels if args.far_levels is not None else (tune_main["far_levels_concurrent"] if tune_main
+                                                                 else 0)
+    if args.overlap is not None or args.near_evict is not None or args.far_levels is not None:
+        fdbem.fda_overlap_force(S.plan, overlap, evict, farp)
     info = S.info()
     X = inputs.complex_gaussian(N, 20131120, nrhs=nrhs if nrhs > 1 else None)
     xd = torch.from_numpy(X).to(dev).contiguous()
@@ -635,7 +640,8 @@ def main():
         "mixed": {"matvec_per_s": 1000.0 / ms32, "ms_per_matvec": ms32, "phase_ms": ph32,
                   "schedule": ["serial", "two streams, near field at 2 CTAs/SM",
                                "two streams, near field at 1 CTA/SM"][overlap]
-                  + (", near-field matrices evict-first in L2" if evict else ""),
+                  + (", near-field matrices evict-first in L2" if evict else "")
+                  + (", M2L levels on concurrent streams" if farp else ""),
                   "phase_note": "phase_ms come from one serial product with an event between phases"},
         "speedup_matvec_mixed_vs_fp64": ms64 / ms32,
         "near_field": {"kernel": near_kernel, "ms": ph32["near"], "achieved_gbs": near_gbs,

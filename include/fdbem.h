@@ -249,9 +249,11 @@ typedef struct {
                                L2L) on a stream of the plan, beside the near field on the caller's stream with two
                                (1) or one (2) near-field CTAs per SM */
   int32_t near_evict_first; /* 1: the near-field matrix copies carry an L2 evict-first policy */
-  double overlap_ms[6];     /* whole FP32 products, best of 5, with schedules 0, 1, 2 ([0..2]) and the same with
-                               the evict-first policy ([3..5]); -1 when not timed (no near field in the stream
-                               form; schedules 1 and 2 also need a far field) */
+  int32_t far_levels_concurrent; /* 1: the M2L of each level runs on its own stream of the plan */
+  int32_t reserved;
+  double schedule_ms[12];   /* whole FP32 products, best of 5, at index overlap + 3 evict_first + 6 far_levels
+                               (the three settings of fda_overlap_force); -1 where not timed (the setting needs
+                               a near field in the stream form or a far field that the plan lacks) */
 } fda_tune_report_t;
 int fda_autotune(fda_plan_t* plan, int nrhs, void* stream, fda_tune_report_t* report);
 
@@ -269,16 +271,20 @@ int fda_autotune(fda_plan_t* plan, int nrhs, void* stream, fda_tune_report_t* re
  * the kernel's operators). */
 int fda_m2l_force(fda_plan_t* plan, int variant);
 
-/* Set the schedule of FP32 products (no paper counterpart; fda_autotune chooses both settings by timing whole
- * products). evict_first = 1 gives the near field's bulk copies of its matrices an L2 evict-first policy (they
- * are read once per pass), 0 the default policy. mode: 0 = every step on the caller's stream in order; 1 and
+/* Set the schedule of FP32 products (no paper counterpart; fda_autotune chooses the three settings by timing
+ * whole products). far_levels = 1 runs the M2L of each level on a stream of the plan of its own (four streams,
+ * shared round-robin beyond four levels), forked when the level's outgoing coefficients are complete and joined
+ * before L2L; 0 runs the levels in sequence. evict_first = 1 gives the near field's bulk copies of its matrices
+ * an L2 evict-first policy (they are read once per pass), 0 the default policy. mode: 0 = the near field and
+ * the far field in sequence on the caller's stream; 1 and
  * 2 = S2M, M2M, M2L and L2L (which read x and write only the expansion coefficients) on a stream the plan
  * owns, forked after the permutation of x and joined before L2T, while the near field streams on the caller's
  * stream with two (1) or one (2) persistent CTAs per SM. Products stay ordered on the caller's stream and
  * graph capture follows the fork and join. The two-stream forms apply only to FP32 products of plans whose
- * near field runs in the stream form, and never while phase events are recorded. Errors: FDA_E_INVALID_ARG
- * (mode outside [0, 2] or evict_first outside [0, 1]), FDA_E_STATE (plan without FP32 operators). */
-int fda_overlap_force(fda_plan_t* plan, int mode, int evict_first);
+ * near field runs in the stream form; no stream but the caller's is used while phase events are recorded.
+ * Errors: FDA_E_INVALID_ARG (mode outside [0, 2], evict_first or far_levels outside [0, 1]), FDA_E_STATE (plan
+ * without FP32 operators). */
+int fda_overlap_force(fda_plan_t* plan, int mode, int evict_first, int far_levels);
 
 /* CUDA-graph form of one product (the batched matvec of many incident directions replayed without
  * per-kernel launch cost; no paper counterpart). fda_matvec_graph_create runs the product once on `stream`

@@ -303,16 +303,18 @@ int fda_m2l_force(fda_plan_t* plan, int variant) {
   return FDA_OK;
 }
 
-int fda_overlap_force(fda_plan_t* plan, int mode, int evict_first) {
+int fda_overlap_force(fda_plan_t* plan, int mode, int evict_first, int far_levels) {
   ARG_CHECK(plan, "NULL plan");
   ARG_CHECK(mode >= 0 && mode <= 2, "mode outside [0, 2]");
   ARG_CHECK(evict_first == 0 || evict_first == 1, "evict_first outside [0, 1]");
-  if ((mode > 0 || evict_first) && plan->cfg.precision != FDA_PREC_FP32) {
+  ARG_CHECK(far_levels == 0 || far_levels == 1, "far_levels outside [0, 1]");
+  if ((mode > 0 || evict_first || far_levels) && plan->cfg.precision != FDA_PREC_FP32) {
     set_error("the product schedules need a plan built with FDA_PREC_FP32");
     return FDA_E_STATE;
   }
   plan->overlap = mode;
   plan->near_evict = evict_first;
+  plan->far_par = far_levels;
   return FDA_OK;
 }
 

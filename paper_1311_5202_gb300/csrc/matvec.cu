@@ -638,6 +638,12 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
     const bool tc_mm = std::is_same<C, float2>::value && (P->cfg.m2l_tensor == 1 || P->cfg.m2l_tensor == 3);
     const int mm_shape = P->cfg.m2l_tensor == 3 ? 6 : 0;
     if (tc_mm) FDA_TRY(zero_parent_coefs<C>(P, cout, nrhs, sf));
+    // M2L of every level on its own stream (FP32): the incoming coefficients are cleared before anything forks
+    const bool fpar = std::is_same<C, float2>::value && P->far_par == 1 && !P->phase_ev && P->lvs[0];
+    if (fpar) FDA_CUDA(cudaMemsetAsync(cin.p, 0, sizeof(C) * P->n_coef * nrhs, sf));
+    auto lev_ready = [&](int l) {  // the outgoing coefficients of level l are complete on sf
+      if (fpar) cudaEventRecord(P->ev_lev[l], sf);
+    };
     // S2M
     if (!P->h_leaves.empty()) {
       int rc = chunk(maxleaf);
@@ -653,6 +659,7 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
     ev(3);
     // M2M bottom-up
     for (int l = P->lmax - 1; l >= P->lmin; --l) {
+      lev_ready(l + 1);
       if (P->h_parents[l].empty()) continue;
       if (tc_mm && !P->h_mm_units[l].empty()) {
         FDA_TRY(m2l_tc3_launch(P->mm_units[l].p, P->h_mm_units[l].size(), P->tc_img.p, P->mm_src.p, P->mm_tgt.p,
@@ -674,11 +681,30 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
         ++nl;
       }
     }
+    lev_ready(P->lmin);
     ev(4);
     // M2L
-    FDA_CUDA(cudaMemsetAsync(cin.p, 0, sizeof(C) * P->n_coef * nrhs, sf));
-    for (int l = P->lmin; l <= P->lmax; ++l)
-      for (int st = 0; st < 2; ++st) FDA_TRY(m2l_stage<C>(P, op, cout, cin, mid, l, st, m2l_variant(P, l, st), nrhs, sf, &nl));
+    if (fpar) {
+      // deepest level first: its coefficients are ready first; the levels share no output and no scratch
+      int used = 0;
+      for (int l = P->lmax; l >= P->lmin; --l) {
+        const int q = (l - P->lmin) % 4;
+        FDA_CUDA(cudaStreamWaitEvent(P->lvs[q], P->ev_lev[l], 0));
+        for (int st = 0; st < 2; ++st)
+          FDA_TRY(m2l_stage<C>(P, op, cout, cin, mid, l, st, m2l_variant(P, l, st), nrhs, P->lvs[q], &nl));
+        used |= 1 << q;
+      }
+      for (int q = 0; q < 4; ++q)
+        if (used & (1 << q)) {
+          FDA_CUDA(cudaEventRecord(P->ev_lvj[q], P->lvs[q]));
+          FDA_CUDA(cudaStreamWaitEvent(sf, P->ev_lvj[q], 0));
+        }
+    } else {
+      FDA_CUDA(cudaMemsetAsync(cin.p, 0, sizeof(C) * P->n_coef * nrhs, sf));
+      for (int l = P->lmin; l <= P->lmax; ++l)
+        for (int st = 0; st < 2; ++st)
+          FDA_TRY(m2l_stage<C>(P, op, cout, cin, mid, l, st, m2l_variant(P, l, st), nrhs, sf, &nl));
+    }
     ev(5);
     // L2L top-down
     for (int l = P->lmin; l < P->lmax; ++l) {
@@ -797,6 +823,7 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
   P->near_csep = -1;
   P->overlap = 0;
   P->near_evict = 0;
+  P->far_par = 0;
   FDA_TRY(plan_matvec(P, FDA_PREC_FP32, x.p, y.p, nrhs, FDA_CPLX64, s, false));  // workspaces hold valid data
   FDA_CUDA(cudaStreamSynchronize(s));
   int64_t nl = 0;
@@ -876,27 +903,36 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
   }
   R->near_split = P->near_csep < 0 ? 0 : P->near_csep;
   // whole products: serial, or near and far field on two streams with two or one near-field CTAs per SM; each
-  // with and without the L2 evict-first policy on the near-field matrix copies
+  // with and without the L2 evict-first policy on the near-field matrix copies, and with the M2L levels in
+  // sequence or each on its own stream
   P->overlap = 0;
   P->near_evict = 0;
+  P->far_par = 0;
   R->overlap = 0;
   R->near_evict_first = 0;
-  for (int q = 0; q < 6; ++q) R->overlap_ms[q] = -1;
-  if (P->n_near_tleaf > 0 && P->near_max_nr <= 256 && !P->phase_ev) {
-    const int nov = (P->n_coef > 0 && P->side) ? 3 : 1;
-    int best = 0;
-    for (int q = 0; q < 6; ++q) {
-      if (q % 3 >= nov) continue;
-      P->overlap = q % 3;
-      P->near_evict = q / 3;
+  R->far_levels_concurrent = 0;
+  for (int q = 0; q < 12; ++q) R->schedule_ms[q] = -1;
+  if (!P->phase_ev && (P->n_coef > 0 || (P->n_near_tleaf > 0 && P->near_max_nr <= 256))) {
+    const bool near_s = P->n_near_tleaf > 0 && P->near_max_nr <= 256;
+    const bool far = P->n_coef > 0 && P->side;
+    int best = -1;
+    for (int q = 0; q < 12; ++q) {
+      const int ov = q % 3, evf = (q / 3) % 2, fp = q / 6;
+      if ((ov > 0 && !(far && near_s)) || (evf && !near_s) || (fp && !far)) continue;
+      P->overlap = ov;
+      P->near_evict = evf;
+      P->far_par = fp;
       FDA_TRY(time_ms(s, [&]() { return plan_matvec(P, FDA_PREC_FP32, x.p, y.p, nrhs, FDA_CPLX64, s, false); }, 5,
-                      &R->overlap_ms[q]));
-      if (R->overlap_ms[q] < R->overlap_ms[best]) best = q;
+                      &R->schedule_ms[q]));
+      if (best < 0 || R->schedule_ms[q] < R->schedule_ms[best]) best = q;
     }
+    if (best < 0) best = 0;
     P->overlap = best % 3;
-    P->near_evict = best / 3;
-    R->overlap = best % 3;
-    R->near_evict_first = best / 3;
+    P->near_evict = (best / 3) % 2;
+    P->far_par = best / 6;
+    R->overlap = P->overlap;
+    R->near_evict_first = P->near_evict;
+    R->far_levels_concurrent = P->far_par;
   }
   FDA_TRY(plan_matvec(P, FDA_PREC_FP32, x.p, y.p, nrhs, FDA_CPLX64, s, false));
   FDA_CUDA(cudaStreamSynchronize(s));

@@ -77,6 +77,12 @@ struct fda_plan_s {
     if (side) cudaStreamDestroy(side);
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
+    for (int i = 0; i < 4; ++i) {
+      if (lvs[i]) cudaStreamDestroy(lvs[i]);
+      if (ev_lvj[i]) cudaEventDestroy(ev_lvj[i]);
+    }
+    for (int l = 0; l < FDA_MAXLEV; ++l)
+      if (ev_lev[l]) cudaEventDestroy(ev_lev[l]);
   }
   // near field and far field of an FP32 product on two streams: the far field (S2M, M2M, M2L, L2L) on the
   // plan's side stream, forked after the permutation and joined before L2T; the near field on the caller's
@@ -90,6 +96,13 @@ struct fda_plan_s {
   fda::DBuf<int32_t> near_part_ov[2];
   int near_sel = 0;    // the overlap code of the near-field launch being issued (0: the full grid)
   int near_evict = 0;  // 1: the near-field matrix copies carry an L2 evict-first policy
+  // FP32 products with far_par = 1 run the M2L of each level on its own stream (lvs[(l - lmin) % 4]), forked
+  // when that level's outgoing coefficients are complete (ev_lev[l], after S2M or its M2M step) and joined
+  // (ev_lvj) before L2L
+  int far_par = 0;
+  cudaStream_t lvs[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_lvj[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_lev[FDA_MAXLEV] = {};
   fda_tree_s* tree = nullptr;
   bm_problem_s* prob = nullptr;
   fda_config_t cfg;

@@ -1659,6 +1659,11 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
       int lo = 0, hi = 0;
       FDA_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
       FDA_CUDA(cudaStreamCreateWithPriority(&P->side, cudaStreamNonBlocking, hi));
+      for (int i = 0; i < 4; ++i) {
+        FDA_CUDA(cudaStreamCreateWithPriority(&P->lvs[i], cudaStreamNonBlocking, hi));
+        FDA_CUDA(cudaEventCreateWithFlags(&P->ev_lvj[i], cudaEventDisableTiming));
+      }
+      for (int l = 0; l < FDA_MAXLEV; ++l) FDA_CUDA(cudaEventCreateWithFlags(&P->ev_lev[l], cudaEventDisableTiming));
     }
     FDA_CUDA(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
     FDA_CUDA(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));

@@ -76,7 +76,8 @@ class fda_tune_report_t(C.Structure):
                 ("ms_fma", C.c_double * 64), ("ms_tensor", C.c_double * 64), ("chosen", C.c_int32 * 64),
                 ("near_ms", C.c_double * 2), ("near_rhs_per_pass", C.c_int32), ("near_split", C.c_int32),
                 ("near_split_ms", C.c_double * 2), ("near_window_ms", C.c_double), ("overlap", C.c_int32),
-                ("near_evict_first", C.c_int32), ("overlap_ms", C.c_double * 6)]
+                ("near_evict_first", C.c_int32), ("far_levels_concurrent", C.c_int32), ("reserved", C.c_int32),
+                ("schedule_ms", C.c_double * 12)]
 
 
 class fda_plan_info_t(C.Structure):
@@ -116,7 +117,7 @@ _SIGS = [
     ("fda_wait_selftest", C.c_int, [C.c_double, C.POINTER(C.c_int)]),
     ("fda_autotune", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(fda_tune_report_t)]),
     ("fda_m2l_force", C.c_int, [C.c_void_p, C.c_int]),
-    ("fda_overlap_force", C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    ("fda_overlap_force", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     ("fda_graph_nodes", C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     ("fda_graph_destroy", None, [C.c_void_p]),
     ("fda_corrections_export", C.c_int, [C.c_void_p, _i64p, C.c_int64, C.c_int64, _i64p, _i64p, _dp]),
@@ -335,7 +336,8 @@ def fda_autotune(plan, nrhs=1, stream=None) -> dict:
             for e in range(R.entries)]
     return dict(m2l=rows, near_ms=list(R.near_ms), near_rhs_per_pass=R.near_rhs_per_pass,
                 near_split=R.near_split, near_split_ms=list(R.near_split_ms), near_window_ms=R.near_window_ms,
-                overlap=R.overlap, near_evict_first=R.near_evict_first, overlap_ms=list(R.overlap_ms))
+                overlap=R.overlap, near_evict_first=R.near_evict_first,
+                far_levels_concurrent=R.far_levels_concurrent, schedule_ms=list(R.schedule_ms))
 
 
 def fda_m2l_force(plan, variant):
@@ -343,10 +345,11 @@ def fda_m2l_force(plan, variant):
     _check(lib().fda_m2l_force(plan, int(variant)))
 
 
-def fda_overlap_force(plan, mode, evict_first=0):
-    """FP32 product schedule: 0 serial, 1 or 2 far field on the plan's stream beside the near field (two or one
-    near-field CTAs per SM); evict_first = 1 gives the near-field matrix copies an L2 evict-first policy."""
-    _check(lib().fda_overlap_force(plan, int(mode), int(evict_first)))
+def fda_overlap_force(plan, mode, evict_first=0, far_levels=0):
+    """FP32 product schedule: mode 0 serial, 1 or 2 far field on the plan's stream beside the near field (two or
+    one near-field CTAs per SM); evict_first = 1 gives the near-field matrix copies an L2 evict-first policy;
+    far_levels = 1 runs the M2L of each level on its own stream."""
+    _check(lib().fda_overlap_force(plan, int(mode), int(evict_first), int(far_levels)))
 
 
 def fda_plan_check(plan):

@@ -546,15 +546,15 @@ def test_block_gmres_several_directions_match_oracle(refine):
         S.close()
 
 
-@pytest.mark.parametrize("mode,evict", [(0, 1), (1, 0), (2, 0), (1, 1)])
-def test_two_stream_schedule_matches_serial(kd100_variants, mode, evict):
+@pytest.mark.parametrize("mode,evict,far", [(0, 1, 0), (1, 0, 0), (2, 0, 0), (1, 1, 0), (0, 0, 1), (1, 1, 1)])
+def test_two_stream_schedule_matches_serial(kd100_variants, mode, evict, far):
     """FP32 products with the far field (S2M, M2M, M2L, L2L) on the plan's own stream beside the near field on
-    the caller's stream (two or one near-field CTAs per SM), and with the L2 evict-first policy on the near-field
-    matrix copies, meet the mixed bar on 256 oracle rows and equal the serial product up to the order of the M2L
-    additions; one right-hand side, and a captured graph of the product replayed after x is refreshed in place,
-    as well."""
+    the caller's stream (two or one near-field CTAs per SM), with the L2 evict-first policy on the near-field
+    matrix copies, and with the M2L of each level on its own stream, meet the mixed bar on 256 oracle rows and
+    equal the serial product up to the order of the M2L additions; one right-hand side, and a captured graph of
+    the product replayed after x is refreshed in place, as well."""
     S, xd, y0, rows, yo = kd100_variants
-    fdbem.fda_overlap_force(S.plan, mode, evict)
+    fdbem.fda_overlap_force(S.plan, mode, evict, far)
     try:
         yd = torch.empty_like(xd)
         S.matvec(xd, yd)
@@ -582,7 +582,7 @@ def test_two_stream_schedule_matches_serial(kd100_variants, mode, evict):
             fdbem.fda_graph_destroy(g)
         assert fdbem.fda_plan_check(S.plan) == fdbem.FDA_OK
     finally:
-        fdbem.fda_overlap_force(S.plan, 0, 0)
+        fdbem.fda_overlap_force(S.plan, 0, 0, 0)
 
 
 # ------------------------------------------------------------------ CUDA-graph replay and the autotuner
