@@ -53,7 +53,11 @@ enum { FDA_CPLX128 = 0, FDA_CPLX64 = 1 };
 /* Arithmetic of the matrix-vector product (near field and translations). */
 enum {
   FDA_PREC_FP64 = 0, /* plain FP64 everywhere */
-  FDA_PREC_FP32 = 1  /* near field and translations in FP32 with FP32 accumulation */
+  FDA_PREC_FP32 = 1, /* near field and translations in FP32 with FP32 accumulation */
+  FDA_PREC_TF32 = 2  /* products only (fda_matvec_ex): as FDA_PREC_FP32, with the tensor-core translations in one
+                        TF32 pass also on a plan built with 3xTF32 images (m2l_tensor = 3: the leading TF32
+                        part of each image is read, its remainder skipped); on other FP32 plans the same product
+                        as FDA_PREC_FP32 */
 };
 
 typedef struct bm_problem_s bm_problem_t;
@@ -187,7 +191,8 @@ typedef struct {
                         refine = 0 (FP64 Krylov basis around the FP32 operator; with TF32 translations the
                         rounding stalls GMRES near a 1e-4 residual, with 3xTF32 ones, m2l_tensor = 3, it
                         reaches 1e-5 and below) and no preconditioner. */
-  int reserved;
+  int near_deep_ring; /* 1 = the near-field stream of one right-hand side keeps four ring stages of about 14 KB
+                        instead of three of 16 KB (fda_autotune chooses it by timing); same sums */
   double gamma_re, gamma_im;  /* op = 2: the Robin coefficient gamma = a/b (ignored otherwise) */
 } fda_config_t;
 
@@ -212,8 +217,9 @@ int fda_precompute_translations(fda_tree_t* tree, const fda_config_t* cfg, fda_p
  * DOF order; x and y must not overlap. 1 <= nrhs <= cfg.nrhs_max. Asynchronous on `stream`. */
 int fda_matvec(fda_plan_t* plan, const void* x, void* y, int nrhs, int dtype, void* stream);
 
-/* fda_matvec with an explicit arithmetic: FDA_PREC_FP64 always works (every plan keeps its FP64 operators);
- * FDA_PREC_FP32 needs a plan built with cfg.precision = FDA_PREC_FP32 (else FDA_E_STATE). */
+/* fda_matvec with an explicit arithmetic: FDA_PREC_FP64 works on every plan that keeps its FP64 operators
+ * (not drop_fp64); FDA_PREC_FP32 and FDA_PREC_TF32 need a plan built with cfg.precision = FDA_PREC_FP32 (else
+ * FDA_E_STATE). */
 int fda_matvec_ex(fda_plan_t* plan, int precision, const void* x, void* y, int nrhs, int dtype, void* stream);
 
 /* Autotuner (no paper counterpart). For an FP32 plan and a batch width nrhs (1..nrhs_max), times on the
@@ -250,10 +256,12 @@ typedef struct {
                                (1) or one (2) near-field CTAs per SM */
   int32_t near_evict_first; /* 1: the near-field matrix copies carry an L2 evict-first policy */
   int32_t far_levels_concurrent; /* 1: the M2L of each level runs on its own stream of the plan */
-  int32_t reserved;
+  int32_t near_deep_ring;   /* 1: one right-hand side with the near field's four-stage ring (else three) */
   double schedule_ms[12];   /* whole FP32 products, best of 5, at index overlap + 3 evict_first + 6 far_levels
                                (the three settings of fda_overlap_force); -1 where not timed (the setting needs
                                a near field in the stream form or a far field that the plan lacks) */
+  double near_deep_ring_ms[3]; /* one right-hand side: near field schedules 0, 1, 2 with the four-stage ring (-1
+                                  for wider batches) */
 } fda_tune_report_t;
 int fda_autotune(fda_plan_t* plan, int nrhs, void* stream, fda_tune_report_t* report);
 
@@ -288,10 +296,11 @@ int fda_overlap_force(fda_plan_t* plan, int mode, int evict_first, int far_level
 
 /* CUDA-graph form of one product (the batched matvec of many incident directions replayed without
  * per-kernel launch cost; no paper counterpart). fda_matvec_graph_create runs the product once on `stream`
- * (synchronously; a null stream means an internal one for the capture), then captures the same product for
- * these exact x, y (DEVICE, as fda_matvec_ex), nrhs, dtype and precision into a graph. fda_graph_launch
- * replays it on any stream: the caller refreshes x in place and reads y after the replay; the graph keeps
- * pointers to x, y and the plan, which must stay alive. fda_graph_nodes returns its kernel/memset node
+ * (synchronously; a null stream means an internal one for the capture, used after the whole device has been
+ * synchronised, so that no earlier work on the plan's workspaces is still running), then captures the same
+ * product for these exact x, y (DEVICE, as fda_matvec_ex), nrhs, dtype and precision into a graph.
+ * fda_graph_launch replays it on any stream: the caller refreshes x in place and reads y after the replay; the
+ * graph keeps pointers to x, y and the plan, which must stay alive. fda_graph_nodes returns its kernel/memset node
  * count. Errors: FDA_E_INVALID_ARG, FDA_E_CUDA (capture or instantiation refused). */
 typedef struct fda_graph_s fda_graph_t;
 int fda_matvec_graph_create(fda_plan_t* plan, int precision, const void* x, void* y, int nrhs, int dtype,
@@ -352,17 +361,22 @@ typedef struct {
   int restart;         /* Krylov dimension m of GMRES(m) (1..512) */
   int max_iter;        /* total matvec budget */
   int x0_given;        /* 1: x holds the initial guess on entry; 0: x0 = 0 */
-  int refine;          /* 1: FP64 iterative refinement around an inner solve in the plan's
-                          precision (outer residual with the FP64 operator); 0: plain GMRES */
+  int refine;          /* 1: FP64 iterative refinement around an inner solve with FP32 products (their
+                          translations in one TF32 pass, FDA_PREC_TF32); outer residual with the FP64
+                          operator, or see refine_residual; 0: plain GMRES */
   int inner_restart;   /* inner Krylov dimension when refine = 1 */
   double inner_tol;    /* inner relative tolerance when refine = 1 */
-  int reserved[6];
+  int refine_residual; /* refine = 1, plans built with m2l_tensor = 3 (drop_fp64 plans too): 1 = the outer
+                          residual with the plan's FP32 product and its 3xTF32 translations (accurate to FP32
+                          rounding, far below the eps of the compressed operator); 0 = with the FP64 operator */
+  int reserved[5];
 } bm_gmres_opts_t;
 
 typedef struct {
   int iterations;      /* matvecs in the Krylov loops (inner + outer) */
   int outer_iterations;/* refinement steps (refine = 1) */
-  double rel_residual; /* final true relative residual with the FP64 operator */
+  double rel_residual; /* final true relative residual with the outer operator (FP64, or the 3xTF32 FP32
+                          product when refine_residual = 1; with refine = 0 the operator of the solve) */
   double ms_total;
   double ms_matvec;
   int status;          /* same as the return code */

@@ -231,6 +231,7 @@ int fda_precompute_translations(fda_tree_t* tree, const fda_config_t* cfg, fda_p
   ARG_CHECK(cfg->m2l_tensor >= 0 && cfg->m2l_tensor <= 3, "m2l_tensor must be 0, 1, 2 or 3");
   ARG_CHECK(cfg->op >= 0 && cfg->op <= 2, "op must be 0, 1 or 2");
   ARG_CHECK(cfg->drop_fp64 == 0 || cfg->drop_fp64 == 1, "drop_fp64 must be 0 or 1");
+  ARG_CHECK(cfg->near_deep_ring == 0 || cfg->near_deep_ring == 1, "near_deep_ring must be 0 or 1");
   ARG_CHECK(cfg->drop_fp64 == 0 || cfg->precision == FDA_PREC_FP32, "drop_fp64 needs precision FDA_PREC_FP32");
   ARG_CHECK(cfg->op != 2 || (std::isfinite(cfg->gamma_re) && std::isfinite(cfg->gamma_im)),
             "op = 2 needs a finite Robin coefficient gamma");
@@ -260,7 +261,8 @@ int fda_matvec(fda_plan_t* plan, const void* x, void* y, int nrhs, int dtype, vo
 int fda_matvec_ex(fda_plan_t* plan, int precision, const void* x, void* y, int nrhs, int dtype, void* stream) {
   ARG_CHECK(plan && x && y, "NULL argument");
   ARG_CHECK(dtype == FDA_CPLX128 || dtype == FDA_CPLX64, "unknown dtype");
-  ARG_CHECK(precision == FDA_PREC_FP64 || precision == FDA_PREC_FP32, "unknown precision");
+  ARG_CHECK(precision == FDA_PREC_FP64 || precision == FDA_PREC_FP32 || precision == FDA_PREC_TF32,
+            "unknown precision");
   ARG_CHECK(x != y, "x and y must not overlap");
   return plan_matvec(plan, precision, x, y, nrhs, dtype, (cudaStream_t)stream, false);
 }
@@ -344,12 +346,15 @@ int fda_matvec_graph_create(fda_plan_t* plan, int precision, const void* x, void
                             void* stream, fda_graph_t** out) {
   ARG_CHECK(plan && x && y && out, "NULL argument");
   ARG_CHECK(dtype == FDA_CPLX128 || dtype == FDA_CPLX64, "unknown dtype");
-  ARG_CHECK(precision == FDA_PREC_FP64 || precision == FDA_PREC_FP32, "unknown precision");
+  ARG_CHECK(precision == FDA_PREC_FP64 || precision == FDA_PREC_FP32 || precision == FDA_PREC_TF32,
+            "unknown precision");
   ARG_CHECK(x != y, "x and y must not overlap");
   *out = nullptr;
-  // capture needs a stream other than the legacy default one
+  // capture needs a stream other than the legacy default one; the internal stream does not wait for work that
+  // the caller queued elsewhere on the plan's workspaces, so the device is drained first
   cudaStream_t s = (cudaStream_t)stream, own = nullptr;
   if (!s) {
+    FDA_CUDA(cudaDeviceSynchronize());
     FDA_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
     s = own;
   }
@@ -415,7 +420,8 @@ void fda_graph_destroy(fda_graph_t* g) {
 int fda_matvec_phases(fda_plan_t* plan, int precision, const void* x, void* y, int nrhs, int dtype, void* stream,
                       double* ms) {
   ARG_CHECK(plan && x && y && ms, "NULL argument");
-  ARG_CHECK(precision == FDA_PREC_FP64 || precision == FDA_PREC_FP32, "unknown precision");
+  ARG_CHECK(precision == FDA_PREC_FP64 || precision == FDA_PREC_FP32 || precision == FDA_PREC_TF32,
+            "unknown precision");
   ARG_CHECK(dtype == FDA_CPLX128 || dtype == FDA_CPLX64, "unknown dtype");
   cudaEvent_t ev[9];
   for (int q = 0; q < 9; ++q) FDA_CUDA(cudaEventCreate(&ev[q]));

@@ -583,6 +583,10 @@ static int gmres_solve_block(GmCtx& C, const double2* b, double2* x, int nc, con
   BlkWork B;
   std::vector<double> rel;
   int it = 0;
+  // refinement: outer residual with the FP64 operator or the 3xTF32 FP32 product; the inner solve needs only a
+  // few digits and runs single-pass TF32 translations (on plans without 3xTF32 images the plain FP32 product)
+  const int oprec = o->refine_residual ? FDA_PREC_FP32 : FDA_PREC_FP64;
+  const int iprec = FDA_PREC_TF32;
   if (!o->refine) {
     const int aprec = P->cfg.drop_fp64 ? FDA_PREC_FP32 : FDA_PREC_FP64;  // FP32-only plans: FP32 operator
     int rc = gmres_block(C, aprec, b, x, nc, o->tol, m, o->max_iter, &it, rel, !o->x0_given, B);
@@ -609,7 +613,7 @@ static int gmres_solve_block(GmCtx& C, const double2* b, double2* x, int nc, con
     if (k == 0 && !o->x0_given) {
       FDA_CUDA(cudaMemcpyAsync(Rb.p, b, sizeof(double2) * NB, cudaMemcpyDeviceToDevice, C.s));
     } else {
-      FDA_TRY(apply_A_blk(C, FDA_PREC_FP64, x, Rb.p, nc));
+      FDA_TRY(apply_A_blk(C, oprec, x, Rb.p, nc));
       k_resid_blk<<<cdiv(NB, 256), 256, 0, C.s>>>(Rb.p, b, NB);
       FDA_LAUNCH_CHECK();
     }
@@ -650,7 +654,7 @@ static int gmres_solve_block(GmCtx& C, const double2* b, double2* x, int nc, con
     }
     const double itol = o->inner_tol > 0 ? o->inner_tol : 1e-4;
     int iit = 0;
-    int irc = gmres_block(C, FDA_PREC_FP32, Rb.p, Z.p, nc, std::max(itol, o->tol / std::max(wr, 1e-300)), mi,
+    int irc = gmres_block(C, iprec, Rb.p, Z.p, nc, std::max(itol, o->tol / std::max(wr, 1e-300)), mi,
                           o->max_iter - *total_it, &iit, rel, true, B);
     *total_it += iit;
     if (irc != FDA_OK && irc != FDA_E_NOT_CONVERGED && irc != FDA_E_BREAKDOWN) {
@@ -675,10 +679,20 @@ int gmres_solve(fda_plan_s* P, const double2* b, double2* x, int nrhs, const bm_
   C.nb = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (C.N + GM_NB - 1) / GM_NB));
   int m = std::max(1, std::min(512, o->restart));
   int mi = std::max(1, std::min(512, o->inner_restart > 0 ? o->inner_restart : o->restart));
-  if (P->cfg.drop_fp64 && o->refine) {
-    set_error("the plan released its FP64 operators (drop_fp64): solve with refine = 0");
+  if (o->refine_residual != 0 && o->refine_residual != 1) {
+    set_error("refine_residual must be 0 or 1");
+    return FDA_E_INVALID_ARG;
+  }
+  if (o->refine && o->refine_residual && (P->cfg.precision != FDA_PREC_FP32 || P->cfg.m2l_tensor != 3)) {
+    set_error("refine_residual = 1 needs a plan built with FDA_PREC_FP32 and m2l_tensor = 3 (3xTF32 images)");
     return FDA_E_STATE;
   }
+  if (P->cfg.drop_fp64 && o->refine && !o->refine_residual) {
+    set_error("the plan released its FP64 operators (drop_fp64): solve with refine = 0, or refine_residual = 1");
+    return FDA_E_STATE;
+  }
+  const int oprec = o->refine_residual ? FDA_PREC_FP32 : FDA_PREC_FP64;
+  const int iprec = FDA_PREC_TF32;  // see gmres_solve_block
   FDA_TRY(C.partial.alloc((size_t)C.nb * (std::max(m, mi) + 1)));
   FDA_TRY(C.h.alloc(std::max(m, mi) + 1));
   FDA_TRY(C.hacc.alloc(std::max(m, mi) + 1));
@@ -721,11 +735,11 @@ int gmres_solve(fda_plan_s* P, const double2* b, double2* x, int nrhs, const bm_
       double prev = 1e300;
       rc = FDA_E_NOT_CONVERGED;
       for (int k = 0; k < 50; ++k) {
-        // outer residual with the FP64 operator
+        // outer residual with the FP64 operator (or the 3xTF32 FP32 product)
         if (k == 0 && !o->x0_given) {
           FDA_CUDA(cudaMemcpyAsync(P->gm_b.p, bc, sizeof(double2) * C.N, cudaMemcpyDeviceToDevice, s));
         } else {
-          FDA_TRY(apply_A(C, FDA_PREC_FP64, xc, P->gm_b.p));
+          FDA_TRY(apply_A(C, oprec, xc, P->gm_b.p));
           k_axpby<<<cdiv(C.N, 256), 256, 0, s>>>(P->gm_b.p, bc, 1.0, -1.0, C.N);
           FDA_LAUNCH_CHECK();
         }
@@ -755,7 +769,7 @@ int gmres_solve(fda_plan_s* P, const double2* b, double2* x, int nrhs, const bm_
         double itol = o->inner_tol > 0 ? o->inner_tol : 1e-4;
         int iit = 0;
         double irel = 0;
-        int irc = gmres_core(C, FDA_PREC_FP32, P->gm_b.p, P->gm_z.p, std::max(itol, o->tol / std::max(rel, 1e-300)),
+        int irc = gmres_core(C, iprec, P->gm_b.p, P->gm_z.p, std::max(itol, o->tol / std::max(rel, 1e-300)),
                              mi, o->max_iter - total_it, &iit, &irel, true);
         total_it += iit;
         if (irc != FDA_OK && irc != FDA_E_NOT_CONVERGED && irc != FDA_E_BREAKDOWN) {

@@ -454,7 +454,8 @@ static __global__ void __launch_bounds__(256) k_m2l(const GemmUnit* units, const
 // gathers with four and three stages (one right-hand side; otherwise variant 8), 14 and 15 = stage 0 only: the
 // swapped V^ kernel with 16-wide K chunks, two and three in flight (6 to 15: autotuner only)
 int m2l_variant(const fda_plan_s* P, int l, int st) {
-  if (P->m2l_choice[l][st] >= 0) return P->m2l_choice[l][st];
+  const int ch = P->fast_tf32 ? P->m2l_choice_fast[l][st] : P->m2l_choice[l][st];
+  if (ch >= 0) return ch;
   if ((P->cfg.m2l_tensor == 1 || P->cfg.m2l_tensor == 3) && !P->h_tc3_units[l][st].empty() &&
       P->tc3_mt[l][st] <= 4)
     return 1;
@@ -468,7 +469,8 @@ int m2l_stage(fda_plan_s* P, RunOps<C>& op, DBuf<C>& cout, DBuf<C>& cin, DBuf<C>
   const bool f32 = std::is_same<C, float2>::value;
   // the image kernels cover at most 4 row tiles (256 complex rows): a forced variant falls back to FMA beyond
   const bool tc3_fits = P->tc3_mt[l][st] <= 4;
-  const bool x3 = P->cfg.m2l_tensor == 3;  // 3xTF32 images: the split kernel for every tensor-core variant
+  // 3xTF32 images: the split kernel for every tensor-core variant, unless the product asks for one TF32 pass
+  const bool x3 = P->cfg.m2l_tensor == 3 && !P->fast_tf32;
   // the TMA-fed V^ kernel serves one right-hand side; for more it is the swapped kernel
   const bool vtm = (variant == 12 || variant == 13) && nrhs == 1 && P->vtm_ok[l];
   if ((variant == 8 || variant == 9 || variant == 12 || variant == 13 || variant == 14 || variant == 15) && f32 &&
@@ -636,7 +638,7 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
     auto chunk = [&](size_t rows) { return (int)std::max<size_t>(1, std::min<size_t>(nrhs, SMEM / (rows * sizeof(C)))); };
     // the grouped tensor-core M2M accumulates into the parents: clear the outgoing coefficients first
     const bool tc_mm = std::is_same<C, float2>::value && (P->cfg.m2l_tensor == 1 || P->cfg.m2l_tensor == 3);
-    const int mm_shape = P->cfg.m2l_tensor == 3 ? 6 : 0;
+    const int mm_shape = (P->cfg.m2l_tensor == 3 && !P->fast_tf32) ? 6 : 0;
     if (tc_mm) FDA_TRY(zero_parent_coefs<C>(P, cout, nrhs, sf));
     // M2L of every level on its own stream (FP32): the incoming coefficients are cleared before anything forks
     const bool fpar = std::is_same<C, float2>::value && P->far_par == 1 && !P->phase_ev && P->lvs[0];
@@ -773,12 +775,16 @@ int plan_matvec(fda_plan_s* P, int prec, const void* x, void* y, int nrhs, int i
     set_error("nrhs %d outside [1, %d]", nrhs, P->cfg.nrhs_max);
     return FDA_E_INVALID_ARG;
   }
-  if (prec == FDA_PREC_FP32) {
+  if (prec == FDA_PREC_FP32 || prec == FDA_PREC_TF32) {
     if (P->cfg.precision != FDA_PREC_FP32) {
       set_error("plan was built without FP32 operators");
       return FDA_E_STATE;
     }
-    return matvec_t<float2>(P, P->op32, P->xt32, P->yt32, P->cout32, P->cin32, P->mid32, x, y, nrhs, io_dtype, s);
+    P->fast_tf32 = prec == FDA_PREC_TF32 && P->cfg.m2l_tensor == 3;
+    const int rc =
+        matvec_t<float2>(P, P->op32, P->xt32, P->yt32, P->cout32, P->cin32, P->mid32, x, y, nrhs, io_dtype, s);
+    P->fast_tf32 = 0;
+    return rc;
   }
   if (P->cfg.drop_fp64) {
     set_error("the plan released its FP64 operators (drop_fp64): FP32 products only");
@@ -818,9 +824,11 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
   FDA_TRY(x.alloc((size_t)N * nrhs));
   FDA_TRY(y.alloc((size_t)N * nrhs));
   FDA_TRY(x.zero(s));
-  for (int l = 0; l < FDA_MAXLEV; ++l) P->m2l_choice[l][0] = P->m2l_choice[l][1] = -1;
+  for (int l = 0; l < FDA_MAXLEV; ++l)
+    P->m2l_choice[l][0] = P->m2l_choice[l][1] = P->m2l_choice_fast[l][0] = P->m2l_choice_fast[l][1] = -1;
   P->near_wide = -1;
   P->near_csep = -1;
+  P->near_ring = 0;
   P->overlap = 0;
   P->near_evict = 0;
   P->far_par = 0;
@@ -828,10 +836,15 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
   FDA_CUDA(cudaStreamSynchronize(s));
   int64_t nl = 0;
   int e = 0;
+  // a 3xTF32 plan also serves single-pass TF32 products (FDA_PREC_TF32): their kernels are tuned first, into
+  // their own choices; the report lists the plan's own (3xTF32) choices
+  for (int pass = P->cfg.m2l_tensor == 3 ? 0 : 1; pass < 2; ++pass) {
+  P->fast_tf32 = pass == 0;
   for (int l = P->lmin; l <= P->lmax && P->n_coef > 0; ++l)
     for (int st = 0; st < 2; ++st) {
       if (P->h_units[l][st].empty() || e >= 64) continue;
       const int tv = m2l_variant(P, l, st);  // the plan's tensor-core variant, if any
+      const bool x3p = P->cfg.m2l_tensor == 3 && !P->fast_tf32;  // the split kernels of a 3xTF32 product
       double t0 = 0, t1 = -1;
       FDA_TRY(time_ms(s, [&]() { return m2l_stage<float2>(P, P->op32, P->cout32, P->cin32, P->mid32, l, st, 0, nrhs, s,
                                                           &nl); },
@@ -843,13 +856,13 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
       int tvb = tv;  // the tensor-core variant kept
       if (tv == 1) {
         std::vector<int> alts = {3, 4, 5, 6, 7};
-        if (P->cfg.m2l_tensor == 3) alts = {7};  // 3xTF32: atomics (1) or bulk reductions (7)
+        if (x3p) alts = {7};  // 3xTF32: atomics (1) or bulk reductions (7)
         else if (st == 0 && !P->h_vsw_units[l].empty()) {
           alts.push_back(8), alts.push_back(9), alts.push_back(14), alts.push_back(15);
           if (nrhs == 1 && P->vtm_ok[l]) alts.push_back(12), alts.push_back(13);
         }
         else if (st == 1 && !P->h_ws_units[l].empty()) alts.push_back(10);
-        if (P->cfg.m2l_tensor != 3) alts.push_back(11);
+        if (!x3p) alts.push_back(11);
         for (int alt : alts) {
           double ta = 0;
           FDA_TRY(time_ms(s, [&]() { return m2l_stage<float2>(P, P->op32, P->cout32, P->cin32, P->mid32, l, st, alt,
@@ -858,15 +871,21 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
           if (ta < t1) t1 = ta, tvb = alt;
         }
       }
+      const int pick = (tv != 0 && t1 < t0) ? tvb : 0;
+      if (P->fast_tf32) {
+        P->m2l_choice_fast[l][st] = pick;
+        continue;
+      }
       R->level[e] = l;
       R->stage[e] = st;
       R->ms_fma[e] = t0;
       R->ms_tensor[e] = t1;
-      const int pick = (tv != 0 && t1 < t0) ? tvb : 0;
       R->chosen[e] = pick == 0 ? 0 : (pick >= 3 ? pick - 1 : 1);
       P->m2l_choice[l][st] = pick;
       ++e;
     }
+  }
+  P->fast_tf32 = 0;
   R->entries = e;
   if (nrhs >= 12 && P->n_near_tleaf > 0 && P->near_max_nr <= 256) {
     double tn[2];
@@ -884,22 +903,32 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
     R->near_rhs_per_pass = nrhs == 1 ? 1 : 4;
   }
   R->near_window_ms = -1;
+  for (int q = 0; q < 3; ++q) R->near_deep_ring_ms[q] = -1;
+  P->near_ring = 0;
+  R->near_deep_ring = 0;
   if (P->n_near_tleaf > 0 && P->near_max_nr <= 256) {
-    // schedules: 0 corrections per leaf; 1 split; 2 split with double-buffered windows (one right-hand side)
-    double tc[3] = {0, 0, -1};
+    // schedules: 0 corrections per leaf; 1 split; 2 split with double-buffered windows (one right-hand side);
+    // one right-hand side also with the four-stage ring
+    double tc[2][3] = {{0, 0, -1}, {-1, -1, -1}};
     const int ncs = nrhs == 1 ? 3 : 2;
-    int best = 0;
-    for (int cs = 0; cs < ncs; ++cs) {
-      P->near_csep = cs;
-      FDA_TRY(time_ms(s, [&]() { return near_stream<float2>(P, P->op32.near.p, P->op32.corr.p, P->xt32.p, P->yt32.p,
-                                                            nrhs, s, &nl); },
-                      3, &tc[cs]));
-      if (tc[cs] < tc[best]) best = cs;
-    }
-    R->near_split_ms[0] = tc[0];
-    R->near_split_ms[1] = tc[1];
-    R->near_window_ms = tc[2];
+    const int nring = nrhs == 1 ? 2 : 1;
+    int best = 0, best_ring = 0;
+    for (int ring = 0; ring < nring; ++ring)
+      for (int cs = 0; cs < ncs; ++cs) {
+        P->near_csep = cs;
+        P->near_ring = ring;
+        FDA_TRY(time_ms(s, [&]() { return near_stream<float2>(P, P->op32.near.p, P->op32.corr.p, P->xt32.p,
+                                                              P->yt32.p, nrhs, s, &nl); },
+                        3, &tc[ring][cs]));
+        if (tc[ring][cs] < tc[best_ring][best]) best = cs, best_ring = ring;
+      }
+    R->near_split_ms[0] = tc[0][0];
+    R->near_split_ms[1] = tc[0][1];
+    R->near_window_ms = tc[0][2];
+    for (int q = 0; q < 3; ++q) R->near_deep_ring_ms[q] = tc[1][q];
     P->near_csep = best;
+    P->near_ring = best_ring;
+    R->near_deep_ring = best_ring;
   }
   R->near_split = P->near_csep < 0 ? 0 : P->near_csep;
   // whole products: serial, or near and far field on two streams with two or one near-field CTAs per SM; each

@@ -96,36 +96,41 @@ __device__ __forceinline__ void ns_cons_sync() { asm volatile("bar.sync 1, %0;" 
 // is used; corrections always by the separate CSR kernel (no correction buffer). 16 right-hand sides per pass
 // always run this way (two windows of at most 256 columns, 32 KB each); one right-hand side does when W is set
 // (two windows of 8 KB: 1024 FP32 or 512 FP64 columns, several per thread).
-template <typename C, int NR, bool W = false>
+// D (FP32, one right-hand side only): a deeper ring of four stages that still fits three CTAs per SM (each CTA
+// at 76,768 bytes of the 76,800 that three CTAs may take); the stage shrinks to 14,272 or 13,760 bytes. FP64
+// products keep the three-stage ring.
+template <typename C, int NR, bool W = false, int D = 0>
 struct NsLayout {
   static constexpr int E = sizeof(C);
   static constexpr bool DB = NR == 16 || W;
-  static constexpr int STAGES = NR == 1 ? 3 : 4;
+  static constexpr bool DEEP = D == 1 && NR == 1 && E == 8;
+  static constexpr int SB = DEEP ? (W ? 14272 : 13760) : NS_STAGE_BYTES;  // bytes per stage (multiple of 16)
+  static constexpr int STAGES = NR == 1 ? (DEEP ? 4 : 3) : 4;
   static constexpr int MINB = NR == 1 ? 3 : (NR <= 4 ? 2 : 1);
   static constexpr int XBYTES = NR == 16 ? 32768 : (W ? 8192 : ((NR == 1 || E * NR >= 64) ? 16384 : 32768));
   static constexpr int XW0 = (XBYTES / (NR * E)) & ~1;
   static constexpr int XW = NR == 16 && XW0 > NS_CONS ? NS_CONS : XW0;  // columns per density window (even)
   static constexpr int CPT = DB && XW > NS_CONS ? XW / NS_CONS : 1;     // window columns per consumer thread
   static_assert(!DB || XW <= NS_CONS || XW % NS_CONS == 0, "double-buffered window: whole columns per thread");
-  static constexpr size_t ring = (size_t)STAGES * NS_STAGE_BYTES;
+  static constexpr size_t ring = (size_t)STAGES * SB;
   static constexpr size_t xs = ring;
   static constexpr size_t red = xs + (size_t)(DB ? 2 : 1) * XW * NR * E;
   static constexpr size_t cor = red + (size_t)NS_CONS * NR * E;
   static constexpr size_t crow = cor + (DB ? (size_t)0 : (size_t)NS_CONS * NR * E);
   static constexpr size_t bars = crow + (NS_CONS + 8) * sizeof(int);
   static constexpr size_t total = bars + 2 * STAGES * sizeof(uint64_t) + 128;  // + alignment slack
+  static_assert(!DEEP || total <= 76800, "the deep ring must leave room for three CTAs per SM");
 };
 
 // columns per chunk: whole columns, an even count, at most one stage
-__device__ __forceinline__ int ns_cpc(int nr, int E) { return max(2, (NS_STAGE_BYTES / (nr * E)) & ~1); }
+__device__ __forceinline__ int ns_cpc(int nr, int E, int sb) { return max(2, (sb / (nr * E)) & ~1); }
 
-template <typename C, int NR, bool W>
-static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR, W>::MINB) k_near_stream(
-    const int32_t* part, const int64_t* tleaf, const int64_t* pb, const int64_t* pe, const int64_t* nbase,
-    const int32_t* ncolv, const int64_t* xbase, const int32_t* xcol, const C* B, const int64_t* cptr,
-    const int32_t* ccol, const C* cval, const C* xt, C* yt, int nrhs, int r0, int rc, int csep, int evict_first,
-    int* err) {
-  typedef NsLayout<C, NR, W> Ly;
+template <typename C, int NR, bool W, int D>
+static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR, W, D>::MINB) k_near_stream(
+    const int32_t* part, const NsMeta* meta, const int32_t* ncolv, const int64_t* xbase, const int32_t* xcol,
+    const C* B, const int64_t* cptr, const int32_t* ccol, const C* cval, const C* xt, C* yt, int nrhs, int r0,
+    int rc, int csep, int evict_first, int* err) {
+  typedef NsLayout<C, NR, W, D> Ly;
   typedef decltype(xt[0].x) R;
   constexpr int E = Ly::E, XW = Ly::XW, NS_STAGES = Ly::STAGES;
   extern __shared__ unsigned char smem_raw[];
@@ -156,12 +161,15 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR, W>::MINB) k_near
       bool ok = true;
       uint64_t pol = 0;
       if (evict_first) asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+      NsMeta mn;  // the next leaf's description, loaded while this leaf's copies are issued
+      if (u0 < u1) mn = meta[u0];
       for (int u = u0; u < u1 && ok; ++u) {
-        const int64_t L = tleaf[u];
-        const int nr = (int)(pe[L] - pb[L]);
-        const int ncol = ncolv[u];
-        const unsigned char* src = (const unsigned char*)(B + nbase[u]);
-        const int cpc = ns_cpc(nr, E);
+        const NsMeta m = mn;
+        if (u + 1 < u1) mn = meta[u + 1];
+        const int nr = m.nr;
+        const int ncol = m.ncol;
+        const unsigned char* src = (const unsigned char*)(B + m.nb);
+        const int cpc = ns_cpc(nr, E, Ly::SB);
         for (int c = 0; c < ncol;) {
           const int wend = min(ncol, (c / XW + 1) * XW);
           const int cc = min(cpc, wend - c);
@@ -174,9 +182,9 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR, W>::MINB) k_near
           const uint32_t bytes = (uint32_t)(((int64_t)cc * nr * E + 15) & ~(int64_t)15);
           ns_expect_tx(&full[st], bytes);
           if (evict_first)
-            ns_bulk_hint(ring + (size_t)st * NS_STAGE_BYTES, src + (int64_t)c * nr * E, bytes, &full[st], pol);
+            ns_bulk_hint(ring + (size_t)st * Ly::SB, src + (int64_t)c * nr * E, bytes, &full[st], pol);
           else
-            ns_bulk(ring + (size_t)st * NS_STAGE_BYTES, src + (int64_t)c * nr * E, bytes, &full[st]);
+            ns_bulk(ring + (size_t)st * Ly::SB, src + (int64_t)c * nr * E, bytes, &full[st]);
           c += cc;
           ++it;
         }
@@ -242,13 +250,31 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR, W>::MINB) k_near
     advance();
     load_cols();
   }
+  // FP32: each leaf's description is loaded one leaf ahead, so that no leaf starts on a global load (FP64 has
+  // no registers to spare for it)
+  NsMeta mnext;
+  if (E == 8 && u0 < u1) mnext = meta[u0];
   for (int u = u0; u < u1; ++u) {
-    const int64_t L = tleaf[u];
-    const int64_t tb = pb[L];
-    const int nr = (int)(pe[L] - tb);
-    const int ncol = ncolv[u];
-    const int64_t xb = xbase[u];
-    const int cpc = ns_cpc(nr, E);
+    NsMeta m;
+    if constexpr (E == 8) {
+      m = mnext;
+      if (u + 1 < u1) mnext = meta[u + 1];
+    } else {
+      m = meta[u];
+    }
+    const int64_t tb = m.tb;
+    const int nr = m.nr;
+    const int ncol = m.ncol;
+    const int64_t xb = m.xb;
+    const int cpc = ns_cpc(nr, E, Ly::SB);
+    // split schedule: the correction sums that k_near_corr stored for this leaf's rows, read now and added at
+    // the leaf's end
+    const bool ypre_ok = E == 8 && csep && nr * rc <= NS_CONS;  // FP64: registers are short
+    C ypre = mk((R)0, (R)0);
+    if (ypre_ok && t < nr * rc) {
+      const int r = t / rc, rr = t - r * rc;
+      ypre = yt[(tb + r) * nrhs + r0 + rr];
+    }
     const int G = NS_CONS / nr;
     const int i = t % nr, g = t / nr;
     const bool act = g < G;
@@ -354,7 +380,7 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR, W>::MINB) k_near
           atomicExch(err, 1);
         }
         if (!failed && act) {
-          const C* Bs = (const C*)(ring + (size_t)st * NS_STAGE_BYTES) + i;
+          const C* Bs = (const C*)(ring + (size_t)st * Ly::SB) + i;
           const C* xw = xcur + (c - wb) * NR;
           int cl = g;
           for (; cl + 3 * G < cc; cl += 4 * G) {
@@ -385,7 +411,7 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR, W>::MINB) k_near
     for (int q = t; q < nr * rc; q += NS_CONS) {
       const int r = q / rc, rr = q - r * rc;
       C* yp = yt + (tb + r) * nrhs + r0 + rr;
-      C s = csep ? *yp : cor[r * NR + rr];
+      C s = csep ? (ypre_ok ? ypre : *yp) : cor[r * NR + rr];
       for (int gg = 0; gg < G; ++gg) s = cadd(s, red[(gg * nr + r) * NR + rr]);
       *yp = s;
     }
@@ -442,13 +468,13 @@ static __global__ void __launch_bounds__(256) k_near_corr(const int64_t* cptr, c
   if ((lane & ((1 << (5 - LOGNR)) - 1)) == 0 && qi < rc) yt[row * nrhs + r0 + qi] = a[0];
 }
 
-template <typename C, int NR, bool W>
+template <typename C, int NR, bool W, int D = 0>
 static int near_stream_t(fda_plan_s* P, const C* B, const C* cval, const C* xt, C* yt, int nrhs, cudaStream_t s,
                          int64_t* launches) {
-  typedef NsLayout<C, NR, W> Ly;
+  typedef NsLayout<C, NR, W, D> Ly;
   static bool attr = false;
   if (!attr) {
-    FDA_CUDA(cudaFuncSetAttribute(k_near_stream<C, NR, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    FDA_CUDA(cudaFuncSetAttribute(k_near_stream<C, NR, W, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)Ly::total));
     attr = true;
   }
@@ -463,9 +489,8 @@ static int near_stream_t(fda_plan_s* P, const C* B, const C* cval, const C* xt, 
       ++*launches;
     }
     const int ov = (P->near_sel == 1 || P->near_sel == 2) && P->near_grid_ov[P->near_sel - 1] > 0 ? P->near_sel : 0;
-    k_near_stream<C, NR, W><<<(unsigned)(ov ? P->near_grid_ov[ov - 1] : P->near_grid), NS_NT, Ly::total, s>>>(
-        ov ? P->near_part_ov[ov - 1].p : P->near_part.p, P->near_tleaf.p, T->pb.p, T->pe.p, P->near_nbase.p,
-        P->near_ncol.p, P->near_xbase.p,
+    k_near_stream<C, NR, W, D><<<(unsigned)(ov ? P->near_grid_ov[ov - 1] : P->near_grid), NS_NT, Ly::total, s>>>(
+        ov ? P->near_part_ov[ov - 1].p : P->near_part.p, P->near_meta.p, P->near_ncol.p, P->near_xbase.p,
         P->near_xcol.p, B, P->corr_ptr.p, P->corr_col.p, cval, xt, yt, nrhs, r0, rc, csep, P->near_evict,
         P->tc_err.p);
     FDA_LAUNCH_CHECK();
@@ -482,9 +507,13 @@ int near_stream(fda_plan_s* P, const C* B, const C* cval, const C* xt, C* yt, in
     return FDA_E_INVALID_ARG;
   }
   // right-hand sides per pass over the matrix: 1, 4, or 16 for wide batches (each pass streams it once)
-  if (nrhs == 1)
+  if (nrhs == 1) {
+    if (P->near_ring == 1)
+      return P->near_csep == 2 ? near_stream_t<C, 1, true, 1>(P, B, cval, xt, yt, nrhs, s, launches)
+                               : near_stream_t<C, 1, false, 1>(P, B, cval, xt, yt, nrhs, s, launches);
     return P->near_csep == 2 ? near_stream_t<C, 1, true>(P, B, cval, xt, yt, nrhs, s, launches)
                              : near_stream_t<C, 1, false>(P, B, cval, xt, yt, nrhs, s, launches);
+  }
   if (nrhs < 12 || P->near_wide == 0) return near_stream_t<C, 4, false>(P, B, cval, xt, yt, nrhs, s, launches);
   return near_stream_t<C, 16, false>(P, B, cval, xt, yt, nrhs, s, launches);
 }

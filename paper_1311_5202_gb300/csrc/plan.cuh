@@ -35,6 +35,13 @@ struct LevelOps {
 // One operator expanded into the tensor-core image (see m2l_tc.cu): the TF32 image, followed for split = 1
 // by the image of the TF32 remainders (value - TF32(value)), so that three products hi*hi + hi*lo + lo*hi
 // keep FP32 accuracy.
+// One target leaf of the near-field stream: its first row (tree order), the first entry of its column list,
+// the first entry of its matrix, its rows and its columns
+struct alignas(16) NsMeta {
+  int64_t tb, xb, nb;
+  int32_t nr, ncol;
+};
+
 struct TcImgJob {
   const double2* src;  // the M x K operator: src[i + k ld], or src[k + i ld] when trans
   int M, K;
@@ -71,7 +78,8 @@ struct RunOps {
 
 struct fda_plan_s {
   fda_plan_s() {
-    for (int l = 0; l < FDA_MAXLEV; ++l) m2l_choice[l][0] = m2l_choice[l][1] = -1;
+    for (int l = 0; l < FDA_MAXLEV; ++l)
+      m2l_choice[l][0] = m2l_choice[l][1] = m2l_choice_fast[l][0] = m2l_choice_fast[l][1] = -1;
   }
   ~fda_plan_s() {
     if (side) cudaStreamDestroy(side);
@@ -125,6 +133,8 @@ struct fda_plan_s {
   fda::DBuf<int32_t> near_ncol;      // target leaf -> number of columns
   fda::DBuf<int64_t> near_xbase;     // target leaf -> first entry of its column list in near_xcol
   fda::DBuf<int32_t> near_xcol;      // column -> tree position of its source point
+  fda::DBuf<fda::NsMeta> near_meta;      // target leaf -> rows, columns and offsets, one 32-byte record
+  int near_ring = 0;                 // one right-hand side: 1 = four-stage ring (autotuned)
   fda::DBuf<int32_t> near_part;      // persistent CTA -> first target leaf (grid + 1 entries)
   int near_grid = 0, near_max_nr = 0;
   int64_t corr_merged = 0;           // correction entries folded into the direct blocks
@@ -175,6 +185,10 @@ struct fda_plan_s {
   int mm_mt[FDA_MAXLEV] = {0}, ll_mt[FDA_MAXLEV] = {0};
   int fma_tm[FDA_MAXLEV][2] = {{0}};  // row tile of the FMA M2L units (16, 32 or 64)
   int m2l_choice[FDA_MAXLEV][2];      // autotuned M2L kernel per (level, stage), -1: from the plan options
+  // products in FDA_PREC_TF32 on a plan with 3xTF32 images: single-pass TF32 kernels on the leading part of
+  // each image, with their own autotuned choices
+  int fast_tf32 = 0;
+  int m2l_choice_fast[FDA_MAXLEV][2];
   int near_csep = -1;                 // near-field schedule: 0 per-leaf corrections, 1 split, 2 split + DB windows
   int near_wide = -1;                 // autotuned right-hand sides per near-field pass for wide batches
   fda::DBuf<int64_t> pair_src, pair_tgt;  // coefficient indices (slot + wedge * s)

@@ -471,6 +471,7 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
   P->prob = pr;
   P->cfg = *cfg;
   P->near_csep = cfg->near_split;  // 0, 1 or 2 (checked at the entry point)
+  P->near_ring = cfg->near_deep_ring;
   if (P->cfg.nrhs_max < 1) P->cfg.nrhs_max = 1;
   FDA_TRY(upload_geometry_constants());
   const int64_t N = T->N, nbox = T->nbox;
@@ -1581,6 +1582,17 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
     FDA_TRY(P->near_ncol.upload(ncolv));
     FDA_TRY(P->near_xbase.upload(xbase));
     FDA_TRY(P->near_xcol.upload(xcol));
+    {
+      std::vector<NsMeta> meta(tleaf.size());
+      for (size_t u = 0; u < tleaf.size(); ++u) {
+        meta[u].tb = T->h_pb[tleaf[u]];
+        meta[u].xb = xbase[u];
+        meta[u].nb = nbase[u];
+        meta[u].nr = (int32_t)(T->h_pe[tleaf[u]] - T->h_pb[tleaf[u]]);
+        meta[u].ncol = ncolv[u];
+      }
+      FDA_TRY(P->near_meta.upload(meta));
+    }
     FDA_TRY(P->op64.near.alloc(alloc_entries));
     FDA_TRY(P->op64.near.zero());
     DBuf<NearJob> dj;

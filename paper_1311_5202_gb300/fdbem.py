@@ -29,6 +29,7 @@ FDA_CPLX128 = 0
 FDA_CPLX64 = 1
 FDA_PREC_FP64 = 0
 FDA_PREC_FP32 = 1
+FDA_PREC_TF32 = 2
 
 
 class FdaError(RuntimeError):
@@ -40,13 +41,14 @@ class FdaError(RuntimeError):
 class fda_config_t(C.Structure):
     _fields_ = [("eps", C.c_double), ("precision", C.c_int), ("lowrank", C.c_int), ("nrhs_max", C.c_int),
                 ("m2l_tensor", C.c_int), ("op", C.c_int), ("near_split", C.c_int),
-                ("drop_fp64", C.c_int), ("reserved", C.c_int), ("gamma_re", C.c_double), ("gamma_im", C.c_double)]
+                ("drop_fp64", C.c_int), ("near_deep_ring", C.c_int), ("gamma_re", C.c_double),
+                ("gamma_im", C.c_double)]
 
 
 class bm_gmres_opts_t(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("max_iter", C.c_int), ("x0_given", C.c_int),
                 ("refine", C.c_int), ("inner_restart", C.c_int), ("inner_tol", C.c_double),
-                ("reserved", C.c_int * 6)]
+                ("refine_residual", C.c_int), ("reserved", C.c_int * 5)]
 
 
 class bm_gmres_stats_t(C.Structure):
@@ -76,8 +78,9 @@ class fda_tune_report_t(C.Structure):
                 ("ms_fma", C.c_double * 64), ("ms_tensor", C.c_double * 64), ("chosen", C.c_int32 * 64),
                 ("near_ms", C.c_double * 2), ("near_rhs_per_pass", C.c_int32), ("near_split", C.c_int32),
                 ("near_split_ms", C.c_double * 2), ("near_window_ms", C.c_double), ("overlap", C.c_int32),
-                ("near_evict_first", C.c_int32), ("far_levels_concurrent", C.c_int32), ("reserved", C.c_int32),
-                ("schedule_ms", C.c_double * 12)]
+                ("near_evict_first", C.c_int32), ("far_levels_concurrent", C.c_int32),
+                ("near_deep_ring", C.c_int32), ("schedule_ms", C.c_double * 12),
+                ("near_deep_ring_ms", C.c_double * 3)]
 
 
 class fda_plan_info_t(C.Structure):
@@ -257,9 +260,10 @@ def fda_tree_destroy(tree):
 
 
 def fda_precompute_translations(tree, eps, precision=FDA_PREC_FP64, lowrank=1, nrhs_max=1, m2l_tensor=0, op=0,
-                                near_split=0, gamma=0.0, drop_fp64=False):
+                                near_split=0, gamma=0.0, drop_fp64=False, near_deep_ring=0):
     cfg = fda_config_t()
     cfg.drop_fp64 = int(bool(drop_fp64))
+    cfg.near_deep_ring = int(near_deep_ring)
     cfg.gamma_re = complex(gamma).real
     cfg.gamma_im = complex(gamma).imag
     cfg.eps = float(eps)
@@ -337,7 +341,8 @@ def fda_autotune(plan, nrhs=1, stream=None) -> dict:
     return dict(m2l=rows, near_ms=list(R.near_ms), near_rhs_per_pass=R.near_rhs_per_pass,
                 near_split=R.near_split, near_split_ms=list(R.near_split_ms), near_window_ms=R.near_window_ms,
                 overlap=R.overlap, near_evict_first=R.near_evict_first,
-                far_levels_concurrent=R.far_levels_concurrent, schedule_ms=list(R.schedule_ms))
+                far_levels_concurrent=R.far_levels_concurrent, schedule_ms=list(R.schedule_ms),
+                near_deep_ring=R.near_deep_ring, near_deep_ring_ms=list(R.near_deep_ring_ms))
 
 
 def fda_m2l_force(plan, variant):
@@ -408,8 +413,9 @@ def fda_plan_destroy(plan):
 
 
 def bm_gmres_solve(plan, b, x, tol=1e-6, restart=50, max_iter=1000, x0_given=False, refine=False,
-                   inner_restart=0, inner_tol=1e-4, stream=None, raise_on_error=True):
+                   inner_restart=0, inner_tol=1e-4, stream=None, raise_on_error=True, refine_residual=0):
     o = bm_gmres_opts_t()
+    o.refine_residual = int(refine_residual)
     o.tol = float(tol)
     o.restart = int(restart)
     o.max_iter = int(max_iter)
@@ -489,8 +495,9 @@ def bm_residual_pair(plan, b, xstar, x, r, e, stream=None):
 
 
 def bm_fgmres_solve(plan, pc, net, b, x, tol=1e-6, restart=50, max_iter=1000, x0_given=False, refine=False,
-                    inner_restart=0, inner_tol=1e-4, stream=None, raise_on_error=True):
+                    inner_restart=0, inner_tol=1e-4, stream=None, raise_on_error=True, refine_residual=0):
     o = bm_gmres_opts_t()
+    o.refine_residual = int(refine_residual)
     o.tol = float(tol)
     o.restart = int(restart)
     o.max_iter = int(max_iter)
@@ -554,12 +561,12 @@ class Solver:
     """Problem + tree + plan with ordered destruction."""
 
     def __init__(self, nodes, elems, k, eps=1e-4, leaf_max=64, precision=FDA_PREC_FP64, lowrank=1, nrhs_max=1,
-                 alpha=None, m2l_tensor=0, op=0, near_split=0, gamma=0.0, drop_fp64=False):
+                 alpha=None, m2l_tensor=0, op=0, near_split=0, gamma=0.0, drop_fp64=False, near_deep_ring=0):
         self.k = float(k)
         self.prob = bm_problem_create(nodes, elems, k, alpha)
         self.tree = fda_build_tree(self.prob, leaf_max)
         self.plan = fda_precompute_translations(self.tree, eps, precision, lowrank, nrhs_max, m2l_tensor, op,
-                                                near_split, gamma, drop_fp64)
+                                                near_split, gamma, drop_fp64, near_deep_ring)
         self.N = 6 * int(np.asarray(elems).shape[0])
 
     def matvec(self, x, y, stream=None):

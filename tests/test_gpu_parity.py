@@ -152,16 +152,17 @@ def test_matvec_batched_rhs_equals_single(c1):
         assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-6
 
 
-@pytest.mark.parametrize("split", [1, 2])
-def test_near_correction_split_schedule(c1, split):
+@pytest.mark.parametrize("split,deep", [(1, 0), (2, 0), (0, 1), (1, 1), (2, 1)])
+def test_near_correction_split_schedule(c1, split, deep):
     """The off-block correction entries of Eq. kcorrection as their own CSR kernel before the near-field stream
-    (near_split = 1), and with the stream's density windows double-buffered (near_split = 2): the FP64 product on
-    all rows against the oracle (1e-4), and against the per-leaf schedule of the same plan (same sums in another
-    order: 1e-12 in FP64, 1e-5 in FP32); for split = 1 also 16 right-hand sides (the 16-wide pass reduces lane
-    sums by recursive halving and always double-buffers its windows)."""
+    (near_split = 1), and with the stream's density windows double-buffered (near_split = 2); each schedule also
+    with the four-stage ring of one right-hand side (deep = 1): the FP64 product on all rows against the oracle
+    (1e-4), and against the per-leaf schedule of the same plan (same sums in another order: 1e-12 in FP64, 1e-5
+    in FP32); for split = 1 also 16 right-hand sides (the 16-wide pass reduces lane sums by recursive halving and
+    always double-buffers its windows)."""
     mesh, S0 = c1
     S1 = fdbem.Solver(mesh.nodes, mesh.elems, 10.0, eps=1e-6, leaf_max=64, precision=fdbem.FDA_PREC_FP32,
-                      nrhs_max=16, near_split=split)
+                      nrhs_max=16, near_split=split, near_deep_ring=deep)
     try:
         x = inputs.complex_gaussian(S1.N, 77)
         xd = torch.from_numpy(x).to(DEV)
@@ -513,6 +514,15 @@ def test_fp32_only_plan():
         assert st["status"] == fdbem.FDA_E_STATE
         st = S2.solve(bb, u, tol=1e-5, restart=100, max_iter=3000)
         assert st["status"] == fdbem.FDA_OK and st["rel_residual"] <= 1e-5
+        # refinement with the 3xTF32 FP32 product as the outer residual needs no FP64 operator
+        u3 = torch.zeros_like(bb)
+        st = S2.solve(bb, u3, tol=1e-5, restart=100, max_iter=3000, refine=True, inner_tol=1e-3,
+                      refine_residual=1)
+        assert st["status"] == fdbem.FDA_OK and st["rel_residual"] <= 1e-5 and st["outer_iterations"] >= 1
+        r = torch.empty_like(bb)
+        fdbem.fda_matvec_ex(S1.plan, fdbem.FDA_PREC_FP64, u3, r)  # S1: the same operator with its FP64 copy
+        torch.cuda.synchronize()
+        assert (torch.linalg.norm(bb - r) / torch.linalg.norm(bb)).item() < 2e-5
         assert fdbem.fda_plan_check(S2.plan) == fdbem.FDA_OK
     finally:
         S2.close()
@@ -544,6 +554,69 @@ def test_block_gmres_several_directions_match_oracle(refine):
             assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) < 1e-4, c
     finally:
         S.close()
+
+
+def test_tf32_pass_on_3xtf32_images_and_refinement_with_their_residual():
+    """A plan with 3xTF32 images (m2l_tensor = 3) serves products in two arithmetics. FDA_PREC_FP32 runs the
+    three-product split form; FDA_PREC_TF32 runs single-pass TF32 kernels on the leading part of the same images,
+    the arithmetic of a TF32 plan (m2l_tensor = 1). Both meet the mixed bar (3e-4) on 256 oracle rows. The TF32
+    pass agrees with the TF32 plan's product up to the rounding of the images (1e-4) and differs from the split
+    form by more than FP32 rounding; an autotuned TF32 pass and a captured graph of it give the same product.
+    Refinement with the split product as the outer residual (refine_residual = 1) reaches 1e-6 and, checked
+    with the FP64 operator, 1e-5; it agrees with the refinement around the FP64 residual (5e-5); a plan
+    without 3xTF32 images refuses it with FDA_E_STATE."""
+    _need_gpu()
+    mesh = inputs.icosphere(14, 0.5)
+    k = 100.0
+    kw = dict(eps=1e-5, leaf_max=64, precision=fdbem.FDA_PREC_FP32, alpha=-1j / k)
+    S3 = fdbem.Solver(mesh.nodes, mesh.elems, k, m2l_tensor=3, **kw)
+    S1 = fdbem.Solver(mesh.nodes, mesh.elems, k, m2l_tensor=1, **kw)
+    try:
+        x = inputs.complex_gaussian(S3.N, 31)
+        xd = torch.from_numpy(x.astype(np.complex64)).to(DEV)
+        y3, yt, y1 = torch.empty_like(xd), torch.empty_like(xd), torch.empty_like(xd)
+        fdbem.fda_matvec_ex(S3.plan, fdbem.FDA_PREC_FP32, xd, y3)
+        fdbem.fda_matvec_ex(S3.plan, fdbem.FDA_PREC_TF32, xd, yt)
+        fdbem.fda_matvec_ex(S1.plan, fdbem.FDA_PREC_FP32, xd, y1)
+        torch.cuda.synchronize()
+        a3, at, a1 = y3.cpu().numpy(), yt.cpu().numpy(), y1.cpu().numpy()
+        rows = inputs.sample_rows(S3.N, 256, 7)
+        yo = O.matvec_rows(mesh.nodes, mesh.elems, k, x, rows, beta_h=-1j / k)
+        for a in (a3, at):
+            assert np.linalg.norm(a[rows] - yo) / np.linalg.norm(yo) < 3e-4
+        assert np.linalg.norm(at - a1) / np.linalg.norm(a1) < 1e-4
+        d = np.linalg.norm(at - a3) / np.linalg.norm(a3)
+        assert 1e-7 < d < 5e-4, d
+        fdbem.fda_autotune(S3.plan, 1)
+        yt2 = torch.empty_like(xd)
+        fdbem.fda_matvec_ex(S3.plan, fdbem.FDA_PREC_TF32, xd, yt2)
+        xg, yg = xd.clone(), torch.empty_like(xd)
+        g = fdbem.fda_matvec_graph_create(S3.plan, fdbem.FDA_PREC_TF32, xg, yg)
+        try:
+            fdbem.fda_graph_launch(g)
+            torch.cuda.synchronize()
+            assert (torch.linalg.norm(yg - yt2) / torch.linalg.norm(yt2)).item() < 1e-5
+        finally:
+            fdbem.fda_graph_destroy(g)
+        assert np.linalg.norm(yt2.cpu().numpy() - at) / np.linalg.norm(at) < 2e-5
+        b = torch.empty(S3.N, dtype=torch.complex128, device=DEV)
+        fdbem.bm_rhs_plane_wave(S3.prob, [0.0, 0.0, 1.0], b)
+        u0, u1 = torch.zeros_like(b), torch.zeros_like(b)
+        st0 = S3.solve(b, u0, tol=1e-6, restart=100, max_iter=2000, refine=True, inner_tol=1e-3)
+        st1 = S3.solve(b, u1, tol=1e-6, restart=100, max_iter=2000, refine=True, inner_tol=1e-3, refine_residual=1)
+        assert st0["status"] == fdbem.FDA_OK and st1["status"] == fdbem.FDA_OK and st1["rel_residual"] <= 1e-6
+        r = torch.empty_like(b)
+        fdbem.fda_matvec_ex(S3.plan, fdbem.FDA_PREC_FP64, u1, r)
+        torch.cuda.synchronize()
+        assert (torch.linalg.norm(b - r) / torch.linalg.norm(b)).item() < 1e-5
+        assert (torch.linalg.norm(u1 - u0) / torch.linalg.norm(u0)).item() < 5e-5
+        st = S1.solve(b, torch.zeros_like(b), tol=1e-6, restart=100, max_iter=2000, refine=True, refine_residual=1,
+                      raise_on_error=False)
+        assert st["status"] == fdbem.FDA_E_STATE and "m2l_tensor = 3" in fdbem.fda_last_error()
+        assert fdbem.fda_plan_check(S3.plan) == fdbem.FDA_OK
+    finally:
+        S1.close()
+        S3.close()
 
 
 @pytest.mark.parametrize("mode,evict,far", [(0, 1, 0), (1, 0, 0), (2, 0, 0), (1, 1, 0), (0, 0, 1), (1, 1, 1)])
