@@ -191,8 +191,9 @@ typedef struct {
                         refine = 0 (FP64 Krylov basis around the FP32 operator; with TF32 translations the
                         rounding stalls GMRES near a 1e-4 residual, with 3xTF32 ones, m2l_tensor = 3, it
                         reaches 1e-5 and below) and no preconditioner. */
-  int near_deep_ring; /* 1 = the near-field stream of one right-hand side keeps four ring stages of about 14 KB
-                        instead of three of 16 KB (fda_autotune chooses it by timing); same sums */
+  int near_form;      /* near-field stream of one right-hand side (fda_autotune chooses it by timing): 0 = three
+                        ring stages of 16 KB; 1 = four of about 14 KB; 2 = (with near_split = 2, FP32) packed
+                        FP32x2 FMAs on densities kept twice over, (x.x, x.x, x.y, x.y). Same sums, other order */
   double gamma_re, gamma_im;  /* op = 2: the Robin coefficient gamma = a/b (ignored otherwise) */
 } fda_config_t;
 
@@ -256,12 +257,12 @@ typedef struct {
                                (1) or one (2) near-field CTAs per SM */
   int32_t near_evict_first; /* 1: the near-field matrix copies carry an L2 evict-first policy */
   int32_t far_levels_concurrent; /* 1: the M2L of each level runs on its own stream of the plan */
-  int32_t near_deep_ring;   /* 1: one right-hand side with the near field's four-stage ring (else three) */
+  int32_t near_form;        /* one right-hand side: near-field form kept (as fda_config_t.near_form) */
   double schedule_ms[12];   /* whole FP32 products, best of 5, at index overlap + 3 evict_first + 6 far_levels
                                (the three settings of fda_overlap_force); -1 where not timed (the setting needs
                                a near field in the stream form or a far field that the plan lacks) */
-  double near_deep_ring_ms[3]; /* one right-hand side: near field schedules 0, 1, 2 with the four-stage ring (-1
-                                  for wider batches) */
+  double near_form_ms[3][3]; /* one right-hand side: near field in form f (row) and schedule q (column); -1
+                                where not timed (form 2 runs schedule 2 only; wider batches time form 0) */
 } fda_tune_report_t;
 int fda_autotune(fda_plan_t* plan, int nrhs, void* stream, fda_tune_report_t* report);
 

@@ -828,7 +828,7 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
     P->m2l_choice[l][0] = P->m2l_choice[l][1] = P->m2l_choice_fast[l][0] = P->m2l_choice_fast[l][1] = -1;
   P->near_wide = -1;
   P->near_csep = -1;
-  P->near_ring = 0;
+  P->near_form = 0;
   P->overlap = 0;
   P->near_evict = 0;
   P->far_par = 0;
@@ -903,32 +903,35 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
     R->near_rhs_per_pass = nrhs == 1 ? 1 : 4;
   }
   R->near_window_ms = -1;
-  for (int q = 0; q < 3; ++q) R->near_deep_ring_ms[q] = -1;
-  P->near_ring = 0;
-  R->near_deep_ring = 0;
+  for (int f = 0; f < 3; ++f)
+    for (int q = 0; q < 3; ++q) R->near_form_ms[f][q] = -1;
+  P->near_form = 0;
+  R->near_form = 0;
   if (P->n_near_tleaf > 0 && P->near_max_nr <= 256) {
     // schedules: 0 corrections per leaf; 1 split; 2 split with double-buffered windows (one right-hand side);
-    // one right-hand side also with the four-stage ring
-    double tc[2][3] = {{0, 0, -1}, {-1, -1, -1}};
+    // one right-hand side also with the four-stage ring (form 1) and, for schedule 2, the packed FMAs (form 2)
+    double tc[3][3] = {{0, 0, -1}, {-1, -1, -1}, {-1, -1, -1}};
     const int ncs = nrhs == 1 ? 3 : 2;
-    const int nring = nrhs == 1 ? 2 : 1;
-    int best = 0, best_ring = 0;
-    for (int ring = 0; ring < nring; ++ring)
+    const int nform = nrhs == 1 ? 3 : 1;
+    int best = 0, best_form = 0;
+    for (int form = 0; form < nform; ++form)
       for (int cs = 0; cs < ncs; ++cs) {
+        if (form == 2 && cs != 2) continue;
         P->near_csep = cs;
-        P->near_ring = ring;
+        P->near_form = form;
         FDA_TRY(time_ms(s, [&]() { return near_stream<float2>(P, P->op32.near.p, P->op32.corr.p, P->xt32.p,
                                                               P->yt32.p, nrhs, s, &nl); },
-                        3, &tc[ring][cs]));
-        if (tc[ring][cs] < tc[best_ring][best]) best = cs, best_ring = ring;
+                        3, &tc[form][cs]));
+        if (tc[form][cs] < tc[best_form][best]) best = cs, best_form = form;
       }
     R->near_split_ms[0] = tc[0][0];
     R->near_split_ms[1] = tc[0][1];
     R->near_window_ms = tc[0][2];
-    for (int q = 0; q < 3; ++q) R->near_deep_ring_ms[q] = tc[1][q];
+    for (int f = 0; f < 3; ++f)
+      for (int q = 0; q < 3; ++q) R->near_form_ms[f][q] = tc[f][q];
     P->near_csep = best;
-    P->near_ring = best_ring;
-    R->near_deep_ring = best_ring;
+    P->near_form = best_form;
+    R->near_form = best_form;
   }
   R->near_split = P->near_csep < 0 ? 0 : P->near_csep;
   // whole products: serial, or near and far field on two streams with two or one near-field CTAs per SM; each

@@ -99,22 +99,27 @@ __device__ __forceinline__ void ns_cons_sync() { asm volatile("bar.sync 1, %0;" 
 // D (FP32, one right-hand side only): a deeper ring of four stages that still fits three CTAs per SM (each CTA
 // at 76,768 bytes of the 76,800 that three CTAs may take); the stage shrinks to 14,272 or 13,760 bytes. FP64
 // products keep the three-stage ring.
+// D = 2 (FP32, one right-hand side, double-buffered windows): each density is kept in the window as
+// (x.x, x.x, x.y, x.y), so that a complex entry b costs two packed FP32x2 FMAs, b (x.x, x.x) and b (x.y, x.y),
+// into two accumulators that give the complex sum at the leaf's end; 512 columns per window.
 template <typename C, int NR, bool W = false, int D = 0>
 struct NsLayout {
   static constexpr int E = sizeof(C);
   static constexpr bool DB = NR == 16 || W;
   static constexpr bool DEEP = D == 1 && NR == 1 && E == 8;
+  static constexpr bool X2 = D == 2 && NR == 1 && E == 8 && W;
+  static constexpr int XE = X2 ? 16 : NR * E;  // window bytes per column
   static constexpr int SB = DEEP ? (W ? 14272 : 13760) : NS_STAGE_BYTES;  // bytes per stage (multiple of 16)
   static constexpr int STAGES = NR == 1 ? (DEEP ? 4 : 3) : 4;
   static constexpr int MINB = NR == 1 ? 3 : (NR <= 4 ? 2 : 1);
   static constexpr int XBYTES = NR == 16 ? 32768 : (W ? 8192 : ((NR == 1 || E * NR >= 64) ? 16384 : 32768));
-  static constexpr int XW0 = (XBYTES / (NR * E)) & ~1;
+  static constexpr int XW0 = (XBYTES / XE) & ~1;
   static constexpr int XW = NR == 16 && XW0 > NS_CONS ? NS_CONS : XW0;  // columns per density window (even)
   static constexpr int CPT = DB && XW > NS_CONS ? XW / NS_CONS : 1;     // window columns per consumer thread
   static_assert(!DB || XW <= NS_CONS || XW % NS_CONS == 0, "double-buffered window: whole columns per thread");
   static constexpr size_t ring = (size_t)STAGES * SB;
   static constexpr size_t xs = ring;
-  static constexpr size_t red = xs + (size_t)(DB ? 2 : 1) * XW * NR * E;
+  static constexpr size_t red = xs + (size_t)(DB ? 2 : 1) * XW * XE;
   static constexpr size_t cor = red + (size_t)NS_CONS * NR * E;
   static constexpr size_t crow = cor + (DB ? (size_t)0 : (size_t)NS_CONS * NR * E);
   static constexpr size_t bars = crow + (NS_CONS + 8) * sizeof(int);
@@ -128,8 +133,8 @@ __device__ __forceinline__ int ns_cpc(int nr, int E, int sb) { return max(2, (sb
 template <typename C, int NR, bool W, int D>
 static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR, W, D>::MINB) k_near_stream(
     const int32_t* part, const NsMeta* meta, const int32_t* ncolv, const int64_t* xbase, const int32_t* xcol,
-    const C* B, const int64_t* cptr, const int32_t* ccol, const C* cval, const C* xt, C* yt, int nrhs, int r0,
-    int rc, int csep, int evict_first, int* err) {
+    const C* B, const int64_t* cptr, const int32_t* ccol, const C* cval, const C* xt, const float4* xdup, C* yt,
+    int nrhs, int r0, int rc, int csep, int evict_first, int* err) {
   typedef NsLayout<C, NR, W, D> Ly;
   typedef decltype(xt[0].x) R;
   constexpr int E = Ly::E, XW = Ly::XW, NS_STAGES = Ly::STAGES;
@@ -227,6 +232,10 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR, W, D>::MINB) k_n
     for (int j = 0; j < CPT; ++j) {
       const int col = colA[j];
       if (col < 0) continue;
+      if constexpr (Ly::X2) {  // the duplicated densities, 16 bytes a column
+        ns_cp16((float4*)xs + ((size_t)b * XW + t + j * NS_CONS), xdup + col, 16u);
+        continue;
+      }
       C* dst = xs + ((size_t)b * XW + t + j * NS_CONS) * NR;
       const C* src = xt + (int64_t)col * nrhs + r0;
       if (E == 16 || (NR > 1 && (nrhs & 1) == 0)) {  // 16-byte aligned runs of 16 / E right-hand sides
@@ -351,6 +360,7 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR, W, D>::MINB) k_n
     C acc[NR];
 #pragma unroll
     for (int q = 0; q < NR; ++q) acc[q] = mk((R)0, (R)0);
+    float2 accA = make_float2(0.f, 0.f), accB = make_float2(0.f, 0.f);  // X2: sums of b x.x and b x.y
     for (int wb = 0; wb < ncol; wb += XW) {
       const int we = min(ncol, wb + XW);
       const C* xcur = xs;
@@ -361,7 +371,7 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR, W, D>::MINB) k_n
         copy_window(buf ^ 1);
         advance();
         load_cols();
-        xcur = xs + (size_t)buf * XW * NR;
+        xcur = (const C*)((const unsigned char*)xs + (size_t)buf * XW * Ly::XE);
         buf ^= 1;
       } else {
         ns_cons_sync();  // readers of the previous window are done
@@ -379,7 +389,32 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR, W, D>::MINB) k_n
           failed = true;
           atomicExch(err, 1);
         }
-        if (!failed && act) {
+        if constexpr (Ly::X2) {
+          if (!failed && act) {
+            const float2* Bs = (const float2*)(ring + (size_t)st * Ly::SB) + i;
+            const float4* xw = (const float4*)xcur + (c - wb);
+            int cl = g;
+            for (; cl + 3 * G < cc; cl += 4 * G) {
+              const float2 b0 = Bs[cl * nr], b1 = Bs[(cl + G) * nr], b2 = Bs[(cl + 2 * G) * nr],
+                           b3 = Bs[(cl + 3 * G) * nr];
+              const float4 x0 = xw[cl], x1 = xw[cl + G], x2 = xw[cl + 2 * G], x3 = xw[cl + 3 * G];
+              accA = __ffma2_rn(b0, make_float2(x0.x, x0.y), accA);
+              accB = __ffma2_rn(b0, make_float2(x0.z, x0.w), accB);
+              accA = __ffma2_rn(b1, make_float2(x1.x, x1.y), accA);
+              accB = __ffma2_rn(b1, make_float2(x1.z, x1.w), accB);
+              accA = __ffma2_rn(b2, make_float2(x2.x, x2.y), accA);
+              accB = __ffma2_rn(b2, make_float2(x2.z, x2.w), accB);
+              accA = __ffma2_rn(b3, make_float2(x3.x, x3.y), accA);
+              accB = __ffma2_rn(b3, make_float2(x3.z, x3.w), accB);
+            }
+            for (; cl < cc; cl += G) {
+              const float2 bv = Bs[cl * nr];
+              const float4 xv = xw[cl];
+              accA = __ffma2_rn(bv, make_float2(xv.x, xv.y), accA);
+              accB = __ffma2_rn(bv, make_float2(xv.z, xv.w), accB);
+            }
+          }
+        } else if (!failed && act) {
           const C* Bs = (const C*)(ring + (size_t)st * Ly::SB) + i;
           const C* xw = xcur + (c - wb) * NR;
           int cl = g;
@@ -405,6 +440,8 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR, W, D>::MINB) k_n
         ++it;
       }
     }
+    // X2: b x = (b.x x.x - b.y x.y, b.y x.x + b.x x.y) from the two packed sums
+    if constexpr (Ly::X2) acc[0] = mk(accA.x - accB.y, accA.y + accB.x);
 #pragma unroll
     for (int q = 0; q < NR; ++q) red[t * NR + q] = act ? acc[q] : mk((R)0, (R)0);
     ns_cons_sync();
@@ -468,6 +505,14 @@ static __global__ void __launch_bounds__(256) k_near_corr(const int64_t* cptr, c
   if ((lane & ((1 << (5 - LOGNR)) - 1)) == 0 && qi < rc) yt[row * nrhs + r0 + qi] = a[0];
 }
 
+static __global__ void k_dup_x(const float2* xt, float4* xdup, int64_t N) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    const float2 v = xt[i];
+    xdup[i] = make_float4(v.x, v.x, v.y, v.y);
+  }
+}
+
 template <typename C, int NR, bool W, int D = 0>
 static int near_stream_t(fda_plan_s* P, const C* B, const C* cval, const C* xt, C* yt, int nrhs, cudaStream_t s,
                          int64_t* launches) {
@@ -480,6 +525,13 @@ static int near_stream_t(fda_plan_s* P, const C* B, const C* cval, const C* xt, 
   }
   fda_tree_s* T = P->tree;
   const int csep = (Ly::DB || P->near_csep >= 1) ? 1 : 0;  // double-buffered passes have no correction buffer
+  const float4* xdup = nullptr;
+  if constexpr (Ly::X2) {  // (x.x, x.x, x.y, x.y) per point for the packed FMAs
+    k_dup_x<<<(unsigned)((T->N + 255) / 256), 256, 0, s>>>((const float2*)xt, P->xdup32.p, T->N);
+    FDA_LAUNCH_CHECK();
+    ++*launches;
+    xdup = P->xdup32.p;
+  }
   for (int r0 = 0; r0 < nrhs; r0 += NR) {
     const int rc = std::min(NR, nrhs - r0);
     if (csep) {
@@ -491,7 +543,7 @@ static int near_stream_t(fda_plan_s* P, const C* B, const C* cval, const C* xt, 
     const int ov = (P->near_sel == 1 || P->near_sel == 2) && P->near_grid_ov[P->near_sel - 1] > 0 ? P->near_sel : 0;
     k_near_stream<C, NR, W, D><<<(unsigned)(ov ? P->near_grid_ov[ov - 1] : P->near_grid), NS_NT, Ly::total, s>>>(
         ov ? P->near_part_ov[ov - 1].p : P->near_part.p, P->near_meta.p, P->near_ncol.p, P->near_xbase.p,
-        P->near_xcol.p, B, P->corr_ptr.p, P->corr_col.p, cval, xt, yt, nrhs, r0, rc, csep, P->near_evict,
+        P->near_xcol.p, B, P->corr_ptr.p, P->corr_col.p, cval, xt, xdup, yt, nrhs, r0, rc, csep, P->near_evict,
         P->tc_err.p);
     FDA_LAUNCH_CHECK();
     ++*launches;
@@ -508,7 +560,10 @@ int near_stream(fda_plan_s* P, const C* B, const C* cval, const C* xt, C* yt, in
   }
   // right-hand sides per pass over the matrix: 1, 4, or 16 for wide batches (each pass streams it once)
   if (nrhs == 1) {
-    if (P->near_ring == 1)
+    if constexpr (std::is_same<C, float2>::value)
+      if (P->near_form == 2 && P->near_csep == 2 && P->xdup32.p)
+        return near_stream_t<C, 1, true, 2>(P, B, cval, xt, yt, nrhs, s, launches);
+    if (P->near_form == 1)
       return P->near_csep == 2 ? near_stream_t<C, 1, true, 1>(P, B, cval, xt, yt, nrhs, s, launches)
                                : near_stream_t<C, 1, false, 1>(P, B, cval, xt, yt, nrhs, s, launches);
     return P->near_csep == 2 ? near_stream_t<C, 1, true>(P, B, cval, xt, yt, nrhs, s, launches)

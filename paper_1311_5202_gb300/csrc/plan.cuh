@@ -134,7 +134,10 @@ struct fda_plan_s {
   fda::DBuf<int64_t> near_xbase;     // target leaf -> first entry of its column list in near_xcol
   fda::DBuf<int32_t> near_xcol;      // column -> tree position of its source point
   fda::DBuf<fda::NsMeta> near_meta;      // target leaf -> rows, columns and offsets, one 32-byte record
-  int near_ring = 0;                 // one right-hand side: 1 = four-stage ring (autotuned)
+  // one right-hand side: 0 = three-stage ring, 1 = four-stage ring, 2 = packed FP32x2 FMAs on duplicated
+  // densities (double-buffered windows only; autotuned)
+  int near_form = 0;
+  fda::DBuf<float4> xdup32;          // (x.x, x.x, x.y, x.y) per point for near_form = 2
   fda::DBuf<int32_t> near_part;      // persistent CTA -> first target leaf (grid + 1 entries)
   int near_grid = 0, near_max_nr = 0;
   int64_t corr_merged = 0;           // correction entries folded into the direct blocks

@@ -471,7 +471,7 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
   P->prob = pr;
   P->cfg = *cfg;
   P->near_csep = cfg->near_split;  // 0, 1 or 2 (checked at the entry point)
-  P->near_ring = cfg->near_deep_ring;
+  P->near_form = cfg->near_form;
   if (P->cfg.nrhs_max < 1) P->cfg.nrhs_max = 1;
   FDA_TRY(upload_geometry_constants());
   const int64_t N = T->N, nbox = T->nbox;
@@ -1662,6 +1662,7 @@ int plan_build(fda_tree_s* T, const fda_config_t* cfg, fda_plan_s* P) {
     FDA_TRY(to_fp32(P->op64.corr, P->op32.corr));
     if (P->op64.lr.n) FDA_TRY(to_fp32(P->op64.lr, P->op32.lr));
     FDA_TRY(P->xt32.alloc((size_t)N * nr));
+    FDA_TRY(P->xdup32.alloc((size_t)N));
     FDA_TRY(P->yt32.alloc((size_t)N * nr));
     FDA_TRY(P->cout32.alloc((size_t)std::max<int64_t>(P->n_coef, 1) * nr));
     FDA_TRY(P->cin32.alloc((size_t)std::max<int64_t>(P->n_coef, 1) * nr));

@@ -41,7 +41,7 @@ class FdaError(RuntimeError):
 class fda_config_t(C.Structure):
     _fields_ = [("eps", C.c_double), ("precision", C.c_int), ("lowrank", C.c_int), ("nrhs_max", C.c_int),
                 ("m2l_tensor", C.c_int), ("op", C.c_int), ("near_split", C.c_int),
-                ("drop_fp64", C.c_int), ("near_deep_ring", C.c_int), ("gamma_re", C.c_double),
+                ("drop_fp64", C.c_int), ("near_form", C.c_int), ("gamma_re", C.c_double),
                 ("gamma_im", C.c_double)]
 
 
@@ -79,8 +79,8 @@ class fda_tune_report_t(C.Structure):
                 ("near_ms", C.c_double * 2), ("near_rhs_per_pass", C.c_int32), ("near_split", C.c_int32),
                 ("near_split_ms", C.c_double * 2), ("near_window_ms", C.c_double), ("overlap", C.c_int32),
                 ("near_evict_first", C.c_int32), ("far_levels_concurrent", C.c_int32),
-                ("near_deep_ring", C.c_int32), ("schedule_ms", C.c_double * 12),
-                ("near_deep_ring_ms", C.c_double * 3)]
+                ("near_form", C.c_int32), ("schedule_ms", C.c_double * 12),
+                ("near_form_ms", (C.c_double * 3) * 3)]
 
 
 class fda_plan_info_t(C.Structure):
@@ -260,10 +260,10 @@ def fda_tree_destroy(tree):
 
 
 def fda_precompute_translations(tree, eps, precision=FDA_PREC_FP64, lowrank=1, nrhs_max=1, m2l_tensor=0, op=0,
-                                near_split=0, gamma=0.0, drop_fp64=False, near_deep_ring=0):
+                                near_split=0, gamma=0.0, drop_fp64=False, near_form=0):
     cfg = fda_config_t()
     cfg.drop_fp64 = int(bool(drop_fp64))
-    cfg.near_deep_ring = int(near_deep_ring)
+    cfg.near_form = int(near_form)
     cfg.gamma_re = complex(gamma).real
     cfg.gamma_im = complex(gamma).imag
     cfg.eps = float(eps)
@@ -342,7 +342,7 @@ def fda_autotune(plan, nrhs=1, stream=None) -> dict:
                 near_split=R.near_split, near_split_ms=list(R.near_split_ms), near_window_ms=R.near_window_ms,
                 overlap=R.overlap, near_evict_first=R.near_evict_first,
                 far_levels_concurrent=R.far_levels_concurrent, schedule_ms=list(R.schedule_ms),
-                near_deep_ring=R.near_deep_ring, near_deep_ring_ms=list(R.near_deep_ring_ms))
+                near_form=R.near_form, near_form_ms=[list(r) for r in R.near_form_ms])
 
 
 def fda_m2l_force(plan, variant):
@@ -561,12 +561,12 @@ class Solver:
     """Problem + tree + plan with ordered destruction."""
 
     def __init__(self, nodes, elems, k, eps=1e-4, leaf_max=64, precision=FDA_PREC_FP64, lowrank=1, nrhs_max=1,
-                 alpha=None, m2l_tensor=0, op=0, near_split=0, gamma=0.0, drop_fp64=False, near_deep_ring=0):
+                 alpha=None, m2l_tensor=0, op=0, near_split=0, gamma=0.0, drop_fp64=False, near_form=0):
         self.k = float(k)
         self.prob = bm_problem_create(nodes, elems, k, alpha)
         self.tree = fda_build_tree(self.prob, leaf_max)
         self.plan = fda_precompute_translations(self.tree, eps, precision, lowrank, nrhs_max, m2l_tensor, op,
-                                                near_split, gamma, drop_fp64, near_deep_ring)
+                                                near_split, gamma, drop_fp64, near_form)
         self.N = 6 * int(np.asarray(elems).shape[0])
 
     def matvec(self, x, y, stream=None):
