@@ -241,11 +241,11 @@ def run_batched(S2, args, N, dev, stream, single_mixed, fdbem, torch):
     if single_mixed:
         out["speedup_per_direction_vs_single_mixed_solve"] = single_mixed["wall_s"] / st["per_direction_s"]
     if args.solve_m2l_tensor == 3:
-        # the same block solve with the 3xTF32 product as the outer residual (stops at 0.95e-5; the worst FP64
-        # residual over the directions is reported beside)
+        # the same block solve with the 3xTF32 product as the outer residual; it stops at 0.9e-5, since over many
+        # directions the worst FP64 residual sits further from the 3xTF32 one (reported beside)
         xs3 = torch.zeros_like(b)
         t2 = time.perf_counter()
-        st3 = fdbem.bm_gmres_solve(S2.plan, b, xs3, tol=0.95e-5, restart=60, max_iter=2000, refine=True,
+        st3 = fdbem.bm_gmres_solve(S2.plan, b, xs3, tol=0.9e-5, restart=60, max_iter=2000, refine=True,
                                    inner_tol=1e-3, stream=stream, raise_on_error=False, refine_residual=1)
         torch.cuda.synchronize()
         st3["wall_s"] = time.perf_counter() - t2

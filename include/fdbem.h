@@ -191,9 +191,11 @@ typedef struct {
                         refine = 0 (FP64 Krylov basis around the FP32 operator; with TF32 translations the
                         rounding stalls GMRES near a 1e-4 residual, with 3xTF32 ones, m2l_tensor = 3, it
                         reaches 1e-5 and below) and no preconditioner. */
-  int near_form;      /* near-field stream of one right-hand side (fda_autotune chooses it by timing): 0 = three
-                        ring stages of 16 KB; 1 = four of about 14 KB; 2 = (with near_split = 2, FP32) packed
-                        FP32x2 FMAs on densities kept twice over, (x.x, x.x, x.y, x.y). Same sums, other order */
+  int near_form;      /* near-field stream (fda_autotune chooses it by timing): 0 = the FMA form with three ring
+                        stages of 16 KB (one right-hand side); 1 = one right-hand side with four stages of about
+                        14 KB; 2 = packed FP32x2 FMAs (FP32): one right-hand side with near_split = 2 on densities
+                        kept twice over, (x.x, x.x, x.y, x.y); passes of 4 or 16 right-hand sides with each
+                        matrix entry paired in registers. Same sums, other order */
   double gamma_re, gamma_im;  /* op = 2: the Robin coefficient gamma = a/b (ignored otherwise) */
 } fda_config_t;
 
@@ -261,8 +263,9 @@ typedef struct {
   double schedule_ms[12];   /* whole FP32 products, best of 5, at index overlap + 3 evict_first + 6 far_levels
                                (the three settings of fda_overlap_force); -1 where not timed (the setting needs
                                a near field in the stream form or a far field that the plan lacks) */
-  double near_form_ms[3][3]; /* one right-hand side: near field in form f (row) and schedule q (column); -1
-                                where not timed (form 2 runs schedule 2 only; wider batches time form 0) */
+  double near_form_ms[3][3]; /* near field in form f (row) and schedule q (column) at the chosen width; -1 where
+                                not timed (form 1: one right-hand side; form 2 with one right-hand side:
+                                schedule 2 only) */
 } fda_tune_report_t;
 int fda_autotune(fda_plan_t* plan, int nrhs, void* stream, fda_tune_report_t* report);
 

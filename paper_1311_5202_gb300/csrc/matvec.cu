@@ -889,6 +889,7 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
   R->entries = e;
   if (nrhs >= 12 && P->n_near_tleaf > 0 && P->near_max_nr <= 256) {
     double tn[2];
+    P->near_form = 0;
     for (int wide = 0; wide < 2; ++wide) {
       P->near_wide = wide;
       FDA_TRY(time_ms(s, [&]() { return near_stream<float2>(P, P->op32.near.p, P->op32.corr.p, P->xt32.p, P->yt32.p,
@@ -909,14 +910,13 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
   R->near_form = 0;
   if (P->n_near_tleaf > 0 && P->near_max_nr <= 256) {
     // schedules: 0 corrections per leaf; 1 split; 2 split with double-buffered windows (one right-hand side);
-    // one right-hand side also with the four-stage ring (form 1) and, for schedule 2, the packed FMAs (form 2)
+    // forms: 1 the four-stage ring (one right-hand side), 2 packed FMAs (one right-hand side: schedule 2 only)
     double tc[3][3] = {{0, 0, -1}, {-1, -1, -1}, {-1, -1, -1}};
     const int ncs = nrhs == 1 ? 3 : 2;
-    const int nform = nrhs == 1 ? 3 : 1;
     int best = 0, best_form = 0;
-    for (int form = 0; form < nform; ++form)
+    for (int form = 0; form < 3; ++form)
       for (int cs = 0; cs < ncs; ++cs) {
-        if (form == 2 && cs != 2) continue;
+        if ((form == 1 && nrhs > 1) || (form == 2 && nrhs == 1 && cs != 2)) continue;
         P->near_csep = cs;
         P->near_form = form;
         FDA_TRY(time_ms(s, [&]() { return near_stream<float2>(P, P->op32.near.p, P->op32.corr.p, P->xt32.p,

@@ -108,6 +108,9 @@ struct NsLayout {
   static constexpr bool DB = NR == 16 || W;
   static constexpr bool DEEP = D == 1 && NR == 1 && E == 8;
   static constexpr bool X2 = D == 2 && NR == 1 && E == 8 && W;
+  // D = 2 with several right-hand sides (FP32): the matrix entry b is paired in registers, (b.x, b.x) and
+  // (b.y, b.y), and each density x of the pass takes two packed FMAs into two accumulators
+  static constexpr bool PK = D == 2 && NR > 1 && E == 8;
   static constexpr int XE = X2 ? 16 : NR * E;  // window bytes per column
   static constexpr int SB = DEEP ? (W ? 14272 : 13760) : NS_STAGE_BYTES;  // bytes per stage (multiple of 16)
   static constexpr int STAGES = NR == 1 ? (DEEP ? 4 : 3) : 4;
@@ -361,6 +364,9 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR, W, D>::MINB) k_n
 #pragma unroll
     for (int q = 0; q < NR; ++q) acc[q] = mk((R)0, (R)0);
     float2 accA = make_float2(0.f, 0.f), accB = make_float2(0.f, 0.f);  // X2: sums of b x.x and b x.y
+    float2 pkP[Ly::PK ? NR : 1], pkQ[Ly::PK ? NR : 1];  // PK: sums of b.x x and b.y x per right-hand side
+#pragma unroll
+    for (int q = 0; q < (Ly::PK ? NR : 1); ++q) pkP[q] = pkQ[q] = make_float2(0.f, 0.f);
     for (int wb = 0; wb < ncol; wb += XW) {
       const int we = min(ncol, wb + XW);
       const C* xcur = xs;
@@ -414,6 +420,35 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR, W, D>::MINB) k_n
               accB = __ffma2_rn(bv, make_float2(xv.z, xv.w), accB);
             }
           }
+        } else if constexpr (Ly::PK) {
+          if (!failed && act) {
+            const float2* Bs = (const float2*)(ring + (size_t)st * Ly::SB) + i;
+            const float2* xw = (const float2*)xcur + (c - wb) * NR;
+            int cl = g;
+            for (; cl + G < cc; cl += 2 * G) {
+              const float2 b0 = Bs[cl * nr], b1 = Bs[(cl + G) * nr];
+              const float2 bx0 = make_float2(b0.x, b0.x), by0 = make_float2(b0.y, b0.y);
+              const float2 bx1 = make_float2(b1.x, b1.x), by1 = make_float2(b1.y, b1.y);
+#pragma unroll
+              for (int q = 0; q < NR; ++q) {
+                const float2 x0 = xw[cl * NR + q], x1 = xw[(cl + G) * NR + q];
+                pkP[q] = __ffma2_rn(bx0, x0, pkP[q]);
+                pkQ[q] = __ffma2_rn(by0, x0, pkQ[q]);
+                pkP[q] = __ffma2_rn(bx1, x1, pkP[q]);
+                pkQ[q] = __ffma2_rn(by1, x1, pkQ[q]);
+              }
+            }
+            for (; cl < cc; cl += G) {
+              const float2 b0 = Bs[cl * nr];
+              const float2 bx0 = make_float2(b0.x, b0.x), by0 = make_float2(b0.y, b0.y);
+#pragma unroll
+              for (int q = 0; q < NR; ++q) {
+                const float2 x0 = xw[cl * NR + q];
+                pkP[q] = __ffma2_rn(bx0, x0, pkP[q]);
+                pkQ[q] = __ffma2_rn(by0, x0, pkQ[q]);
+              }
+            }
+          }
         } else if (!failed && act) {
           const C* Bs = (const C*)(ring + (size_t)st * Ly::SB) + i;
           const C* xw = xcur + (c - wb) * NR;
@@ -442,6 +477,10 @@ static __global__ void __launch_bounds__(NS_NT, NsLayout<C, NR, W, D>::MINB) k_n
     }
     // X2: b x = (b.x x.x - b.y x.y, b.y x.x + b.x x.y) from the two packed sums
     if constexpr (Ly::X2) acc[0] = mk(accA.x - accB.y, accA.y + accB.x);
+    if constexpr (Ly::PK) {  // b x = (b.x x.x - b.y x.y, b.x x.y + b.y x.x)
+#pragma unroll
+      for (int q = 0; q < NR; ++q) acc[q] = mk(pkP[q].x - pkQ[q].y, pkP[q].y + pkQ[q].x);
+    }
 #pragma unroll
     for (int q = 0; q < NR; ++q) red[t * NR + q] = act ? acc[q] : mk((R)0, (R)0);
     ns_cons_sync();
@@ -569,6 +608,11 @@ int near_stream(fda_plan_s* P, const C* B, const C* cval, const C* xt, C* yt, in
     return P->near_csep == 2 ? near_stream_t<C, 1, true>(P, B, cval, xt, yt, nrhs, s, launches)
                              : near_stream_t<C, 1, false>(P, B, cval, xt, yt, nrhs, s, launches);
   }
+  if constexpr (std::is_same<C, float2>::value)
+    if (P->near_form == 2) {
+      if (nrhs < 12 || P->near_wide == 0) return near_stream_t<C, 4, false, 2>(P, B, cval, xt, yt, nrhs, s, launches);
+      return near_stream_t<C, 16, false, 2>(P, B, cval, xt, yt, nrhs, s, launches);
+    }
   if (nrhs < 12 || P->near_wide == 0) return near_stream_t<C, 4, false>(P, B, cval, xt, yt, nrhs, s, launches);
   return near_stream_t<C, 16, false>(P, B, cval, xt, yt, nrhs, s, launches);
 }

@@ -152,7 +152,7 @@ def test_matvec_batched_rhs_equals_single(c1):
         assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-6
 
 
-@pytest.mark.parametrize("split,form", [(1, 0), (2, 0), (0, 1), (1, 1), (2, 1), (2, 2)])
+@pytest.mark.parametrize("split,form", [(1, 0), (2, 0), (0, 1), (1, 1), (2, 1), (2, 2), (1, 2)])
 def test_near_correction_split_schedule(c1, split, form):
     """The off-block correction entries of Eq. kcorrection as their own CSR kernel before the near-field stream
     (near_split = 1), and with the stream's density windows double-buffered (near_split = 2); each schedule also
@@ -160,7 +160,7 @@ def test_near_correction_split_schedule(c1, split, form):
     on duplicated densities (form 2, FP32 products only): the FP64 product on all rows against the oracle
     (1e-4), and against the per-leaf schedule of the same plan (same sums in another order: 1e-12 in FP64, 1e-5
     in FP32); for split = 1 also 16 right-hand sides (the 16-wide pass reduces lane sums by recursive halving and
-    always double-buffers its windows)."""
+    always double-buffers its windows; with form 2 it pairs each matrix entry in registers for packed FMAs)."""
     mesh, S0 = c1
     S1 = fdbem.Solver(mesh.nodes, mesh.elems, 10.0, eps=1e-6, leaf_max=64, precision=fdbem.FDA_PREC_FP32,
                       nrhs_max=16, near_split=split, near_form=form)
