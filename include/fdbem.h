@@ -266,6 +266,11 @@ typedef struct {
   double near_form_ms[3][3]; /* near field in form f (row) and schedule q (column) at the chosen width; -1 where
                                 not timed (form 1: one right-hand side; form 2 with one right-hand side:
                                 schedule 2 only) */
+  int32_t m2l_rechosen;     /* M2L choices changed by the last pass: variants within 15% of the fastest of their
+                               (level, stage) when timed alone, timed again inside whole products under the
+                               chosen schedule (a change must gain at least 0.5%) */
+  int32_t reserved2;
+  double product_ms;        /* the whole FP32 product with every choice made, best of 5 (-1 without far field) */
 } fda_tune_report_t;
 int fda_autotune(fda_plan_t* plan, int nrhs, void* stream, fda_tune_report_t* report);
 

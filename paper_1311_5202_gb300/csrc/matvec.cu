@@ -836,6 +836,8 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
   FDA_CUDA(cudaStreamSynchronize(s));
   int64_t nl = 0;
   int e = 0;
+  // variants of the plan's own choices timed alone, per (level, stage): (variant, ms), for the re-weighing below
+  std::vector<std::pair<int, double>> cand[FDA_MAXLEV][2];
   // a 3xTF32 plan also serves single-pass TF32 products (FDA_PREC_TF32): their kernels are tuned first, into
   // their own choices; the report lists the plan's own (3xTF32) choices
   for (int pass = P->cfg.m2l_tensor == 3 ? 0 : 1; pass < 2; ++pass) {
@@ -854,6 +856,8 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
                                                             s, &nl); },
                         3, &t1));
       int tvb = tv;  // the tensor-core variant kept
+      std::vector<std::pair<int, double>> tried = {{0, t0}};
+      if (tv != 0) tried.push_back({tv, t1});
       if (tv == 1) {
         std::vector<int> alts = {3, 4, 5, 6, 7};
         if (x3p) alts = {7};  // 3xTF32: atomics (1) or bulk reductions (7)
@@ -868,6 +872,7 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
           FDA_TRY(time_ms(s, [&]() { return m2l_stage<float2>(P, P->op32, P->cout32, P->cin32, P->mid32, l, st, alt,
                                                               nrhs, s, &nl); },
                           3, &ta));
+          tried.push_back({alt, ta});
           if (ta < t1) t1 = ta, tvb = alt;
         }
       }
@@ -876,6 +881,7 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
         P->m2l_choice_fast[l][st] = pick;
         continue;
       }
+      cand[l][st] = tried;
       R->level[e] = l;
       R->stage[e] = st;
       R->ms_fma[e] = t0;
@@ -965,6 +971,42 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
     R->overlap = P->overlap;
     R->near_evict_first = P->near_evict;
     R->far_levels_concurrent = P->far_par;
+  }
+  // Kernels timed alone do not see the contention of a two-stream product: M2L variants within 15% of the
+  // fastest one of their (level, stage) are timed again inside whole products under the chosen schedule.
+  R->m2l_rechosen = 0;
+  R->product_ms = -1;
+  if (P->n_coef > 0) {
+    double cur = 0;
+    FDA_TRY(time_ms(s, [&]() { return plan_matvec(P, FDA_PREC_FP32, x.p, y.p, nrhs, FDA_CPLX64, s, false); }, 5,
+                    &cur));
+    for (int l = P->lmin; l <= P->lmax; ++l)
+      for (int st = 0; st < 2; ++st) {
+        const auto& cv = cand[l][st];
+        if (cv.size() < 2) continue;
+        double tbest = 1e300;
+        for (const auto& c : cv) tbest = std::min(tbest, c.second);
+        const int keep = P->m2l_choice[l][st];
+        for (const auto& c : cv) {
+          if (c.first == keep || c.second > 1.15 * tbest) continue;
+          P->m2l_choice[l][st] = c.first;
+          double tp = 0;
+          FDA_TRY(time_ms(s, [&]() { return plan_matvec(P, FDA_PREC_FP32, x.p, y.p, nrhs, FDA_CPLX64, s, false); }, 5,
+                          &tp));
+          if (tp < 0.995 * cur) {
+            cur = tp;
+            ++R->m2l_rechosen;
+          } else {
+            P->m2l_choice[l][st] = keep;
+          }
+        }
+        for (int q = 0; q < R->entries; ++q)  // the report shows the final choice
+          if (R->level[q] == l && R->stage[q] == st) {
+            const int pick = P->m2l_choice[l][st];
+            R->chosen[q] = pick == 0 ? 0 : (pick >= 3 ? pick - 1 : 1);
+          }
+      }
+    R->product_ms = cur;
   }
   FDA_TRY(plan_matvec(P, FDA_PREC_FP32, x.p, y.p, nrhs, FDA_CPLX64, s, false));
   FDA_CUDA(cudaStreamSynchronize(s));

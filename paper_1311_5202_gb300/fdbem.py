@@ -80,7 +80,8 @@ class fda_tune_report_t(C.Structure):
                 ("near_split_ms", C.c_double * 2), ("near_window_ms", C.c_double), ("overlap", C.c_int32),
                 ("near_evict_first", C.c_int32), ("far_levels_concurrent", C.c_int32),
                 ("near_form", C.c_int32), ("schedule_ms", C.c_double * 12),
-                ("near_form_ms", (C.c_double * 3) * 3)]
+                ("near_form_ms", (C.c_double * 3) * 3), ("m2l_rechosen", C.c_int32), ("reserved2", C.c_int32),
+                ("product_ms", C.c_double)]
 
 
 class fda_plan_info_t(C.Structure):
@@ -342,7 +343,8 @@ def fda_autotune(plan, nrhs=1, stream=None) -> dict:
                 near_split=R.near_split, near_split_ms=list(R.near_split_ms), near_window_ms=R.near_window_ms,
                 overlap=R.overlap, near_evict_first=R.near_evict_first,
                 far_levels_concurrent=R.far_levels_concurrent, schedule_ms=list(R.schedule_ms),
-                near_form=R.near_form, near_form_ms=[list(r) for r in R.near_form_ms])
+                near_form=R.near_form, near_form_ms=[list(r) for r in R.near_form_ms],
+                m2l_rechosen=R.m2l_rechosen, product_ms=R.product_ms)
 
 
 def fda_m2l_force(plan, variant):
