@@ -365,9 +365,10 @@ def main():
     ap.add_argument("--m2l-variant", type=int, default=None,
                     help="pin one M2L kernel variant for every level and stage instead of autotuning "
                          "(fda_m2l_force; used to profile one kernel)")
-    ap.add_argument("--overlap", type=int, default=None, choices=[0, 1, 2],
-                    help="force the FP32 product schedule instead of the autotuner's (0 serial; 1, 2 far field on "
-                         "a second stream beside the near field at two or one CTAs per SM; fda_overlap_force)")
+    ap.add_argument("--overlap", type=int, default=None, choices=[0, 1, 2, 3],
+                    help="force the FP32 product schedule instead of the autotuner's (0 serial; 1, 2, 3 far field "
+                         "on a second stream beside the near field at two, one or three CTAs per SM; "
+                         "fda_overlap_force)")
     ap.add_argument("--near-evict", type=int, default=None, choices=[0, 1],
                     help="force the L2 policy of the near-field matrix copies (1 evict-first) instead of the "
                          "autotuner's")
@@ -690,7 +691,7 @@ def main():
         "fp64": {"matvec_per_s": 1000.0 / ms64, "ms_per_matvec": ms64, "phase_ms": ph64},
         "mixed": {"matvec_per_s": 1000.0 / ms32, "ms_per_matvec": ms32, "phase_ms": ph32,
                   "schedule": ["serial", "two streams, near field at 2 CTAs/SM",
-                               "two streams, near field at 1 CTA/SM"][overlap]
+                               "two streams, near field at 1 CTA/SM", "two streams, near field at 3 CTAs/SM"][overlap]
                   + (", near-field matrices evict-first in L2" if evict else "")
                   + (", M2L levels on concurrent streams" if farp else ""),
                   "phase_note": "phase_ms come from one serial product with an event between phases"},

@@ -195,7 +195,9 @@ typedef struct {
                         stages of 16 KB (one right-hand side); 1 = one right-hand side with four stages of about
                         14 KB; 2 = packed FP32x2 FMAs (FP32): one right-hand side with near_split = 2 on densities
                         kept twice over, (x.x, x.x, x.y, x.y); passes of 4 or 16 right-hand sides with each
-                        matrix entry paired in registers. Same sums, other order */
+                        matrix entry paired in registers; 3 = one right-hand side with near_split = 2 in a slim
+                        CTA (three 12 KB stages, two 4 KB windows) that leaves shared memory to a far field
+                        running beside it. Same sums, other order */
   double gamma_re, gamma_im;  /* op = 2: the Robin coefficient gamma = a/b (ignored otherwise) */
 } fda_config_t;
 
@@ -254,13 +256,13 @@ typedef struct {
                              and the stream's density windows double-buffered (one right-hand side) */
   double near_split_ms[2];  /* near field (at the chosen width) with schedules 0 and 1 */
   double near_window_ms;    /* schedule 2 (nrhs = 1; else -1) */
-  int32_t overlap;          /* FP32 product schedule kept: 0 = serial; 1 and 2 = the far field (S2M, M2M, M2L,
+  int32_t overlap;          /* FP32 product schedule kept: 0 = serial; 1 to 3 = the far field (S2M, M2M, M2L,
                                L2L) on a stream of the plan, beside the near field on the caller's stream with two
-                               (1) or one (2) near-field CTAs per SM */
+                               (1), one (2) or three (3) near-field CTAs per SM */
   int32_t near_evict_first; /* 1: the near-field matrix copies carry an L2 evict-first policy */
   int32_t far_levels_concurrent; /* 1: the M2L of each level runs on its own stream of the plan */
   int32_t near_form;        /* one right-hand side: near-field form kept (as fda_config_t.near_form) */
-  double schedule_ms[12];   /* whole FP32 products, best of 5, at index overlap + 3 evict_first + 6 far_levels
+  double schedule_ms[16];   /* whole FP32 products, best of 5, at index overlap + 4 evict_first + 8 far_levels
                                (the three settings of fda_overlap_force); -1 where not timed (the setting needs
                                a near field in the stream form or a far field that the plan lacks) */
   double near_form_ms[3][3]; /* near field in form f (row) and schedule q (column) at the chosen width; -1 where
@@ -269,7 +271,9 @@ typedef struct {
   int32_t m2l_rechosen;     /* M2L choices changed by the last pass: variants within 15% of the fastest of their
                                (level, stage) when timed alone, timed again inside whole products under the
                                chosen schedule (a change must gain at least 0.5%) */
-  int32_t reserved2;
+  int32_t near_slim;        /* 1: the two-stream product runs the slim near-field CTA (near_form = 3: three
+                               12 KB stages and two 4 KB windows, about 47 KB; one right-hand side, near_split 2) */
+  double schedule_slim_ms[16]; /* schedule_ms with the slim near-field CTA (two-stream schedules only; else -1) */
   double product_ms;        /* the whole FP32 product with every choice made, best of 5 (-1 without far field) */
 } fda_tune_report_t;
 int fda_autotune(fda_plan_t* plan, int nrhs, void* stream, fda_tune_report_t* report);
@@ -293,13 +297,13 @@ int fda_m2l_force(fda_plan_t* plan, int variant);
  * shared round-robin beyond four levels), forked when the level's outgoing coefficients are complete and joined
  * before L2L; 0 runs the levels in sequence. evict_first = 1 gives the near field's bulk copies of its matrices
  * an L2 evict-first policy (they are read once per pass), 0 the default policy. mode: 0 = the near field and
- * the far field in sequence on the caller's stream; 1 and
- * 2 = S2M, M2M, M2L and L2L (which read x and write only the expansion coefficients) on a stream the plan
- * owns, forked after the permutation of x and joined before L2T, while the near field streams on the caller's
- * stream with two (1) or one (2) persistent CTAs per SM. Products stay ordered on the caller's stream and
+ * the far field in sequence on the caller's stream; 1 to 3 = S2M, M2M, M2L and L2L (which read x and write
+ * only the expansion coefficients) on a stream the plan owns, forked after the permutation of x and joined
+ * before L2T, while the near field streams on the caller's stream with two (1), one (2) or three (3)
+ * persistent CTAs per SM. Products stay ordered on the caller's stream and
  * graph capture follows the fork and join. The two-stream forms apply only to FP32 products of plans whose
  * near field runs in the stream form; no stream but the caller's is used while phase events are recorded.
- * Errors: FDA_E_INVALID_ARG (mode outside [0, 2], evict_first or far_levels outside [0, 1]), FDA_E_STATE (plan
+ * Errors: FDA_E_INVALID_ARG (mode outside [0, 3], evict_first or far_levels outside [0, 1]), FDA_E_STATE (plan
  * without FP32 operators). */
 int fda_overlap_force(fda_plan_t* plan, int mode, int evict_first, int far_levels);
 

@@ -231,7 +231,7 @@ int fda_precompute_translations(fda_tree_t* tree, const fda_config_t* cfg, fda_p
   ARG_CHECK(cfg->m2l_tensor >= 0 && cfg->m2l_tensor <= 3, "m2l_tensor must be 0, 1, 2 or 3");
   ARG_CHECK(cfg->op >= 0 && cfg->op <= 2, "op must be 0, 1 or 2");
   ARG_CHECK(cfg->drop_fp64 == 0 || cfg->drop_fp64 == 1, "drop_fp64 must be 0 or 1");
-  ARG_CHECK(cfg->near_form >= 0 && cfg->near_form <= 2, "near_form must be 0, 1 or 2");
+  ARG_CHECK(cfg->near_form >= 0 && cfg->near_form <= 3, "near_form must be 0, 1, 2 or 3");
   ARG_CHECK(cfg->drop_fp64 == 0 || cfg->precision == FDA_PREC_FP32, "drop_fp64 needs precision FDA_PREC_FP32");
   ARG_CHECK(cfg->op != 2 || (std::isfinite(cfg->gamma_re) && std::isfinite(cfg->gamma_im)),
             "op = 2 needs a finite Robin coefficient gamma");
@@ -307,7 +307,7 @@ int fda_m2l_force(fda_plan_t* plan, int variant) {
 
 int fda_overlap_force(fda_plan_t* plan, int mode, int evict_first, int far_levels) {
   ARG_CHECK(plan, "NULL plan");
-  ARG_CHECK(mode >= 0 && mode <= 2, "mode outside [0, 2]");
+  ARG_CHECK(mode >= 0 && mode <= 3, "mode outside [0, 3]");
   ARG_CHECK(evict_first == 0 || evict_first == 1, "evict_first outside [0, 1]");
   ARG_CHECK(far_levels == 0 || far_levels == 1, "far_levels outside [0, 1]");
   if ((mode > 0 || evict_first || far_levels) && plan->cfg.precision != FDA_PREC_FP32) {

@@ -583,7 +583,7 @@ static int matvec_t(fda_plan_s* P, RunOps<C>& op, DBuf<C>& xt, DBuf<C>& yt, DBuf
   ev(1);
   // FP32 products may run the far field on the plan's side stream while the near field streams on s. The
   // two share only xt (read by both) and yt (written by the near field, then added to by L2T after the join).
-  const bool ovl = std::is_same<C, float2>::value && (P->overlap == 1 || P->overlap == 2) && !P->phase_ev &&
+  const bool ovl = std::is_same<C, float2>::value && P->overlap >= 1 && P->overlap <= 3 && !P->phase_ev &&
                    P->side && P->n_coef > 0 && P->n_near_tleaf > 0 && P->near_max_nr <= 256;
   const cudaStream_t sf = ovl ? P->side : s;
   if (ovl) {
@@ -940,7 +940,7 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
     R->near_form = best_form;
   }
   R->near_split = P->near_csep < 0 ? 0 : P->near_csep;
-  // whole products: serial, or near and far field on two streams with two or one near-field CTAs per SM; each
+  // whole products: serial, or near and far field on two streams with two, one or three near-field CTAs per SM; each
   // with and without the L2 evict-first policy on the near-field matrix copies, and with the M2L levels in
   // sequence or each on its own stream
   P->overlap = 0;
@@ -949,25 +949,38 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
   R->overlap = 0;
   R->near_evict_first = 0;
   R->far_levels_concurrent = 0;
-  for (int q = 0; q < 12; ++q) R->schedule_ms[q] = -1;
+  R->near_slim = 0;
+  for (int q = 0; q < 16; ++q) R->schedule_ms[q] = R->schedule_slim_ms[q] = -1;
   if (!P->phase_ev && (P->n_coef > 0 || (P->n_near_tleaf > 0 && P->near_max_nr <= 256))) {
     const bool near_s = P->n_near_tleaf > 0 && P->near_max_nr <= 256;
     const bool far = P->n_coef > 0 && P->side;
     int best = -1;
-    for (int q = 0; q < 12; ++q) {
-      const int ov = q % 3, evf = (q / 3) % 2, fp = q / 6;
+    // one right-hand side in schedule 2: the two-stream forms are also timed with the slim near-field CTA
+    const int form0 = P->near_form;
+    const bool slim_ok = nrhs == 1 && P->near_csep == 2;
+    bool best_slim = false;
+    double best_ms = 1e300;
+    for (int q = 0; q < 16; ++q) R->schedule_slim_ms[q] = -1;
+    for (int q = 0; q < 16; ++q) {
+      const int ov = q % 4, evf = (q / 4) % 2, fp = q / 8;
       if ((ov > 0 && !(far && near_s)) || (evf && !near_s) || (fp && !far)) continue;
       P->overlap = ov;
       P->near_evict = evf;
       P->far_par = fp;
-      FDA_TRY(time_ms(s, [&]() { return plan_matvec(P, FDA_PREC_FP32, x.p, y.p, nrhs, FDA_CPLX64, s, false); }, 5,
-                      &R->schedule_ms[q]));
-      if (best < 0 || R->schedule_ms[q] < R->schedule_ms[best]) best = q;
+      for (int sl = 0; sl < ((ov > 0 && slim_ok) ? 2 : 1); ++sl) {
+        P->near_form = sl ? 3 : form0;
+        double* t = sl ? &R->schedule_slim_ms[q] : &R->schedule_ms[q];
+        FDA_TRY(time_ms(s, [&]() { return plan_matvec(P, FDA_PREC_FP32, x.p, y.p, nrhs, FDA_CPLX64, s, false); }, 5,
+                        t));
+        if (*t < best_ms) best_ms = *t, best = q, best_slim = sl == 1;
+      }
     }
     if (best < 0) best = 0;
-    P->overlap = best % 3;
-    P->near_evict = (best / 3) % 2;
-    P->far_par = best / 6;
+    P->near_form = best_slim ? 3 : form0;
+    R->near_slim = best_slim ? 1 : 0;
+    P->overlap = best % 4;
+    P->near_evict = (best / 4) % 2;
+    P->far_par = best / 8;
     R->overlap = P->overlap;
     R->near_evict_first = P->near_evict;
     R->far_levels_concurrent = P->far_par;

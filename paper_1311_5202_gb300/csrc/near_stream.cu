@@ -111,11 +111,15 @@ struct NsLayout {
   // D = 2 with several right-hand sides (FP32): the matrix entry b is paired in registers, (b.x, b.x) and
   // (b.y, b.y), and each density x of the pass takes two packed FMAs into two accumulators
   static constexpr bool PK = D == 2 && NR > 1 && E == 8;
+  // D = 3 (FP32, one right-hand side, double-buffered windows): a slim CTA of about 47 KB (three 12 KB stages,
+  // two 4 KB windows) for products whose far field runs beside the near field and needs the shared memory
+  static constexpr bool SLIM = D == 3 && NR == 1 && E == 8 && W;
   static constexpr int XE = X2 ? 16 : NR * E;  // window bytes per column
-  static constexpr int SB = DEEP ? (W ? 14272 : 13760) : NS_STAGE_BYTES;  // bytes per stage (multiple of 16)
+  static constexpr int SB = DEEP ? (W ? 14272 : 13760) : (SLIM ? 12288 : NS_STAGE_BYTES);  // multiple of 16
   static constexpr int STAGES = NR == 1 ? (DEEP ? 4 : 3) : 4;
   static constexpr int MINB = NR == 1 ? 3 : (NR <= 4 ? 2 : 1);
-  static constexpr int XBYTES = NR == 16 ? 32768 : (W ? 8192 : ((NR == 1 || E * NR >= 64) ? 16384 : 32768));
+  static constexpr int XBYTES =
+      NR == 16 ? 32768 : (W ? (SLIM ? 4096 : 8192) : ((NR == 1 || E * NR >= 64) ? 16384 : 32768));
   static constexpr int XW0 = (XBYTES / XE) & ~1;
   static constexpr int XW = NR == 16 && XW0 > NS_CONS ? NS_CONS : XW0;  // columns per density window (even)
   static constexpr int CPT = DB && XW > NS_CONS ? XW / NS_CONS : 1;     // window columns per consumer thread
@@ -602,6 +606,9 @@ int near_stream(fda_plan_s* P, const C* B, const C* cval, const C* xt, C* yt, in
     if constexpr (std::is_same<C, float2>::value)
       if (P->near_form == 2 && P->near_csep == 2 && P->xdup32.p)
         return near_stream_t<C, 1, true, 2>(P, B, cval, xt, yt, nrhs, s, launches);
+    if constexpr (std::is_same<C, float2>::value)
+      if (P->near_form == 3 && P->near_csep == 2)
+        return near_stream_t<C, 1, true, 3>(P, B, cval, xt, yt, nrhs, s, launches);
     if (P->near_form == 1)
       return P->near_csep == 2 ? near_stream_t<C, 1, true, 1>(P, B, cval, xt, yt, nrhs, s, launches)
                                : near_stream_t<C, 1, false, 1>(P, B, cval, xt, yt, nrhs, s, launches);

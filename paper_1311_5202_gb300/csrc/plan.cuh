@@ -96,7 +96,7 @@ struct fda_plan_s {
   // plan's side stream, forked after the permutation and joined before L2T; the near field on the caller's
   // stream with a smaller persistent grid, so that the far-field kernels find room on every SM.
   // overlap: -1 or 0 serial (the default until the autotuner or fda_overlap_force sets it), 1 two streams
-  // with two near-field CTAs per SM, 2 two streams with one near-field CTA per SM.
+  // with two near-field CTAs per SM, 2 two streams with one, 3 two streams with the full grid of three.
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int overlap = -1;

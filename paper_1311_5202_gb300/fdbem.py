@@ -79,9 +79,9 @@ class fda_tune_report_t(C.Structure):
                 ("near_ms", C.c_double * 2), ("near_rhs_per_pass", C.c_int32), ("near_split", C.c_int32),
                 ("near_split_ms", C.c_double * 2), ("near_window_ms", C.c_double), ("overlap", C.c_int32),
                 ("near_evict_first", C.c_int32), ("far_levels_concurrent", C.c_int32),
-                ("near_form", C.c_int32), ("schedule_ms", C.c_double * 12),
-                ("near_form_ms", (C.c_double * 3) * 3), ("m2l_rechosen", C.c_int32), ("reserved2", C.c_int32),
-                ("product_ms", C.c_double)]
+                ("near_form", C.c_int32), ("schedule_ms", C.c_double * 16),
+                ("near_form_ms", (C.c_double * 3) * 3), ("m2l_rechosen", C.c_int32), ("near_slim", C.c_int32),
+                ("schedule_slim_ms", C.c_double * 16), ("product_ms", C.c_double)]
 
 
 class fda_plan_info_t(C.Structure):
@@ -344,7 +344,8 @@ def fda_autotune(plan, nrhs=1, stream=None) -> dict:
                 overlap=R.overlap, near_evict_first=R.near_evict_first,
                 far_levels_concurrent=R.far_levels_concurrent, schedule_ms=list(R.schedule_ms),
                 near_form=R.near_form, near_form_ms=[list(r) for r in R.near_form_ms],
-                m2l_rechosen=R.m2l_rechosen, product_ms=R.product_ms)
+                m2l_rechosen=R.m2l_rechosen, product_ms=R.product_ms, near_slim=R.near_slim,
+                schedule_slim_ms=list(R.schedule_slim_ms))
 
 
 def fda_m2l_force(plan, variant):
@@ -353,8 +354,8 @@ def fda_m2l_force(plan, variant):
 
 
 def fda_overlap_force(plan, mode, evict_first=0, far_levels=0):
-    """FP32 product schedule: mode 0 serial, 1 or 2 far field on the plan's stream beside the near field (two or
-    one near-field CTAs per SM); evict_first = 1 gives the near-field matrix copies an L2 evict-first policy;
+    """FP32 product schedule: mode 0 serial, 1, 2 or 3 far field on the plan's stream beside the near field (two,
+    one or three near-field CTAs per SM); evict_first = 1 gives the near-field matrix copies an L2 evict-first policy;
     far_levels = 1 runs the M2L of each level on its own stream."""
     _check(lib().fda_overlap_force(plan, int(mode), int(evict_first), int(far_levels)))
 

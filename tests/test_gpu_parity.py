@@ -152,12 +152,13 @@ def test_matvec_batched_rhs_equals_single(c1):
         assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-6
 
 
-@pytest.mark.parametrize("split,form", [(1, 0), (2, 0), (0, 1), (1, 1), (2, 1), (2, 2), (1, 2)])
+@pytest.mark.parametrize("split,form", [(1, 0), (2, 0), (0, 1), (1, 1), (2, 1), (2, 2), (1, 2), (2, 3)])
 def test_near_correction_split_schedule(c1, split, form):
     """The off-block correction entries of Eq. kcorrection as their own CSR kernel before the near-field stream
     (near_split = 1), and with the stream's density windows double-buffered (near_split = 2); each schedule also
     with the four-stage ring of one right-hand side (form 1), and the double-buffered one with packed FP32x2 FMAs
-    on duplicated densities (form 2, FP32 products only): the FP64 product on all rows against the oracle
+    on duplicated densities (form 2) and in the slim CTA (form 3; both FP32 products only): the FP64 product on
+    all rows against the oracle
     (1e-4), and against the per-leaf schedule of the same plan (same sums in another order: 1e-12 in FP64, 1e-5
     in FP32); for split = 1 also 16 right-hand sides (the 16-wide pass reduces lane sums by recursive halving and
     always double-buffers its windows; with form 2 it pairs each matrix entry in registers for packed FMAs)."""
@@ -620,7 +621,8 @@ def test_tf32_pass_on_3xtf32_images_and_refinement_with_their_residual():
         S3.close()
 
 
-@pytest.mark.parametrize("mode,evict,far", [(0, 1, 0), (1, 0, 0), (2, 0, 0), (1, 1, 0), (0, 0, 1), (1, 1, 1)])
+@pytest.mark.parametrize("mode,evict,far", [(0, 1, 0), (1, 0, 0), (2, 0, 0), (3, 0, 0), (1, 1, 0), (0, 0, 1),
+                                            (1, 1, 1)])
 def test_two_stream_schedule_matches_serial(kd100_variants, mode, evict, far):
     """FP32 products with the far field (S2M, M2M, M2L, L2L) on the plan's own stream beside the near field on
     the caller's stream (two or one near-field CTAs per SM), with the L2 evict-first policy on the near-field
