@@ -197,7 +197,10 @@ typedef struct {
                         kept twice over, (x.x, x.x, x.y, x.y); passes of 4 or 16 right-hand sides with each
                         matrix entry paired in registers; 3 = one right-hand side with near_split = 2 in a slim
                         CTA (three 12 KB stages, two 4 KB windows) that leaves shared memory to a far field
-                        running beside it. Same sums, other order */
+                        running beside it; 4 = products of 16 or more right-hand sides (FP32, leaves of at most
+                        64 points) on the tensor cores in 3xTF32, up to 64 right-hand sides per pass over the
+                        matrices, corrections outside the direct blocks by their own kernel. Same sums, other
+                        order */
   double gamma_re, gamma_im;  /* op = 2: the Robin coefficient gamma = a/b (ignored otherwise) */
 } fda_config_t;
 
@@ -275,6 +278,8 @@ typedef struct {
                                12 KB stages and two 4 KB windows, about 47 KB; one right-hand side, near_split 2) */
   double schedule_slim_ms[16]; /* schedule_ms with the slim near-field CTA (two-stream schedules only; else -1) */
   double product_ms;        /* the whole FP32 product with every choice made, best of 5 (-1 without far field) */
+  double near_tc_ms;        /* the near field on the tensor cores (near_form = 4), best of 3; -1 when not timed
+                               (fewer than 16 right-hand sides, leaves of more than 64 points) */
 } fda_tune_report_t;
 int fda_autotune(fda_plan_t* plan, int nrhs, void* stream, fda_tune_report_t* report);
 

@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 OUT = os.path.join(HERE, "_libfdbem.so")
 BUILD = os.path.join(HERE, "_build")
-UNITS = ["api", "tree", "geometry", "linalg", "translations", "matvec", "gmres", "rhs_noalloc", "precond", "m2l_tc", "near_stream"]
+UNITS = ["api", "tree", "geometry", "linalg", "translations", "matvec", "gmres", "rhs_noalloc", "precond", "m2l_tc",
+         "near_stream", "near_tc"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "-Xptxas", "-O3",
          "-I", os.path.join(ROOT, "include"), "-diag-suppress", "177,550"]

@@ -231,7 +231,7 @@ int fda_precompute_translations(fda_tree_t* tree, const fda_config_t* cfg, fda_p
   ARG_CHECK(cfg->m2l_tensor >= 0 && cfg->m2l_tensor <= 3, "m2l_tensor must be 0, 1, 2 or 3");
   ARG_CHECK(cfg->op >= 0 && cfg->op <= 2, "op must be 0, 1 or 2");
   ARG_CHECK(cfg->drop_fp64 == 0 || cfg->drop_fp64 == 1, "drop_fp64 must be 0 or 1");
-  ARG_CHECK(cfg->near_form >= 0 && cfg->near_form <= 3, "near_form must be 0, 1, 2 or 3");
+  ARG_CHECK(cfg->near_form >= 0 && cfg->near_form <= 4, "near_form must be 0 to 4");
   ARG_CHECK(cfg->drop_fp64 == 0 || cfg->precision == FDA_PREC_FP32, "drop_fp64 needs precision FDA_PREC_FP32");
   ARG_CHECK(cfg->op != 2 || (std::isfinite(cfg->gamma_re) && std::isfinite(cfg->gamma_im)),
             "op = 2 needs a finite Robin coefficient gamma");

@@ -912,17 +912,21 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
   R->near_window_ms = -1;
   for (int f = 0; f < 3; ++f)
     for (int q = 0; q < 3; ++q) R->near_form_ms[f][q] = -1;
+  R->near_tc_ms = -1;
   P->near_form = 0;
   R->near_form = 0;
   if (P->n_near_tleaf > 0 && P->near_max_nr <= 256) {
     // schedules: 0 corrections per leaf; 1 split; 2 split with double-buffered windows (one right-hand side);
-    // forms: 1 the four-stage ring (one right-hand side), 2 packed FMAs (one right-hand side: schedule 2 only)
-    double tc[3][3] = {{0, 0, -1}, {-1, -1, -1}, {-1, -1, -1}};
+    // forms: 1 the four-stage ring (one right-hand side), 2 packed FMAs (one right-hand side: schedule 2 only),
+    // 3 the slim CTA (weighed in whole products below), 4 tensor cores (16 or more right-hand sides; its
+    // corrections always run split, so it is timed once)
+    double tc[5][3] = {{0, 0, -1}, {-1, -1, -1}, {-1, -1, -1}, {-1, -1, -1}, {-1, -1, -1}};
     const int ncs = nrhs == 1 ? 3 : 2;
     int best = 0, best_form = 0;
-    for (int form = 0; form < 3; ++form)
+    for (int form = 0; form < 5; ++form)
       for (int cs = 0; cs < ncs; ++cs) {
-        if ((form == 1 && nrhs > 1) || (form == 2 && nrhs == 1 && cs != 2)) continue;
+        if ((form == 1 && nrhs > 1) || (form == 2 && nrhs == 1 && cs != 2) || form == 3) continue;
+        if (form == 4 && (nrhs < 16 || P->near_max_nr > 64 || cs != 1)) continue;
         P->near_csep = cs;
         P->near_form = form;
         FDA_TRY(time_ms(s, [&]() { return near_stream<float2>(P, P->op32.near.p, P->op32.corr.p, P->xt32.p,
@@ -935,6 +939,7 @@ int autotune(fda_plan_s* P, int nrhs, cudaStream_t s, fda_tune_report_t* R) {
     R->near_window_ms = tc[0][2];
     for (int f = 0; f < 3; ++f)
       for (int q = 0; q < 3; ++q) R->near_form_ms[f][q] = tc[f][q];
+    R->near_tc_ms = tc[4][1];
     P->near_csep = best;
     P->near_form = best_form;
     R->near_form = best_form;

@@ -594,6 +594,29 @@ static int near_stream_t(fda_plan_s* P, const C* B, const C* cval, const C* xt, 
   return FDA_OK;
 }
 
+int near_tc_launch(fda_plan_s* P, const float2* B, const float2* xt, float2* yt, int nrhs, int r0, int rc,
+                   cudaStream_t s);
+
+// wide batches on the tensor cores (near_form = 4): per pass of up to 64 right-hand sides, the off-block
+// corrections by the CSR kernel (16 at a time), then one tensor-core pass over the matrices
+static int near_tc_passes(fda_plan_s* P, const float2* B, const float2* cval, const float2* xt, float2* yt, int nrhs,
+                          cudaStream_t s, int64_t* launches) {
+  fda_tree_s* T = P->tree;
+  for (int r0 = 0; r0 < nrhs; r0 += 64) {
+    const int rc = std::min(64, nrhs - r0);
+    for (int q0 = r0; q0 < r0 + rc; q0 += 16) {
+      const int qc = std::min(16, r0 + rc - q0);
+      k_near_corr<float2, 16><<<(unsigned)((T->N + 7) / 8), 256, 0, s>>>(P->corr_ptr.p, P->corr_col.p, cval, xt, yt,
+                                                                         T->N, nrhs, q0, qc);
+      FDA_LAUNCH_CHECK();
+      ++*launches;
+    }
+    FDA_TRY(near_tc_launch(P, B, xt, yt, nrhs, r0, rc, s));
+    ++*launches;
+  }
+  return FDA_OK;
+}
+
 template <typename C>
 int near_stream(fda_plan_s* P, const C* B, const C* cval, const C* xt, C* yt, int nrhs, cudaStream_t s,
                 int64_t* launches) {
@@ -601,6 +624,9 @@ int near_stream(fda_plan_s* P, const C* B, const C* cval, const C* xt, C* yt, in
     set_error("near-field stream needs leaves of at most %d points (got %d)", NS_CONS, P->near_max_nr);
     return FDA_E_INVALID_ARG;
   }
+  // the tensor-core form serves any batch width once chosen (the autotuner offers it from 16 right-hand sides)
+  if constexpr (std::is_same<C, float2>::value)
+    if (P->near_form == 4 && P->near_max_nr <= 64) return near_tc_passes(P, B, cval, xt, yt, nrhs, s, launches);
   // right-hand sides per pass over the matrix: 1, 4, or 16 for wide batches (each pass streams it once)
   if (nrhs == 1) {
     if constexpr (std::is_same<C, float2>::value)

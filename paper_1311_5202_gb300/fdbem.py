@@ -81,7 +81,7 @@ class fda_tune_report_t(C.Structure):
                 ("near_evict_first", C.c_int32), ("far_levels_concurrent", C.c_int32),
                 ("near_form", C.c_int32), ("schedule_ms", C.c_double * 16),
                 ("near_form_ms", (C.c_double * 3) * 3), ("m2l_rechosen", C.c_int32), ("near_slim", C.c_int32),
-                ("schedule_slim_ms", C.c_double * 16), ("product_ms", C.c_double)]
+                ("schedule_slim_ms", C.c_double * 16), ("product_ms", C.c_double), ("near_tc_ms", C.c_double)]
 
 
 class fda_plan_info_t(C.Structure):
@@ -344,7 +344,7 @@ def fda_autotune(plan, nrhs=1, stream=None) -> dict:
                 overlap=R.overlap, near_evict_first=R.near_evict_first,
                 far_levels_concurrent=R.far_levels_concurrent, schedule_ms=list(R.schedule_ms),
                 near_form=R.near_form, near_form_ms=[list(r) for r in R.near_form_ms],
-                m2l_rechosen=R.m2l_rechosen, product_ms=R.product_ms, near_slim=R.near_slim,
+                m2l_rechosen=R.m2l_rechosen, product_ms=R.product_ms, near_slim=R.near_slim, near_tc_ms=R.near_tc_ms,
                 schedule_slim_ms=list(R.schedule_slim_ms))
 
 

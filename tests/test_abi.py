@@ -72,7 +72,7 @@ def test_invalid_arguments_fail_cleanly_without_gpu(built):
     # configuration fields are checked before the tree
     cfg.eps, cfg.precision, cfg.nrhs_max = 1e-4, fdbem.FDA_PREC_FP32, 1
     for field, bad, word in (("m2l_tensor", 4, "m2l_tensor"), ("op", 3, "op"), ("near_split", 3, "near_split"),
-                             ("drop_fp64", 2, "drop_fp64"), ("near_form", 4, "near_form"),
+                             ("drop_fp64", 2, "drop_fp64"), ("near_form", 5, "near_form"),
                              ("nrhs_max", 0, "nrhs_max")):
         good = getattr(cfg, field)
         setattr(cfg, field, bad)

@@ -621,6 +621,56 @@ def test_tf32_pass_on_3xtf32_images_and_refinement_with_their_residual():
         S3.close()
 
 
+def test_near_field_on_tensor_cores_for_wide_batches():
+    """The near field of a batch on the tensor cores (near_form = 4: 3xTF32, up to 64 right-hand sides per pass
+    over the matrices, off-block corrections by the CSR kernel). Each right-hand side has its own rows of the
+    accumulator, so batched columns equal the same plan's single products (1e-6): columns 0, 15, 16 and 19 of
+    20 (two TMEM lane quadrants) and 0, 63, 64 and 69 of 70 (a full pass of 64 and a ragged one of 6). Against
+    the FP32 FMA stream of the same configuration the product differs by the order of FP32 additions in sums
+    with heavy cancellation, in the tensor cores' accumulator and in the FMA lanes (1e-4); both meet the mixed
+    bar on 128 oracle rows (3e-4)."""
+    _need_gpu()
+    mesh = inputs.icosphere(14, 0.5)
+    k = 100.0
+    kw = dict(eps=1e-5, leaf_max=64, precision=fdbem.FDA_PREC_FP32, m2l_tensor=1, nrhs_max=70, near_split=1)
+    S0 = fdbem.Solver(mesh.nodes, mesh.elems, k, **kw)
+    S4 = fdbem.Solver(mesh.nodes, mesh.elems, k, near_form=4, **kw)
+
+    def single(S, col):
+        xc = col.contiguous()
+        yc = torch.empty_like(xc)
+        S.matvec(xc, yc)
+        torch.cuda.synchronize()
+        return yc
+
+    def rel(a, b):
+        return (torch.linalg.norm(a - b) / torch.linalg.norm(b)).item()
+
+    try:
+        rows = inputs.sample_rows(S0.N, 128, 9)
+        for nrhs, cols in ((20, (0, 15, 16, 19)), (70, (0, 63, 64, 69))):
+            x = inputs.complex_gaussian(S0.N, 50 + nrhs, nrhs=nrhs)
+            xd = torch.from_numpy(x.astype(np.complex64)).to(DEV).contiguous()
+            y4, y0 = torch.empty_like(xd), torch.empty_like(xd)
+            S4.matvec(xd, y4)
+            S0.matvec(xd, y0)
+            torch.cuda.synchronize()
+            diffs = {c: rel(y4[c], single(S4, xd[c])) for c in cols}
+            assert max(diffs.values()) < 1e-6, (nrhs, diffs)
+            d = rel(y4, y0)
+            assert d < 1e-4, (nrhs, d)
+            a, b = y4.cpu().numpy(), y0.cpu().numpy()
+            for c in cols[::3]:
+                yo = _oracle_rows(mesh, k, x[c].astype(np.complex128), rows)
+                e4 = np.linalg.norm(a[c][rows] - yo) / np.linalg.norm(yo)
+                e0 = np.linalg.norm(b[c][rows] - yo) / np.linalg.norm(yo)
+                assert e4 < 3e-4 and e0 < 3e-4, (nrhs, c, e4, e0)
+        assert fdbem.fda_plan_check(S4.plan) == fdbem.FDA_OK
+    finally:
+        S4.close()
+        S0.close()
+
+
 @pytest.mark.parametrize("mode,evict,far", [(0, 1, 0), (1, 0, 0), (2, 0, 0), (3, 0, 0), (1, 1, 0), (0, 0, 1),
                                             (1, 1, 1)])
 def test_two_stream_schedule_matches_serial(kd100_variants, mode, evict, far):
