@@ -264,7 +264,8 @@ typedef struct {
                                (1), one (2) or three (3) near-field CTAs per SM */
   int32_t near_evict_first; /* 1: the near-field matrix copies carry an L2 evict-first policy */
   int32_t far_levels_concurrent; /* 1: the M2L of each level runs on its own stream of the plan */
-  int32_t near_form;        /* one right-hand side: near-field form kept (as fda_config_t.near_form) */
+  int32_t near_form;        /* near-field form kept (as fda_config_t.near_form; forms 1 and 3 serve one
+                               right-hand side, form 4 batches) */
   double schedule_ms[16];   /* whole FP32 products, best of 5, at index overlap + 4 evict_first + 8 far_levels
                                (the three settings of fda_overlap_force); -1 where not timed (the setting needs
                                a near field in the stream form or a far field that the plan lacks) */
