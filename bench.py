@@ -372,6 +372,9 @@ def main():
     ap.add_argument("--near-evict", type=int, default=None, choices=[0, 1],
                     help="force the L2 policy of the near-field matrix copies (1 evict-first) instead of the "
                          "autotuner's")
+    ap.add_argument("--near-form", type=int, default=0, choices=[0, 1, 2, 3, 4],
+                    help="near-field form of the product plan before autotuning (fda_config_t.near_form; with "
+                         "--no-tune it stays: 4 = the tensor-core form for batches)")
     ap.add_argument("--far-levels", type=int, default=None, choices=[0, 1],
                     help="force the M2L levels onto concurrent streams (1) or in sequence (0) instead of the "
                          "autotuner's choice")
@@ -412,7 +415,8 @@ def main():
     nrhs = args.nrhs
     t0 = time.perf_counter()
     S = fdbem.Solver(mesh.nodes, mesh.elems, k, eps=eps, leaf_max=spec["leaf"], precision=fdbem.FDA_PREC_FP32,
-                     lowrank=1, nrhs_max=nrhs, m2l_tensor=args.m2l_tensor, near_split=args.near_split)
+                     lowrank=1, nrhs_max=nrhs, m2l_tensor=args.m2l_tensor, near_split=args.near_split,
+                     near_form=args.near_form)
     setup_s = time.perf_counter() - t0
     tune_main = None if (args.no_tune or args.m2l_variant is not None) else fdbem.fda_autotune(S.plan, nrhs)
     if args.m2l_variant is not None:
