@@ -81,6 +81,12 @@ def test_invalid_arguments_fail_cleanly_without_gpu(built):
         setattr(cfg, field, good)
     rc = fdbem.lib().fda_precompute_translations(None, C.byref(cfg), C.byref(h))
     assert rc == fdbem.FDA_E_INVALID_ARG and "tree" in fdbem.fda_last_error()
+    # product schedule and precision checks come before the plan is touched
+    assert fdbem.lib().fda_overlap_force(None, 1, 0, 0) == fdbem.FDA_E_INVALID_ARG
+    assert "NULL plan" in fdbem.fda_last_error()
+    x = (C.c_double * 4)()
+    rc = fdbem.lib().fda_matvec_ex(None, fdbem.FDA_PREC_TF32, x, x, 1, fdbem.FDA_CPLX64, None)
+    assert rc == fdbem.FDA_E_INVALID_ARG and "NULL" in fdbem.fda_last_error()
 
 
 def test_struct_layouts_match_the_binding(tmp_path):
