@@ -385,9 +385,12 @@ typedef struct {
                           operator, or see refine_residual; 0: plain GMRES */
   int inner_restart;   /* inner Krylov dimension when refine = 1 */
   double inner_tol;    /* inner relative tolerance when refine = 1 */
-  int refine_residual; /* refine = 1, plans built with m2l_tensor = 3 (drop_fp64 plans too): 1 = the outer
-                          residual with the plan's FP32 product and its 3xTF32 translations (accurate to FP32
-                          rounding, far below the eps of the compressed operator); 0 = with the FP64 operator */
+  int refine_residual; /* refine = 1, plans built with m2l_tensor = 3: 1 = the outer residual with the plan's
+                          FP32 product and its 3xTF32 translations (accurate to FP32 rounding, far below the eps
+                          of the compressed operator; drop_fp64 plans too); 2 = as 1 until it meets tol, then
+                          the residual with the FP64 operator, and FP64 residuals from there on until that
+                          one meets tol too (the result is certified against the FP64 operator; plans that
+                          keep it); 0 = the FP64 operator throughout */
   int reserved[5];
 } bm_gmres_opts_t;
 

@@ -585,7 +585,7 @@ static int gmres_solve_block(GmCtx& C, const double2* b, double2* x, int nc, con
   int it = 0;
   // refinement: outer residual with the FP64 operator or the 3xTF32 FP32 product; the inner solve needs only a
   // few digits and runs single-pass TF32 translations (on plans without 3xTF32 images the plain FP32 product)
-  const int oprec = o->refine_residual ? FDA_PREC_FP32 : FDA_PREC_FP64;
+  int oprec = o->refine_residual ? FDA_PREC_FP32 : FDA_PREC_FP64;  // refine_residual = 2 ends on FP64
   const int iprec = FDA_PREC_TF32;
   if (!o->refine) {
     const int aprec = P->cfg.drop_fp64 ? FDA_PREC_FP32 : FDA_PREC_FP64;  // FP32-only plans: FP32 operator
@@ -631,6 +631,11 @@ static int gmres_solve_block(GmCtx& C, const double2* b, double2* x, int nc, con
     }
     *worst = wr;
     if (wr <= o->tol) {
+      if (o->refine_residual == 2 && oprec != FDA_PREC_FP64) {  // confirm with the FP64 residual
+        oprec = FDA_PREC_FP64;
+        prev = 1e300;
+        continue;
+      }
       rc = FDA_OK;
       break;
     }
@@ -679,19 +684,19 @@ int gmres_solve(fda_plan_s* P, const double2* b, double2* x, int nrhs, const bm_
   C.nb = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (C.N + GM_NB - 1) / GM_NB));
   int m = std::max(1, std::min(512, o->restart));
   int mi = std::max(1, std::min(512, o->inner_restart > 0 ? o->inner_restart : o->restart));
-  if (o->refine_residual != 0 && o->refine_residual != 1) {
-    set_error("refine_residual must be 0 or 1");
+  if (o->refine_residual < 0 || o->refine_residual > 2) {
+    set_error("refine_residual must be 0, 1 or 2");
     return FDA_E_INVALID_ARG;
   }
   if (o->refine && o->refine_residual && (P->cfg.precision != FDA_PREC_FP32 || P->cfg.m2l_tensor != 3)) {
-    set_error("refine_residual = 1 needs a plan built with FDA_PREC_FP32 and m2l_tensor = 3 (3xTF32 images)");
+    set_error("refine_residual = 1 or 2 needs a plan built with FDA_PREC_FP32 and m2l_tensor = 3 (3xTF32 images)");
     return FDA_E_STATE;
   }
-  if (P->cfg.drop_fp64 && o->refine && !o->refine_residual) {
+  if (P->cfg.drop_fp64 && o->refine && o->refine_residual != 1) {
     set_error("the plan released its FP64 operators (drop_fp64): solve with refine = 0, or refine_residual = 1");
     return FDA_E_STATE;
   }
-  const int oprec = o->refine_residual ? FDA_PREC_FP32 : FDA_PREC_FP64;
+  const int oprec0 = o->refine_residual ? FDA_PREC_FP32 : FDA_PREC_FP64;
   const int iprec = FDA_PREC_TF32;  // see gmres_solve_block
   FDA_TRY(C.partial.alloc((size_t)C.nb * (std::max(m, mi) + 1)));
   FDA_TRY(C.h.alloc(std::max(m, mi) + 1));
@@ -733,6 +738,7 @@ int gmres_solve(fda_plan_s* P, const double2* b, double2* x, int nrhs, const bm_
       FDA_TRY(dev_norm(C, bc, &bn));
       if (!o->x0_given) FDA_CUDA(cudaMemsetAsync(xc, 0, sizeof(double2) * C.N, s));
       double prev = 1e300;
+      int oprec = oprec0;  // refine_residual = 2 switches to FP64 for the final check
       rc = FDA_E_NOT_CONVERGED;
       for (int k = 0; k < 50; ++k) {
         // outer residual with the FP64 operator (or the 3xTF32 FP32 product)
@@ -752,6 +758,11 @@ int gmres_solve(fda_plan_s* P, const double2* b, double2* x, int nrhs, const bm_
           break;
         }
         if (rel <= o->tol) {
+          if (o->refine_residual == 2 && oprec != FDA_PREC_FP64) {  // confirm with the FP64 residual
+            oprec = FDA_PREC_FP64;
+            prev = 1e300;
+            continue;
+          }
           rc = FDA_OK;
           break;
         }

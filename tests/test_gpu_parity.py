@@ -565,8 +565,9 @@ def test_tf32_pass_on_3xtf32_images_and_refinement_with_their_residual():
     pass agrees with the TF32 plan's product up to the rounding of the images (1e-4) and differs from the split
     form by more than FP32 rounding; an autotuned TF32 pass and a captured graph of it give the same product.
     Refinement with the split product as the outer residual (refine_residual = 1) reaches 1e-6 and, checked
-    with the FP64 operator, 1e-5; it agrees with the refinement around the FP64 residual (5e-5); a plan
-    without 3xTF32 images refuses it with FDA_E_STATE."""
+    with the FP64 operator, 1e-5; it agrees with the refinement around the FP64 residual (5e-5); with the FP64
+    confirmation (refine_residual = 2) the FP64 residual itself meets 1e-6; a plan without 3xTF32 images
+    refuses it with FDA_E_STATE."""
     _need_gpu()
     mesh = inputs.icosphere(14, 0.5)
     k = 100.0
@@ -612,6 +613,13 @@ def test_tf32_pass_on_3xtf32_images_and_refinement_with_their_residual():
         torch.cuda.synchronize()
         assert (torch.linalg.norm(b - r) / torch.linalg.norm(b)).item() < 1e-5
         assert (torch.linalg.norm(u1 - u0) / torch.linalg.norm(u0)).item() < 5e-5
+        # refine_residual = 2: the 3xTF32 residual first, then certified with the FP64 operator
+        u2 = torch.zeros_like(b)
+        st2 = S3.solve(b, u2, tol=1e-6, restart=100, max_iter=2000, refine=True, inner_tol=1e-3, refine_residual=2)
+        assert st2["status"] == fdbem.FDA_OK and st2["rel_residual"] <= 1e-6
+        fdbem.fda_matvec_ex(S3.plan, fdbem.FDA_PREC_FP64, u2, r)
+        torch.cuda.synchronize()
+        assert (torch.linalg.norm(b - r) / torch.linalg.norm(b)).item() <= 1.000001e-6
         st = S1.solve(b, torch.zeros_like(b), tol=1e-6, restart=100, max_iter=2000, refine=True, refine_residual=1,
                       raise_on_error=False)
         assert st["status"] == fdbem.FDA_E_STATE and "m2l_tensor = 3" in fdbem.fda_last_error()
